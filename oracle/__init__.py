@@ -1,0 +1,6 @@
+"""FP64 CPU oracle of the LETKF analysis (test infrastructure only).
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and reference
+legs import this package. It shares no code with the CUDA library.
+"""
+from .letkf_oracle import *  # noqa: F401,F403

@@ -1,0 +1,31 @@
+"""Algorithmic operation counts of the paper (Appendix B), used as the numerator
+of the roofline fraction.
+
+Appendix B.1 counts the multiplications of one ETKF update on a zonal basis,
+(m^2 + m) n + (m^2 + 7m + 41) p + 2 m^3 + 3 m^2 + (3 + gamma) m, and states that
+the additions are of the same order; Table 1 quotes twice that number (7.65e6
+for m = 101, n = 32, p = 128). Appendix B.2 counts the prediction step,
+(3/2 m + 1) n multiplications plus (5/2 m - 1) n additions.
+"""
+from __future__ import annotations
+
+
+def update_mults(m: int, n: int, p: int, gamma: int = 1) -> int:
+    """Multiplications of one (local) update with state size n and p observations."""
+    return (m * m + m) * n + (m * m + 7 * m + 41) * p + 2 * m ** 3 + 3 * m * m + (3 + gamma) * m
+
+
+def update_ops(m: int, n: int, p: int, gamma: int = 1) -> int:
+    """Multiplications plus as many additions (the Table 1 convention)."""
+    return 2 * update_mults(m, n, p, gamma)
+
+
+def prediction_ops(m: int, n: int) -> float:
+    """(3/2 m + 1) n multiplications + (5/2 m - 1) n additions."""
+    return (1.5 * m + 1) * n + (2.5 * m - 1) * n
+
+
+def frame_analysis_ops(m: int, window_slopes) -> int:
+    """Per-frame analysis ops of the per-node LETKF: every node is one local
+    domain with n_d = 2 state rows and p_l = its window's slope count."""
+    return sum(update_ops(m, 2, int(p)) for p in window_slopes)
