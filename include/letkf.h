@@ -1,0 +1,149 @@
+/*
+ * letkf.h - C ABI of libletkf.so, a GB300 (sm_103a) implementation of the
+ * per-frame local ensemble transform Kalman filter (LETKF) analysis for
+ * adaptive optics, after Gray et al., "Local ensemble transform Kalman filter,
+ * a fast non-stationary control law for adaptive optics on ELTs"
+ * (arXiv:1408.7069).
+ *
+ * Model (Section 2.2): the state of actuator node g is the pair
+ * (phi_k(g), phi_{k-1}(g)); slopes y_k = D1 phi_{k-1} + w_k with D1 the Fried
+ * slope operator (Appendix B) and w_k ~ N(0, sigma2 I); the forecast is the
+ * AR(1) model x_{k+1} = A1 x_k + v_k with A1 = [[a I, 0], [I, 0]]
+ * (Section 2.2, Eq. Mem_pre).
+ *
+ * Conventions shared by every entry point:
+ *  - Nodes ("points") are the corners of valid subapertures, ordered row-major
+ *    over the (nsub+1) x (nsub+1) grid. n_pts of them.
+ *  - The ensemble is stored [n_pts][2][m]: row 0 = phi_k, row 1 = phi_{k-1},
+ *    member index fastest.
+ *  - Slopes y are [p] with p = 2 * (number of valid subapertures): all x-slopes
+ *    sx(s,t) = (phi[s+1,t] + phi[s+1,t+1] - phi[s,t] - phi[s,t+1]) / 2 of the
+ *    valid subapertures in row-major order, then all y-slopes sy(s,t) =
+ *    (phi[s,t+1] + phi[s+1,t+1] - phi[s,t] - phi[s+1,t]) / 2. Radians per
+ *    subaperture.
+ *  - Floating-point buffers have the handle's storage type: float when
+ *    precision = 0, double when precision = 1 ("real" below).
+ *  - Pointers named *_dev are device pointers the caller owns; they must stay
+ *    valid until the stream reaches the work that uses them. Pointers named
+ *    *_host are host pointers read before the call returns.
+ *  - Every call is ordered on the handle's CUDA stream and returns without
+ *    synchronising, except letkf_create, letkf_destroy, letkf_sync and the
+ *    query functions. Faults found on the device (non-finite data, a Jacobi
+ *    sweep limit reached) are recorded in a device status word and returned by
+ *    the next letkf_sync.
+ *  - No C++ exception crosses this boundary; a failing call returns a status and
+ *    letkf_last_error() describes it.
+ */
+#ifndef LETKF_H
+#define LETKF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct letkf_ctx *letkf_t; /* opaque handle owned by the library */
+
+typedef enum {
+  LETKF_OK = 0,
+  LETKF_ERR_ARG = 1,        /* invalid argument: nothing was launched */
+  LETKF_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+  LETKF_ERR_NOCONVERGE = 3, /* a Jacobi eigensolve hit its sweep limit */
+  LETKF_ERR_TIMEOUT = 4,    /* a bounded device wait gave up */
+  LETKF_ERR_NONFINITE = 5,  /* NaN or Inf met in slopes or ensemble */
+  LETKF_ERR_STATE = 6,      /* call not valid in the handle's current state */
+  LETKF_ERR_NOMEM = 7       /* device or host allocation failed */
+} letkf_status;
+
+typedef struct {
+  int32_t nsub;                /* subapertures per side; nodes (nsub+1)^2. 1..1024 */
+  const uint8_t *subap_mask;   /* host [nsub*nsub] row-major, nonzero = valid; copied */
+  int32_t m;                   /* ensemble size, 2..32 */
+  int32_t window;              /* localization window: w x w subapertures, odd or even, 1..31 */
+  int32_t taper;               /* 0 = box (tau = 1), 1 = Gaspari-Cohn tau on R^-1 */
+  double loc_len;              /* Gaspari-Cohn half-support c in pitches; <= 0 -> w / 4 */
+  double rho;                  /* multiplicative inflation, > 0 */
+  double sigma2;               /* slope noise variance (rad^2), > 0 */
+  double a_ar1;                /* AR(1) coefficient of the forecast */
+  double noise_std;            /* forecast noise = noise_std * bank screen value */
+  int32_t precision;           /* 0 = FP32 storage and analysis with FP64 fallback, 1 = FP64 */
+  double fp64_kappa;           /* FP64 fallback threshold on kappa_hat; <= 0 disables it */
+  uint64_t seed;               /* SplitMix64 seed of the forecast-noise draws */
+  const float *noise_bank;     /* host [bank_B][bank_G][bank_G] screens, or NULL; copied */
+  int32_t bank_B, bank_G;      /* bank shape (ignored when noise_bank is NULL) */
+  int32_t max_sweeps;          /* Jacobi sweep limit; <= 0 -> 12 (FP32) / 20 (FP64) */
+} letkf_config;
+
+/* Validate the configuration, build the node list, the per-node observation
+ * windows (Section 4.1: subapertures s in [i - w/2, i - w/2 + w - 1], same
+ * for t; Gaspari-Cohn weight of the distance from the node to the subaperture
+ * centre), upload masks, windows and the noise bank, and allocate the ensemble
+ * (zero: X_{1/0} = 0, Section 3.1) and device scratch. stream: a cudaStream_t
+ * (NULL = legacy default stream) on the current device. On success *out owns
+ * all of it. */
+letkf_status letkf_create(const letkf_config *cfg, void *stream, letkf_t *out);
+
+/* Synchronise the handle's stream and free everything it owns. NULL is a no-op. */
+letkf_status letkf_destroy(letkf_t h);
+
+/* Sizes: number of nodes, of slopes and the ensemble size. Host pointers, any may be NULL. */
+letkf_status letkf_query(letkf_t h, int32_t *n_pts, int32_t *p, int32_t *m);
+
+/* Host copies of the node coordinates [n_pts][2] (i, j) and of the number of
+ * valid window slopes per node [n_pts] (p_l, Section 4.2's p_d). Either may be NULL. */
+letkf_status letkf_query_points(letkf_t h, int32_t *ij_host, int32_t *window_slopes_host);
+
+/* Copy the ensemble [n_pts][2][m] (real) from / into device memory. */
+letkf_status letkf_get_state(letkf_t h, void *X_dev);
+letkf_status letkf_set_state(letkf_t h, const void *X_dev);
+
+/* Forecast, Section 3.1.2 Eq. Mem_pre with the AR(1) A1 of Section 2.2:
+ * phi_{k+1}^i = a phi_k^i + v^i, phi_k^i moved to row 1. noise_dev: device
+ * [n_pts][m] real added as v, or NULL to draw v from the noise bank: member i
+ * of forecast number f takes screen h % B at offset ((h >> 16) % G,
+ * (h >> 40) % G), wrapped, with h = SplitMix64(seed, f * 2^16 + i), times
+ * noise_std. Increments the handle's forecast counter f. */
+letkf_status letkf_forecast(letkf_t h, const void *noise_dev);
+
+/* Local analysis of every node (Section 4.2 with Section 3.1 and Appendix A):
+ * mean and anomalies of the background, slope anomalies Yb = D1 (phi_{k-1}
+ * anomalies), innovations d = y - D1 mean(phi_{k-1}); per node, with the
+ * window's slopes and R_l^-1 = diag(tau_j / sigma2): A = (m-1)/rho I + C Yb_l,
+ * C = Yb_l^T R_l^-1, A = Q Lambda Q^T, wbar = Q Lambda^-1 Q^T C d,
+ * W = Q ((m-1) Lambda^-1)^(1/2) Q^T, X_a = xbar + X_b' (wbar 1^T + W).
+ * y_dev: device [p] real. mean_dev, spread_dev: device [n_pts][2] real or
+ * NULL; spread is the sample standard deviation over members (m - 1). The
+ * ensemble is replaced by the analysis. */
+letkf_status letkf_analyze(letkf_t h, const void *y_dev, void *mean_dev, void *spread_dev);
+
+/* Loop criterion (Section 2.1 Eq. Crit_Opt; Section 5): spatial variance over
+ * nodes of truth - mean(row 0), piston removed, of the current (forecast)
+ * ensemble. truth_dev: device [n_pts] real. resvar_dev: device double[1]. */
+letkf_status letkf_residual(letkf_t h, const void *truth_dev, double *resvar_dev);
+
+/* Closed loop over `frames` frames: for frame k, the residual of the current
+ * prediction against truth_seq[k] into resvar[k], the analysis of
+ * y_seq[k], then a forecast with bank noise. y_seq_dev: device [frames][p]
+ * real; truth_seq_dev: device [frames][n_pts] real or NULL (then no residual);
+ * resvar_dev: device double[frames] or NULL. use_graph != 0 captures the frame
+ * into a CUDA graph once and replays it. Requires a noise bank. */
+letkf_status letkf_run(letkf_t h, int32_t frames, const void *y_seq_dev, const void *truth_seq_dev,
+                       double *resvar_dev, int32_t use_graph);
+
+/* Synchronise the stream, return and clear the first error recorded on the
+ * device since the last call (LETKF_OK if none). */
+letkf_status letkf_sync(letkf_t h);
+
+/* Counters of the last analysis, host pointers (any may be NULL): points that
+ * took the FP64 fallback, maximum Jacobi sweeps used by a point. Synchronises. */
+letkf_status letkf_stats(letkf_t h, int32_t *fp64_points, int32_t *max_sweeps);
+
+/* Text of the last error on this handle (or of the last failed create when h is NULL). */
+const char *letkf_last_error(letkf_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LETKF_H */

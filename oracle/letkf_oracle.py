@@ -280,17 +280,20 @@ def residual_variance(truth_k, X):
 
 
 def closed_loop(geom: Geometry, truth, slopes, bank, m: int, sigma2: float, rho: float,
-                a: float, noise_scale: float, seed: int, frames: int, X0=None):
+                a: float, noise_scale: float, seed: int, frames: int, X0=None,
+                batched: bool = False):
     """Run the loop: at frame k record the residual of the prediction X_{k/k-1},
-    analyse y_k, forecast with the bank noise of frame k. X_{0/-1} = 0
-    (Section 3.1: the initial prediction ensemble is all zeros).
-    Returns (resvar [frames], final X, per-frame analysis means)."""
+    analyse y_k, forecast with the bank noise of frame k. Without X0 the first
+    prediction ensemble is all zeros (Section 3.1). ``batched`` uses the stacked
+    form of the analysis. Returns (resvar [frames], final X, per-frame
+    analysis means)."""
     X = np.zeros((geom.n_pts, 2, m)) if X0 is None else np.array(X0, dtype=np.float64)
     resvar = np.empty(frames)
     means = []
+    ana = analysis_batched if batched else analysis
     for k in range(frames):
         resvar[k] = residual_variance(truth[k], X)
-        Xa, mean, _ = analysis(geom, X, slopes[k], sigma2, rho)
+        Xa, mean, _ = ana(geom, X, slopes[k], sigma2, rho)
         means.append(mean)
         v = bank_noise(bank, geom.points, m, seed, k, noise_scale)
         X = forecast(Xa, v, a)

@@ -1,0 +1,421 @@
+// Local ensemble transform analysis (Section 4.2 with Section 3.1 and Appendix A).
+//
+// One warp analyses one node. A CTA owns a tile of LK_TILE_I x LK_TILE_J nodes
+// and stages the (tile + window - 1)^2 halo of slope anomalies and innovations
+// in shared memory once; every warp then reads its own w x w window from it.
+//
+// Per node, with lane l standing for member / column l of the m x m problem
+// (zero-padded to MP = 16 or 32 columns):
+//   Gram     A = (m-1)/rho I + sum_j tau_j/sigma2 Yb_j Yb_j^T,  C d = sum_j tau_j/sigma2 d_j Yb_j
+//   EVD      one-sided (Hestenes) Jacobi on the columns of A: A V = V Lambda, pairs
+//            chosen by the xor tournament (step t pairs column l with l ^ t, a
+//            perfect matching for every t in 1..MP-1, all pairs once per sweep)
+//   weights  wbar = V Lambda^-1 V^T C d,  W = V ((m-1) Lambda^-1)^(1/2) V^T
+//   apply    Xa_r = xbar_r + X'_r wbar + X'_r W for the node's two rows
+// kappa_hat = 1 + rho tr(G)/(m-1) bounds the condition number of A before the
+// eigensolve (its eigenvalues lie in [(m-1)/rho, (m-1)/rho + tr G]); in FP32 mode
+// nodes above the threshold are queued and redone in FP64 by a second kernel.
+#include "letkf_common.cuh"
+
+namespace {
+
+constexpr int LIST_WARPS = 4;
+constexpr unsigned FULL = 0xffffffffu;
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <int MP, typename T>
+__host__ __device__ constexpr size_t scratch_elems() {
+  return (size_t)MP * (MP + 1) + 3 * MP;
+}
+
+// Shared-memory layout of the tile kernel (offsets in bytes).
+struct TileLayout {
+  size_t halo, dh, tap, scr, total;
+};
+template <int MP, typename S, typename T>
+__host__ __device__ TileLayout tile_layout(int w) {
+  TileLayout L;
+  const size_t ncell = (size_t)(LK_TILE_I + w - 1) * (LK_TILE_J + w - 1);
+  L.halo = 0;
+  L.dh = align16(ncell * 2 * MP * sizeof(S));
+  L.tap = align16(L.dh + ncell * 2 * sizeof(S));
+  L.scr = align16(L.tap + (size_t)w * w * sizeof(T));
+  L.total = L.scr + (size_t)LK_TILE_I * LK_TILE_J * scratch_elems<MP, T>() * sizeof(T);
+  return L;
+}
+
+// Shared-memory layout of one warp of the FP64 list kernel.
+template <int MP>
+__host__ __device__ size_t list_warp_bytes(int w) {
+  const size_t wc = (size_t)w * w;
+  return align16(wc * 2 * MP * sizeof(float)) + align16(wc * 2 * sizeof(float)) +
+         align16(wc * sizeof(double)) + scratch_elems<MP, double>() * sizeof(double);
+}
+
+__device__ __forceinline__ void ld4(const float *p, float &a, float &b, float &c, float &d) {
+  const float4 v = *reinterpret_cast<const float4 *>(p);
+  a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void ld4(const float *p, double &a, double &b, double &c, double &d) {
+  const float4 v = *reinterpret_cast<const float4 *>(p);
+  a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double &a, double &b, double &c, double &d) {
+  const double2 u = *reinterpret_cast<const double2 *>(p);
+  const double2 v = *reinterpret_cast<const double2 *>(p + 2);
+  a = u.x; b = u.y; c = v.x; d = v.y;
+}
+
+__device__ __forceinline__ float lk_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double lk_rsqrt(double x) { return rsqrt(x); }
+
+// Analysis of one node by one warp. win / dwin point at the node's window in
+// shared memory (cell (ds, dt) at row stride `stride` cells); xrow points at the
+// node's two ensemble rows in global memory (read, then overwritten by Xa).
+template <int MP, typename S, typename T>
+__device__ __forceinline__ void analyze_node(const S *__restrict__ win, const S *__restrict__ dwin,
+                                             int stride, const T *__restrict__ tap, int w, int m,
+                                             T alpha, T tol, int max_sweeps, S *__restrict__ xrow,
+                                             S *__restrict__ mean_out, S *__restrict__ spread_out,
+                                             T *__restrict__ scr, int *__restrict__ counters,
+                                             T kappa_thr, int *__restrict__ worklist, int pid) {
+  const int lane = threadIdx.x & 31;
+  const bool col = lane < MP;   // lane carries a column of the padded problem
+  const bool mem = lane < m;    // lane carries a real member / eigenpair
+
+  // ---- Gram: row `lane` of A, (C d)_lane and G_lane,lane -------------------
+  T b[MP];
+#pragma unroll
+  for (int k = 0; k < MP; ++k) b[k] = T(0);
+  T diag = T(0), cd = T(0);
+  for (int ds = 0; ds < w; ++ds) {
+    for (int dt = 0; dt < w; ++dt) {
+      const int cell = ds * stride + dt;
+      const S *cy2 = win + (size_t)cell * 2 * MP;
+      const T tw = tap[ds * w + dt];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const S *yv = cy2 + c * MP;
+        const T yl = col ? T(yv[lane]) : T(0);
+        const T cy = tw * yl;
+        diag = fma(cy, yl, diag);
+        cd = fma(cy, T(dwin[cell * 2 + c]), cd);
+#pragma unroll
+        for (int k = 0; k < MP; k += 4) {
+          T y0, y1, y2, y3;
+          ld4(yv + k, y0, y1, y2, y3);
+          b[k] = fma(cy, y0, b[k]);
+          b[k + 1] = fma(cy, y1, b[k + 1]);
+          b[k + 2] = fma(cy, y2, b[k + 2]);
+          b[k + 3] = fma(cy, y3, b[k + 3]);
+        }
+      }
+    }
+  }
+  const T dval = mem ? alpha : T(1);  // identity on the zero padding
+#pragma unroll
+  for (int k = 0; k < MP; ++k)
+    if (k == lane) b[k] += dval;
+
+  if (kappa_thr > T(0)) {
+    const T trg = lk_warp_sum(diag);
+    if (T(1) + trg / alpha > kappa_thr) {
+      if (lane == 0) worklist[atomicAdd(&counters[1], 1)] = pid;
+      return;
+    }
+  }
+
+  // ---- one-sided Jacobi: B = A V with orthogonal columns -------------------
+  T v[MP];
+#pragma unroll
+  for (int k = 0; k < MP; ++k) v[k] = (k == lane) ? T(1) : T(0);
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps; ++sweep) {
+    T nrm = T(0);
+#pragma unroll
+    for (int k = 0; k < MP; ++k) nrm = fma(b[k], b[k], nrm);
+    int rotated = 0;
+    for (int t = 1; t < MP; ++t) {
+      T pb[MP];
+#pragma unroll
+      for (int k = 0; k < MP; ++k) pb[k] = __shfl_xor_sync(FULL, b[k], t);
+      T dot = T(0);
+#pragma unroll
+      for (int k = 0; k < MP; ++k) dot = fma(b[k], pb[k], dot);
+      const T pn = __shfl_xor_sync(FULL, nrm, t);
+      const bool isp = lane < (lane ^ t);     // this lane holds column p of the pair (p < q)
+      const T app = isp ? nrm : pn;
+      const T aqq = isp ? pn : nrm;
+      T cs = T(1), sn = T(0), tr = T(0);
+      if (fabs(dot) > tol * sqrt(app * aqq)) {
+        const T zeta = (aqq - app) / (T(2) * dot);
+        const T az = fabs(zeta);
+        tr = az > T(1e15) ? T(0.5) / zeta
+                          : copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
+        cs = lk_rsqrt(T(1) + tr * tr);
+        sn = cs * tr;
+        rotated = 1;
+      }
+      // p' = c p - s q ; q' = s p + c q
+      const T sg = isp ? -sn : sn;
+#pragma unroll
+      for (int k = 0; k < MP; ++k) b[k] = fma(sg, pb[k], cs * b[k]);
+      nrm = isp ? (app - tr * dot) : (aqq + tr * dot);
+#pragma unroll
+      for (int k = 0; k < MP; ++k) pb[k] = __shfl_xor_sync(FULL, v[k], t);
+#pragma unroll
+      for (int k = 0; k < MP; ++k) v[k] = fma(sg, pb[k], cs * v[k]);
+    }
+    if (!__any_sync(FULL, rotated)) {
+      converged = true;
+      break;
+    }
+  }
+  if (lane == 0) {
+    atomicMax(&counters[2], converged ? sweep + 1 : sweep);
+    if (!converged) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
+  }
+
+  // ---- transform and apply --------------------------------------------------
+  T *vt = scr;                      // vt[i*(MP+1)+j] = V[i][j]
+  T *vec = scr + MP * (MP + 1);     // [3][MP]
+  const T x0 = mem ? T(xrow[lane]) : T(0);
+  const T x1 = mem ? T(xrow[m + lane]) : T(0);
+  const T inv_m = T(1) / T(m);
+  const T xb0 = lk_warp_sum(x0) * inv_m;
+  const T xb1 = lk_warp_sum(x1) * inv_m;
+  const T xp0 = mem ? x0 - xb0 : T(0);
+  const T xp1 = mem ? x1 - xb1 : T(0);
+  if (col) {
+    vec[lane] = cd;
+    vec[MP + lane] = xp0;
+    vec[2 * MP + lane] = xp1;
+#pragma unroll
+    for (int k = 0; k < MP; ++k) vt[k * (MP + 1) + lane] = v[k];
+  }
+  __syncwarp();
+  T u = T(0), g0 = T(0), g1 = T(0), nrm = T(0);
+#pragma unroll
+  for (int k = 0; k < MP; ++k) {
+    u = fma(v[k], vec[k], u);               // (V^T C d)_lane
+    g0 = fma(v[k], vec[MP + k], g0);        // (X'_0 V)_lane
+    g1 = fma(v[k], vec[2 * MP + k], g1);    // (X'_1 V)_lane
+    nrm = fma(b[k], b[k], nrm);
+  }
+  const T lam = (col && nrm > T(0)) ? sqrt(nrm) : T(1);   // |A v_j| = lambda_j
+  const T z = u / lam;
+  const T P0 = lk_warp_sum(g0 * z);           // X'_0 wbar
+  const T P1 = lk_warp_sum(g1 * z);
+  const T sroot = mem ? sqrt(T(m - 1) / lam) : T(0);
+  __syncwarp();
+  if (col) {
+    vec[MP + lane] = g0 * sroot;
+    vec[2 * MP + lane] = g1 * sroot;
+  }
+  __syncwarp();
+  T q0 = T(0), q1 = T(0);
+  if (col) {
+    const T *vr = vt + lane * (MP + 1);
+#pragma unroll
+    for (int j = 0; j < MP; ++j) {
+      q0 = fma(vr[j], vec[MP + j], q0);        // (X'_0 W)_lane
+      q1 = fma(vr[j], vec[2 * MP + j], q1);
+    }
+  }
+  const T xa0 = xb0 + P0 + q0;
+  const T xa1 = xb1 + P1 + q1;
+  if (mem) {
+    xrow[lane] = S(xa0);
+    xrow[m + lane] = S(xa1);
+  }
+  const T mu0 = lk_warp_sum(mem ? xa0 : T(0)) * inv_m;
+  const T mu1 = lk_warp_sum(mem ? xa1 : T(0)) * inv_m;
+  const T e0 = mem ? xa0 - mu0 : T(0);
+  const T e1 = mem ? xa1 - mu1 : T(0);
+  const T sp0 = sqrt(lk_warp_sum(e0 * e0) / T(m - 1));
+  const T sp1 = sqrt(lk_warp_sum(e1 * e1) / T(m - 1));
+  if (lane == 0) {
+    if (mean_out) {
+      mean_out[0] = S(mu0);
+      mean_out[1] = S(mu1);
+    }
+    if (spread_out) {
+      spread_out[0] = S(sp0);
+      spread_out[1] = S(sp1);
+    }
+    if (!isfinite(mu0) || !isfinite(mu1) || !isfinite(sp0) || !isfinite(sp1))
+      atomicOr(&counters[0], LK_BIT_NONFINITE);
+  }
+}
+
+template <int MP, typename S, typename T, bool FALLBACK>
+__global__ void __launch_bounds__(LK_TILE_I *LK_TILE_J * 32)
+    analysis_tile_kernel(LkGeom g, const int2 *__restrict__ tiles, const S *__restrict__ Ybp,
+                         const S *__restrict__ dp, const S *__restrict__ taper, S *__restrict__ X,
+                         S *__restrict__ mean, S *__restrict__ spread, T alpha, T tol,
+                         int max_sweeps, T kappa_thr, int *__restrict__ counters,
+                         int *__restrict__ worklist) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int w = g.w;
+  const TileLayout L = tile_layout<MP, S, T>(w);
+  const int HJ = LK_TILE_J + w - 1;
+  const int ncell = (LK_TILE_I + w - 1) * HJ;
+  S *halo = reinterpret_cast<S *>(smem + L.halo);
+  S *dh = reinterpret_cast<S *>(smem + L.dh);
+  T *tap = reinterpret_cast<T *>(smem + L.tap);
+  T *scr = reinterpret_cast<T *>(smem + L.scr);
+  const int2 org = tiles[blockIdx.x];
+  const int m = g.m;
+  for (int e = threadIdx.x; e < ncell * 2 * MP; e += blockDim.x) {
+    const int cell = e / (2 * MP);
+    const int r = e - cell * 2 * MP;
+    const int c = r / MP;
+    const int mm = r - c * MP;
+    const int hi = cell / HJ, hj = cell - (cell / HJ) * HJ;
+    const size_t src = (size_t)(org.x + hi) * g.gs_cols + (org.y + hj);
+    halo[e] = mm < m ? Ybp[(src * 2 + c) * m + mm] : S(0);
+  }
+  for (int e = threadIdx.x; e < ncell * 2; e += blockDim.x) {
+    const int cell = e >> 1;
+    const int hi = cell / HJ, hj = cell - (cell / HJ) * HJ;
+    const size_t src = (size_t)(org.x + hi) * g.gs_cols + (org.y + hj);
+    dh[e] = dp[src * 2 + (e & 1)];
+  }
+  for (int e = threadIdx.x; e < w * w; e += blockDim.x) tap[e] = T(taper[e]);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  const int ti = warp / LK_TILE_J, tj = warp - (warp / LK_TILE_J) * LK_TILE_J;
+  const int i = org.x + ti, j = org.y + tj;
+  if (i > g.nsub || j > g.nsub) return;
+  const int pid = g.pid_map[i * (g.nsub + 1) + j];
+  if (pid < 0) return;
+  const int off = ti * HJ + tj;
+  analyze_node<MP, S, T>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m, alpha, tol,
+                         max_sweeps, X + (size_t)pid * 2 * m, mean ? mean + 2 * pid : nullptr,
+                         spread ? spread + 2 * pid : nullptr,
+                         scr + (size_t)warp * scratch_elems<MP, T>(), counters,
+                         FALLBACK ? kappa_thr : T(0), worklist, pid);
+}
+
+// FP64 re-analysis of the queued nodes of an FP32 handle: one warp per node,
+// window staged per warp from the padded grid.
+template <int MP>
+__global__ void __launch_bounds__(LIST_WARPS * 32)
+    analysis_list_kernel(LkGeom g, const int *__restrict__ worklist, const float *__restrict__ Ybp,
+                         const float *__restrict__ dp, const float *__restrict__ taper,
+                         float *__restrict__ X, float *__restrict__ mean, float *__restrict__ spread,
+                         double alpha, double tol, int max_sweeps, int *__restrict__ counters) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int w = g.w, wc = w * w, m = g.m;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * LIST_WARPS + warp;
+  if (idx >= counters[1]) return;
+  unsigned char *base = smem + (size_t)warp * list_warp_bytes<MP>(w);
+  float *win = reinterpret_cast<float *>(base);
+  float *dwin = reinterpret_cast<float *>(base + align16((size_t)wc * 2 * MP * sizeof(float)));
+  double *tap = reinterpret_cast<double *>(base + align16((size_t)wc * 2 * MP * sizeof(float)) +
+                                           align16((size_t)wc * 2 * sizeof(float)));
+  double *scr = tap + align16((size_t)wc * sizeof(double)) / sizeof(double);
+  const int pid = worklist[idx];
+  const int2 ij = g.pts[pid];
+  for (int e = lane; e < wc * 2 * MP; e += 32) {
+    const int cell = e / (2 * MP);
+    const int r = e - cell * 2 * MP;
+    const int c = r / MP;
+    const int mm = r - c * MP;
+    const int ds = cell / w, dt = cell - (cell / w) * w;
+    const size_t src = (size_t)(ij.x + ds) * g.gs_cols + (ij.y + dt);
+    win[e] = mm < m ? Ybp[(src * 2 + c) * m + mm] : 0.f;
+  }
+  for (int e = lane; e < wc * 2; e += 32) {
+    const int cell = e >> 1;
+    const int ds = cell / w, dt = cell - (cell / w) * w;
+    const size_t src = (size_t)(ij.x + ds) * g.gs_cols + (ij.y + dt);
+    dwin[e] = dp[src * 2 + (e & 1)];
+  }
+  for (int e = lane; e < wc; e += 32) tap[e] = (double)taper[e];
+  __syncwarp();
+  analyze_node<MP, float, double>(win, dwin, w, tap, w, m, alpha, tol, max_sweeps,
+                                  X + (size_t)pid * 2 * m, mean ? mean + 2 * pid : nullptr,
+                                  spread ? spread + 2 * pid : nullptr, scr, counters, 0.0,
+                                  nullptr, pid);
+}
+
+template <int MP, typename S, typename T, bool FB>
+cudaError_t launch_tile(letkf_ctx *h, void *mean, void *spread, T tol) {
+  const TileLayout L = tile_layout<MP, S, T>(h->g.w);
+  auto kern = analysis_tile_kernel<MP, S, T, FB>;
+  kern<<<h->n_tiles, LK_TILE_I * LK_TILE_J * 32, L.total, h->stream>>>(
+      h->g, h->tiles, (const S *)h->Ybp, (const S *)h->dp, (const S *)h->taper, (S *)h->X,
+      (S *)mean, (S *)spread, (T)h->alpha, tol, h->max_sweeps, (T)h->cfg.fp64_kappa, h->counters,
+      h->worklist);
+  return cudaGetLastError();
+}
+
+template <int MP>
+cudaError_t launch_list(letkf_ctx *h, void *mean, void *spread) {
+  const size_t bytes = (size_t)LIST_WARPS * list_warp_bytes<MP>(h->g.w);
+  auto kern = analysis_list_kernel<MP>;
+  const int blocks = (h->g.n_pts + LIST_WARPS - 1) / LIST_WARPS;
+  kern<<<blocks, LIST_WARPS * 32, bytes, h->stream>>>(
+      h->g, h->worklist, (const float *)h->Ybp, (const float *)h->dp, (const float *)h->taper,
+      (float *)h->X, (float *)mean, (float *)spread, h->alpha, h->tol64, h->max_sweeps,
+      h->counters);
+  return cudaGetLastError();
+}
+
+template <int MP>
+cudaError_t launch_all(letkf_ctx *h, void *mean, void *spread) {
+  cudaError_t e;
+  if (h->precision == 1) return launch_tile<MP, double, double, false>(h, mean, spread, h->tol64);
+  if (h->cfg.fp64_kappa > 0) {
+    e = launch_tile<MP, float, float, true>(h, mean, spread, (float)h->tol32);
+    if (e != cudaSuccess) return e;
+    return launch_list<MP>(h, mean, spread);
+  }
+  return launch_tile<MP, float, float, false>(h, mean, spread, (float)h->tol32);
+}
+
+template <int MP>
+cudaError_t setup_all(letkf_ctx *h) {
+  const int w = h->g.w;
+  cudaError_t e;
+  if (h->precision == 1)
+    return cudaFuncSetAttribute(analysis_tile_kernel<MP, double, double, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tile_layout<MP, double, double>(w).total);
+  const int tb = (int)tile_layout<MP, float, float>(w).total;
+  e = cudaFuncSetAttribute(analysis_tile_kernel<MP, float, float, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(analysis_tile_kernel<MP, float, float, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(analysis_list_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(LIST_WARPS * list_warp_bytes<MP>(w)));
+}
+
+}  // namespace
+
+// Raises the dynamic shared-memory limit of the analysis kernels this handle uses.
+cudaError_t lk_setup_analysis(letkf_ctx *h) {
+  return h->mp == 16 ? setup_all<16>(h) : setup_all<32>(h);
+}
+
+size_t lk_tile_smem_bytes(int mp, int precision, int w) {
+  if (mp == 16)
+    return precision ? tile_layout<16, double, double>(w).total : tile_layout<16, float, float>(w).total;
+  return precision ? tile_layout<32, double, double>(w).total : tile_layout<32, float, float>(w).total;
+}
+
+size_t lk_list_smem_bytes(int mp, int w) {
+  return (size_t)LIST_WARPS * (mp == 16 ? list_warp_bytes<16>(w) : list_warp_bytes<32>(w));
+}
+
+cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread) {
+  cudaError_t e = cudaMemsetAsync(h->counters + 1, 0, 2 * sizeof(int), h->stream);
+  if (e != cudaSuccess) return e;
+  return h->mp == 16 ? launch_all<16>(h, mean, spread) : launch_all<32>(h, mean, spread);
+}

@@ -1,0 +1,303 @@
+"""Python binding of libletkf.so (see include/letkf.h).
+
+Argument marshalling only: every step of the analysis, forecast and residual
+runs in the CUDA library. Torch supplies device memory and streams. Importing
+this module does not need a GPU; creating a handle does, and fails loudly when
+the library is not built or no GPU is present. There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from ctypes import POINTER, byref, c_char_p, c_double, c_int32, c_uint64, c_void_p
+
+import numpy as np
+
+PKG_DIR = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG_DIR, "libletkf.so")
+HEADER = os.path.join(os.path.dirname(PKG_DIR), "include", "letkf.h")
+
+LETKF_OK = 0
+STATUS_NAMES = {0: "LETKF_OK", 1: "LETKF_ERR_ARG", 2: "LETKF_ERR_CUDA", 3: "LETKF_ERR_NOCONVERGE",
+                4: "LETKF_ERR_TIMEOUT", 5: "LETKF_ERR_NONFINITE", 6: "LETKF_ERR_STATE",
+                7: "LETKF_ERR_NOMEM"}
+
+
+class LetkfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class letkf_config(ctypes.Structure):
+    _fields_ = [("nsub", c_int32), ("subap_mask", c_void_p), ("m", c_int32), ("window", c_int32),
+                ("taper", c_int32), ("loc_len", c_double), ("rho", c_double), ("sigma2", c_double),
+                ("a_ar1", c_double), ("noise_std", c_double), ("precision", c_int32),
+                ("fp64_kappa", c_double), ("seed", c_uint64), ("noise_bank", c_void_p),
+                ("bank_B", c_int32), ("bank_G", c_int32), ("max_sweeps", c_int32)]
+
+
+_SIGS = {
+    "letkf_create": [POINTER(letkf_config), c_void_p, POINTER(c_void_p)],
+    "letkf_destroy": [c_void_p],
+    "letkf_query": [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)],
+    "letkf_query_points": [c_void_p, c_void_p, c_void_p],
+    "letkf_get_state": [c_void_p, c_void_p],
+    "letkf_set_state": [c_void_p, c_void_p],
+    "letkf_forecast": [c_void_p, c_void_p],
+    "letkf_analyze": [c_void_p, c_void_p, c_void_p, c_void_p],
+    "letkf_residual": [c_void_p, c_void_p, c_void_p],
+    "letkf_run": [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32],
+    "letkf_sync": [c_void_p],
+    "letkf_stats": [c_void_p, POINTER(c_int32), POINTER(c_int32)],
+}
+
+_lib = None
+
+
+def header_symbols() -> list:
+    """Entry points declared in include/letkf.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:letkf_status|const char \*)\s*(letkf_\w+)\s*\(", text,
+                                 re.M)))
+
+
+def lib() -> ctypes.CDLL:
+    """Load libletkf.so (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is not built; run `python -m paper_1408_7069_gb300.build` "
+                "(the CUDA library is the only implementation)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = c_int32
+        L.letkf_last_error.argtypes = [c_void_p]
+        L.letkf_last_error.restype = c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int, h) -> None:
+    if status != LETKF_OK:
+        msg = lib().letkf_last_error(h)
+        raise LetkfError(status, msg.decode() if msg else "")
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------------------
+# Functions named as the C ABI (handles are ctypes.c_void_p).
+# ---------------------------------------------------------------------------
+def letkf_create(cfg: letkf_config, stream_ptr: int) -> c_void_p:
+    h = c_void_p()
+    _check(lib().letkf_create(byref(cfg), c_void_p(stream_ptr), byref(h)), None)
+    return h
+
+
+def letkf_destroy(h) -> None:
+    _check(lib().letkf_destroy(h), None)
+
+
+def letkf_query(h):
+    n, p, m = c_int32(), c_int32(), c_int32()
+    _check(lib().letkf_query(h, byref(n), byref(p), byref(m)), h)
+    return n.value, p.value, m.value
+
+
+def letkf_query_points(h, n_pts: int):
+    ij = np.zeros((n_pts, 2), np.int32)
+    ws = np.zeros(n_pts, np.int32)
+    _check(lib().letkf_query_points(h, ij.ctypes.data, ws.ctypes.data), h)
+    return ij, ws
+
+
+def letkf_get_state(h, X) -> None:
+    _check(lib().letkf_get_state(h, _ptr(X)), h)
+
+
+def letkf_set_state(h, X) -> None:
+    _check(lib().letkf_set_state(h, _ptr(X)), h)
+
+
+def letkf_forecast(h, noise=None) -> None:
+    _check(lib().letkf_forecast(h, _ptr(noise)), h)
+
+
+def letkf_analyze(h, y, mean=None, spread=None) -> None:
+    _check(lib().letkf_analyze(h, _ptr(y), _ptr(mean), _ptr(spread)), h)
+
+
+def letkf_residual(h, truth, resvar) -> None:
+    _check(lib().letkf_residual(h, _ptr(truth), _ptr(resvar)), h)
+
+
+def letkf_run(h, frames: int, y_seq, truth_seq=None, resvar=None, use_graph: bool = True) -> None:
+    _check(lib().letkf_run(h, int(frames), _ptr(y_seq), _ptr(truth_seq), _ptr(resvar),
+                           1 if use_graph else 0), h)
+
+
+def letkf_sync(h) -> None:
+    _check(lib().letkf_sync(h), h)
+
+
+def letkf_stats(h):
+    a, b = c_int32(), c_int32()
+    _check(lib().letkf_stats(h, byref(a), byref(b)), h)
+    return a.value, b.value
+
+
+def letkf_last_error(h=None) -> str:
+    msg = lib().letkf_last_error(h)
+    return msg.decode() if msg else ""
+
+
+# ---------------------------------------------------------------------------
+# Handle object
+# ---------------------------------------------------------------------------
+class Letkf:
+    """One LETKF instance on one GPU, on its own CUDA stream.
+
+    Tensor arguments are CUDA tensors of the handle's dtype (float32 when
+    precision = 0, float64 when precision = 1), contiguous, in the layouts of
+    include/letkf.h. Calls order the handle's stream after torch's current
+    stream on entry and torch's current stream after the handle's on exit, so
+    they compose with ordinary torch code.
+    """
+
+    def __init__(self, subap_mask, m: int, window: int, taper: int = 1, loc_len: float = 0.0,
+                 rho: float = 1.0, sigma2: float = 0.01, a_ar1: float = 1.0,
+                 noise_std: float = 0.0, precision: int = 0, fp64_kappa: float = 1000.0,
+                 seed: int = 0, bank=None, max_sweeps: int = 0, stream=None):
+        import torch
+        self._torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Letkf needs a CUDA GPU; there is no CPU implementation")
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        mask = np.ascontiguousarray(subap_mask, dtype=np.uint8)
+        self._bank = None if bank is None else np.ascontiguousarray(bank, dtype=np.float32)
+        cfg = letkf_config()
+        cfg.nsub = mask.shape[0]
+        cfg.subap_mask = mask.ctypes.data
+        cfg.m, cfg.window, cfg.taper, cfg.loc_len = m, window, taper, loc_len
+        cfg.rho, cfg.sigma2, cfg.a_ar1, cfg.noise_std = rho, sigma2, a_ar1, noise_std
+        cfg.precision, cfg.fp64_kappa, cfg.seed = precision, fp64_kappa, seed
+        if self._bank is not None:
+            cfg.noise_bank = self._bank.ctypes.data
+            cfg.bank_B, cfg.bank_G = self._bank.shape[0], self._bank.shape[1]
+        cfg.max_sweeps = max_sweeps
+        self.h = letkf_create(cfg, self.stream.cuda_stream)
+        self.n_pts, self.p, self.m = letkf_query(self.h)
+        self.dtype = torch.float32 if precision == 0 else torch.float64
+        self.precision = precision
+
+    @classmethod
+    def from_workload(cls, w, bank=None, **kw):
+        from .synth import pupil_subap_mask
+        mask = pupil_subap_mask(w.nsub, w.obscuration, w.square)
+        args = dict(m=w.m, window=w.window, taper=w.taper, loc_len=w.loc_len, rho=w.rho,
+                    sigma2=w.sigma2, a_ar1=w.a_ar1, noise_std=w.noise_std,
+                    precision=w.precision, seed=w.seeds[2], bank=bank)
+        args.update(kw)
+        return cls(mask, **args)
+
+    # -- stream ordering ---------------------------------------------------
+    def _enter(self):
+        self.stream.wait_stream(self._torch.cuda.current_stream())
+
+    def _leave(self):
+        self._torch.cuda.current_stream().wait_stream(self.stream)
+
+    def _t(self, t, shape):
+        if t is None:
+            return None
+        if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous()):
+            raise ValueError(f"expected a contiguous CUDA {self.dtype} tensor, got {t.dtype} "
+                             f"on {t.device} (contiguous={t.is_contiguous()})")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+        return t
+
+    # -- API -----------------------------------------------------------------
+    def points(self):
+        return letkf_query_points(self.h, self.n_pts)
+
+    def new(self, *shape):
+        return self._torch.zeros(*shape, dtype=self.dtype, device="cuda")
+
+    def set_state(self, X):
+        self._enter()
+        letkf_set_state(self.h, self._t(X, (self.n_pts, 2, self.m)))
+        self._leave()
+
+    def get_state(self):
+        X = self.new(self.n_pts, 2, self.m)
+        self._enter()
+        letkf_get_state(self.h, X)
+        self._leave()
+        return X
+
+    def forecast(self, noise=None):
+        self._enter()
+        letkf_forecast(self.h, self._t(noise, (self.n_pts, self.m)))
+        self._leave()
+
+    def analyze(self, y, mean=None, spread=None, outputs: bool = True):
+        if outputs and mean is None:
+            mean = self.new(self.n_pts, 2)
+        if outputs and spread is None:
+            spread = self.new(self.n_pts, 2)
+        self._enter()
+        letkf_analyze(self.h, self._t(y, (self.p,)), self._t(mean, (self.n_pts, 2)),
+                      self._t(spread, (self.n_pts, 2)))
+        self._leave()
+        return mean, spread
+
+    def residual(self, truth, resvar=None):
+        if resvar is None:
+            resvar = self._torch.zeros(1, dtype=self._torch.float64, device="cuda")
+        self._enter()
+        letkf_residual(self.h, self._t(truth, (self.n_pts,)), resvar)
+        self._leave()
+        return resvar
+
+    def run(self, frames: int, y_seq, truth_seq=None, resvar=None, use_graph: bool = True):
+        self._t(y_seq, (y_seq.shape[0], self.p))
+        if y_seq.shape[0] < frames:
+            raise ValueError("y_seq shorter than frames")
+        if truth_seq is not None:
+            self._t(truth_seq, (truth_seq.shape[0], self.n_pts))
+            if truth_seq.shape[0] < frames:
+                raise ValueError("truth_seq shorter than frames")
+            if resvar is None:
+                resvar = self._torch.zeros(frames, dtype=self._torch.float64, device="cuda")
+        self._enter()
+        letkf_run(self.h, frames, y_seq, truth_seq, resvar, use_graph)
+        self._leave()
+        return resvar
+
+    def sync(self):
+        letkf_sync(self.h)
+
+    def stats(self):
+        return letkf_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            letkf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -139,29 +139,49 @@ def ar1_truth(seed: int, frames: int, nsub: int, pitch: float, r0: float, L0: fl
 
 
 def frozen_flow_truth(seed: int, frames: int, nsub: int, pitch: float, r0: float, L0: float,
-                      px_per_pitch: int = 25) -> np.ndarray:
-    """One frozen-flow layer moving one screen pixel per frame along axis 0.
+                      shift: float, px_per_pitch: int = 8) -> np.ndarray:
+    """One frozen-flow layer moving ``shift`` pitches per frame along axis 0.
 
-    The screen spacing is pitch/px_per_pitch, so the wind speed is
-    spacing * 500 Hz (0.02 m/frame, i.e. 10 m/s, for pitch 0.5 m and 25 px).
-    Returns float64 [frames, nsub+1, nsub+1]."""
+    The screen is drawn at spacing pitch/px_per_pitch; a sub-pixel position is
+    read by linear interpolation along the flow axis (the nodes sit on screen
+    columns). Returns float64 [frames, nsub+1, nsub+1]."""
     nn = nsub + 1
     dx = pitch / px_per_pitch
     span = (nn - 1) * px_per_pitch + 1
-    nx = span + frames
-    ny = span
+    nx = span + int(math.ceil(frames * shift * px_per_pitch)) + 2
     fx = 1
     while fx < nx:
         fx *= 2
     fy = 1
-    while fy < ny:
+    while fy < span:
         fy *= 2
     scr = von_karman_screens(seed, 1, fx, fy, dx, r0, L0)[0]
     idx = np.arange(nn) * px_per_pitch
     out = np.empty((frames, nn, nn))
     for k in range(frames):
-        out[k] = scr[np.ix_(idx + k, idx)]
+        pos = k * shift * px_per_pitch
+        i0 = int(pos)
+        f = pos - i0
+        out[k] = (1 - f) * scr[np.ix_(idx + i0, idx)] + f * scr[np.ix_(idx + i0 + 1, idx)]
     return out
+
+
+def prior_ensemble(seed: int, subap_mask: np.ndarray, m: int, a: float, q: float,
+                   pitch: float, r0: float, L0: float) -> np.ndarray:
+    """Initial forecast ensemble [n_pts, 2, m] drawn from the AR(1) model's
+    stationary law: phi_{-1} a von Karman screen at the nodes, phi_0 =
+    a phi_{-1} + q xi with xi an independent screen."""
+    nodes = node_mask_of(subap_mask)
+    pts = np.argwhere(nodes)
+    g = bank_size(subap_mask.shape[0])
+    scr = von_karman_screens(seed, 2 * m, g, g, pitch, r0, L0, subharmonics=False)
+    X = np.empty((len(pts), 2, m))
+    for i in range(m):
+        prev = scr[2 * i][pts[:, 0], pts[:, 1]]
+        nxt = scr[2 * i + 1][pts[:, 0], pts[:, 1]]
+        X[:, 1, i] = prev
+        X[:, 0, i] = a * prev + q * nxt
+    return X
 
 
 # --------------------------------------------------------------------------
@@ -202,11 +222,13 @@ class LoopInputs:
     truth   [frames, n_pts]  phi^tur_k at the valid nodes (row-major order), float64
     slopes  [frames, p]      y_k = D phi^tur_{k-1} + w_k (y_0 sees a flat phase), float64
     bank    [B, G, G]        forecast-noise screens, float32
+    X0      [n_pts, 2, m]    initial forecast ensemble (prior draw), float64
     """
     subap_mask: np.ndarray
     truth: np.ndarray
     slopes: np.ndarray
     bank: np.ndarray
+    X0: np.ndarray
 
 
 def make_loop_inputs(w, frames: int | None = None) -> LoopInputs:
@@ -217,8 +239,7 @@ def make_loop_inputs(w, frames: int | None = None) -> LoopInputs:
     if w.truth == "ar1":
         phi = ar1_truth(seeds[0], frames, w.nsub, w.pitch, w.r0, w.L0, w.a_ar1)
     else:
-        phi = frozen_flow_truth(seeds[0], frames, w.nsub, w.pitch, w.r0, w.L0,
-                                w.px_per_pitch)
+        phi = frozen_flow_truth(seeds[0], frames, w.nsub, w.pitch, w.r0, w.L0, w.shift)
     nodes = node_mask_of(mask)
     truth = phi[:, nodes]
     clean = wfs_slopes(phi, mask)                      # slopes of frame k's phase
@@ -228,7 +249,9 @@ def make_loop_inputs(w, frames: int | None = None) -> LoopInputs:
     slopes[0] = noise[0]                               # y_0 = D*0 + w_0
     slopes[1:] = clean[:-1] + noise[1:]                # y_k = D phi_{k-1} + w_k
     bank = noise_bank(seeds[2], w.bank_count, bank_size(w.nsub), w.pitch, w.r0, w.L0)
-    return LoopInputs(mask, truth, slopes, bank)
+    X0 = prior_ensemble(seeds[0] + 1000, mask, w.m, w.a_ar1, w.noise_std, w.pitch, w.r0, w.L0)
+    c = np.ascontiguousarray
+    return LoopInputs(mask, c(truth), c(slopes), c(bank), c(X0))
 
 
 def random_ensemble(seed: int, n_pts: int, m: int, scale: float = 1.0,

@@ -1,0 +1,265 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Every case feeds both sides the same seeded inputs, rounded to the handle's
+storage type. Tolerances (norm-wise over all nodes of a frame): analysis mean
+1e-4 and ensemble spread 1e-3 relative for FP32 handles; 1e-9 / 1e-8 for FP64
+handles; plus max-abs checks scaled by the RMS of the reference.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1408_7069_gb300 import synth, workloads as W  # noqa: E402
+from paper_1408_7069_gb300.letkf import Letkf, LetkfError  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: dict(mean=1e-4, spread=1e-3, anom=1e-3), 1: dict(mean=1e-9, spread=1e-8, anom=1e-8)}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+@functools.lru_cache(maxsize=None)
+def inputs(w, frames):
+    inp = synth.make_loop_inputs(w, frames=frames)
+    geom = oracle.build_geometry(inp.subap_mask, w.window, w.taper, w.loc_len)
+    return inp, geom
+
+
+def oracle_background(w, inp, geom, frames):
+    X = inp.X0.copy()
+    for k in range(frames):
+        Xa, _, _ = oracle.analysis_batched(geom, X, inp.slopes[k], w.sigma2, w.rho)
+        v = oracle.bank_noise(inp.bank, geom.points, w.m, w.seeds[2], k, w.noise_std)
+        X = oracle.forecast(Xa, v, w.a_ar1)
+    return X
+
+
+def dtype_of(w):
+    return np.float32 if w.precision == 0 else np.float64
+
+
+def check_analysis(tol, Xa, mean, spread, ref):
+    rXa, rmean, rspread = ref
+    assert rel(mean, rmean) <= tol["mean"], rel(mean, rmean)
+    assert rel(spread, rspread) <= tol["spread"], rel(spread, rspread)
+    anom = Xa - Xa.mean(-1, keepdims=True)
+    ranom = rXa - rXa.mean(-1, keepdims=True)
+    assert rel(anom, ranom) <= tol["anom"], rel(anom, ranom)
+    rms_m = np.sqrt(np.mean(rmean**2))
+    rms_s = np.sqrt(np.mean(rspread**2))
+    assert np.abs(mean - rmean).max() <= 10 * tol["mean"] * rms_m
+    assert np.abs(spread - rspread).max() <= 10 * tol["spread"] * rms_s
+
+
+CASES = [(W.TINY_4X4, 0), (W.TINY_4X4, 3), (W.TOY_8X8, 0), (W.TOY_8X8, 6), (W.TEL_16M, 0),
+         (W.TEL_16M, 6), (W.ELT_80X80, 0), (W.ELT_80X80, 3)]
+
+
+@pytest.mark.parametrize("w,k", CASES, ids=[f"{w.name}-f{k}" for w, k in CASES])
+def test_analysis_teacher_forced(w, k):
+    inp, geom = inputs(w, 8)
+    Xb = oracle_background(w, inp, geom, k) if k else inp.X0
+    dt = dtype_of(w)
+    Xb_r = Xb.astype(dt)
+    y_r = inp.slopes[k].astype(dt)
+    ref = oracle.analysis(geom, Xb_r.astype(np.float64), y_r.astype(np.float64), w.sigma2, w.rho)
+    f = Letkf.from_workload(w, bank=inp.bank)
+    ij, ws = f.points()
+    assert np.array_equal(ij, geom.points)
+    assert np.array_equal(ws, [len(i) for i in geom.win_idx])
+    f.set_state(torch.from_numpy(Xb_r).cuda())
+    mean, spread = f.analyze(torch.from_numpy(y_r).cuda())
+    f.sync()
+    Xa = f.get_state().cpu().numpy().astype(np.float64)
+    check_analysis(TOL[w.precision], Xa, mean.cpu().numpy(), spread.cpu().numpy(), ref)
+    f.close()
+
+
+def test_fp64_fallback_matches_oracle_and_counts_points():
+    """Prior-draw background (kappa ~ 1e4): every node routed to the FP64
+    eigensolve meets the FP32 tolerances; the FP32-only path does not reach
+    them at this conditioning, which is what the kappa_hat rule is for."""
+    w = W.TEL_16M
+    inp, geom = inputs(w, 8)
+    Xb_r = inp.X0.astype(np.float32)
+    y_r = inp.slopes[0].astype(np.float32)
+    ref = oracle.analysis(geom, Xb_r.astype(np.float64), y_r.astype(np.float64), w.sigma2, w.rho)
+    err = {}
+    for kappa in (1.0000001, 0.0):
+        f = Letkf.from_workload(w, bank=inp.bank, fp64_kappa=kappa)
+        f.set_state(torch.from_numpy(Xb_r).cuda())
+        mean, spread = f.analyze(torch.from_numpy(y_r).cuda())
+        f.sync()
+        nfp64, sweeps = f.stats()
+        assert nfp64 == (f.n_pts if kappa > 0 else 0)
+        assert 1 <= sweeps <= 20
+        Xa = f.get_state().cpu().numpy().astype(np.float64)
+        err[kappa] = rel(mean.cpu().numpy(), ref[1])
+        if kappa > 0:
+            check_analysis(TOL[0], Xa, mean.cpu().numpy(), spread.cpu().numpy(), ref)
+        f.close()
+    assert err[1.0000001] < err[0.0] <= 1e-3, err
+
+
+def test_forecast_bank_noise_matches_oracle():
+    for w in (W.TOY_8X8, W.TEL_16M):
+        inp, geom = inputs(w, 8)
+        dt = dtype_of(w)
+        X = inp.X0.astype(dt)
+        f = Letkf.from_workload(w, bank=inp.bank)
+        f.set_state(torch.from_numpy(X).cuda())
+        ref = X.astype(np.float64)
+        for k in range(3):
+            f.forecast()
+            v = oracle.bank_noise(inp.bank, geom.points, w.m, w.seeds[2], k, w.noise_std)
+            ref = oracle.forecast(ref, v, w.a_ar1)
+        got = f.get_state().cpu().numpy()
+        assert np.abs(got - ref).max() <= (1e-5 if dt == np.float32 else 1e-12) * np.abs(ref).max()
+        f.close()
+
+
+def test_forecast_with_given_noise_and_residual():
+    w = W.TEL_16M
+    inp, geom = inputs(w, 8)
+    X = inp.X0.astype(np.float32)
+    v = np.random.default_rng(5).standard_normal((geom.n_pts, w.m)).astype(np.float32)
+    f = Letkf.from_workload(w, bank=None)
+    f.set_state(torch.from_numpy(X).cuda())
+    f.forecast(torch.from_numpy(v).cuda())
+    ref = oracle.forecast(X.astype(np.float64), v.astype(np.float64), w.a_ar1)
+    got = f.get_state().cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+    truth = inp.truth[3].astype(np.float32)
+    rv = f.residual(torch.from_numpy(truth).cuda())
+    f.sync()
+    expect = oracle.residual_variance(truth.astype(np.float64), got.astype(np.float64))
+    assert abs(rv.item() - expect) <= 1e-6 * expect
+    with pytest.raises(LetkfError):
+        f.forecast()          # no noise and no bank
+    f.close()
+
+
+@pytest.mark.parametrize("w,frames", [(W.TOY_8X8, 100), (W.TEL_16M, 60)],
+                         ids=["toy-fp64-100f", "16m-fp32-60f"])
+def test_closed_loop_free_running(w, frames):
+    inp, geom = inputs(w, frames)
+    dt = dtype_of(w)
+    rv_ref, X_ref, _ = oracle.closed_loop(
+        geom, inp.truth.astype(dt).astype(np.float64), inp.slopes.astype(dt).astype(np.float64),
+        inp.bank, w.m, w.sigma2, w.rho, w.a_ar1, w.noise_std, w.seeds[2], frames,
+        X0=inp.X0.astype(dt).astype(np.float64), batched=True)
+    f = Letkf.from_workload(w, bank=inp.bank)
+    f.set_state(torch.from_numpy(inp.X0.astype(dt)).cuda())
+    y = torch.from_numpy(inp.slopes.astype(dt)).cuda()
+    truth = torch.from_numpy(inp.truth.astype(dt)).cuda()
+    rv = f.run(frames, y, truth, use_graph=True)
+    f.sync()
+    rv = rv.cpu().numpy()
+    tol = 1e-3 if w.precision == 0 else 1e-8
+    assert np.max(np.abs(rv - rv_ref) / rv_ref) <= tol, np.max(np.abs(rv - rv_ref) / rv_ref)
+    # piston (and other barely damped unobservable modes) drift apart by rounding;
+    # compare the piston-removed estimates, as the criterion does
+    X = f.get_state().cpu().numpy().astype(np.float64)
+    assert rel(depiston(X.mean(-1)), depiston(X_ref.mean(-1))) <= tol
+    f.close()
+
+
+def depiston(mean):
+    return mean - mean.mean(0, keepdims=True)
+
+
+def test_elt_scale_closed_loop_in_bench_configuration():
+    """80x80, m = 32, 7x7 window: graph-captured closed loop against the oracle."""
+    w = W.ELT_80X80
+    frames = 8
+    inp, geom = inputs(w, 8)
+    rv_ref, X_ref, _ = oracle.closed_loop(
+        geom, inp.truth[:frames].astype(np.float32).astype(np.float64),
+        inp.slopes[:frames].astype(np.float32).astype(np.float64), inp.bank, w.m, w.sigma2,
+        w.rho, w.a_ar1, w.noise_std, w.seeds[2], frames,
+        X0=inp.X0.astype(np.float32).astype(np.float64), batched=True)
+    f = Letkf.from_workload(w, bank=inp.bank)
+    f.set_state(torch.from_numpy(inp.X0.astype(np.float32)).cuda())
+    rv = f.run(frames, torch.from_numpy(inp.slopes[:frames].astype(np.float32)).cuda(),
+               torch.from_numpy(inp.truth[:frames].astype(np.float32)).cuda(), use_graph=True)
+    f.sync()
+    assert np.max(np.abs(rv.cpu().numpy() - rv_ref) / rv_ref) <= 1e-3
+    X = f.get_state().cpu().numpy().astype(np.float64)
+    assert rel(depiston(X.mean(-1)), depiston(X_ref.mean(-1))) <= 1e-3
+    f.close()
+
+
+def test_graph_and_plain_launches_agree_bitwise():
+    w = W.TEL_16M
+    inp, geom = inputs(w, 8)
+    y = torch.from_numpy(inp.slopes[:8].astype(np.float32)).cuda()
+    out = []
+    for use_graph in (True, False):
+        f = Letkf.from_workload(w, bank=inp.bank)
+        f.set_state(torch.from_numpy(inp.X0.astype(np.float32)).cuda())
+        f.run(8, y, use_graph=use_graph)
+        f.sync()
+        out.append(f.get_state().cpu().numpy())
+        f.close()
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("nsub,m,window,square", [(1, 2, 1, True), (3, 16, 9, True),
+                                                  (6, 17, 3, True), (10, 32, 5, False),
+                                                  (5, 5, 2, True)])
+def test_edge_shapes(nsub, m, window, square):
+    """Degenerate and boundary shapes: a single subaperture, the smallest ensemble,
+    a window wider than the pupil (global ETKF), m at the 16/32 padding edges,
+    an even window."""
+    mask = synth.pupil_subap_mask(nsub, 0.0 if square else 0.2, square)
+    geom = oracle.build_geometry(mask, window, 1, 0.0)
+    rng = np.random.default_rng(nsub * 100 + m)
+    Xb = (3 * rng.standard_normal((geom.n_pts, 2, 1)) +
+          0.5 * rng.standard_normal((geom.n_pts, 2, m))).astype(np.float32)
+    y = rng.standard_normal(geom.p).astype(np.float32)
+    ref = oracle.analysis(geom, Xb.astype(np.float64), y.astype(np.float64), 0.01, 1.03)
+    f = Letkf(mask, m=m, window=window, taper=1, rho=1.03, sigma2=0.01)
+    f.set_state(torch.from_numpy(Xb).cuda())
+    mean, spread = f.analyze(torch.from_numpy(y).cuda())
+    f.sync()
+    Xa = f.get_state().cpu().numpy().astype(np.float64)
+    check_analysis(TOL[0], Xa, mean.cpu().numpy(), spread.cpu().numpy(), ref)
+    f.close()
+
+
+def test_zero_spread_background_is_left_unchanged():
+    mask = synth.pupil_subap_mask(8, square=True)
+    geom = oracle.build_geometry(mask, 3)
+    Xb = np.repeat(np.random.default_rng(3).standard_normal((geom.n_pts, 2, 1)), 10, 2)
+    f = Letkf(mask, m=10, window=3, taper=0, rho=1.05, sigma2=0.01)
+    f.set_state(torch.from_numpy(Xb.astype(np.float32)).cuda())
+    y = torch.randn(geom.p, device="cuda")
+    mean, spread = f.analyze(y)
+    f.sync()
+    assert np.allclose(f.get_state().cpu().numpy(), Xb, atol=1e-5)
+    assert spread.abs().max().item() < 1e-5
+    f.close()
+
+
+def test_nonfinite_slopes_are_reported_and_handle_survives():
+    w = W.TOY_8X8
+    inp, geom = inputs(w, 8)
+    f = Letkf.from_workload(w, bank=inp.bank, precision=0)
+    f.set_state(torch.from_numpy(inp.X0.astype(np.float32)).cuda())
+    y = torch.from_numpy(inp.slopes[0].astype(np.float32)).cuda()
+    y[3] = float("nan")
+    f.analyze(y)
+    with pytest.raises(LetkfError) as e:
+        f.sync()
+    assert e.value.status == 5
+    f.set_state(torch.from_numpy(inp.X0.astype(np.float32)).cuda())
+    f.analyze(torch.from_numpy(inp.slopes[0].astype(np.float32)).cuda())
+    f.sync()
+    f.close()
