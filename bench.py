@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""LETKF closed-loop benchmark on GB300: frames/s and p50/p99 us/frame at
+80x80 subapertures with an ensemble of 32 members (7x7 Gaspari-Cohn window).
+
+One step = one frame of the loop: residual criterion of the prediction,
+observation + local analysis of every node, AR(1) forecast with bank noise.
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
+on the same workload instead. Multi-GPU runs (torchrun) run one independent AO
+instance per GPU (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LETKF frames/s and p50/p99 µs/frame at 80×80 subaps k=32; grad time vs FD"
+UNIT = "frames/s"
+L2_FLUSH_BYTES = 256 << 20
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "analysis_tile_kernel_elt80.md")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="CPU work budget of the oracle baseline")
+    ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args(argv)
+
+
+# --------------------------------------------------------------------------- helpers
+def workload(rank: int = 0):
+    from dataclasses import replace
+    from paper_1408_7069_gb300 import workloads as W
+    w = W.ELT_80X80
+    if rank:
+        w = replace(w, seeds=tuple(s + 1000 * rank for s in w.seeds))
+    return w
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return float("nan")
+    k = (len(xs) - 1) * q / 100.0
+    lo, hi = math.floor(k), math.ceil(k)
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+def combine(total_s_local: float, steps: int, world: int, reduce_max) -> dict:
+    """Whole-job throughput: every rank processes `steps` frames of its own
+    instance; the job time is the slowest rank's."""
+    t = reduce_max(total_s_local)
+    return {"value": world * steps / t, "ms_per_step": 1e3 * t / steps, "max_total_s": t}
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the analysis kernel from the committed ncu
+    summary (line 'dram_bytes_per_launch: N'), or None."""
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            for line in f:
+                if line.startswith("dram_bytes_per_launch:"):
+                    return float(line.split(":", 1)[1].split()[0])
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def cpu_worker(seconds: float):
+    """Runs in a single-threaded subprocess: the FP64 oracle on full frames of
+    the workload until the time budget is spent (at least one frame)."""
+    import numpy as np
+    import oracle
+    from paper_1408_7069_gb300 import synth
+    w = workload()
+    inp = synth.make_loop_inputs(w, frames=64)
+    geom = oracle.build_geometry(inp.subap_mask, w.window, w.taper, w.loc_len)
+    X = inp.X0.copy()
+    frames, t0 = 0, time.perf_counter()
+    while frames < 64:
+        oracle.residual_variance(inp.truth[frames], X)
+        Xa, _, _ = oracle.analysis_batched(geom, X, inp.slopes[frames], w.sigma2, w.rho)
+        v = oracle.bank_noise(inp.bank, geom.points, w.m, w.seeds[2], frames, w.noise_std)
+        X = oracle.forecast(Xa, v, w.a_ar1)
+        frames += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    print(json.dumps({"frames": frames, "seconds": dt, "n_pts": geom.n_pts}))
+
+
+def cpu_baseline(seconds: float):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker",
+                        "--cpu-seconds", str(seconds)], capture_output=True, text=True, env=env,
+                       timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr else "failed"}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["frames"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{d['frames']} full frames of the same 80x80 loop ({d['n_pts']} nodes; "
+                      "batched numpy.linalg.eigh, FP64), BLAS/OpenMP limited to 1 thread"}
+
+
+def reference_arm(args):
+    """The FP64 oracle timed as the reference: each step is a bounded sample of
+    one frame (observation and forecast of the whole grid, analysis of a fixed
+    256-node sample), scaled to a whole frame."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import numpy as np
+    import oracle
+    from paper_1408_7069_gb300 import synth
+    w = workload()
+    frames_needed = args.warmup + args.steps + 1
+    inp = synth.make_loop_inputs(w, frames=frames_needed)
+    geom = oracle.build_geometry(inp.subap_mask, w.window, w.taper, w.loc_len)
+    sample = np.linspace(0, geom.n_pts - 1, 256).astype(int)
+    scale = geom.n_pts / len(sample)
+    X = inp.X0.copy()
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.residual_variance(inp.truth[k], X)
+        obs = oracle.observe(geom, X)
+        t1 = time.perf_counter()
+        Xa, _, _ = oracle.analysis_batched(geom, X, inp.slopes[k], w.sigma2, w.rho, nodes=sample,
+                                           obs=obs)
+        t2 = time.perf_counter()
+        v = oracle.bank_noise(inp.bank, geom.points, w.m, w.seeds[2], k, w.noise_std)
+        X = oracle.forecast(Xa, v, w.a_ar1)
+        t3 = time.perf_counter()
+        if k >= args.warmup:
+            times.append((t1 - t0) + (t3 - t2) + (t2 - t1) * scale)
+    total = sum(times)
+    value = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "nsub": w.nsub, "m": w.m, "window": w.window,
+                       "n_pts": geom.n_pts},
+            "p50_us": 1e6 * percentile(times, 50), "p99_us": 1e6 * percentile(times, 99),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: residual, observation and forecast of the "
+                                       "whole 80x80 grid, analysis of 256 of the "
+                                       f"{geom.n_pts} nodes scaled to all nodes"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1408_7069_gb300 import opcount, synth
+    from paper_1408_7069_gb300 import letkf as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = workload(rank)
+    K, Wm = args.steps, args.warmup
+    frames = Wm + K + 1
+    inp = synth.make_loop_inputs(w, frames=frames)
+    f = L.Letkf.from_workload(w, bank=inp.bank)
+    h, s = f.h, f.stream
+    X0 = torch.from_numpy(inp.X0.astype(np.float32)).cuda()
+    y = torch.from_numpy(inp.slopes.astype(np.float32)).cuda()
+    truth = torch.from_numpy(inp.truth.astype(np.float32)).cuda()
+    resvar = torch.zeros(frames, dtype=torch.float64, device="cuda")
+    mean = torch.zeros(f.n_pts, 2, device="cuda")
+    spread = torch.zeros(f.n_pts, 2, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    f.set_state(X0)
+    torch.cuda.synchronize()
+
+    def frame(k):
+        L.letkf_residual(h, truth[k], resvar[k:k + 1])
+        L.letkf_analyze(h, y[k], mean, spread)
+        L.letkf_forecast(h)
+
+    with torch.cuda.stream(s):
+        for k in range(Wm):
+            frame(k)
+    L.letkf_sync(h)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        with torch.cuda.stream(s):
+            for i in range(K):
+                k = Wm + i
+                flush.fill_(float(i))                    # evict L2 between timed frames
+                e = ev[i]
+                e[0].record(s)
+                L.letkf_residual(h, truth[k], resvar[k:k + 1])
+                e[1].record(s)
+                L.letkf_analyze(h, y[k], mean, spread)
+                e[2].record(s)
+                L.letkf_forecast(h)
+                e[3].record(s)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    L.letkf_sync(h)
+    nfp64, sweeps, total_sweeps = L.letkf_stats(h)
+    frame_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    ana_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    total_s = sum(frame_ms) / 1e3
+
+    def reduce_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    agg = combine(total_s, K, world, reduce_max)
+
+    # graph-captured loop over the same frames (state resident in L2, no flush)
+    f.set_state(X0)
+    torch.cuda.synchronize()
+    L.letkf_run(h, Wm, y, truth, resvar, True)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(s)
+    L.letkf_run(h, K, y, truth, resvar, True)
+    g1.record(s)
+    torch.cuda.synchronize()
+    L.letkf_sync(h)
+    graph_fps = K / (g0.elapsed_time(g1) / 1e3)
+
+    # end to end through the public API with host buffers (pinned), one frame at a time
+    f.set_state(X0)
+    y_h = torch.from_numpy(inp.slopes.astype(np.float32)).pin_memory()
+    t_h = torch.from_numpy(inp.truth.astype(np.float32)).pin_memory()
+    y_d = torch.zeros(f.p, device="cuda")
+    t_d = torch.zeros(f.n_pts, device="cuda")
+    out_h = torch.zeros(K, f.n_pts, 2).pin_memory()
+    rv_h = torch.zeros(K, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    with torch.cuda.stream(s):
+        for i in range(K):
+            k = Wm + i
+            y_d.copy_(y_h[k], non_blocking=True)
+            t_d.copy_(t_h[k], non_blocking=True)
+            L.letkf_residual(h, t_d, resvar[k:k + 1])
+            L.letkf_analyze(h, y_d, mean, spread)
+            L.letkf_forecast(h)
+            out_h[i].copy_(mean, non_blocking=True)
+            rv_h[i:i + 1].copy_(resvar[k:k + 1], non_blocking=True)
+            s.synchronize()
+    te = time.perf_counter() - te0
+    L.letkf_sync(h)
+    e2e_fps = K / te if world == 1 else combine(te, K, world, reduce_max)["value"]
+
+    ws = f.points()[1]
+    flops = opcount.frame_analysis_ops(w.m, ws)
+    ana_mean_s = statistics.mean(ana_ms) / 1e3
+    achieved = flops / ana_mean_s / 1e12
+    fallback = 1 if f.precision == 0 else 0
+    launches_per_frame = 2 + (2 + fallback) + 2   # residual 2, observe + tile (+ FP64 list), forecast + tick
+    line = {
+        "metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": Wm, "ms_per_step": agg["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "nsub": w.nsub, "m": w.m, "window": w.window,
+                   "taper": "gaspari-cohn", "n_pts": f.n_pts, "p": f.p,
+                   "fp64_fallback_kappa": 300.0, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed frames (256 MiB write, outside the frame events)",
+                   "step": "residual + observation + local analysis + forecast, per-frame launches"},
+        "p50_us": 1e3 * percentile(frame_ms, 50), "p99_us": 1e3 * percentile(frame_ms, 99),
+        "graph_frames_per_s": graph_fps,
+        "e2e": {"value": e2e_fps, "unit": UNIT, "h2d_bytes_per_step": 4 * (f.p + f.n_pts),
+                "d2h_bytes_per_step": 4 * 2 * f.n_pts + 8},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": profile_traffic(),
+                     "kernel": "letkf_analyze (observation + analysis tile + FP64 list kernels)",
+                     "flops_per_launch": flops,
+                     "launch_us": 1e6 * ana_mean_s},
+        "gpu_launches": launches_per_frame * K,
+        "jacobi_sweeps_max": sweeps, "jacobi_sweeps_mean": total_sweeps / max(1, f.n_pts - nfp64),
+        "fp64_nodes_last_frame": nfp64,
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0:
+        line["clocks"] = clk.summary()
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line))
+    f.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.cpu_worker:
+        cpu_worker(args.cpu_seconds)
+        return 0
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

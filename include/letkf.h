@@ -69,11 +69,11 @@ typedef struct {
   double a_ar1;                /* AR(1) coefficient of the forecast */
   double noise_std;            /* forecast noise = noise_std * bank screen value */
   int32_t precision;           /* 0 = FP32 storage and analysis with FP64 fallback, 1 = FP64 */
-  double fp64_kappa;           /* FP64 fallback threshold on kappa_hat; <= 0 disables it */
+  double fp64_kappa;           /* FP64 fallback threshold on kappa_hat (e.g. 300); <= 0 disables it */
   uint64_t seed;               /* SplitMix64 seed of the forecast-noise draws */
   const float *noise_bank;     /* host [bank_B][bank_G][bank_G] screens, or NULL; copied */
   int32_t bank_B, bank_G;      /* bank shape (ignored when noise_bank is NULL) */
-  int32_t max_sweeps;          /* Jacobi sweep limit; <= 0 -> 12 (FP32) / 20 (FP64) */
+  int32_t max_sweeps;          /* Jacobi sweep limit per node; <= 0 -> 20 */
 } letkf_config;
 
 /* Validate the configuration, build the node list, the per-node observation
@@ -136,9 +136,11 @@ letkf_status letkf_run(letkf_t h, int32_t frames, const void *y_seq_dev, const v
  * device since the last call (LETKF_OK if none). */
 letkf_status letkf_sync(letkf_t h);
 
-/* Counters of the last analysis, host pointers (any may be NULL): points that
- * took the FP64 fallback, maximum Jacobi sweeps used by a point. Synchronises. */
-letkf_status letkf_stats(letkf_t h, int32_t *fp64_points, int32_t *max_sweeps);
+/* Counters of the last analysis, host pointers (any may be NULL): nodes that
+ * took the FP64 fallback, the largest and the total number of Jacobi sweeps
+ * over the nodes. Synchronises. */
+letkf_status letkf_stats(letkf_t h, int32_t *fp64_points, int32_t *max_sweeps,
+                         int32_t *total_sweeps);
 
 /* Text of the last error on this handle (or of the last failed create when h is NULL). */
 const char *letkf_last_error(letkf_t h);

@@ -36,6 +36,7 @@ import math
 from dataclasses import dataclass
 
 import numpy as np
+import scipy.sparse
 
 # ---------------------------------------------------------------------------
 # Geometry
@@ -48,7 +49,7 @@ class Geometry:
     subap_mask: np.ndarray        # bool [nsub, nsub]
     points: np.ndarray            # int [n_pts, 2] node (i, j), row-major
     subaps: np.ndarray            # int [n_sap, 2] valid subap (s, t), row-major
-    D1: np.ndarray                # float64 [p, n_pts] Fried slope operator
+    D1: scipy.sparse.csr_matrix   # float64 [p, n_pts] Fried slope operator (4 nonzeros per row)
     win_idx: list                 # per point: int array of slope indices into y
     win_tau: list                 # per point: float64 taper of each slope
 
@@ -104,7 +105,7 @@ def build_geometry(subap_mask, window: int, taper: int = 0, loc_len: float = 0.0
     sid = -np.ones((nsub, nsub), int)
     sid[sm] = np.arange(len(subaps))
     n_sap = len(subaps)
-    D1 = np.zeros((2 * n_sap, len(points)))
+    D1 = scipy.sparse.lil_matrix((2 * n_sap, len(points)))
     for k, (s, t) in enumerate(subaps):
         D1[k, pid[s + 1, t]] += 0.5
         D1[k, pid[s + 1, t + 1]] += 0.5
@@ -114,6 +115,7 @@ def build_geometry(subap_mask, window: int, taper: int = 0, loc_len: float = 0.0
         D1[n_sap + k, pid[s + 1, t + 1]] += 0.5
         D1[n_sap + k, pid[s, t]] -= 0.5
         D1[n_sap + k, pid[s + 1, t]] -= 0.5
+    D1 = D1.tocsr()
     h = window // 2
     c = loc_len if loc_len > 0 else window / 4.0
     win_idx, win_tau = [], []
@@ -201,22 +203,25 @@ def analysis(geom: Geometry, Xb, y, sigma2: float, rho: float, return_local: boo
     return Xa, mean, spread
 
 
-def analysis_batched(geom: Geometry, Xb, y, sigma2: float, rho: float):
+def analysis_batched(geom: Geometry, Xb, y, sigma2: float, rho: float, nodes=None, obs=None):
     """The same analysis with every window padded to a common length with zero
     weight (exact: a zero weight adds nothing to A or C d) and one stacked
-    numpy.linalg.eigh over all nodes. Used to time the CPU baseline."""
+    numpy.linalg.eigh over the nodes. ``nodes`` (indices) restricts the work to
+    a subset; the other nodes keep their background members. ``obs`` passes a
+    precomputed observe(geom, Xb). Used to time the CPU baseline."""
     Xb = np.asarray(Xb, dtype=np.float64)
     m = Xb.shape[-1]
-    xbar, Xp, Yb, ybar = observe(geom, Xb)
+    xbar, Xp, Yb, ybar = observe(geom, Xb) if obs is None else obs
     d = np.asarray(y, dtype=np.float64) - ybar
-    L = max(len(i) for i in geom.win_idx)
-    n = geom.n_pts
+    sel = np.arange(geom.n_pts) if nodes is None else np.asarray(nodes)
+    L = max(len(geom.win_idx[g]) for g in sel)
+    n = len(sel)
     idx = np.zeros((n, L), int)
     wts = np.zeros((n, L))
-    for g in range(n):
+    for r, g in enumerate(sel):
         k = len(geom.win_idx[g])
-        idx[g, :k] = geom.win_idx[g]
-        wts[g, :k] = geom.win_tau[g] / sigma2
+        idx[r, :k] = geom.win_idx[g]
+        wts[r, :k] = geom.win_tau[g] / sigma2
     Yl = Yb[idx]                                  # [n, L, m]
     dl = d[idx]                                   # [n, L]
     C = np.swapaxes(Yl, 1, 2) * wts[:, None, :]   # [n, m, L]
@@ -226,7 +231,8 @@ def analysis_batched(geom: Geometry, Xb, y, sigma2: float, rho: float):
     wbar = np.einsum("nij,nj->ni", Q, np.einsum("nji,nj->ni", Q, Cd) / lam)
     W = np.einsum("nij,nj,nkj->nik", Q, np.sqrt((m - 1) / lam), Q)
     T = wbar[:, :, None] + W
-    Xa = xbar[..., None] + np.einsum("nrj,nji->nri", Xp, T)
+    Xa = Xb.copy()
+    Xa[sel] = xbar[sel][..., None] + np.einsum("nrj,nji->nri", Xp[sel], T)
     return Xa, Xa.mean(axis=-1), Xa.std(axis=-1, ddof=1)
 
 

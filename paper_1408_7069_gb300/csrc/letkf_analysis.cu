@@ -5,16 +5,26 @@
 // in shared memory once; every warp then reads its own w x w window from it.
 //
 // Per node, with lane l standing for member / column l of the m x m problem
-// (zero-padded to MP = 16 or 32 columns):
+// (zero-padded to MP = 16 or 32 columns, identity on the padding):
 //   Gram     A = (m-1)/rho I + sum_j tau_j/sigma2 Yb_j Yb_j^T,  C d = sum_j tau_j/sigma2 d_j Yb_j
-//   EVD      one-sided (Hestenes) Jacobi on the columns of A: A V = V Lambda, pairs
-//            chosen by the xor tournament (step t pairs column l with l ^ t, a
-//            perfect matching for every t in 1..MP-1, all pairs once per sweep)
+//   EVD      one-sided (Hestenes) Jacobi on the columns of B = A V0: rotations J make
+//            the columns of B J orthogonal, so A (V0 J) = (V0 J) Lambda. Pairs follow
+//            the xor tournament (step t pairs column l with l ^ t: a perfect matching
+//            for every t in 1..MP-1, all pairs once per sweep).
 //   weights  wbar = V Lambda^-1 V^T C d,  W = V ((m-1) Lambda^-1)^(1/2) V^T
 //   apply    Xa_r = xbar_r + X'_r wbar + X'_r W for the node's two rows
+//
+// FP32 nodes start from the eigenbasis the node had in the previous analysis
+// (V0, kept per node): the transform W maps member space along A's own
+// eigenvectors, so the next frame's matrix is nearly diagonal in that basis
+// and the sweep converges in a few sweeps. They iterate on B only and recover
+// V as the normalised columns of B (B = V Lambda at convergence).
 // kappa_hat = 1 + rho tr(G)/(m-1) bounds the condition number of A before the
 // eigensolve (its eigenvalues lie in [(m-1)/rho, (m-1)/rho + tr G]); in FP32 mode
-// nodes above the threshold are queued and redone in FP64 by a second kernel.
+// nodes above the threshold are queued and redone in FP64 by a second kernel,
+// which accumulates V explicitly.
+#include <type_traits>
+
 #include "letkf_common.cuh"
 
 namespace {
@@ -24,9 +34,11 @@ constexpr unsigned FULL = 0xffffffffu;
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// Per-warp scratch: V staging [MP][MP+1] + 3 vectors, or A staging [MP][MP+4].
 template <int MP, typename T>
 __host__ __device__ constexpr size_t scratch_elems() {
-  return (size_t)MP * (MP + 1) + 3 * MP;
+  return (size_t)MP * (MP + 1) + 3 * MP > (size_t)MP * (MP + 4) ? (size_t)MP * (MP + 1) + 3 * MP
+                                                                 : (size_t)MP * (MP + 4);
 }
 
 // Shared-memory layout of the tile kernel (offsets in bytes).
@@ -70,25 +82,34 @@ __device__ __forceinline__ void ld4(const double *p, double &a, double &b, doubl
 __device__ __forceinline__ float lk_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double lk_rsqrt(double x) { return rsqrt(x); }
 
-// Analysis of one node by one warp. win / dwin point at the node's window in
-// shared memory (cell (ds, dt) at row stride `stride` cells); xrow points at the
-// node's two ensemble rows in global memory (read, then overwritten by Xa).
-template <int MP, typename S, typename T>
-__device__ __forceinline__ void analyze_node(const S *__restrict__ win, const S *__restrict__ dwin,
-                                             int stride, const T *__restrict__ tap, int w, int m,
-                                             T alpha, T tol, int max_sweeps, S *__restrict__ xrow,
-                                             S *__restrict__ mean_out, S *__restrict__ spread_out,
-                                             T *__restrict__ scr, int *__restrict__ counters,
-                                             T kappa_thr, int *__restrict__ worklist, int pid) {
-  const int lane = threadIdx.x & 31;
-  const bool col = lane < MP;   // lane carries a column of the padded problem
-  const bool mem = lane < m;    // lane carries a real member / eigenpair
+// Dot product of two register columns with four independent FMA chains (the
+// grouping is the same on both lanes of a pair, so both get the same bits).
+template <int MP, typename T>
+__device__ __forceinline__ T dot4(const T (&a)[MP], const T (&b)[MP]) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+#pragma unroll
+  for (int k = 0; k < MP; k += 4) {
+    s0 = fma(a[k], b[k], s0);
+    s1 = fma(a[k + 1], b[k + 1], s1);
+    s2 = fma(a[k + 2], b[k + 2], s2);
+    s3 = fma(a[k + 3], b[k + 3], s3);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
 
-  // ---- Gram: row `lane` of A, (C d)_lane and G_lane,lane -------------------
-  T b[MP];
+// Row `lane` of A = (m-1)/rho I + sum_j c_j y_j y_j^T (identity on the padding),
+// plus (C d)_lane and G_lane,lane. win / dwin: the node's window in shared memory,
+// cell (ds, dt) at row stride `stride` cells.
+template <int MP, typename S, typename T>
+__device__ __forceinline__ void gram(const S *__restrict__ win, const S *__restrict__ dwin,
+                                     int stride, const T *__restrict__ tap, int w, int m, T alpha,
+                                     T (&b)[MP], T &diag, T &cd) {
+  const int lane = threadIdx.x & 31;
+  const bool col = lane < MP;
 #pragma unroll
   for (int k = 0; k < MP; ++k) b[k] = T(0);
-  T diag = T(0), cd = T(0);
+  diag = T(0);
+  cd = T(0);
   for (int ds = 0; ds < w; ++ds) {
     for (int dt = 0; dt < w; ++dt) {
       const int cell = ds * stride + dt;
@@ -113,72 +134,81 @@ __device__ __forceinline__ void analyze_node(const S *__restrict__ win, const S 
       }
     }
   }
-  const T dval = mem ? alpha : T(1);  // identity on the zero padding
+  const T dval = lane < m ? alpha : T(1);
 #pragma unroll
   for (int k = 0; k < MP; ++k)
     if (k == lane) b[k] += dval;
+}
 
-  if (kappa_thr > T(0)) {
-    const T trg = lk_warp_sum(diag);
-    if (T(1) + trg / alpha > kappa_thr) {
-      if (lane == 0) worklist[atomicAdd(&counters[1], 1)] = pid;
-      return;
-    }
-  }
-
-  // ---- one-sided Jacobi: B = A V with orthogonal columns -------------------
-  T v[MP];
+// One Hestenes rotation step for pair (lane, lane ^ t) on column b (and v when
+// ACCUM). nrm = |b|^2 of this lane's column. Returns whether it rotated.
+template <int MP, typename T, bool ACCUM>
+__device__ __forceinline__ int jacobi_step(T (&b)[MP], T (&v)[MP], T &nrm, int t, T tol) {
+  const int lane = threadIdx.x & 31;
+  T pb[MP];
 #pragma unroll
-  for (int k = 0; k < MP; ++k) v[k] = (k == lane) ? T(1) : T(0);
+  for (int k = 0; k < MP; ++k) pb[k] = __shfl_xor_sync(FULL, b[k], t);
+  const T dot = dot4<MP, T>(b, pb);
+  const T pn = __shfl_xor_sync(FULL, nrm, t);
+  const bool isp = lane < (lane ^ t);  // this lane holds column p of the pair (p < q)
+  const T app = isp ? nrm : pn;
+  const T aqq = isp ? pn : nrm;
+  T cs = T(1), sn = T(0), tr = T(0);
+  int rot = 0;
+  if (fabs(dot) > tol * sqrt(app * aqq)) {
+    const T zeta = (aqq - app) / (T(2) * dot);
+    const T az = fabs(zeta);
+    tr = az > T(1e15) ? T(0.5) / zeta : copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
+    cs = lk_rsqrt(T(1) + tr * tr);
+    sn = cs * tr;
+    rot = 1;
+  }
+  const T sg = isp ? -sn : sn;  // p' = c p - s q ; q' = s p + c q
+#pragma unroll
+  for (int k = 0; k < MP; ++k) b[k] = fma(sg, pb[k], cs * b[k]);
+  nrm = isp ? (app - tr * dot) : (aqq + tr * dot);
+  if (ACCUM) {
+#pragma unroll
+    for (int k = 0; k < MP; ++k) pb[k] = __shfl_xor_sync(FULL, v[k], t);
+#pragma unroll
+    for (int k = 0; k < MP; ++k) v[k] = fma(sg, pb[k], cs * v[k]);
+  }
+  return rot;
+}
+
+// Sweeps until a full sweep makes no rotation. Records the sweep count and a
+// non-convergence flag.
+template <int MP, typename T, bool ACCUM>
+__device__ __forceinline__ void jacobi(T (&b)[MP], T (&v)[MP], T tol, int max_sweeps,
+                                       int *__restrict__ counters) {
   int sweep = 0;
   bool converged = false;
   for (; sweep < max_sweeps; ++sweep) {
-    T nrm = T(0);
-#pragma unroll
-    for (int k = 0; k < MP; ++k) nrm = fma(b[k], b[k], nrm);
+    T nrm = dot4<MP, T>(b, b);
     int rotated = 0;
-    for (int t = 1; t < MP; ++t) {
-      T pb[MP];
-#pragma unroll
-      for (int k = 0; k < MP; ++k) pb[k] = __shfl_xor_sync(FULL, b[k], t);
-      T dot = T(0);
-#pragma unroll
-      for (int k = 0; k < MP; ++k) dot = fma(b[k], pb[k], dot);
-      const T pn = __shfl_xor_sync(FULL, nrm, t);
-      const bool isp = lane < (lane ^ t);     // this lane holds column p of the pair (p < q)
-      const T app = isp ? nrm : pn;
-      const T aqq = isp ? pn : nrm;
-      T cs = T(1), sn = T(0), tr = T(0);
-      if (fabs(dot) > tol * sqrt(app * aqq)) {
-        const T zeta = (aqq - app) / (T(2) * dot);
-        const T az = fabs(zeta);
-        tr = az > T(1e15) ? T(0.5) / zeta
-                          : copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
-        cs = lk_rsqrt(T(1) + tr * tr);
-        sn = cs * tr;
-        rotated = 1;
-      }
-      // p' = c p - s q ; q' = s p + c q
-      const T sg = isp ? -sn : sn;
-#pragma unroll
-      for (int k = 0; k < MP; ++k) b[k] = fma(sg, pb[k], cs * b[k]);
-      nrm = isp ? (app - tr * dot) : (aqq + tr * dot);
-#pragma unroll
-      for (int k = 0; k < MP; ++k) pb[k] = __shfl_xor_sync(FULL, v[k], t);
-#pragma unroll
-      for (int k = 0; k < MP; ++k) v[k] = fma(sg, pb[k], cs * v[k]);
-    }
+    for (int t = 1; t < MP; ++t) rotated |= jacobi_step<MP, T, ACCUM>(b, v, nrm, t, tol);
     if (!__any_sync(FULL, rotated)) {
       converged = true;
       break;
     }
   }
-  if (lane == 0) {
+  if ((threadIdx.x & 31) == 0) {
     atomicMax(&counters[2], converged ? sweep + 1 : sweep);
+    atomicAdd(&counters[3], converged ? sweep + 1 : sweep);
     if (!converged) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
   }
+}
 
-  // ---- transform and apply --------------------------------------------------
+// wbar, W from the eigenpairs (lane j: eigenvector column v, eigenvalue lam) and
+// the update of the node's two rows; writes Xa, the mean and the spread.
+template <int MP, typename S, typename T>
+__device__ __forceinline__ void transform_apply(const T (&v)[MP], T lam, T cd, int m,
+                                                S *__restrict__ xrow, S *__restrict__ mean_out,
+                                                S *__restrict__ spread_out, T *__restrict__ scr,
+                                                int *__restrict__ counters) {
+  const int lane = threadIdx.x & 31;
+  const bool col = lane < MP;
+  const bool mem = lane < m;
   T *vt = scr;                      // vt[i*(MP+1)+j] = V[i][j]
   T *vec = scr + MP * (MP + 1);     // [3][MP]
   const T x0 = mem ? T(xrow[lane]) : T(0);
@@ -188,6 +218,7 @@ __device__ __forceinline__ void analyze_node(const S *__restrict__ win, const S 
   const T xb1 = lk_warp_sum(x1) * inv_m;
   const T xp0 = mem ? x0 - xb0 : T(0);
   const T xp1 = mem ? x1 - xb1 : T(0);
+  __syncwarp();
   if (col) {
     vec[lane] = cd;
     vec[MP + lane] = xp0;
@@ -196,15 +227,13 @@ __device__ __forceinline__ void analyze_node(const S *__restrict__ win, const S 
     for (int k = 0; k < MP; ++k) vt[k * (MP + 1) + lane] = v[k];
   }
   __syncwarp();
-  T u = T(0), g0 = T(0), g1 = T(0), nrm = T(0);
+  T u = T(0), g0 = T(0), g1 = T(0);
 #pragma unroll
   for (int k = 0; k < MP; ++k) {
     u = fma(v[k], vec[k], u);               // (V^T C d)_lane
     g0 = fma(v[k], vec[MP + k], g0);        // (X'_0 V)_lane
     g1 = fma(v[k], vec[2 * MP + k], g1);    // (X'_1 V)_lane
-    nrm = fma(b[k], b[k], nrm);
   }
-  const T lam = (col && nrm > T(0)) ? sqrt(nrm) : T(1);   // |A v_j| = lambda_j
   const T z = u / lam;
   const T P0 = lk_warp_sum(g0 * z);           // X'_0 wbar
   const T P1 = lk_warp_sum(g1 * z);
@@ -250,13 +279,110 @@ __device__ __forceinline__ void analyze_node(const S *__restrict__ win, const S 
   }
 }
 
+// Stores the node's eigenbasis (column `lane` = v) for the next analysis; a
+// non-finite basis is replaced by the identity.
+template <int MP, typename T>
+__device__ __forceinline__ void store_basis(const T (&v)[MP], float *__restrict__ U) {
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < MP; ++k) ok = ok && isfinite(v[k]);
+  ok = __all_sync(FULL, ok);
+  if (lane < MP) {
+#pragma unroll
+    for (int k = 0; k < MP; ++k) U[k * MP + lane] = ok ? float(v[k]) : (k == lane ? 1.f : 0.f);
+  }
+}
+
+// FP64 (or accumulate-V) analysis of one node, starting from the identity.
+template <int MP, typename S, typename T>
+__device__ __forceinline__ void analyze_node_accum(const S *__restrict__ win,
+                                                   const S *__restrict__ dwin, int stride,
+                                                   const T *__restrict__ tap, int w, int m,
+                                                   T alpha, T tol, int max_sweeps,
+                                                   S *__restrict__ xrow, S *__restrict__ mean_out,
+                                                   S *__restrict__ spread_out,
+                                                   T *__restrict__ scr, int *__restrict__ counters,
+                                                   float *__restrict__ U) {
+  const int lane = threadIdx.x & 31;
+  T b[MP], diag, cd;
+  gram<MP, S, T>(win, dwin, stride, tap, w, m, alpha, b, diag, cd);
+  T v[MP];
+#pragma unroll
+  for (int k = 0; k < MP; ++k) v[k] = (k == lane) ? T(1) : T(0);
+  jacobi<MP, T, true>(b, v, tol, max_sweeps, counters);
+  const T nrm = dot4<MP, T>(b, b);
+  const T lam = (lane < MP && nrm > T(0)) ? sqrt(nrm) : T(1);   // |A v_j| = lambda_j
+  transform_apply<MP, S, T>(v, lam, cd, m, xrow, mean_out, spread_out, scr, counters);
+  if (U) store_basis<MP, T>(v, U);
+}
+
+// FP32 analysis of one node from its stored eigenbasis U (see the file comment).
+// Nodes whose kappa_hat exceeds kappa_thr (> 0) are queued for FP64 instead.
+template <int MP>
+__device__ __forceinline__ void analyze_node_f32(const float *__restrict__ win,
+                                                 const float *__restrict__ dwin, int stride,
+                                                 const float *__restrict__ tap, int w, int m,
+                                                 float alpha, float tol, int max_sweeps,
+                                                 float *__restrict__ xrow,
+                                                 float *__restrict__ mean_out,
+                                                 float *__restrict__ spread_out,
+                                                 float *__restrict__ scr,
+                                                 int *__restrict__ counters, float kappa_thr,
+                                                 int *__restrict__ worklist, int pid,
+                                                 float *__restrict__ U) {
+  const int lane = threadIdx.x & 31;
+  const bool col = lane < MP;
+  float b[MP], diag, cd;
+  gram<MP, float, float>(win, dwin, stride, tap, w, m, alpha, b, diag, cd);
+  if (kappa_thr > 0.f) {
+    const float trg = lk_warp_sum(diag);
+    if (1.f + trg / alpha > kappa_thr) {
+      if (lane == 0) worklist[atomicAdd(&counters[1], 1)] = pid;
+      return;
+    }
+  }
+  // B = A U0: stage the rows of A, each lane multiplies A by its basis column.
+  constexpr int LDA = MP + 4;
+  if (col) {
+#pragma unroll
+    for (int k = 0; k < MP; k += 4)
+      *reinterpret_cast<float4 *>(scr + lane * LDA + k) = make_float4(b[k], b[k + 1], b[k + 2], b[k + 3]);
+  }
+  float u[MP];
+#pragma unroll
+  for (int k = 0; k < MP; ++k) u[k] = col ? U[k * MP + lane] : 0.f;
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < MP; ++i) {
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < MP; k += 4) {
+      const float4 a4 = *reinterpret_cast<const float4 *>(scr + i * LDA + k);
+      s0 = fmaf(a4.x, u[k], s0);
+      s1 = fmaf(a4.y, u[k + 1], s1);
+      s0 = fmaf(a4.z, u[k + 2], s0);
+      s1 = fmaf(a4.w, u[k + 3], s1);
+    }
+    b[i] = s0 + s1;
+  }
+  jacobi<MP, float, false>(b, u, tol, max_sweeps, counters);
+  const float nrm = dot4<MP, float>(b, b);
+  const float lam = (col && nrm > 0.f) ? sqrtf(nrm) : 1.f;
+  const float inv = 1.f / lam;
+#pragma unroll
+  for (int k = 0; k < MP; ++k) b[k] *= inv;            // eigenvector column
+  transform_apply<MP, float, float>(b, lam, cd, m, xrow, mean_out, spread_out, scr, counters);
+  store_basis<MP, float>(b, U);
+}
+
 template <int MP, typename S, typename T, bool FALLBACK>
 __global__ void __launch_bounds__(LK_TILE_I *LK_TILE_J * 32)
     analysis_tile_kernel(LkGeom g, const int2 *__restrict__ tiles, const S *__restrict__ Ybp,
                          const S *__restrict__ dp, const S *__restrict__ taper, S *__restrict__ X,
                          S *__restrict__ mean, S *__restrict__ spread, T alpha, T tol,
                          int max_sweeps, T kappa_thr, int *__restrict__ counters,
-                         int *__restrict__ worklist) {
+                         int *__restrict__ worklist, float *__restrict__ basis) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int w = g.w;
   const TileLayout L = tile_layout<MP, S, T>(w);
@@ -292,11 +418,19 @@ __global__ void __launch_bounds__(LK_TILE_I *LK_TILE_J * 32)
   const int pid = g.pid_map[i * (g.nsub + 1) + j];
   if (pid < 0) return;
   const int off = ti * HJ + tj;
-  analyze_node<MP, S, T>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m, alpha, tol,
+  T *wscr = scr + (size_t)warp * scratch_elems<MP, T>();
+  if constexpr (std::is_same<T, float>::value) {
+    analyze_node_f32<MP>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m, alpha, tol,
                          max_sweeps, X + (size_t)pid * 2 * m, mean ? mean + 2 * pid : nullptr,
-                         spread ? spread + 2 * pid : nullptr,
-                         scr + (size_t)warp * scratch_elems<MP, T>(), counters,
-                         FALLBACK ? kappa_thr : T(0), worklist, pid);
+                         spread ? spread + 2 * pid : nullptr, wscr, counters,
+                         FALLBACK ? kappa_thr : 0.f, worklist, pid,
+                         basis + (size_t)pid * MP * MP);
+  } else {
+    analyze_node_accum<MP, S, T>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m, alpha,
+                                 tol, max_sweeps, X + (size_t)pid * 2 * m,
+                                 mean ? mean + 2 * pid : nullptr,
+                                 spread ? spread + 2 * pid : nullptr, wscr, counters, nullptr);
+  }
 }
 
 // FP64 re-analysis of the queued nodes of an FP32 handle: one warp per node,
@@ -306,7 +440,8 @@ __global__ void __launch_bounds__(LIST_WARPS * 32)
     analysis_list_kernel(LkGeom g, const int *__restrict__ worklist, const float *__restrict__ Ybp,
                          const float *__restrict__ dp, const float *__restrict__ taper,
                          float *__restrict__ X, float *__restrict__ mean, float *__restrict__ spread,
-                         double alpha, double tol, int max_sweeps, int *__restrict__ counters) {
+                         double alpha, double tol, int max_sweeps, int *__restrict__ counters,
+                         float *__restrict__ basis) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int w = g.w, wc = w * w, m = g.m;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -337,32 +472,30 @@ __global__ void __launch_bounds__(LIST_WARPS * 32)
   }
   for (int e = lane; e < wc; e += 32) tap[e] = (double)taper[e];
   __syncwarp();
-  analyze_node<MP, float, double>(win, dwin, w, tap, w, m, alpha, tol, max_sweeps,
-                                  X + (size_t)pid * 2 * m, mean ? mean + 2 * pid : nullptr,
-                                  spread ? spread + 2 * pid : nullptr, scr, counters, 0.0,
-                                  nullptr, pid);
+  analyze_node_accum<MP, float, double>(win, dwin, w, tap, w, m, alpha, tol, max_sweeps,
+                                        X + (size_t)pid * 2 * m, mean ? mean + 2 * pid : nullptr,
+                                        spread ? spread + 2 * pid : nullptr, scr, counters,
+                                        basis + (size_t)pid * MP * MP);
 }
 
 template <int MP, typename S, typename T, bool FB>
 cudaError_t launch_tile(letkf_ctx *h, void *mean, void *spread, T tol) {
   const TileLayout L = tile_layout<MP, S, T>(h->g.w);
-  auto kern = analysis_tile_kernel<MP, S, T, FB>;
-  kern<<<h->n_tiles, LK_TILE_I * LK_TILE_J * 32, L.total, h->stream>>>(
+  analysis_tile_kernel<MP, S, T, FB><<<h->n_tiles, LK_TILE_I * LK_TILE_J * 32, L.total, h->stream>>>(
       h->g, h->tiles, (const S *)h->Ybp, (const S *)h->dp, (const S *)h->taper, (S *)h->X,
       (S *)mean, (S *)spread, (T)h->alpha, tol, h->max_sweeps, (T)h->cfg.fp64_kappa, h->counters,
-      h->worklist);
+      h->worklist, h->basis);
   return cudaGetLastError();
 }
 
 template <int MP>
 cudaError_t launch_list(letkf_ctx *h, void *mean, void *spread) {
   const size_t bytes = (size_t)LIST_WARPS * list_warp_bytes<MP>(h->g.w);
-  auto kern = analysis_list_kernel<MP>;
   const int blocks = (h->g.n_pts + LIST_WARPS - 1) / LIST_WARPS;
-  kern<<<blocks, LIST_WARPS * 32, bytes, h->stream>>>(
+  analysis_list_kernel<MP><<<blocks, LIST_WARPS * 32, bytes, h->stream>>>(
       h->g, h->worklist, (const float *)h->Ybp, (const float *)h->dp, (const float *)h->taper,
       (float *)h->X, (float *)mean, (float *)spread, h->alpha, h->tol64, h->max_sweeps,
-      h->counters);
+      h->counters, h->basis);
   return cudaGetLastError();
 }
 
@@ -404,18 +537,8 @@ cudaError_t lk_setup_analysis(letkf_ctx *h) {
   return h->mp == 16 ? setup_all<16>(h) : setup_all<32>(h);
 }
 
-size_t lk_tile_smem_bytes(int mp, int precision, int w) {
-  if (mp == 16)
-    return precision ? tile_layout<16, double, double>(w).total : tile_layout<16, float, float>(w).total;
-  return precision ? tile_layout<32, double, double>(w).total : tile_layout<32, float, float>(w).total;
-}
-
-size_t lk_list_smem_bytes(int mp, int w) {
-  return (size_t)LIST_WARPS * (mp == 16 ? list_warp_bytes<16>(w) : list_warp_bytes<32>(w));
-}
-
 cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread) {
-  cudaError_t e = cudaMemsetAsync(h->counters + 1, 0, 2 * sizeof(int), h->stream);
+  cudaError_t e = cudaMemsetAsync(h->counters + 1, 0, 3 * sizeof(int), h->stream);
   if (e != cudaSuccess) return e;
   return h->mp == 16 ? launch_all<16>(h, mean, spread) : launch_all<32>(h, mean, spread);
 }

@@ -61,8 +61,9 @@ letkf_status upload(letkf_ctx *h, T **dst, const void *src, size_t bytes) {
 
 void release(letkf_ctx *h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
-  void *bufs[] = {h->X, h->Ybp, h->dp, h->taper, h->pid_map, h->pts, h->saps, h->tiles,
-                  h->bank, h->counters, h->worklist, h->frame, h->zero_scalar};
+  void *bufs[] = {h->X,        h->Ybp,      h->dp,       h->taper,    h->pid_map,
+                  h->pts,      h->saps,     h->tiles,    h->bank,     h->counters,
+                  h->worklist, h->frame,    h->basis,    h->partial,  h->zero_scalar};
   for (void *p : bufs)
     if (p) cudaFree(p);
 }
@@ -229,6 +230,15 @@ letkf_status letkf_create(const letkf_config *cfg, void *stream, letkf_t *out) {
   LK_TRY(upload(h, &h->counters, nullptr, 4 * sizeof(int)));
   LK_TRY(upload(h, &h->worklist, nullptr, npt * sizeof(int)));
   LK_TRY(upload(h, &h->frame, nullptr, 2 * sizeof(long long)));
+  LK_TRY(upload(h, &h->partial, nullptr, LK_RES_BLOCKS * sizeof(double2)));
+  {
+    // every node's eigenbasis starts as the identity
+    const size_t mp = (size_t)h->mp;
+    std::vector<float> eye(npt * mp * mp, 0.f);
+    for (size_t g = 0; g < npt; ++g)
+      for (size_t k = 0; k < mp; ++k) eye[(g * mp + k) * mp + k] = 1.f;
+    LK_TRY(upload(h, &h->basis, eye.data(), eye.size() * sizeof(float)));
+  }
   if (c.noise_bank) {
     h->bank_B = c.bank_B;
     h->bank_G = c.bank_G;
@@ -385,7 +395,8 @@ letkf_status letkf_sync(letkf_t h) {
   return LETKF_OK;
 }
 
-letkf_status letkf_stats(letkf_t h, int32_t *fp64_points, int32_t *max_sweeps) {
+letkf_status letkf_stats(letkf_t h, int32_t *fp64_points, int32_t *max_sweeps,
+                         int32_t *total_sweeps) {
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
   DeviceGuard dg(h->device);
   LK_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -393,6 +404,7 @@ letkf_status letkf_stats(letkf_t h, int32_t *fp64_points, int32_t *max_sweeps) {
   LK_CUDA(h, cudaMemcpy(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost));
   if (fp64_points) *fp64_points = c[1];
   if (max_sweeps) *max_sweeps = c[2];
+  if (total_sweeps) *total_sweeps = c[3];
   return LETKF_OK;
 }
 

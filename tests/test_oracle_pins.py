@@ -102,7 +102,7 @@ def _global_etkf(geom, Xb, y, sigma2, rho):
     Z = np.sqrt(rho) * (Xb - xbar[..., None]) / np.sqrt(m - 1)
     Zf = Z.reshape(2 * n_pts, m)
     C1 = np.zeros((geom.p, 2 * n_pts))
-    C1[:, 1::2] = geom.D1
+    C1[:, 1::2] = geom.D1.toarray()
     s = 1 / np.sqrt(sigma2)
     Scz = s * (C1 @ Zf)
     Sinov = s * (y - C1 @ xbar.reshape(-1))
@@ -147,7 +147,7 @@ def test_T2_exact_kalman_filter():
     y = rng.standard_normal(geom.p)
     Xa, mean, spread = oracle.analysis(geom, Xb, y, sigma2, rho)
     H = np.zeros((geom.p, n))
-    H[:, 1::2] = geom.D1
+    H[:, 1::2] = geom.D1.toarray()
     Pf = rho * P
     K = Pf @ H.T @ np.linalg.inv(H @ Pf @ H.T + sigma2 * np.eye(geom.p))
     xa = mu + K @ (y - H @ mu)
@@ -174,7 +174,7 @@ def test_T3_bruteforce_primal_gain_4x4():
     Xp = Xf - xbar[:, None]
     Pb = w.rho * Xp @ Xp.T / (w.m - 1)
     H = np.zeros((geom.p, n))
-    H[:, 1::2] = geom.D1
+    H[:, 1::2] = geom.D1.toarray()
     for g in range(geom.n_pts):
         keep = geom.win_tau[g] > 0
         idx = geom.win_idx[g][keep]
