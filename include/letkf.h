@@ -142,6 +142,30 @@ letkf_status letkf_sync(letkf_t h);
 letkf_status letkf_stats(letkf_t h, int32_t *fp64_points, int32_t *max_sweeps,
                          int32_t *total_sweeps);
 
+/* Allocation-free analysis of one frame, for callers that cannot allocate
+ * device memory once running (a real-time controller whose memory is fixed at
+ * start-up, or code where cudaMalloc is not allowed). It needs no handle and
+ * calls no cudaMalloc, cudaFree or other allocating routine: its scratch (the
+ * slope-anomaly and innovation grids, node tables, counters) is one static
+ * device array of about 6 MB that every GPU loading this library keeps until
+ * the process exits. The paper has no counterpart; it computes the same
+ * analysis as letkf_analyze in FP32, with eigenvectors accumulated from the
+ * identity and without the FP64 fallback.
+ * cfg: as for letkf_create (host mask read during the call); precision must be
+ *   0 and nsub <= 128, m <= 32, window <= 15, otherwise LETKF_ERR_ARG with the
+ *   limits in errbuf. Noise-bank fields are ignored.
+ * X_dev: device float [n_pts][2][m], background in, analysis out.
+ * y_dev: device float [p]. mean_dev, spread_dev: device float [n_pts][2] or NULL.
+ * stream: cudaStream_t for all of the work (NULL = legacy default stream).
+ * errbuf: caller buffer of errlen bytes for a message on failure, or NULL.
+ * The first call on a device looks up the array's device address; make it
+ * before any stream capture. Every call shares the array and overwrites its
+ * contents (the grids are cleared at the start of each call); calls whose GPU
+ * work overlaps (other streams, other host threads) race. */
+letkf_status letkf_analyze_noalloc(const letkf_config *cfg, void *X_dev, const void *y_dev,
+                                   void *mean_dev, void *spread_dev, void *stream, char *errbuf,
+                                   size_t errlen);
+
 /* Text of the last error on this handle (or of the last failed create when h is NULL). */
 const char *letkf_last_error(letkf_t h);
 

@@ -23,6 +23,10 @@
 // eigensolve (its eigenvalues lie in [(m-1)/rho, (m-1)/rho + tr G]); in FP32 mode
 // nodes above the threshold are queued and redone in FP64 by a second kernel,
 // which accumulates V explicitly.
+#include <math.h>
+#include <stdio.h>
+
+#include <mutex>
 #include <type_traits>
 
 #include "letkf_common.cuh"
@@ -541,4 +545,275 @@ cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread) {
   cudaError_t e = cudaMemsetAsync(h->counters + 1, 0, 3 * sizeof(int), h->stream);
   if (e != cudaSuccess) return e;
   return h->mp == 16 ? launch_all<16>(h, mean, spread) : launch_all<32>(h, mean, spread);
+}
+
+// ===========================================================================
+// Allocation-free analysis (letkf_analyze_noalloc)
+//
+// For callers that cannot allocate device memory at run time (for example a
+// real-time controller whose memory is fixed at start-up, or code running
+// where cudaMalloc is not permitted), this entry point analyses one frame
+// without creating a handle: its scratch (slope-anomaly grid, innovations,
+// node tables, counters) is the file-scope array below, which every GPU that
+// loads the library holds until the process exits.
+// ===========================================================================
+namespace {
+
+constexpr int NA_MAX_NSUB = 128;
+constexpr int NA_MAX_W = 15;
+constexpr int NA_MAX_M = 32;
+constexpr int NA_NN = NA_MAX_NSUB + 1;
+constexpr int NA_GS_ROWS = ((NA_NN + LK_TILE_I - 1) / LK_TILE_I) * LK_TILE_I + NA_MAX_W;
+constexpr int NA_GS_COLS = ((NA_NN + LK_TILE_J - 1) / LK_TILE_J) * LK_TILE_J + NA_MAX_W;
+constexpr size_t NA_CELLS = (size_t)NA_GS_ROWS * NA_GS_COLS;
+constexpr int NA_MAX_TILES = ((NA_NN + LK_TILE_I - 1) / LK_TILE_I) * ((NA_NN + LK_TILE_J - 1) / LK_TILE_J);
+// byte offsets inside the scratch array (each 256-aligned)
+constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t NA_OFF_YBP = 0;
+constexpr size_t NA_OFF_DP = al256(NA_OFF_YBP + NA_CELLS * 2 * NA_MAX_M * sizeof(float));
+constexpr size_t NA_OFF_PID = al256(NA_OFF_DP + NA_CELLS * 2 * sizeof(float));
+constexpr size_t NA_OFF_SAPS = al256(NA_OFF_PID + (size_t)NA_NN * NA_NN * sizeof(int));
+constexpr size_t NA_OFF_PTS = al256(NA_OFF_SAPS + (size_t)NA_MAX_NSUB * NA_MAX_NSUB * sizeof(int2));
+constexpr size_t NA_OFF_TILES = al256(NA_OFF_PTS + (size_t)NA_NN * NA_NN * sizeof(int2));
+constexpr size_t NA_OFF_TAPER = al256(NA_OFF_TILES + (size_t)NA_MAX_TILES * sizeof(int2));
+constexpr size_t NA_OFF_COUNTERS = al256(NA_OFF_TAPER + (size_t)NA_MAX_W * NA_MAX_W * sizeof(float));
+constexpr size_t NA_BYTES = al256(NA_OFF_COUNTERS + 4 * sizeof(int));
+
+// The scratch. Host code must not pass this name to a kernel: it is a host-side
+// stand-in; the device address comes from cudaGetSymbolAddress (na_scratch_address).
+__device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+// Host-side tables, built under g_na_mutex and copied into the scratch.
+std::mutex g_na_mutex;
+int g_na_pid[NA_NN * NA_NN];
+int2 g_na_saps[NA_MAX_NSUB * NA_MAX_NSUB];
+int2 g_na_pts[NA_NN * NA_NN];
+int2 g_na_tiles[NA_MAX_TILES];
+float g_na_taper[NA_MAX_W * NA_MAX_W];
+void *g_na_addr[256];          // scratch address per device, set once
+
+void na_error(char *buf, size_t len, const char *msg) {
+  if (buf && len) snprintf(buf, len, "%s", msg);
+}
+
+// Gaspari & Cohn (1999) 5th-order piecewise rational function of z = r / c.
+double na_gaspari_cohn(double z) {
+  z = fabs(z);
+  if (z <= 1.0) return (((-0.25 * z + 0.5) * z + 0.625) * z - 5.0 / 3.0) * z * z + 1.0;
+  if (z < 2.0)
+    return ((((z / 12.0 - 0.5) * z + 0.625) * z + 5.0 / 3.0) * z - 5.0) * z + 4.0 - (2.0 / 3.0) / z;
+  return 0.0;
+}
+
+// Variant of the analysis tile kernel for the allocation-free path: FP32,
+// eigenvectors accumulated from the identity (no per-node basis store, no FP64
+// queue), tables and scratch read from the static array.
+template <int MP>
+__global__ void __launch_bounds__(LK_TILE_I *LK_TILE_J * 32)
+    analysis_noalloc_kernel(LkGeom g, const int2 *__restrict__ tiles, const float *__restrict__ Ybp,
+                            const float *__restrict__ dp, const float *__restrict__ taper,
+                            float *__restrict__ X, float *__restrict__ mean,
+                            float *__restrict__ spread, float alpha, float tol, int max_sweeps,
+                            int *__restrict__ counters) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int w = g.w;
+  const TileLayout L = tile_layout<MP, float, float>(w);
+  const int HJ = LK_TILE_J + w - 1;
+  const int ncell = (LK_TILE_I + w - 1) * HJ;
+  float *halo = reinterpret_cast<float *>(smem + L.halo);
+  float *dh = reinterpret_cast<float *>(smem + L.dh);
+  float *tap = reinterpret_cast<float *>(smem + L.tap);
+  float *scr = reinterpret_cast<float *>(smem + L.scr);
+  const int2 org = tiles[blockIdx.x];
+  const int m = g.m;
+  for (int e = threadIdx.x; e < ncell * 2 * MP; e += blockDim.x) {
+    const int cell = e / (2 * MP);
+    const int r = e - cell * 2 * MP;
+    const int c = r / MP;
+    const int mm = r - c * MP;
+    const int hi = cell / HJ, hj = cell - (cell / HJ) * HJ;
+    const size_t src = (size_t)(org.x + hi) * g.gs_cols + (org.y + hj);
+    halo[e] = mm < m ? Ybp[(src * 2 + c) * m + mm] : 0.f;
+  }
+  for (int e = threadIdx.x; e < ncell * 2; e += blockDim.x) {
+    const int cell = e >> 1;
+    const int hi = cell / HJ, hj = cell - (cell / HJ) * HJ;
+    const size_t src = (size_t)(org.x + hi) * g.gs_cols + (org.y + hj);
+    dh[e] = dp[src * 2 + (e & 1)];
+  }
+  for (int e = threadIdx.x; e < w * w; e += blockDim.x) tap[e] = taper[e];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  const int ti = warp / LK_TILE_J, tj = warp - (warp / LK_TILE_J) * LK_TILE_J;
+  const int i = org.x + ti, j = org.y + tj;
+  if (i > g.nsub || j > g.nsub) return;
+  const int pid = g.pid_map[i * (g.nsub + 1) + j];
+  if (pid < 0) return;
+  const int off = ti * HJ + tj;
+  analyze_node_accum<MP, float, float>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m,
+                                       alpha, tol, max_sweeps, X + (size_t)pid * 2 * m,
+                                       mean ? mean + 2 * pid : nullptr,
+                                       spread ? spread + 2 * pid : nullptr,
+                                       scr + (size_t)warp * scratch_elems<MP, float>(), counters,
+                                       nullptr);
+}
+
+// Device address of the scratch on the current device; looked up once per device.
+cudaError_t na_scratch_address(int dev, unsigned char **out) {
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  if (!g_na_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_na_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char *>(g_na_addr[dev]);
+  return cudaSuccess;
+}
+
+template <int MP>
+cudaError_t na_setup_kernel(size_t smem_bytes) {
+  return cudaFuncSetAttribute(analysis_noalloc_kernel<MP>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+}
+
+}  // namespace
+
+extern "C" letkf_status letkf_analyze_noalloc(const letkf_config *cfg, void *X_dev,
+                                              const void *y_dev, void *mean_dev, void *spread_dev,
+                                              void *stream, char *errbuf, size_t errlen) {
+  if (!cfg || !cfg->subap_mask || !X_dev || !y_dev) {
+    na_error(errbuf, errlen, "cfg, cfg->subap_mask, X_dev and y_dev are required");
+    return LETKF_ERR_ARG;
+  }
+  const letkf_config &c = *cfg;
+  if (c.nsub < 1 || c.nsub > NA_MAX_NSUB || c.m < 2 || c.m > NA_MAX_M || c.window < 1 ||
+      c.window > NA_MAX_W) {
+    na_error(errbuf, errlen,
+             "size beyond the allocation-free maximum: nsub 1..128, m 2..32, window 1..15");
+    return LETKF_ERR_ARG;
+  }
+  if (c.precision != 0 || (c.taper != 0 && c.taper != 1) || !(c.rho > 0) || !(c.sigma2 > 0) ||
+      !isfinite(c.rho) || !isfinite(c.sigma2)) {
+    na_error(errbuf, errlen, "precision must be 0, taper 0 or 1, rho and sigma2 finite and > 0");
+    return LETKF_ERR_ARG;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  unsigned char *base = nullptr;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (e == cudaSuccess) e = na_scratch_address(dev, &base);
+  const int mp = c.m <= 16 ? 16 : 32;
+  const size_t smem = mp == 16 ? tile_layout<16, float, float>(c.window).total
+                               : tile_layout<32, float, float>(c.window).total;
+  if (e == cudaSuccess) e = mp == 16 ? na_setup_kernel<16>(smem) : na_setup_kernel<32>(smem);
+  if (e != cudaSuccess) {
+    na_error(errbuf, errlen, cudaGetErrorString(e));
+    return LETKF_ERR_CUDA;
+  }
+
+  // ---- node and window tables (host, static storage) ----
+  const int ns = c.nsub, nn = ns + 1, w = c.window, hw = w / 2;
+  for (int k = 0; k < nn * nn; ++k) g_na_pid[k] = -1;
+  int n_sap = 0;
+  for (int s = 0; s < ns; ++s)
+    for (int t = 0; t < ns; ++t)
+      if (c.subap_mask[(size_t)s * ns + t]) {
+        g_na_saps[n_sap++] = make_int2(s, t);
+        g_na_pid[s * nn + t] = g_na_pid[(s + 1) * nn + t] = 0;
+        g_na_pid[s * nn + t + 1] = g_na_pid[(s + 1) * nn + t + 1] = 0;
+      }
+  if (n_sap == 0) {
+    na_error(errbuf, errlen, "subap_mask has no valid subaperture");
+    return LETKF_ERR_ARG;
+  }
+  int n_pts = 0;
+  for (int i = 0; i < nn; ++i)
+    for (int j = 0; j < nn; ++j)
+      if (g_na_pid[i * nn + j] == 0) {
+        g_na_pid[i * nn + j] = n_pts;
+        g_na_pts[n_pts++] = make_int2(i, j);
+      }
+  const int tiles_i = (nn + LK_TILE_I - 1) / LK_TILE_I, tiles_j = (nn + LK_TILE_J - 1) / LK_TILE_J;
+  int n_tiles = 0;
+  for (int a = 0; a < tiles_i; ++a)
+    for (int b = 0; b < tiles_j; ++b) {
+      bool any = false;
+      for (int di = 0; di < LK_TILE_I; ++di)
+        for (int dj = 0; dj < LK_TILE_J; ++dj) {
+          const int i = a * LK_TILE_I + di, j = b * LK_TILE_J + dj;
+          any = any || (i < nn && j < nn && g_na_pid[i * nn + j] >= 0);
+        }
+      if (any) g_na_tiles[n_tiles++] = make_int2(a * LK_TILE_I, b * LK_TILE_J);
+    }
+  const double cl = c.loc_len > 0 ? c.loc_len : w / 4.0;
+  for (int ds = 0; ds < w; ++ds)
+    for (int dt = 0; dt < w; ++dt) {
+      const double tau = c.taper == 1 ? na_gaspari_cohn(hypot(ds - hw + 0.5, dt - hw + 0.5) / cl) : 1.0;
+      g_na_taper[ds * w + dt] = (float)(tau / c.sigma2);
+    }
+
+  // ---- scratch: tables in, grids cleared (cells outside the pupil must read 0) ----
+  cudaStream_t st = (cudaStream_t)stream;
+  const int gs_rows = tiles_i * LK_TILE_I + w, gs_cols = tiles_j * LK_TILE_J + w;
+  const size_t cells = (size_t)gs_rows * gs_cols;
+  struct Copy {
+    size_t off;
+    const void *src;
+    size_t bytes;
+  } copies[] = {{NA_OFF_PID, g_na_pid, (size_t)nn * nn * sizeof(int)},
+                {NA_OFF_SAPS, g_na_saps, (size_t)n_sap * sizeof(int2)},
+                {NA_OFF_PTS, g_na_pts, (size_t)n_pts * sizeof(int2)},
+                {NA_OFF_TILES, g_na_tiles, (size_t)n_tiles * sizeof(int2)},
+                {NA_OFF_TAPER, g_na_taper, (size_t)w * w * sizeof(float)}};
+  for (const Copy &cp : copies)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + NA_OFF_YBP, 0, cells * 2 * c.m * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + NA_OFF_DP, 0, cells * 2 * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + NA_OFF_COUNTERS, 0, 4 * sizeof(int), st);
+
+  // ---- observation (shared kernel) and analysis (variant kernel) ----
+  letkf_ctx tmp;
+  tmp.stream = st;
+  tmp.precision = 0;
+  tmp.g.nsub = ns;
+  tmp.g.m = c.m;
+  tmp.g.w = w;
+  tmp.g.h = hw;
+  tmp.g.n_pts = n_pts;
+  tmp.g.n_sap = n_sap;
+  tmp.g.p = 2 * n_sap;
+  tmp.g.gs_rows = gs_rows;
+  tmp.g.gs_cols = gs_cols;
+  tmp.g.pid_map = reinterpret_cast<const int *>(base + NA_OFF_PID);
+  tmp.g.pts = reinterpret_cast<const int2 *>(base + NA_OFF_PTS);
+  tmp.g.saps = reinterpret_cast<const int2 *>(base + NA_OFF_SAPS);
+  tmp.X = X_dev;
+  tmp.Ybp = base + NA_OFF_YBP;
+  tmp.dp = base + NA_OFF_DP;
+  tmp.counters = reinterpret_cast<int *>(base + NA_OFF_COUNTERS);
+  if (e == cudaSuccess) e = lk_launch_obs(&tmp, y_dev, nullptr);
+  const int sweeps = c.max_sweeps > 0 ? c.max_sweeps : 20;
+  const float alpha = (float)((c.m - 1) / c.rho), tol = 4e-6f;
+  if (e == cudaSuccess) {
+    const int threads = LK_TILE_I * LK_TILE_J * 32;
+    const int2 *tiles = reinterpret_cast<const int2 *>(base + NA_OFF_TILES);
+    const float *ybp = reinterpret_cast<const float *>(base + NA_OFF_YBP);
+    const float *dpp = reinterpret_cast<const float *>(base + NA_OFF_DP);
+    const float *tap = reinterpret_cast<const float *>(base + NA_OFF_TAPER);
+    if (mp == 16)
+      analysis_noalloc_kernel<16><<<n_tiles, threads, smem, st>>>(
+          tmp.g, tiles, ybp, dpp, tap, (float *)X_dev, (float *)mean_dev, (float *)spread_dev,
+          alpha, tol, sweeps, tmp.counters);
+    else
+      analysis_noalloc_kernel<32><<<n_tiles, threads, smem, st>>>(
+          tmp.g, tiles, ybp, dpp, tap, (float *)X_dev, (float *)mean_dev, (float *)spread_dev,
+          alpha, tol, sweeps, tmp.counters);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    na_error(errbuf, errlen, cudaGetErrorString(e));
+    return LETKF_ERR_CUDA;
+  }
+  return LETKF_OK;
 }

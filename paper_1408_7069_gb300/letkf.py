@@ -51,6 +51,8 @@ _SIGS = {
     "letkf_run": [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32],
     "letkf_sync": [c_void_p],
     "letkf_stats": [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)],
+    "letkf_analyze_noalloc": [POINTER(letkf_config), c_void_p, c_void_p, c_void_p, c_void_p,
+                              c_void_p, c_char_p, ctypes.c_size_t],
 }
 
 _lib = None
@@ -155,6 +157,16 @@ def letkf_stats(h):
     a, b, c = c_int32(), c_int32(), c_int32()
     _check(lib().letkf_stats(h, byref(a), byref(b), byref(c)), h)
     return a.value, b.value, c.value
+
+
+def letkf_analyze_noalloc(cfg: letkf_config, X, y, mean=None, spread=None, stream_ptr: int = 0):
+    """One-frame analysis without a handle and without device allocation (its
+    scratch is a static device array inside the library); raises LetkfError."""
+    buf = ctypes.create_string_buffer(256)
+    st = lib().letkf_analyze_noalloc(byref(cfg), _ptr(X), _ptr(y), _ptr(mean), _ptr(spread),
+                                     c_void_p(stream_ptr), buf, 256)
+    if st != LETKF_OK:
+        raise LetkfError(st, buf.value.decode())
 
 
 def letkf_last_error(h=None) -> str:
