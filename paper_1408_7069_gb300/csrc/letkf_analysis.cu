@@ -203,6 +203,63 @@ __device__ __forceinline__ void jacobi(T (&b)[MP], T (&v)[MP], T tol, int max_sw
   }
 }
 
+// FP32 one-sided Jacobi on B alone with scaled ("fast") rotations: the true
+// column is d * beta, so a rotation updates beta with one FMA per element,
+//   beta_p <- beta_p - t (d_q / d_p) beta_q,   beta_q <- beta_q + t (d_p / d_q) beta_p,
+// and multiplies both scales by cos. Columns are rescaled (beta <- d beta, d = 1)
+// at the start of every sweep, which bounds their growth to (1/cos)^(MP-1).
+// The convergence test is the same as jacobi(): cos(b_p, b_q) <= tol.
+template <int MP>
+__device__ __forceinline__ void jacobi_fast_f32(float (&b)[MP], float tol, int max_sweeps,
+                                                int *__restrict__ counters) {
+  const int lane = threadIdx.x & 31;
+  const float tol2 = tol * tol;
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps; ++sweep) {
+    float nrm = dot4<MP, float>(b, b);   // true squared norm of this lane's column
+    float d = 1.f;                        // scale: true column = d * b
+    int rotated = 0;
+    for (int t = 1; t < MP; ++t) {
+      float pb[MP];
+#pragma unroll
+      for (int k = 0; k < MP; ++k) pb[k] = __shfl_xor_sync(FULL, b[k], t);
+      const float pd = __shfl_xor_sync(FULL, d, t);
+      const float pn = __shfl_xor_sync(FULL, nrm, t);
+      const float dot = d * pd * dot4<MP, float>(b, pb);   // true b_p . b_q
+      const bool isp = lane < (lane ^ t);
+      const float app = isp ? nrm : pn;
+      const float aqq = isp ? pn : nrm;
+      float tr = 0.f, cs = 1.f;
+      if (dot * dot > tol2 * app * aqq) {
+        const float zeta = __fdividef(aqq - app, 2.f * dot);
+        const float az = fabsf(zeta);
+        tr = az > 1e15f ? __fdividef(0.5f, zeta)
+                        : copysignf(__fdividef(1.f, az + __fsqrt_rn(fmaf(zeta, zeta, 1.f))), zeta);
+        cs = rsqrtf(fmaf(tr, tr, 1.f));
+        rotated = 1;
+      }
+      // own' = own -/+ t (d_partner / d_own) partner
+      const float coef = (isp ? -tr : tr) * __fdividef(pd, d);
+#pragma unroll
+      for (int k = 0; k < MP; ++k) b[k] = fmaf(coef, pb[k], b[k]);
+      d *= cs;
+      nrm = isp ? fmaf(-tr, dot, app) : fmaf(tr, dot, aqq);
+    }
+#pragma unroll
+    for (int k = 0; k < MP; ++k) b[k] *= d;
+    if (!__any_sync(FULL, rotated)) {
+      converged = true;
+      break;
+    }
+  }
+  if (lane == 0) {
+    atomicMax(&counters[2], converged ? sweep + 1 : sweep);
+    atomicAdd(&counters[3], converged ? sweep + 1 : sweep);
+    if (!converged) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
+  }
+}
+
 // wbar, W from the eigenpairs (lane j: eigenvector column v, eigenvalue lam) and
 // the update of the node's two rows; writes Xa, the mean and the spread.
 template <int MP, typename S, typename T>
@@ -370,7 +427,7 @@ __device__ __forceinline__ void analyze_node_f32(const float *__restrict__ win,
     }
     b[i] = s0 + s1;
   }
-  jacobi<MP, float, false>(b, u, tol, max_sweeps, counters);
+  jacobi_fast_f32<MP>(b, tol, max_sweeps, counters);
   const float nrm = dot4<MP, float>(b, b);
   const float lam = (col && nrm > 0.f) ? sqrtf(nrm) : 1.f;
   const float inv = 1.f / lam;
