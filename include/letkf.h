@@ -33,6 +33,13 @@
  *    the next letkf_sync.
  *  - No C++ exception crosses this boundary; a failing call returns a status and
  *    letkf_last_error() describes it.
+ *  - A handle holds one or more independent AO instances (letkf_create_batch).
+ *    Per-node, per-slope and per-member buffers of a call are then the
+ *    instances' buffers concatenated in instance order: the ensemble is each
+ *    instance's [n_pts_i][2][m_i] block in turn, slopes y are p_1 + ... + p_n
+ *    values, mean / spread have n_pts_1 + ... + n_pts_n rows of 2, truth has
+ *    n_pts_1 + ... values, forecast noise has the [n_pts_i][m_i] blocks in turn,
+ *    and a residual call writes one double per instance.
  */
 #ifndef LETKF_H
 #define LETKF_H
@@ -85,11 +92,24 @@ typedef struct {
  * all of it. */
 letkf_status letkf_create(const letkf_config *cfg, void *stream, letkf_t *out);
 
+/* One handle for n independent instances of possibly different sizes (grid,
+ * mask, m, window, noise, seeds; one precision for all), analysed together:
+ * every frame's kernels cover all instances, analysis tiles of all instances
+ * are ordered by cost (largest windows and ensembles first), and letkf_run
+ * captures the whole multi-instance frame in one CUDA graph. cfgs: host
+ * array of n configurations (masks and banks copied). */
+letkf_status letkf_create_batch(const letkf_config *cfgs, int32_t n, void *stream, letkf_t *out);
+
 /* Synchronise the handle's stream and free everything it owns. NULL is a no-op. */
 letkf_status letkf_destroy(letkf_t h);
 
-/* Sizes: number of nodes, of slopes and the ensemble size. Host pointers, any may be NULL. */
+/* Sizes summed over the instances: nodes and slopes; m is the ensemble size of
+ * a single-instance handle and 0 for a batch. Host pointers, any may be NULL. */
 letkf_status letkf_query(letkf_t h, int32_t *n_pts, int32_t *p, int32_t *m);
+
+/* Sizes of instance i and the number of instances. Host pointers, any may be NULL. */
+letkf_status letkf_query_instance(letkf_t h, int32_t i, int32_t *n_pts, int32_t *p, int32_t *m,
+                                  int32_t *n_inst);
 
 /* Host copies of the node coordinates [n_pts][2] (i, j) and of the number of
  * valid window slopes per node [n_pts] (p_l, Section 4.2's p_d). Either may be NULL. */
@@ -127,10 +147,28 @@ letkf_status letkf_residual(letkf_t h, const void *truth_dev, double *resvar_dev
  * prediction against truth_seq[k] into resvar[k], the analysis of
  * y_seq[k], then a forecast with bank noise. y_seq_dev: device [frames][p]
  * real; truth_seq_dev: device [frames][n_pts] real or NULL (then no residual);
- * resvar_dev: device double[frames] or NULL. use_graph != 0 captures the frame
- * into a CUDA graph once and replays it. Requires a noise bank. */
+ * resvar_dev: device double[frames][n_inst] or NULL. use_graph != 0 captures
+ * one frame of every instance into a CUDA graph once and replays it. Requires a
+ * noise bank for every instance. */
 letkf_status letkf_run(letkf_t h, int32_t frames, const void *y_seq_dev, const void *truth_seq_dev,
                        double *resvar_dev, int32_t use_graph);
+
+/* Analysis tile shapes. The analysis runs one CTA per tile of tile_i x tile_j
+ * nodes (one warp per node) and stages the tile's window halo in shared
+ * memory once; the best shape depends on the window, the ensemble size and the
+ * mix of instances. letkf_tile_shape describes compiled shape number `shape`
+ * (0 .. count-1; LETKF_ERR_ARG beyond). Instances are grouped in width classes
+ * by ensemble size: 0 for m <= 16, 1 for m <= 32. letkf_set_tile_shape selects
+ * a shape for one class; letkf_autotune times every shape for every class
+ * present on the handle's current ensemble with slopes y_dev (reps timed
+ * analyses each, state restored afterwards), keeps the fastest and writes the
+ * choices to shapes_out[3] and their analysis time in microseconds to us_out[3]
+ * (either may be NULL). Both synchronise; choices may be cached by the caller
+ * and restored with letkf_set_tile_shape. */
+letkf_status letkf_tile_shape(int32_t shape, int32_t *tile_i, int32_t *tile_j);
+letkf_status letkf_set_tile_shape(letkf_t h, int32_t width_class, int32_t shape);
+letkf_status letkf_autotune(letkf_t h, const void *y_dev, int32_t reps, int32_t *shapes_out,
+                            float *us_out);
 
 /* Synchronise the stream, return and clear the first error recorded on the
  * device since the last call (LETKF_OK if none). */

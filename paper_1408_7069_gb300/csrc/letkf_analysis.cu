@@ -31,6 +31,11 @@
 
 #include "letkf_common.cuh"
 
+// Tile shapes (nodes per CTA side) the autotuner chooses from; each divides
+// LK_TILE_MAX so the padded grid covers every tile's halo.
+#define LK_FOR_SHAPES(X) X(0, 2, 4) X(1, 4, 4) X(2, 2, 2) X(3, 1, 8)
+constexpr int LK_NUM_SHAPES = 4;
+
 namespace {
 
 constexpr int LIST_WARPS = 4;
@@ -49,15 +54,15 @@ __host__ __device__ constexpr size_t scratch_elems() {
 struct TileLayout {
   size_t halo, dh, tap, scr, total;
 };
-template <int MP, typename S, typename T>
+template <int MP, typename S, typename T, int TI, int TJ>
 __host__ __device__ TileLayout tile_layout(int w) {
   TileLayout L;
-  const size_t ncell = (size_t)(LK_TILE_I + w - 1) * (LK_TILE_J + w - 1);
+  const size_t ncell = (size_t)(TI + w - 1) * (TJ + w - 1);
   L.halo = 0;
   L.dh = align16(ncell * 2 * MP * sizeof(S));
   L.tap = align16(L.dh + ncell * 2 * sizeof(S));
   L.scr = align16(L.tap + (size_t)w * w * sizeof(T));
-  L.total = L.scr + (size_t)LK_TILE_I * LK_TILE_J * scratch_elems<MP, T>() * sizeof(T);
+  L.total = L.scr + (size_t)TI * TJ * scratch_elems<MP, T>() * sizeof(T);
   return L;
 }
 
@@ -390,8 +395,9 @@ __device__ __forceinline__ void analyze_node_f32(const float *__restrict__ win,
                                                  float *__restrict__ spread_out,
                                                  float *__restrict__ scr,
                                                  int *__restrict__ counters, float kappa_thr,
-                                                 int *__restrict__ worklist, int pid,
-                                                 float *__restrict__ U) {
+                                                 int *__restrict__ queue_len, int pid,
+                                                 float *__restrict__ U,
+                                                 int2 *__restrict__ worklist, int inst) {
   const int lane = threadIdx.x & 31;
   const bool col = lane < MP;
   float b[MP], diag, cd;
@@ -399,7 +405,10 @@ __device__ __forceinline__ void analyze_node_f32(const float *__restrict__ win,
   if (kappa_thr > 0.f) {
     const float trg = lk_warp_sum(diag);
     if (1.f + trg / alpha > kappa_thr) {
-      if (lane == 0) worklist[atomicAdd(&counters[1], 1)] = pid;
+      if (lane == 0) {
+        worklist[atomicAdd(queue_len, 1)] = make_int2(inst, pid);
+        atomicAdd(&counters[1], 1);
+      }
       return;
     }
   }
@@ -437,171 +446,248 @@ __device__ __forceinline__ void analyze_node_f32(const float *__restrict__ win,
   store_basis<MP, float>(b, U);
 }
 
-template <int MP, typename S, typename T, bool FALLBACK>
-__global__ void __launch_bounds__(LK_TILE_I *LK_TILE_J * 32)
-    analysis_tile_kernel(LkGeom g, const int2 *__restrict__ tiles, const S *__restrict__ Ybp,
-                         const S *__restrict__ dp, const S *__restrict__ taper, S *__restrict__ X,
-                         S *__restrict__ mean, S *__restrict__ spread, T alpha, T tol,
-                         int max_sweeps, T kappa_thr, int *__restrict__ counters,
-                         int *__restrict__ worklist, float *__restrict__ basis) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int w = g.w;
-  const TileLayout L = tile_layout<MP, S, T>(w);
-  const int HJ = LK_TILE_J + w - 1;
-  const int ncell = (LK_TILE_I + w - 1) * HJ;
-  S *halo = reinterpret_cast<S *>(smem + L.halo);
-  S *dh = reinterpret_cast<S *>(smem + L.dh);
-  T *tap = reinterpret_cast<T *>(smem + L.tap);
-  T *scr = reinterpret_cast<T *>(smem + L.scr);
-  const int2 org = tiles[blockIdx.x];
-  const int m = g.m;
+
+// Stages a tile's halo (slope anomalies and innovations of the padded grid)
+// and the taper table in shared memory.
+template <int MP, typename S, typename T, int TI, int TJ>
+__device__ __forceinline__ void stage_tile(const LkInst &I, int i0, int j0, S *halo, S *dh, T *tap) {
+  const int w = I.w, m = I.m;
+  const int HJ = TJ + w - 1;
+  const int ncell = (TI + w - 1) * HJ;
+  const S *Ybp = static_cast<const S *>(I.Ybp);
+  const S *dp = static_cast<const S *>(I.dp);
+  const S *taper = static_cast<const S *>(I.taper);
   for (int e = threadIdx.x; e < ncell * 2 * MP; e += blockDim.x) {
     const int cell = e / (2 * MP);
     const int r = e - cell * 2 * MP;
     const int c = r / MP;
     const int mm = r - c * MP;
     const int hi = cell / HJ, hj = cell - (cell / HJ) * HJ;
-    const size_t src = (size_t)(org.x + hi) * g.gs_cols + (org.y + hj);
+    const size_t src = (size_t)(i0 + hi) * I.gs_cols + (j0 + hj);
     halo[e] = mm < m ? Ybp[(src * 2 + c) * m + mm] : S(0);
   }
   for (int e = threadIdx.x; e < ncell * 2; e += blockDim.x) {
     const int cell = e >> 1;
     const int hi = cell / HJ, hj = cell - (cell / HJ) * HJ;
-    const size_t src = (size_t)(org.x + hi) * g.gs_cols + (org.y + hj);
+    const size_t src = (size_t)(i0 + hi) * I.gs_cols + (j0 + hj);
     dh[e] = dp[src * 2 + (e & 1)];
   }
   for (int e = threadIdx.x; e < w * w; e += blockDim.x) tap[e] = T(taper[e]);
+}
+
+// One CTA per tile of TI x TJ nodes of one instance, one warp per node.
+template <int MP, typename S, typename T, int TI, int TJ>
+__global__ void __launch_bounds__(TI *TJ * 32)
+    analysis_tile_kernel(const LkInst *__restrict__ insts, const LkTile *__restrict__ tiles,
+                         S *__restrict__ mean, S *__restrict__ spread, T tol, int max_sweeps,
+                         T kappa_thr, int *__restrict__ counters, int2 *__restrict__ worklist) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const LkTile tl = tiles[blockIdx.x];
+  const LkInst &I = insts[tl.inst];
+  const int w = I.w;
+  const TileLayout L = tile_layout<MP, S, T, TI, TJ>(w);
+  const int HJ = TJ + w - 1;
+  S *halo = reinterpret_cast<S *>(smem + L.halo);
+  S *dh = reinterpret_cast<S *>(smem + L.dh);
+  T *tap = reinterpret_cast<T *>(smem + L.tap);
+  T *scr = reinterpret_cast<T *>(smem + L.scr);
+  stage_tile<MP, S, T, TI, TJ>(I, tl.i0, tl.j0, halo, dh, tap);
   __syncthreads();
   const int warp = threadIdx.x >> 5;
-  const int ti = warp / LK_TILE_J, tj = warp - (warp / LK_TILE_J) * LK_TILE_J;
-  const int i = org.x + ti, j = org.y + tj;
-  if (i > g.nsub || j > g.nsub) return;
-  const int pid = g.pid_map[i * (g.nsub + 1) + j];
+  const int ti = warp / TJ, tj = warp - (warp / TJ) * TJ;
+  const int i = tl.i0 + ti, j = tl.j0 + tj;
+  if (i > I.nsub || j > I.nsub) return;
+  const int pid = I.pid_map[i * (I.nsub + 1) + j];
   if (pid < 0) return;
   const int off = ti * HJ + tj;
+  const int m = I.m;
+  S *xrow = static_cast<S *>(I.X) + (size_t)pid * 2 * m;
+  S *mo = mean ? mean + 2 * (I.node_off + pid) : nullptr;
+  S *so = spread ? spread + 2 * (I.node_off + pid) : nullptr;
   T *wscr = scr + (size_t)warp * scratch_elems<MP, T>();
   if constexpr (std::is_same<T, float>::value) {
-    analyze_node_f32<MP>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m, alpha, tol,
-                         max_sweeps, X + (size_t)pid * 2 * m, mean ? mean + 2 * pid : nullptr,
-                         spread ? spread + 2 * pid : nullptr, wscr, counters,
-                         FALLBACK ? kappa_thr : 0.f, worklist, pid,
-                         basis + (size_t)pid * MP * MP);
+    const int queue = kappa_thr > 0.f ? 1 : 0;
+    int *slot = queue ? &counters[4 + (MP == 16 ? 0 : 1)] : nullptr;
+    analyze_node_f32<MP>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m, float(I.alpha),
+                         tol, max_sweeps, xrow, mo, so, wscr, counters, kappa_thr,
+                         reinterpret_cast<int *>(slot), pid, I.basis + (size_t)pid * MP * MP,
+                         worklist, tl.inst);
   } else {
-    analyze_node_accum<MP, S, T>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m, alpha,
-                                 tol, max_sweeps, X + (size_t)pid * 2 * m,
-                                 mean ? mean + 2 * pid : nullptr,
-                                 spread ? spread + 2 * pid : nullptr, wscr, counters, nullptr);
+    analyze_node_accum<MP, S, T>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m,
+                                 T(I.alpha), tol, max_sweeps, xrow, mo, so, wscr, counters,
+                                 nullptr);
   }
 }
 
-// FP64 re-analysis of the queued nodes of an FP32 handle: one warp per node,
+// FP64 re-analysis of the queued nodes (FP32 handles): one warp per node,
 // window staged per warp from the padded grid.
 template <int MP>
 __global__ void __launch_bounds__(LIST_WARPS * 32)
-    analysis_list_kernel(LkGeom g, const int *__restrict__ worklist, const float *__restrict__ Ybp,
-                         const float *__restrict__ dp, const float *__restrict__ taper,
-                         float *__restrict__ X, float *__restrict__ mean, float *__restrict__ spread,
-                         double alpha, double tol, int max_sweeps, int *__restrict__ counters,
-                         float *__restrict__ basis) {
+    analysis_list_kernel(const LkInst *__restrict__ insts, const int2 *__restrict__ worklist,
+                         const int *__restrict__ queue_len, float *__restrict__ mean,
+                         float *__restrict__ spread, double tol, int max_sweeps,
+                         int *__restrict__ counters, int wmax) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int w = g.w, wc = w * w, m = g.m;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int idx = blockIdx.x * LIST_WARPS + warp;
-  if (idx >= counters[1]) return;
-  unsigned char *base = smem + (size_t)warp * list_warp_bytes<MP>(w);
+  if (idx >= *queue_len) return;
+  const int2 it = worklist[idx];
+  const LkInst &I = insts[it.x];
+  const int w = I.w, wc = w * w, m = I.m;
+  // every warp's region has the size for the class's widest window, whatever
+  // the window of the instance it serves
+  unsigned char *base = smem + (size_t)warp * list_warp_bytes<MP>(wmax);
   float *win = reinterpret_cast<float *>(base);
   float *dwin = reinterpret_cast<float *>(base + align16((size_t)wc * 2 * MP * sizeof(float)));
   double *tap = reinterpret_cast<double *>(base + align16((size_t)wc * 2 * MP * sizeof(float)) +
                                            align16((size_t)wc * 2 * sizeof(float)));
   double *scr = tap + align16((size_t)wc * sizeof(double)) / sizeof(double);
-  const int pid = worklist[idx];
-  const int2 ij = g.pts[pid];
+  const int pid = it.y;
+  const int2 ij = I.pts[pid];
+  const float *Ybp = static_cast<const float *>(I.Ybp);
+  const float *dp = static_cast<const float *>(I.dp);
+  const float *taper = static_cast<const float *>(I.taper);
   for (int e = lane; e < wc * 2 * MP; e += 32) {
     const int cell = e / (2 * MP);
     const int r = e - cell * 2 * MP;
     const int c = r / MP;
     const int mm = r - c * MP;
     const int ds = cell / w, dt = cell - (cell / w) * w;
-    const size_t src = (size_t)(ij.x + ds) * g.gs_cols + (ij.y + dt);
+    const size_t src = (size_t)(ij.x + ds) * I.gs_cols + (ij.y + dt);
     win[e] = mm < m ? Ybp[(src * 2 + c) * m + mm] : 0.f;
   }
   for (int e = lane; e < wc * 2; e += 32) {
     const int cell = e >> 1;
     const int ds = cell / w, dt = cell - (cell / w) * w;
-    const size_t src = (size_t)(ij.x + ds) * g.gs_cols + (ij.y + dt);
+    const size_t src = (size_t)(ij.x + ds) * I.gs_cols + (ij.y + dt);
     dwin[e] = dp[src * 2 + (e & 1)];
   }
   for (int e = lane; e < wc; e += 32) tap[e] = (double)taper[e];
   __syncwarp();
-  analyze_node_accum<MP, float, double>(win, dwin, w, tap, w, m, alpha, tol, max_sweeps,
-                                        X + (size_t)pid * 2 * m, mean ? mean + 2 * pid : nullptr,
-                                        spread ? spread + 2 * pid : nullptr, scr, counters,
-                                        basis + (size_t)pid * MP * MP);
+  analyze_node_accum<MP, float, double>(
+      win, dwin, w, tap, w, m, I.alpha, tol, max_sweeps,
+      static_cast<float *>(I.X) + (size_t)pid * 2 * m,
+      mean ? mean + 2 * (I.node_off + pid) : nullptr,
+      spread ? spread + 2 * (I.node_off + pid) : nullptr, scr, counters,
+      I.basis + (size_t)pid * MP * MP);
 }
 
-template <int MP, typename S, typename T, bool FB>
-cudaError_t launch_tile(letkf_ctx *h, void *mean, void *spread, T tol) {
-  const TileLayout L = tile_layout<MP, S, T>(h->g.w);
-  analysis_tile_kernel<MP, S, T, FB><<<h->n_tiles, LK_TILE_I * LK_TILE_J * 32, L.total, h->stream>>>(
-      h->g, h->tiles, (const S *)h->Ybp, (const S *)h->dp, (const S *)h->taper, (S *)h->X,
-      (S *)mean, (S *)spread, (T)h->alpha, tol, h->max_sweeps, (T)h->cfg.fp64_kappa, h->counters,
-      h->worklist, h->basis);
+template <int MP, typename S, typename T, int TI, int TJ>
+cudaError_t launch_tile_shape(letkf_ctx *h, int cls, void *mean, void *spread, T tol, T kthr) {
+  size_t need = 0;
+  for (const LkInst &I : h->inst)
+    if (I.mp == MP) {
+      const size_t b = tile_layout<MP, S, T, TI, TJ>(I.w).total;
+      need = b > need ? b : need;
+    }
+  analysis_tile_kernel<MP, S, T, TI, TJ><<<h->n_tiles[cls], TI * TJ * 32, need, h->stream>>>(
+      h->d_inst, h->tiles[cls], (S *)mean, (S *)spread, tol, h->max_sweeps, kthr, h->counters,
+      h->worklist + (size_t)cls * h->n_pts_total);
   return cudaGetLastError();
 }
 
-template <int MP>
-cudaError_t launch_list(letkf_ctx *h, void *mean, void *spread) {
-  const size_t bytes = (size_t)LIST_WARPS * list_warp_bytes<MP>(h->g.w);
-  const int blocks = (h->g.n_pts + LIST_WARPS - 1) / LIST_WARPS;
-  analysis_list_kernel<MP><<<blocks, LIST_WARPS * 32, bytes, h->stream>>>(
-      h->g, h->worklist, (const float *)h->Ybp, (const float *)h->dp, (const float *)h->taper,
-      (float *)h->X, (float *)mean, (float *)spread, h->alpha, h->tol64, h->max_sweeps,
-      h->counters, h->basis);
-  return cudaGetLastError();
-}
-
-template <int MP>
-cudaError_t launch_all(letkf_ctx *h, void *mean, void *spread) {
-  cudaError_t e;
-  if (h->precision == 1) return launch_tile<MP, double, double, false>(h, mean, spread, h->tol64);
-  if (h->cfg.fp64_kappa > 0) {
-    e = launch_tile<MP, float, float, true>(h, mean, spread, (float)h->tol32);
-    if (e != cudaSuccess) return e;
-    return launch_list<MP>(h, mean, spread);
+template <int MP, typename S, typename T>
+cudaError_t launch_tile(letkf_ctx *h, int cls, void *mean, void *spread, T tol, T kthr) {
+  switch (h->tile_shape[cls]) {
+#define LK_CASE(id, ti, tj) \
+  case id:                  \
+    return launch_tile_shape<MP, S, T, ti, tj>(h, cls, mean, spread, tol, kthr);
+    LK_FOR_SHAPES(LK_CASE)
+#undef LK_CASE
   }
-  return launch_tile<MP, float, float, false>(h, mean, spread, (float)h->tol32);
+  return cudaErrorInvalidValue;
 }
 
 template <int MP>
-cudaError_t setup_all(letkf_ctx *h) {
-  const int w = h->g.w;
-  cudaError_t e;
+cudaError_t launch_list(letkf_ctx *h, int cls, void *mean, void *spread) {
+  int wmax = 1;
+  for (const LkInst &I : h->inst)
+    if (I.mp == MP) wmax = I.w > wmax ? I.w : wmax;
+  const size_t bytes = (size_t)LIST_WARPS * list_warp_bytes<MP>(wmax);
+  long long n = 0;
+  for (const LkInst &I : h->inst)
+    if (I.mp == MP) n += I.n_pts;
+  const int blocks = (int)((n + LIST_WARPS - 1) / LIST_WARPS);
+  analysis_list_kernel<MP><<<blocks, LIST_WARPS * 32, bytes, h->stream>>>(
+      h->d_inst, h->worklist + (size_t)cls * h->n_pts_total, h->counters + 4 + cls, (float *)mean,
+      (float *)spread, h->tol64, h->max_sweeps, h->counters, wmax);
+  return cudaGetLastError();
+}
+
+template <int MP>
+cudaError_t launch_class(letkf_ctx *h, int cls, void *mean, void *spread) {
+  if (h->n_tiles[cls] == 0) return cudaSuccess;
   if (h->precision == 1)
-    return cudaFuncSetAttribute(analysis_tile_kernel<MP, double, double, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tile_layout<MP, double, double>(w).total);
-  const int tb = (int)tile_layout<MP, float, float>(w).total;
-  e = cudaFuncSetAttribute(analysis_tile_kernel<MP, float, float, false>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(analysis_tile_kernel<MP, float, float, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(analysis_list_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(LIST_WARPS * list_warp_bytes<MP>(w)));
+    return launch_tile<MP, double, double>(h, cls, mean, spread, h->tol64, 0.0);
+  const float kthr = h->fp64_kappa > 0 ? (float)h->fp64_kappa : 0.f;
+  cudaError_t e = launch_tile<MP, float, float>(h, cls, mean, spread, (float)h->tol32, kthr);
+  if (e != cudaSuccess || kthr <= 0.f) return e;
+  return launch_list<MP>(h, cls, mean, spread);
+}
+
+template <int MP, typename S, typename T, int TI, int TJ>
+cudaError_t set_smem(int w) {
+  return cudaFuncSetAttribute(analysis_tile_kernel<MP, S, T, TI, TJ>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tile_layout<MP, S, T, TI, TJ>(w).total);
+}
+
+template <int MP>
+cudaError_t setup_class(letkf_ctx *h) {
+  int wmax = 0;
+  for (const LkInst &I : h->inst)
+    if (I.mp == MP) wmax = I.w > wmax ? I.w : wmax;
+  if (wmax == 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  if (h->precision == 1) {
+#define LK_SET(id, ti, tj) \
+  if (e == cudaSuccess) e = set_smem<MP, double, double, ti, tj>(wmax);
+    LK_FOR_SHAPES(LK_SET)
+#undef LK_SET
+    return e;
+  }
+#define LK_SET(id, ti, tj) \
+  if (e == cudaSuccess) e = set_smem<MP, float, float, ti, tj>(wmax);
+  LK_FOR_SHAPES(LK_SET)
+#undef LK_SET
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(analysis_list_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(LIST_WARPS * list_warp_bytes<MP>(wmax)));
+  return e;
 }
 
 }  // namespace
 
+int lk_num_tile_shapes() { return LK_NUM_SHAPES; }
+
+void lk_tile_shape(int s, int *ti, int *tj) {
+  switch (s) {
+#define LK_CASE(id, a, b) \
+  case id:                \
+    *ti = a;              \
+    *tj = b;              \
+    return;
+    LK_FOR_SHAPES(LK_CASE)
+#undef LK_CASE
+  }
+  *ti = LK_TILE_I;
+  *tj = LK_TILE_J;
+}
+
+int lk_width_class(int m) { return m <= 16 ? 0 : (m <= 32 ? 1 : 2); }
+
 // Raises the dynamic shared-memory limit of the analysis kernels this handle uses.
 cudaError_t lk_setup_analysis(letkf_ctx *h) {
-  return h->mp == 16 ? setup_all<16>(h) : setup_all<32>(h);
+  cudaError_t e = setup_class<16>(h);
+  if (e == cudaSuccess) e = setup_class<32>(h);
+  return e;
 }
 
 cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread) {
-  cudaError_t e = cudaMemsetAsync(h->counters + 1, 0, 3 * sizeof(int), h->stream);
-  if (e != cudaSuccess) return e;
-  return h->mp == 16 ? launch_all<16>(h, mean, spread) : launch_all<32>(h, mean, spread);
+  cudaError_t e = cudaMemsetAsync(h->counters + 1, 0, 7 * sizeof(int), h->stream);
+  if (e == cudaSuccess) e = launch_class<16>(h, 0, mean, spread);
+  if (e == cudaSuccess) e = launch_class<32>(h, 1, mean, spread);
+  return e;
 }
 
 // ===========================================================================
@@ -610,20 +696,21 @@ cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread) {
 // For callers that cannot allocate device memory at run time (for example a
 // real-time controller whose memory is fixed at start-up, or code running
 // where cudaMalloc is not permitted), this entry point analyses one frame
-// without creating a handle: its scratch (slope-anomaly grid, innovations,
-// node tables, counters) is the file-scope array below, which every GPU that
-// loads the library holds until the process exits.
+// without creating a handle: its scratch (instance descriptor, work lists,
+// node tables, slope-anomaly grid, innovations, counters) is the file-scope
+// array below, which every GPU that loads the library holds until the process
+// exits.
 // ===========================================================================
 namespace {
 
 constexpr int NA_MAX_NSUB = 128;
 constexpr int NA_MAX_W = 15;
 constexpr int NA_MAX_M = 32;
+constexpr int NA_TI = 2, NA_TJ = 4;
 constexpr int NA_NN = NA_MAX_NSUB + 1;
-constexpr int NA_GS_ROWS = ((NA_NN + LK_TILE_I - 1) / LK_TILE_I) * LK_TILE_I + NA_MAX_W;
-constexpr int NA_GS_COLS = ((NA_NN + LK_TILE_J - 1) / LK_TILE_J) * LK_TILE_J + NA_MAX_W;
-constexpr size_t NA_CELLS = (size_t)NA_GS_ROWS * NA_GS_COLS;
-constexpr int NA_MAX_TILES = ((NA_NN + LK_TILE_I - 1) / LK_TILE_I) * ((NA_NN + LK_TILE_J - 1) / LK_TILE_J);
+constexpr int NA_GS = ((NA_NN + LK_TILE_MAX - 1) / LK_TILE_MAX) * LK_TILE_MAX + NA_MAX_W;
+constexpr size_t NA_CELLS = (size_t)NA_GS * NA_GS;
+constexpr int NA_MAX_TILES = ((NA_NN + NA_TI - 1) / NA_TI) * ((NA_NN + NA_TJ - 1) / NA_TJ);
 // byte offsets inside the scratch array (each 256-aligned)
 constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t NA_OFF_YBP = 0;
@@ -631,10 +718,12 @@ constexpr size_t NA_OFF_DP = al256(NA_OFF_YBP + NA_CELLS * 2 * NA_MAX_M * sizeof
 constexpr size_t NA_OFF_PID = al256(NA_OFF_DP + NA_CELLS * 2 * sizeof(float));
 constexpr size_t NA_OFF_SAPS = al256(NA_OFF_PID + (size_t)NA_NN * NA_NN * sizeof(int));
 constexpr size_t NA_OFF_PTS = al256(NA_OFF_SAPS + (size_t)NA_MAX_NSUB * NA_MAX_NSUB * sizeof(int2));
-constexpr size_t NA_OFF_TILES = al256(NA_OFF_PTS + (size_t)NA_NN * NA_NN * sizeof(int2));
-constexpr size_t NA_OFF_TAPER = al256(NA_OFF_TILES + (size_t)NA_MAX_TILES * sizeof(int2));
-constexpr size_t NA_OFF_COUNTERS = al256(NA_OFF_TAPER + (size_t)NA_MAX_W * NA_MAX_W * sizeof(float));
-constexpr size_t NA_BYTES = al256(NA_OFF_COUNTERS + 4 * sizeof(int));
+constexpr size_t NA_OFF_OBS = al256(NA_OFF_PTS + (size_t)NA_NN * NA_NN * sizeof(int2));
+constexpr size_t NA_OFF_TILES = al256(NA_OFF_OBS + (size_t)NA_MAX_NSUB * NA_MAX_NSUB * sizeof(int2));
+constexpr size_t NA_OFF_TAPER = al256(NA_OFF_TILES + (size_t)NA_MAX_TILES * sizeof(LkTile));
+constexpr size_t NA_OFF_INST = al256(NA_OFF_TAPER + (size_t)NA_MAX_W * NA_MAX_W * sizeof(float));
+constexpr size_t NA_OFF_COUNTERS = al256(NA_OFF_INST + sizeof(LkInst));
+constexpr size_t NA_BYTES = al256(NA_OFF_COUNTERS + 8 * sizeof(int));
 
 // The scratch. Host code must not pass this name to a kernel: it is a host-side
 // stand-in; the device address comes from cudaGetSymbolAddress (na_scratch_address).
@@ -645,7 +734,8 @@ std::mutex g_na_mutex;
 int g_na_pid[NA_NN * NA_NN];
 int2 g_na_saps[NA_MAX_NSUB * NA_MAX_NSUB];
 int2 g_na_pts[NA_NN * NA_NN];
-int2 g_na_tiles[NA_MAX_TILES];
+int2 g_na_obs[NA_MAX_NSUB * NA_MAX_NSUB];
+LkTile g_na_tiles[NA_MAX_TILES];
 float g_na_taper[NA_MAX_W * NA_MAX_W];
 void *g_na_addr[256];          // scratch address per device, set once
 
@@ -664,51 +754,35 @@ double na_gaspari_cohn(double z) {
 
 // Variant of the analysis tile kernel for the allocation-free path: FP32,
 // eigenvectors accumulated from the identity (no per-node basis store, no FP64
-// queue), tables and scratch read from the static array.
+// queue), descriptor, tables and scratch read from the static array.
 template <int MP>
-__global__ void __launch_bounds__(LK_TILE_I *LK_TILE_J * 32)
-    analysis_noalloc_kernel(LkGeom g, const int2 *__restrict__ tiles, const float *__restrict__ Ybp,
-                            const float *__restrict__ dp, const float *__restrict__ taper,
-                            float *__restrict__ X, float *__restrict__ mean,
-                            float *__restrict__ spread, float alpha, float tol, int max_sweeps,
-                            int *__restrict__ counters) {
+__global__ void __launch_bounds__(NA_TI *NA_TJ * 32)
+    analysis_noalloc_kernel(const LkInst *__restrict__ insts, const LkTile *__restrict__ tiles,
+                            float *__restrict__ mean, float *__restrict__ spread, float tol,
+                            int max_sweeps, int *__restrict__ counters) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int w = g.w;
-  const TileLayout L = tile_layout<MP, float, float>(w);
-  const int HJ = LK_TILE_J + w - 1;
-  const int ncell = (LK_TILE_I + w - 1) * HJ;
+  const LkTile tl = tiles[blockIdx.x];
+  const LkInst &I = insts[tl.inst];
+  const int w = I.w;
+  const TileLayout L = tile_layout<MP, float, float, NA_TI, NA_TJ>(w);
+  const int HJ = NA_TJ + w - 1;
   float *halo = reinterpret_cast<float *>(smem + L.halo);
   float *dh = reinterpret_cast<float *>(smem + L.dh);
   float *tap = reinterpret_cast<float *>(smem + L.tap);
   float *scr = reinterpret_cast<float *>(smem + L.scr);
-  const int2 org = tiles[blockIdx.x];
-  const int m = g.m;
-  for (int e = threadIdx.x; e < ncell * 2 * MP; e += blockDim.x) {
-    const int cell = e / (2 * MP);
-    const int r = e - cell * 2 * MP;
-    const int c = r / MP;
-    const int mm = r - c * MP;
-    const int hi = cell / HJ, hj = cell - (cell / HJ) * HJ;
-    const size_t src = (size_t)(org.x + hi) * g.gs_cols + (org.y + hj);
-    halo[e] = mm < m ? Ybp[(src * 2 + c) * m + mm] : 0.f;
-  }
-  for (int e = threadIdx.x; e < ncell * 2; e += blockDim.x) {
-    const int cell = e >> 1;
-    const int hi = cell / HJ, hj = cell - (cell / HJ) * HJ;
-    const size_t src = (size_t)(org.x + hi) * g.gs_cols + (org.y + hj);
-    dh[e] = dp[src * 2 + (e & 1)];
-  }
-  for (int e = threadIdx.x; e < w * w; e += blockDim.x) tap[e] = taper[e];
+  stage_tile<MP, float, float, NA_TI, NA_TJ>(I, tl.i0, tl.j0, halo, dh, tap);
   __syncthreads();
   const int warp = threadIdx.x >> 5;
-  const int ti = warp / LK_TILE_J, tj = warp - (warp / LK_TILE_J) * LK_TILE_J;
-  const int i = org.x + ti, j = org.y + tj;
-  if (i > g.nsub || j > g.nsub) return;
-  const int pid = g.pid_map[i * (g.nsub + 1) + j];
+  const int ti = warp / NA_TJ, tj = warp - (warp / NA_TJ) * NA_TJ;
+  const int i = tl.i0 + ti, j = tl.j0 + tj;
+  if (i > I.nsub || j > I.nsub) return;
+  const int pid = I.pid_map[i * (I.nsub + 1) + j];
   if (pid < 0) return;
   const int off = ti * HJ + tj;
+  const int m = I.m;
   analyze_node_accum<MP, float, float>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m,
-                                       alpha, tol, max_sweeps, X + (size_t)pid * 2 * m,
+                                       float(I.alpha), tol, max_sweeps,
+                                       static_cast<float *>(I.X) + (size_t)pid * 2 * m,
                                        mean ? mean + 2 * pid : nullptr,
                                        spread ? spread + 2 * pid : nullptr,
                                        scr + (size_t)warp * scratch_elems<MP, float>(), counters,
@@ -761,8 +835,8 @@ extern "C" letkf_status letkf_analyze_noalloc(const letkf_config *cfg, void *X_d
   std::lock_guard<std::mutex> lock(g_na_mutex);
   if (e == cudaSuccess) e = na_scratch_address(dev, &base);
   const int mp = c.m <= 16 ? 16 : 32;
-  const size_t smem = mp == 16 ? tile_layout<16, float, float>(c.window).total
-                               : tile_layout<32, float, float>(c.window).total;
+  const size_t smem = mp == 16 ? tile_layout<16, float, float, NA_TI, NA_TJ>(c.window).total
+                               : tile_layout<32, float, float, NA_TI, NA_TJ>(c.window).total;
   if (e == cudaSuccess) e = mp == 16 ? na_setup_kernel<16>(smem) : na_setup_kernel<32>(smem);
   if (e != cudaSuccess) {
     na_error(errbuf, errlen, cudaGetErrorString(e));
@@ -776,6 +850,7 @@ extern "C" letkf_status letkf_analyze_noalloc(const letkf_config *cfg, void *X_d
   for (int s = 0; s < ns; ++s)
     for (int t = 0; t < ns; ++t)
       if (c.subap_mask[(size_t)s * ns + t]) {
+        g_na_obs[n_sap] = make_int2(0, n_sap);
         g_na_saps[n_sap++] = make_int2(s, t);
         g_na_pid[s * nn + t] = g_na_pid[(s + 1) * nn + t] = 0;
         g_na_pid[s * nn + t + 1] = g_na_pid[(s + 1) * nn + t + 1] = 0;
@@ -791,29 +866,51 @@ extern "C" letkf_status letkf_analyze_noalloc(const letkf_config *cfg, void *X_d
         g_na_pid[i * nn + j] = n_pts;
         g_na_pts[n_pts++] = make_int2(i, j);
       }
-  const int tiles_i = (nn + LK_TILE_I - 1) / LK_TILE_I, tiles_j = (nn + LK_TILE_J - 1) / LK_TILE_J;
   int n_tiles = 0;
-  for (int a = 0; a < tiles_i; ++a)
-    for (int b = 0; b < tiles_j; ++b) {
+  for (int i0 = 0; i0 < nn; i0 += NA_TI)
+    for (int j0 = 0; j0 < nn; j0 += NA_TJ) {
       bool any = false;
-      for (int di = 0; di < LK_TILE_I; ++di)
-        for (int dj = 0; dj < LK_TILE_J; ++dj) {
-          const int i = a * LK_TILE_I + di, j = b * LK_TILE_J + dj;
+      for (int di = 0; di < NA_TI; ++di)
+        for (int dj = 0; dj < NA_TJ; ++dj) {
+          const int i = i0 + di, j = j0 + dj;
           any = any || (i < nn && j < nn && g_na_pid[i * nn + j] >= 0);
         }
-      if (any) g_na_tiles[n_tiles++] = make_int2(a * LK_TILE_I, b * LK_TILE_J);
+      if (any) g_na_tiles[n_tiles++] = LkTile{0, i0, j0, 0};
     }
   const double cl = c.loc_len > 0 ? c.loc_len : w / 4.0;
   for (int ds = 0; ds < w; ++ds)
     for (int dt = 0; dt < w; ++dt) {
-      const double tau = c.taper == 1 ? na_gaspari_cohn(hypot(ds - hw + 0.5, dt - hw + 0.5) / cl) : 1.0;
+      const double tau =
+          c.taper == 1 ? na_gaspari_cohn(hypot(ds - hw + 0.5, dt - hw + 0.5) / cl) : 1.0;
       g_na_taper[ds * w + dt] = (float)(tau / c.sigma2);
     }
+  const int gs = ((nn + LK_TILE_MAX - 1) / LK_TILE_MAX) * LK_TILE_MAX + w;
+  LkInst inst;
+  memset(&inst, 0, sizeof(inst));
+  inst.nsub = ns;
+  inst.m = c.m;
+  inst.w = w;
+  inst.h = hw;
+  inst.mp = mp;
+  inst.n_pts = n_pts;
+  inst.n_sap = n_sap;
+  inst.p = 2 * n_sap;
+  inst.gs_rows = gs;
+  inst.gs_cols = gs;
+  inst.pid_map = reinterpret_cast<const int *>(base + NA_OFF_PID);
+  inst.pts = reinterpret_cast<const int2 *>(base + NA_OFF_PTS);
+  inst.saps = reinterpret_cast<const int2 *>(base + NA_OFF_SAPS);
+  inst.X = X_dev;
+  inst.Ybp = base + NA_OFF_YBP;
+  inst.dp = base + NA_OFF_DP;
+  inst.taper = base + NA_OFF_TAPER;
+  inst.alpha = (c.m - 1) / c.rho;
+  inst.a_ar1 = c.a_ar1;
+  inst.noise_std = c.noise_std;
 
   // ---- scratch: tables in, grids cleared (cells outside the pupil must read 0) ----
   cudaStream_t st = (cudaStream_t)stream;
-  const int gs_rows = tiles_i * LK_TILE_I + w, gs_cols = tiles_j * LK_TILE_J + w;
-  const size_t cells = (size_t)gs_rows * gs_cols;
+  const size_t cells = (size_t)gs * gs;
   struct Copy {
     size_t off;
     const void *src;
@@ -821,51 +918,37 @@ extern "C" letkf_status letkf_analyze_noalloc(const letkf_config *cfg, void *X_d
   } copies[] = {{NA_OFF_PID, g_na_pid, (size_t)nn * nn * sizeof(int)},
                 {NA_OFF_SAPS, g_na_saps, (size_t)n_sap * sizeof(int2)},
                 {NA_OFF_PTS, g_na_pts, (size_t)n_pts * sizeof(int2)},
-                {NA_OFF_TILES, g_na_tiles, (size_t)n_tiles * sizeof(int2)},
-                {NA_OFF_TAPER, g_na_taper, (size_t)w * w * sizeof(float)}};
+                {NA_OFF_OBS, g_na_obs, (size_t)n_sap * sizeof(int2)},
+                {NA_OFF_TILES, g_na_tiles, (size_t)n_tiles * sizeof(LkTile)},
+                {NA_OFF_TAPER, g_na_taper, (size_t)w * w * sizeof(float)},
+                {NA_OFF_INST, &inst, sizeof(LkInst)}};
   for (const Copy &cp : copies)
-    if (e == cudaSuccess) e = cudaMemcpyAsync(base + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(base + cp.off, cp.src, cp.bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + NA_OFF_YBP, 0, cells * 2 * c.m * sizeof(float), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + NA_OFF_DP, 0, cells * 2 * sizeof(float), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(base + NA_OFF_COUNTERS, 0, 4 * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + NA_OFF_COUNTERS, 0, 8 * sizeof(int), st);
 
   // ---- observation (shared kernel) and analysis (variant kernel) ----
   letkf_ctx tmp;
   tmp.stream = st;
   tmp.precision = 0;
-  tmp.g.nsub = ns;
-  tmp.g.m = c.m;
-  tmp.g.w = w;
-  tmp.g.h = hw;
-  tmp.g.n_pts = n_pts;
-  tmp.g.n_sap = n_sap;
-  tmp.g.p = 2 * n_sap;
-  tmp.g.gs_rows = gs_rows;
-  tmp.g.gs_cols = gs_cols;
-  tmp.g.pid_map = reinterpret_cast<const int *>(base + NA_OFF_PID);
-  tmp.g.pts = reinterpret_cast<const int2 *>(base + NA_OFF_PTS);
-  tmp.g.saps = reinterpret_cast<const int2 *>(base + NA_OFF_SAPS);
-  tmp.X = X_dev;
-  tmp.Ybp = base + NA_OFF_YBP;
-  tmp.dp = base + NA_OFF_DP;
+  tmp.n_inst = 1;
+  tmp.d_inst = reinterpret_cast<LkInst *>(base + NA_OFF_INST);
+  tmp.obs_items = reinterpret_cast<int2 *>(base + NA_OFF_OBS);
+  tmp.sap_total = n_sap;
+  tmp.p_total = 2 * n_sap;
   tmp.counters = reinterpret_cast<int *>(base + NA_OFF_COUNTERS);
   if (e == cudaSuccess) e = lk_launch_obs(&tmp, y_dev, nullptr);
   const int sweeps = c.max_sweeps > 0 ? c.max_sweeps : 20;
-  const float alpha = (float)((c.m - 1) / c.rho), tol = 4e-6f;
   if (e == cudaSuccess) {
-    const int threads = LK_TILE_I * LK_TILE_J * 32;
-    const int2 *tiles = reinterpret_cast<const int2 *>(base + NA_OFF_TILES);
-    const float *ybp = reinterpret_cast<const float *>(base + NA_OFF_YBP);
-    const float *dpp = reinterpret_cast<const float *>(base + NA_OFF_DP);
-    const float *tap = reinterpret_cast<const float *>(base + NA_OFF_TAPER);
+    const LkTile *tiles = reinterpret_cast<const LkTile *>(base + NA_OFF_TILES);
     if (mp == 16)
-      analysis_noalloc_kernel<16><<<n_tiles, threads, smem, st>>>(
-          tmp.g, tiles, ybp, dpp, tap, (float *)X_dev, (float *)mean_dev, (float *)spread_dev,
-          alpha, tol, sweeps, tmp.counters);
+      analysis_noalloc_kernel<16><<<n_tiles, NA_TI * NA_TJ * 32, smem, st>>>(
+          tmp.d_inst, tiles, (float *)mean_dev, (float *)spread_dev, 4e-6f, sweeps, tmp.counters);
     else
-      analysis_noalloc_kernel<32><<<n_tiles, threads, smem, st>>>(
-          tmp.g, tiles, ybp, dpp, tap, (float *)X_dev, (float *)mean_dev, (float *)spread_dev,
-          alpha, tol, sweeps, tmp.counters);
+      analysis_noalloc_kernel<32><<<n_tiles, NA_TI * NA_TJ * 32, smem, st>>>(
+          tmp.d_inst, tiles, (float *)mean_dev, (float *)spread_dev, 4e-6f, sweeps, tmp.counters);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {

@@ -9,8 +9,6 @@
 
 #include "letkf_common.cuh"
 
-cudaError_t lk_setup_analysis(letkf_ctx *h);
-
 namespace {
 
 thread_local std::string g_create_error;
@@ -27,10 +25,10 @@ letkf_status cuda_fail(letkf_ctx *h, cudaError_t e, const char *what) {
   return fail(h, LETKF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define LK_CUDA(h, call)                                  \
-  do {                                                    \
-    cudaError_t e_ = (call);                              \
-    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+#define LK_CUDA(h, call)                                      \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);  \
   } while (0)
 
 // Gaspari & Cohn (1999) compactly supported 5th-order piecewise rational
@@ -49,21 +47,25 @@ double gaspari_cohn(double z) {
 }
 
 template <typename T>
-letkf_status upload(letkf_ctx *h, T **dst, const void *src, size_t bytes) {
+letkf_status dalloc(letkf_ctx *h, T **dst, size_t bytes) {
   cudaError_t e = cudaMalloc((void **)dst, bytes ? bytes : 16);
-  if (e != cudaSuccess) return fail(h, LETKF_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-  if (src && bytes) {
-    e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy");
-  }
+  if (e != cudaSuccess)
+    return fail(h, LETKF_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   return LETKF_OK;
+}
+
+letkf_status upload(letkf_ctx *h, void *dst, const void *src, size_t bytes) {
+  if (!bytes) return LETKF_OK;
+  cudaError_t e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? LETKF_OK : cuda_fail(h, e, "cudaMemcpy");
 }
 
 void release(letkf_ctx *h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
-  void *bufs[] = {h->X,        h->Ybp,      h->dp,       h->taper,    h->pid_map,
-                  h->pts,      h->saps,     h->tiles,    h->bank,     h->counters,
-                  h->worklist, h->frame,    h->basis,    h->partial,  h->zero_scalar};
+  void *bufs[] = {h->X,          h->Ybp,      h->dp,       h->taper,    h->pid_map,
+                  h->pts,        h->saps,     h->bank,     h->basis,    h->counters,
+                  h->worklist,   h->frame,    h->partial,  h->d_inst,   h->obs_items,
+                  h->node_items, h->tiles[0], h->tiles[1], h->tiles[2]};
   for (void *p : bufs)
     if (p) cudaFree(p);
 }
@@ -71,19 +73,306 @@ void release(letkf_ctx *h) {
 // Makes the handle's device current for the duration of a call.
 struct DeviceGuard {
   int prev = -1;
-  bool ok = true;
   explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) {
-      ok = false;
-      return;
-    }
-    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    if (prev != dev) cudaSetDevice(dev);
   }
   ~DeviceGuard() {
     int cur;
     if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
   }
 };
+
+letkf_status check_config(const letkf_config &c) {
+  if (c.nsub < 1 || c.nsub > 1024) return fail(nullptr, LETKF_ERR_ARG, "nsub must be in 1..1024");
+  if (!c.subap_mask) return fail(nullptr, LETKF_ERR_ARG, "subap_mask is NULL");
+  if (c.m < 2 || c.m > 32) return fail(nullptr, LETKF_ERR_ARG, "m must be in 2..32");
+  if (c.window < 1 || c.window > 31) return fail(nullptr, LETKF_ERR_ARG, "window must be in 1..31");
+  if (c.taper != 0 && c.taper != 1) return fail(nullptr, LETKF_ERR_ARG, "taper must be 0 or 1");
+  if (!(c.rho > 0) || !(c.sigma2 > 0) || !isfinite(c.rho) || !isfinite(c.sigma2))
+    return fail(nullptr, LETKF_ERR_ARG, "rho and sigma2 must be finite and > 0");
+  if (!isfinite(c.a_ar1) || !isfinite(c.noise_std))
+    return fail(nullptr, LETKF_ERR_ARG, "a_ar1 and noise_std must be finite");
+  if (c.precision != 0 && c.precision != 1)
+    return fail(nullptr, LETKF_ERR_ARG, "precision must be 0 or 1");
+  if (c.noise_bank && (c.bank_B < 1 || c.bank_G < 1))
+    return fail(nullptr, LETKF_ERR_ARG, "bank_B and bank_G must be >= 1 with a noise bank");
+  return LETKF_OK;
+}
+
+// Per-instance host geometry before upload.
+struct HostInst {
+  std::vector<int> pid;
+  std::vector<int2> pts, saps;
+  std::vector<int32_t> wslopes;
+  std::vector<double> taper;
+};
+
+void build_geometry(const letkf_config &c, HostInst &g) {
+  const int ns = c.nsub, nn = ns + 1, w = c.window, hw = w / 2;
+  g.pid.assign((size_t)nn * nn, -1);
+  g.saps.clear();
+  g.pts.clear();
+  for (int s = 0; s < ns; ++s)
+    for (int t = 0; t < ns; ++t)
+      if (c.subap_mask[(size_t)s * ns + t]) {
+        g.saps.push_back(make_int2(s, t));
+        g.pid[(size_t)s * nn + t] = g.pid[(size_t)(s + 1) * nn + t] = 0;
+        g.pid[(size_t)s * nn + t + 1] = g.pid[(size_t)(s + 1) * nn + t + 1] = 0;
+      }
+  for (int i = 0; i < nn; ++i)
+    for (int j = 0; j < nn; ++j)
+      if (g.pid[(size_t)i * nn + j] == 0) {
+        g.pid[(size_t)i * nn + j] = (int)g.pts.size();
+        g.pts.push_back(make_int2(i, j));
+      }
+  g.wslopes.resize(g.pts.size());
+  for (size_t k = 0; k < g.pts.size(); ++k) {
+    int cnt = 0;
+    for (int s = g.pts[k].x - hw; s < g.pts[k].x - hw + w; ++s)
+      for (int t = g.pts[k].y - hw; t < g.pts[k].y - hw + w; ++t)
+        if (s >= 0 && s < ns && t >= 0 && t < ns && c.subap_mask[(size_t)s * ns + t]) cnt += 2;
+    g.wslopes[k] = cnt;
+  }
+  // taper weights tau / sigma2 by window offset: subaperture (s, t) = (i - h + ds, j - h + dt)
+  // has its centre at (ds - h + 0.5, dt - h + 0.5) pitches from node (i, j)
+  const double cl = c.loc_len > 0 ? c.loc_len : w / 4.0;
+  g.taper.resize((size_t)w * w);
+  for (int ds = 0; ds < w; ++ds)
+    for (int dt = 0; dt < w; ++dt) {
+      const double tau = c.taper == 1 ? gaspari_cohn(hypot(ds - hw + 0.5, dt - hw + 0.5) / cl) : 1.0;
+      g.taper[(size_t)ds * w + dt] = tau / c.sigma2;
+    }
+}
+
+int padded_grid(int nsub, int w) {
+  return ((nsub + 1 + LK_TILE_MAX - 1) / LK_TILE_MAX) * LK_TILE_MAX + w;
+}
+
+// Analysis tiles of one width class for its current tile shape, most
+// expensive first (cost: slopes in the tile's windows times mp^2).
+letkf_status build_tiles(letkf_ctx *h, int cls, const std::vector<std::vector<int>> &pids) {
+  int ti, tj;
+  lk_tile_shape(h->tile_shape[cls], &ti, &tj);
+  std::vector<LkTile> &tl = h->tiles_host[cls];
+  tl.clear();
+  for (int k = 0; k < h->n_inst; ++k) {
+    const LkInst &I = h->inst[k];
+    const int nn = I.nsub + 1;
+    if (lk_width_class(I.m) != cls) continue;
+    const std::vector<int> &pid = pids[k];
+    for (int i0 = 0; i0 < nn; i0 += ti)
+      for (int j0 = 0; j0 < nn; j0 += tj) {
+        long long cost = 0;
+        bool any = false;
+        for (int di = 0; di < ti; ++di)
+          for (int dj = 0; dj < tj; ++dj) {
+            const int i = i0 + di, j = j0 + dj;
+            if (i < nn && j < nn && pid[(size_t)i * nn + j] >= 0) {
+              any = true;
+              cost += h->wslopes_host[I.node_off + pid[(size_t)i * nn + j]];
+            }
+          }
+        if (any) tl.push_back(LkTile{k, i0, j0, (int)(cost * I.mp * I.mp / 32)});
+      }
+  }
+  std::stable_sort(tl.begin(), tl.end(),
+                   [](const LkTile &a, const LkTile &b) { return a.cost > b.cost; });
+  if (h->tiles[cls]) cudaFree(h->tiles[cls]);
+  h->tiles[cls] = nullptr;
+  letkf_status st = dalloc(h, &h->tiles[cls], tl.size() * sizeof(LkTile));
+  if (st != LETKF_OK) return st;
+  h->n_tiles[cls] = (int)tl.size();
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return upload(h, h->tiles[cls], tl.data(), tl.size() * sizeof(LkTile));
+}
+
+letkf_status rebuild_tiles(letkf_ctx *h, int cls) {
+  std::vector<std::vector<int>> pids(h->n_inst);
+  for (int k = 0; k < h->n_inst; ++k) {
+    const LkInst &I = h->inst[k];
+    if (lk_width_class(I.m) != cls) continue;
+    pids[k].resize((size_t)(I.nsub + 1) * (I.nsub + 1));
+    cudaError_t e = cudaMemcpy(pids[k].data(), I.pid_map, pids[k].size() * sizeof(int),
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy");
+  }
+  return build_tiles(h, cls, pids);
+}
+
+letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t *out) {
+  if (!out) return fail(nullptr, LETKF_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfgs || n < 1) return fail(nullptr, LETKF_ERR_ARG, "need at least one configuration");
+  for (int k = 0; k < n; ++k) {
+    letkf_status st = check_config(cfgs[k]);
+    if (st != LETKF_OK) return st;
+    if (cfgs[k].precision != cfgs[0].precision)
+      return fail(nullptr, LETKF_ERR_ARG, "all instances of a batch share one precision");
+  }
+  letkf_ctx *h = new (std::nothrow) letkf_ctx();
+  if (!h) return fail(nullptr, LETKF_ERR_NOMEM, "host allocation failed");
+  h->cfg = cfgs[0];
+  h->cfg.subap_mask = nullptr;
+  h->cfg.noise_bank = nullptr;
+  h->stream = (cudaStream_t)stream;
+  h->precision = cfgs[0].precision;
+  h->rsz = h->precision ? sizeof(double) : sizeof(float);
+  h->max_sweeps = cfgs[0].max_sweeps > 0 ? cfgs[0].max_sweeps : 20;
+  h->fp64_kappa = cfgs[0].fp64_kappa;
+  h->n_inst = n;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return fail(nullptr, LETKF_ERR_CUDA, "no CUDA device");
+  }
+  std::vector<HostInst> geo(n);
+  for (int k = 0; k < n; ++k) {
+    build_geometry(cfgs[k], geo[k]);
+    if (geo[k].saps.empty()) {
+      delete h;
+      return fail(nullptr, LETKF_ERR_ARG, "subap_mask has no valid subaperture");
+    }
+  }
+  // ---- sizes and offsets ----
+  h->inst.resize(n);
+  size_t n_ybp = 0, n_dp = 0, n_tap = 0, n_pid = 0, n_basis = 0, n_bank = 0;
+  for (int k = 0; k < n; ++k) {
+    const letkf_config &c = cfgs[k];
+    LkInst &I = h->inst[k];
+    memset(&I, 0, sizeof(I));
+    I.nsub = c.nsub;
+    I.m = c.m;
+    I.w = c.window;
+    I.h = c.window / 2;
+    I.mp = c.m <= 16 ? 16 : 32;
+    I.n_pts = (int)geo[k].pts.size();
+    I.n_sap = (int)geo[k].saps.size();
+    I.p = 2 * I.n_sap;
+    I.gs_rows = padded_grid(c.nsub, c.window);
+    I.gs_cols = padded_grid(c.nsub, c.window);
+    I.alpha = (c.m - 1) / c.rho;
+    I.a_ar1 = c.a_ar1;
+    I.noise_std = c.noise_std;
+    I.seed = c.seed;
+    I.y_off = h->p_total;
+    I.node_off = h->n_pts_total;
+    I.noise_off = h->noise_total;
+    I.state_off = h->state_total;
+    h->p_total += I.p;
+    h->n_pts_total += I.n_pts;
+    h->noise_total += (long long)I.n_pts * I.m;
+    h->state_total += 2LL * I.n_pts * I.m;
+    h->sap_total += I.n_sap;
+    n_ybp += (size_t)I.gs_rows * I.gs_cols * 2 * I.m;
+    n_dp += (size_t)I.gs_rows * I.gs_cols * 2;
+    n_tap += (size_t)I.w * I.w;
+    n_pid += (size_t)(c.nsub + 1) * (c.nsub + 1);
+    n_basis += (size_t)I.n_pts * I.mp * I.mp;
+    if (c.noise_bank) n_bank += (size_t)c.bank_B * c.bank_G * c.bank_G;
+  }
+  letkf_status st = LETKF_OK;
+#define LK_TRY(x)               \
+  do {                          \
+    st = (x);                   \
+    if (st != LETKF_OK) {       \
+      g_create_error = h->err;  \
+      release(h);               \
+      delete h;                 \
+      return st;                \
+    }                           \
+  } while (0)
+  LK_TRY(dalloc(h, &h->X, h->state_total * h->rsz));
+  LK_TRY(dalloc(h, &h->Ybp, n_ybp * h->rsz));
+  LK_TRY(dalloc(h, &h->dp, n_dp * h->rsz));
+  LK_TRY(dalloc(h, &h->taper, n_tap * h->rsz));
+  LK_TRY(dalloc(h, &h->pid_map, n_pid * sizeof(int)));
+  LK_TRY(dalloc(h, &h->pts, h->n_pts_total * sizeof(int2)));
+  LK_TRY(dalloc(h, &h->saps, h->sap_total * sizeof(int2)));
+  LK_TRY(dalloc(h, &h->basis, n_basis * sizeof(float)));
+  LK_TRY(dalloc(h, &h->bank, n_bank * sizeof(float)));
+  LK_TRY(dalloc(h, &h->counters, 8 * sizeof(int)));
+  LK_TRY(dalloc(h, &h->worklist, 3 * h->n_pts_total * sizeof(int2)));
+  LK_TRY(dalloc(h, &h->frame, 2 * sizeof(long long)));
+  LK_TRY(dalloc(h, &h->partial, (size_t)n * LK_RES_BLOCKS * sizeof(double2)));
+  LK_TRY(dalloc(h, &h->d_inst, (size_t)n * sizeof(LkInst)));
+  LK_TRY(dalloc(h, &h->obs_items, h->sap_total * sizeof(int2)));
+  LK_TRY(dalloc(h, &h->node_items, h->n_pts_total * sizeof(int2)));
+  // ---- slice buffers, upload tables ----
+  size_t o_ybp = 0, o_dp = 0, o_tap = 0, o_pid = 0, o_basis = 0, o_bank = 0, o_pts = 0, o_sap = 0;
+  std::vector<int2> obs_items, node_items;
+  std::vector<std::vector<int>> pids(n);
+  for (int k = 0; k < n; ++k) {
+    const letkf_config &c = cfgs[k];
+    LkInst &I = h->inst[k];
+    const HostInst &G = geo[k];
+    I.X = static_cast<char *>(h->X) + I.state_off * h->rsz;
+    I.Ybp = static_cast<char *>(h->Ybp) + o_ybp * h->rsz;
+    I.dp = static_cast<char *>(h->dp) + o_dp * h->rsz;
+    I.taper = static_cast<char *>(h->taper) + o_tap * h->rsz;
+    I.pid_map = h->pid_map + o_pid;
+    I.pts = h->pts + o_pts;
+    I.saps = h->saps + o_sap;
+    I.basis = h->basis + o_basis;
+    if (h->precision) {
+      LK_TRY(upload(h, (void *)I.taper, G.taper.data(), G.taper.size() * sizeof(double)));
+    } else {
+      std::vector<float> t32(G.taper.begin(), G.taper.end());
+      LK_TRY(upload(h, (void *)I.taper, t32.data(), t32.size() * sizeof(float)));
+    }
+    LK_TRY(upload(h, (void *)I.pid_map, G.pid.data(), G.pid.size() * sizeof(int)));
+    LK_TRY(upload(h, (void *)I.pts, G.pts.data(), G.pts.size() * sizeof(int2)));
+    LK_TRY(upload(h, (void *)I.saps, G.saps.data(), G.saps.size() * sizeof(int2)));
+    {
+      const size_t mp = (size_t)I.mp;
+      std::vector<float> eye((size_t)I.n_pts * mp * mp, 0.f);
+      for (size_t g = 0; g < (size_t)I.n_pts; ++g)
+        for (size_t q = 0; q < mp; ++q) eye[(g * mp + q) * mp + q] = 1.f;
+      LK_TRY(upload(h, I.basis, eye.data(), eye.size() * sizeof(float)));
+    }
+    if (c.noise_bank) {
+      I.bank = h->bank + o_bank;
+      I.bank_B = c.bank_B;
+      I.bank_G = c.bank_G;
+      LK_TRY(upload(h, (void *)I.bank, c.noise_bank,
+                    (size_t)c.bank_B * c.bank_G * c.bank_G * sizeof(float)));
+      o_bank += (size_t)c.bank_B * c.bank_G * c.bank_G;
+    }
+    for (int q = 0; q < I.n_sap; ++q) obs_items.push_back(make_int2(k, q));
+    for (int q = 0; q < I.n_pts; ++q) node_items.push_back(make_int2(k, q));
+    for (size_t q = 0; q < G.pts.size(); ++q) {
+      h->pts_host.push_back(G.pts[q].x);
+      h->pts_host.push_back(G.pts[q].y);
+      h->wslopes_host.push_back(G.wslopes[q]);
+    }
+    pids[k] = G.pid;
+    o_ybp += (size_t)I.gs_rows * I.gs_cols * 2 * I.m;
+    o_dp += (size_t)I.gs_rows * I.gs_cols * 2;
+    o_tap += (size_t)I.w * I.w;
+    o_pid += (size_t)(c.nsub + 1) * (c.nsub + 1);
+    o_basis += (size_t)I.n_pts * I.mp * I.mp;
+    o_pts += G.pts.size();
+    o_sap += G.saps.size();
+  }
+  LK_TRY(upload(h, h->d_inst, h->inst.data(), (size_t)n * sizeof(LkInst)));
+  LK_TRY(upload(h, h->obs_items, obs_items.data(), obs_items.size() * sizeof(int2)));
+  LK_TRY(upload(h, h->node_items, node_items.data(), node_items.size() * sizeof(int2)));
+  cudaError_t e = cudaMemset(h->X, 0, h->state_total * h->rsz);
+  if (e == cudaSuccess) e = cudaMemset(h->Ybp, 0, n_ybp * h->rsz);
+  if (e == cudaSuccess) e = cudaMemset(h->dp, 0, n_dp * h->rsz);
+  if (e == cudaSuccess) e = cudaMemset(h->counters, 0, 8 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->frame, 0, 2 * sizeof(long long));
+  if (e != cudaSuccess) LK_TRY(cuda_fail(h, e, "cudaMemset"));
+  for (int cls = 0; cls < 3; ++cls) LK_TRY(build_tiles(h, cls, pids));
+  e = lk_setup_analysis(h);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) LK_TRY(cuda_fail(h, e, "device set-up"));
+#undef LK_TRY
+  *out = h;
+  return LETKF_OK;
+}
 
 letkf_status enqueue_frame(letkf_ctx *h, const void *y_seq, const void *truth_seq,
                            double *resvar) {
@@ -96,173 +385,26 @@ letkf_status enqueue_frame(letkf_ctx *h, const void *y_seq, const void *truth_se
   return LETKF_OK;
 }
 
+bool all_have_banks(const letkf_ctx *h) {
+  for (const LkInst &I : h->inst)
+    if (!I.bank) return false;
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
 
 letkf_status letkf_create(const letkf_config *cfg, void *stream, letkf_t *out) {
-  if (!out) return fail(nullptr, LETKF_ERR_ARG, "out is NULL");
-  *out = nullptr;
-  if (!cfg) return fail(nullptr, LETKF_ERR_ARG, "cfg is NULL");
-  const letkf_config &c = *cfg;
-  if (c.nsub < 1 || c.nsub > 1024) return fail(nullptr, LETKF_ERR_ARG, "nsub must be in 1..1024");
-  if (!c.subap_mask) return fail(nullptr, LETKF_ERR_ARG, "subap_mask is NULL");
-  if (c.m < 2 || c.m > 32) return fail(nullptr, LETKF_ERR_ARG, "m must be in 2..32");
-  if (c.window < 1 || c.window > 31) return fail(nullptr, LETKF_ERR_ARG, "window must be in 1..31");
-  if (c.taper != 0 && c.taper != 1) return fail(nullptr, LETKF_ERR_ARG, "taper must be 0 or 1");
-  if (!(c.rho > 0) || !(c.sigma2 > 0) || !isfinite(c.rho) || !isfinite(c.sigma2))
-    return fail(nullptr, LETKF_ERR_ARG, "rho and sigma2 must be finite and > 0");
-  if (!isfinite(c.a_ar1) || !isfinite(c.noise_std))
-    return fail(nullptr, LETKF_ERR_ARG, "a_ar1 and noise_std must be finite");
-  if (c.precision != 0 && c.precision != 1) return fail(nullptr, LETKF_ERR_ARG, "precision must be 0 or 1");
-  if (c.noise_bank && (c.bank_B < 1 || c.bank_G < 1))
-    return fail(nullptr, LETKF_ERR_ARG, "bank_B and bank_G must be >= 1 with a noise bank");
+  if (!cfg) {
+    if (out) *out = nullptr;
+    return fail(nullptr, LETKF_ERR_ARG, "cfg is NULL");
+  }
+  return build_handle(cfg, 1, stream, out);
+}
 
-  letkf_ctx *h = new (std::nothrow) letkf_ctx();
-  if (!h) return fail(nullptr, LETKF_ERR_NOMEM, "host allocation failed");
-  h->cfg = c;
-  h->cfg.subap_mask = nullptr;
-  h->cfg.noise_bank = nullptr;
-  h->stream = (cudaStream_t)stream;
-  h->precision = c.precision;
-  h->rsz = c.precision ? sizeof(double) : sizeof(float);
-  h->mp = c.m <= 16 ? 16 : 32;
-  h->max_sweeps = c.max_sweeps > 0 ? c.max_sweeps : 20;
-  h->alpha = (c.m - 1) / c.rho;
-  h->tol32 = 4e-6;
-  h->tol64 = 1e-13;
-  if (cudaGetDevice(&h->device) != cudaSuccess) {
-    delete h;
-    return fail(nullptr, LETKF_ERR_CUDA, "no CUDA device");
-  }
-
-  // ---- geometry (host) ----
-  const int ns = c.nsub, nn = ns + 1, w = c.window, hw = w / 2;
-  std::vector<uint8_t> mask(c.subap_mask, c.subap_mask + (size_t)ns * ns);
-  std::vector<int> pid((size_t)nn * nn, -1);
-  std::vector<int2> saps;
-  for (int s = 0; s < ns; ++s)
-    for (int t = 0; t < ns; ++t)
-      if (mask[(size_t)s * ns + t]) {
-        saps.push_back(make_int2(s, t));
-        pid[(size_t)s * nn + t] = pid[(size_t)(s + 1) * nn + t] = 0;
-        pid[(size_t)s * nn + t + 1] = pid[(size_t)(s + 1) * nn + t + 1] = 0;
-      }
-  if (saps.empty()) {
-    delete h;
-    return fail(nullptr, LETKF_ERR_ARG, "subap_mask has no valid subaperture");
-  }
-  std::vector<int2> pts;
-  for (int i = 0; i < nn; ++i)
-    for (int j = 0; j < nn; ++j)
-      if (pid[(size_t)i * nn + j] == 0) {
-        pid[(size_t)i * nn + j] = (int)pts.size();
-        pts.push_back(make_int2(i, j));
-      }
-  h->g.nsub = ns;
-  h->g.m = c.m;
-  h->g.w = w;
-  h->g.h = hw;
-  h->g.n_pts = (int)pts.size();
-  h->g.n_sap = (int)saps.size();
-  h->g.p = 2 * h->g.n_sap;
-  const int tiles_i = (nn + LK_TILE_I - 1) / LK_TILE_I, tiles_j = (nn + LK_TILE_J - 1) / LK_TILE_J;
-  h->g.gs_rows = tiles_i * LK_TILE_I + w;
-  h->g.gs_cols = tiles_j * LK_TILE_J + w;
-  h->pts_host.resize(2 * pts.size());
-  h->wslopes_host.resize(pts.size());
-  for (size_t k = 0; k < pts.size(); ++k) {
-    h->pts_host[2 * k] = pts[k].x;
-    h->pts_host[2 * k + 1] = pts[k].y;
-    int cnt = 0;
-    for (int s = pts[k].x - hw; s < pts[k].x - hw + w; ++s)
-      for (int t = pts[k].y - hw; t < pts[k].y - hw + w; ++t)
-        if (s >= 0 && s < ns && t >= 0 && t < ns && mask[(size_t)s * ns + t]) cnt += 2;
-    h->wslopes_host[k] = cnt;
-  }
-  // taper weights tau / sigma2 by window offset: the subaperture (s, t) =
-  // (i - h + ds, j - h + dt) has its centre at (ds - h + 0.5, dt - h + 0.5) pitches from node (i, j)
-  const double cl = c.loc_len > 0 ? c.loc_len : w / 4.0;
-  std::vector<double> tap64((size_t)w * w);
-  for (int ds = 0; ds < w; ++ds)
-    for (int dt = 0; dt < w; ++dt) {
-      const double dist = hypot(ds - hw + 0.5, dt - hw + 0.5);
-      const double tau = c.taper == 1 ? gaspari_cohn(dist / cl) : 1.0;
-      tap64[(size_t)ds * w + dt] = tau / c.sigma2;
-    }
-  std::vector<float> tap32(tap64.begin(), tap64.end());
-  std::vector<int2> tiles;
-  for (int a = 0; a < tiles_i; ++a)
-    for (int b = 0; b < tiles_j; ++b) {
-      bool any = false;
-      for (int di = 0; di < LK_TILE_I && !any; ++di)
-        for (int dj = 0; dj < LK_TILE_J && !any; ++dj) {
-          const int i = a * LK_TILE_I + di, j = b * LK_TILE_J + dj;
-          if (i < nn && j < nn && pid[(size_t)i * nn + j] >= 0) any = true;
-        }
-      if (any) tiles.push_back(make_int2(a * LK_TILE_I, b * LK_TILE_J));
-    }
-  h->n_tiles = (int)tiles.size();
-
-  // ---- device state ----
-  letkf_status st;
-  const size_t npt = (size_t)h->g.n_pts, m = (size_t)c.m;
-  const size_t ncell = (size_t)h->g.gs_rows * h->g.gs_cols;
-#define LK_TRY(x)    \
-  do {               \
-    st = (x);        \
-    if (st != LETKF_OK) { \
-      g_create_error = h->err; \
-      release(h);    \
-      delete h;      \
-      return st;     \
-    }                \
-  } while (0)
-  LK_TRY(upload(h, &h->X, nullptr, npt * 2 * m * h->rsz));
-  LK_TRY(upload(h, &h->Ybp, nullptr, ncell * 2 * m * h->rsz));
-  LK_TRY(upload(h, &h->dp, nullptr, ncell * 2 * h->rsz));
-  LK_TRY(upload(h, &h->taper, c.precision ? (const void *)tap64.data() : (const void *)tap32.data(),
-                (size_t)w * w * h->rsz));
-  LK_TRY(upload(h, &h->pid_map, pid.data(), pid.size() * sizeof(int)));
-  LK_TRY(upload(h, &h->pts, pts.data(), pts.size() * sizeof(int2)));
-  LK_TRY(upload(h, &h->saps, saps.data(), saps.size() * sizeof(int2)));
-  LK_TRY(upload(h, &h->tiles, tiles.data(), tiles.size() * sizeof(int2)));
-  LK_TRY(upload(h, &h->counters, nullptr, 4 * sizeof(int)));
-  LK_TRY(upload(h, &h->worklist, nullptr, npt * sizeof(int)));
-  LK_TRY(upload(h, &h->frame, nullptr, 2 * sizeof(long long)));
-  LK_TRY(upload(h, &h->partial, nullptr, LK_RES_BLOCKS * sizeof(double2)));
-  {
-    // every node's eigenbasis starts as the identity
-    const size_t mp = (size_t)h->mp;
-    std::vector<float> eye(npt * mp * mp, 0.f);
-    for (size_t g = 0; g < npt; ++g)
-      for (size_t k = 0; k < mp; ++k) eye[(g * mp + k) * mp + k] = 1.f;
-    LK_TRY(upload(h, &h->basis, eye.data(), eye.size() * sizeof(float)));
-  }
-  if (c.noise_bank) {
-    h->bank_B = c.bank_B;
-    h->bank_G = c.bank_G;
-    LK_TRY(upload(h, &h->bank, c.noise_bank, (size_t)c.bank_B * c.bank_G * c.bank_G * sizeof(float)));
-  }
-#undef LK_TRY
-  h->g.pid_map = h->pid_map;
-  h->g.pts = h->pts;
-  h->g.saps = h->saps;
-  cudaError_t e = cudaMemset(h->X, 0, npt * 2 * m * h->rsz);
-  if (e == cudaSuccess) e = cudaMemset(h->Ybp, 0, ncell * 2 * m * h->rsz);
-  if (e == cudaSuccess) e = cudaMemset(h->dp, 0, ncell * 2 * h->rsz);
-  if (e == cudaSuccess) e = cudaMemset(h->counters, 0, 4 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(h->frame, 0, 2 * sizeof(long long));
-  if (e == cudaSuccess) e = lk_setup_analysis(h);
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) {
-    g_create_error = std::string("device set-up: ") + cudaGetErrorString(e);
-    release(h);
-    delete h;
-    return LETKF_ERR_CUDA;
-  }
-  *out = h;
-  return LETKF_OK;
+letkf_status letkf_create_batch(const letkf_config *cfgs, int32_t n, void *stream, letkf_t *out) {
+  return build_handle(cfgs, n, stream, out);
 }
 
 letkf_status letkf_destroy(letkf_t h) {
@@ -276,9 +418,20 @@ letkf_status letkf_destroy(letkf_t h) {
 
 letkf_status letkf_query(letkf_t h, int32_t *n_pts, int32_t *p, int32_t *m) {
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
-  if (n_pts) *n_pts = h->g.n_pts;
-  if (p) *p = h->g.p;
-  if (m) *m = h->g.m;
+  if (n_pts) *n_pts = (int32_t)h->n_pts_total;
+  if (p) *p = (int32_t)h->p_total;
+  if (m) *m = h->n_inst == 1 ? h->inst[0].m : 0;
+  return LETKF_OK;
+}
+
+letkf_status letkf_query_instance(letkf_t h, int32_t i, int32_t *n_pts, int32_t *p, int32_t *m,
+                                  int32_t *n_inst) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (n_inst) *n_inst = h->n_inst;
+  if (i < 0 || i >= h->n_inst) return fail(h, LETKF_ERR_ARG, "instance index out of range");
+  if (n_pts) *n_pts = h->inst[i].n_pts;
+  if (p) *p = h->inst[i].p;
+  if (m) *m = h->inst[i].m;
   return LETKF_OK;
 }
 
@@ -294,8 +447,8 @@ letkf_status letkf_get_state(letkf_t h, void *X_dev) {
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
   if (!X_dev) return fail(h, LETKF_ERR_ARG, "X_dev is NULL");
   DeviceGuard dg(h->device);
-  LK_CUDA(h, cudaMemcpyAsync(X_dev, h->X, (size_t)h->g.n_pts * 2 * h->g.m * h->rsz,
-                             cudaMemcpyDeviceToDevice, h->stream));
+  LK_CUDA(h, cudaMemcpyAsync(X_dev, h->X, h->state_total * h->rsz, cudaMemcpyDeviceToDevice,
+                             h->stream));
   return LETKF_OK;
 }
 
@@ -303,15 +456,15 @@ letkf_status letkf_set_state(letkf_t h, const void *X_dev) {
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
   if (!X_dev) return fail(h, LETKF_ERR_ARG, "X_dev is NULL");
   DeviceGuard dg(h->device);
-  LK_CUDA(h, cudaMemcpyAsync(h->X, X_dev, (size_t)h->g.n_pts * 2 * h->g.m * h->rsz,
-                             cudaMemcpyDeviceToDevice, h->stream));
+  LK_CUDA(h, cudaMemcpyAsync(h->X, X_dev, h->state_total * h->rsz, cudaMemcpyDeviceToDevice,
+                             h->stream));
   return LETKF_OK;
 }
 
 letkf_status letkf_forecast(letkf_t h, const void *noise_dev) {
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
-  if (!noise_dev && !h->bank)
-    return fail(h, LETKF_ERR_STATE, "no noise given and the handle has no noise bank");
+  if (!noise_dev && !all_have_banks(h))
+    return fail(h, LETKF_ERR_STATE, "no noise given and an instance has no noise bank");
   DeviceGuard dg(h->device);
   LK_CUDA(h, lk_launch_forecast(h, noise_dev));
   LK_CUDA(h, lk_launch_tick(h));
@@ -330,7 +483,8 @@ letkf_status letkf_analyze(letkf_t h, const void *y_dev, void *mean_dev, void *s
 
 letkf_status letkf_residual(letkf_t h, const void *truth_dev, double *resvar_dev) {
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
-  if (!truth_dev || !resvar_dev) return fail(h, LETKF_ERR_ARG, "truth_dev and resvar_dev are required");
+  if (!truth_dev || !resvar_dev)
+    return fail(h, LETKF_ERR_ARG, "truth_dev and resvar_dev are required");
   DeviceGuard dg(h->device);
   LK_CUDA(h, lk_launch_residual(h, truth_dev, resvar_dev, nullptr));
   return LETKF_OK;
@@ -341,7 +495,8 @@ letkf_status letkf_run(letkf_t h, int32_t frames, const void *y_seq_dev, const v
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
   if (frames < 0) return fail(h, LETKF_ERR_ARG, "frames < 0");
   if (!y_seq_dev) return fail(h, LETKF_ERR_ARG, "y_seq_dev is NULL");
-  if (!h->bank) return fail(h, LETKF_ERR_STATE, "letkf_run needs a noise bank");
+  if (!all_have_banks(h))
+    return fail(h, LETKF_ERR_STATE, "letkf_run needs a noise bank for every instance");
   if (use_graph && h->stream == nullptr)
     return fail(h, LETKF_ERR_STATE, "graph capture needs a non-default stream");
   DeviceGuard dg(h->device);
@@ -381,6 +536,102 @@ letkf_status letkf_run(letkf_t h, int32_t frames, const void *y_seq_dev, const v
   return LETKF_OK;
 }
 
+letkf_status letkf_tile_shape(int32_t shape, int32_t *tile_i, int32_t *tile_j) {
+  if (shape < 0 || shape >= lk_num_tile_shapes())
+    return fail(nullptr, LETKF_ERR_ARG, "no such tile shape");
+  int a, b;
+  lk_tile_shape(shape, &a, &b);
+  if (tile_i) *tile_i = a;
+  if (tile_j) *tile_j = b;
+  return LETKF_OK;
+}
+
+letkf_status letkf_set_tile_shape(letkf_t h, int32_t width_class, int32_t shape) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (width_class < 0 || width_class > 2 || shape < 0 || shape >= lk_num_tile_shapes())
+    return fail(h, LETKF_ERR_ARG, "width class or tile shape out of range");
+  DeviceGuard dg(h->device);
+  LK_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->tile_shape[width_class] = shape;
+  return rebuild_tiles(h, width_class);
+}
+
+letkf_status letkf_autotune(letkf_t h, const void *y_dev, int32_t reps, int32_t *shapes_out,
+                            float *us_out) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (!y_dev || reps < 1) return fail(h, LETKF_ERR_ARG, "y_dev and reps >= 1 are required");
+  DeviceGuard dg(h->device);
+  LK_CUDA(h, cudaStreamSynchronize(h->stream));
+  const int ns = lk_num_tile_shapes();
+  // every timed analysis starts from the same ensemble and eigenbases
+  size_t n_basis = 0;
+  for (const LkInst &I : h->inst) n_basis += (size_t)I.n_pts * I.mp * I.mp;
+  void *x_save = nullptr;
+  float *b_save = nullptr;
+  LK_CUDA(h, cudaMalloc(&x_save, h->state_total * h->rsz));
+  cudaError_t e = cudaMalloc((void **)&b_save, n_basis * sizeof(float) + 16);
+  if (e != cudaSuccess) {
+    cudaFree(x_save);
+    return cuda_fail(h, e, "cudaMalloc");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  letkf_status st = LETKF_OK;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(x_save, h->X, h->state_total * h->rsz, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b_save, h->basis, n_basis * sizeof(float), cudaMemcpyDeviceToDevice,
+                        h->stream);
+  for (int cls = 0; cls < 3 && e == cudaSuccess && st == LETKF_OK; ++cls) {
+    if (shapes_out) shapes_out[cls] = h->tile_shape[cls];
+    if (us_out) us_out[cls] = 0.f;
+    if (h->n_tiles[cls] == 0) continue;
+    int best = h->tile_shape[cls];
+    float best_ms = 1e30f;
+    for (int s = 0; s < ns && e == cudaSuccess && st == LETKF_OK; ++s) {
+      h->tile_shape[cls] = s;
+      st = rebuild_tiles(h, cls);
+      float total = 0.f;
+      for (int r = 0; r <= reps && e == cudaSuccess && st == LETKF_OK; ++r) {  // r = 0 warms up
+        e = cudaMemcpyAsync(h->X, x_save, h->state_total * h->rsz, cudaMemcpyDeviceToDevice,
+                            h->stream);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(h->basis, b_save, n_basis * sizeof(float), cudaMemcpyDeviceToDevice,
+                              h->stream);
+        if (e == cudaSuccess) e = lk_launch_obs(h, y_dev, nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        if (e == cudaSuccess) e = lk_launch_analysis(h, nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) total += ms;
+      }
+      if (e == cudaSuccess && st == LETKF_OK && total < best_ms) {
+        best_ms = total;
+        best = s;
+      }
+    }
+    if (shapes_out) shapes_out[cls] = best;
+    if (us_out) us_out[cls] = 1e3f * best_ms / reps;
+    h->tile_shape[cls] = best;
+    if (st == LETKF_OK && e == cudaSuccess) st = rebuild_tiles(h, cls);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->X, x_save, h->state_total * h->rsz, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->basis, b_save, n_basis * sizeof(float), cudaMemcpyDeviceToDevice,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(x_save);
+  cudaFree(b_save);
+  if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+  return st;
+}
+
 letkf_status letkf_sync(letkf_t h) {
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
   DeviceGuard dg(h->device);
@@ -400,7 +651,7 @@ letkf_status letkf_stats(letkf_t h, int32_t *fp64_points, int32_t *max_sweeps,
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
   DeviceGuard dg(h->device);
   LK_CUDA(h, cudaStreamSynchronize(h->stream));
-  int c[4];
+  int c[8];
   LK_CUDA(h, cudaMemcpy(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost));
   if (fp64_points) *fp64_points = c[1];
   if (max_sweeps) *max_sweeps = c[2];
@@ -408,8 +659,6 @@ letkf_status letkf_stats(letkf_t h, int32_t *fp64_points, int32_t *max_sweeps,
   return LETKF_OK;
 }
 
-const char *letkf_last_error(letkf_t h) {
-  return h ? h->err.c_str() : g_create_error.c_str();
-}
+const char *letkf_last_error(letkf_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 }  // extern "C"

@@ -16,55 +16,80 @@ enum : int {
   LK_BIT_TIMEOUT = 4,
 };
 
-// Node tile processed by one analysis CTA: TI x TJ nodes.
+// Default node tile of one analysis CTA (TI x TJ nodes, one warp each); the
+// autotuner may choose another of the compiled shapes.
 constexpr int LK_TILE_I = 2;
 constexpr int LK_TILE_J = 4;
-// Extra padding of the slope-anomaly grid so that every tile's halo is in bounds.
+// Padding of the slope-anomaly grid: tiles up to this many nodes per side keep
+// their halo in bounds.
 constexpr int LK_TILE_MAX = 8;
-// CTAs of the residual reduction (fixed, so the sum order is fixed).
+// CTAs of the residual reduction per instance (fixed, so the sum order is fixed).
 constexpr int LK_RES_BLOCKS = 128;
 
-// Everything a frame's kernels need. Device pointers unless noted. The real
-// type of X, Yb, d, y, truth, taper and the outputs is float (precision 0) or
-// double (precision 1).
-struct LkGeom {
-  int nsub, m, w, h;       // h = w / 2
+// One AO instance, as the kernels see it (device pointers, by-value copy in a
+// device array). The real type of X, Yb, d, y, truth, taper and the outputs is
+// float (precision 0) or double (precision 1).
+struct LkInst {
+  int nsub, m, w, h;        // h = w / 2
+  int mp;                   // padded ensemble width of the kernels (16, 32 or 64)
   int n_pts, n_sap, p;
-  int gs_rows, gs_cols;    // padded subaperture grid (cells); cell (s+h, t+h) holds subap (s, t)
-  const int *pid_map;      // [(nsub+1)^2] node -> point id or -1
-  const int2 *pts;         // [n_pts] (i, j)
-  const int2 *saps;        // [n_sap] (s, t)
+  int gs_rows, gs_cols;     // padded subaperture grid: cell (s+h, t+h) holds subap (s, t)
+  const int *pid_map;       // [(nsub+1)^2] node -> point id or -1
+  const int2 *pts;          // [n_pts] (i, j)
+  const int2 *saps;         // [n_sap] (s, t)
+  void *X;                  // [n_pts][2][m]
+  void *Ybp;                // [gs_rows][gs_cols][2][m]
+  void *dp;                 // [gs_rows][gs_cols][2]
+  const void *taper;        // [w*w] tau / sigma2
+  float *basis;             // [n_pts][mp][mp] last eigenbasis (FP32 warm start)
+  const float *bank;        // [bank_B][bank_G][bank_G] or NULL
+  int bank_B, bank_G;
+  double alpha;             // (m - 1) / rho
+  double a_ar1, noise_std;
+  unsigned long long seed;
+  long long y_off;          // offset of this instance in concatenated slopes
+  long long node_off;       // ... in concatenated node arrays (truth, mean/spread rows)
+  long long noise_off;      // ... in concatenated [n_pts][m] noise
+  long long state_off;      // ... in the concatenated ensemble
+};
+
+// Work items.
+struct LkTile {             // one analysis CTA: instance, tile origin (node coordinates)
+  int inst, i0, j0, cost;
 };
 
 struct letkf_ctx {
-  letkf_config cfg;        // host copy, host pointers cleared
+  letkf_config cfg;         // first instance's config (host pointers cleared)
   cudaStream_t stream = nullptr;
   int device = 0;
   int precision = 0;
-  size_t rsz = 4;          // bytes of the real type
-  int mp = 32;             // padded ensemble width of the kernels (16 or 32)
-  LkGeom g{};
-  double alpha = 0, tol32 = 0, tol64 = 0;
-  int max_sweeps = 12;
+  size_t rsz = 4;           // bytes of the real type
+  double tol32 = 4e-6, tol64 = 1e-13, fp64_kappa = 300;
+  int max_sweeps = 20;
 
-  // device buffers
-  void *X = nullptr;       // [n_pts][2][m]
-  void *Ybp = nullptr;     // [gs_rows][gs_cols][2][m]
-  void *dp = nullptr;      // [gs_rows][gs_cols][2]
-  void *taper = nullptr;   // [w*w] tau / sigma2
+  int n_inst = 0;
+  std::vector<LkInst> inst;         // host copies of the descriptors
+  LkInst *d_inst = nullptr;         // device copies
+  long long n_pts_total = 0, p_total = 0, state_total = 0, noise_total = 0;
+  long long sap_total = 0;
+
+  // work lists (device)
+  int2 *obs_items = nullptr;        // [sap_total] (inst, subap)
+  int2 *node_items = nullptr;       // [n_pts_total] (inst, point)
+  LkTile *tiles[3] = {nullptr, nullptr, nullptr};   // per width class 16 / 32 / 64
+  int n_tiles[3] = {0, 0, 0};
+  int tile_shape[3] = {0, 0, 0};    // index into the compiled tile shapes, per class
+  std::vector<LkTile> tiles_host[3];
+
+  // device buffers (single allocations sliced per instance)
+  void *X = nullptr, *Ybp = nullptr, *dp = nullptr, *taper = nullptr;
   int *pid_map = nullptr;
-  int2 *pts = nullptr;
-  int2 *saps = nullptr;
-  int2 *tiles = nullptr;   // analysis tile origins (node coordinates)
-  int n_tiles = 0;
-  float *bank = nullptr;
-  int bank_B = 0, bank_G = 0;
-  int *counters = nullptr; // [0] status bits, [1] fp64 list length, [2] max sweeps
-  int *worklist = nullptr; // [n_pts] FP64 fallback point ids
-  float *basis = nullptr;  // [n_pts][mp][mp] each node's last eigenbasis (warm start)
-  double2 *partial = nullptr;   // [LK_RES_BLOCKS] residual partial sums
-  long long *frame = nullptr;   // [0] forecast counter, [1] index within letkf_run
-  double *zero_scalar = nullptr;
+  int2 *pts = nullptr, *saps = nullptr;
+  float *bank = nullptr, *basis = nullptr;
+  int *counters = nullptr;          // [0] status bits, [1] FP64 queue length, [2] max sweeps, [3] total sweeps
+  int2 *worklist = nullptr;         // [n_pts_total] (inst, point) queued for FP64
+  long long *frame = nullptr;       // [0] forecast counter, [1] frame index within letkf_run
+  double2 *partial = nullptr;       // [n_inst][LK_RES_BLOCKS] residual partial sums
 
   // host copies
   std::vector<int32_t> pts_host, wslopes_host;
@@ -78,14 +103,20 @@ struct letkf_ctx {
   std::string err;
 };
 
-// Launchers (defined in letkf_kernels.cu / letkf_analysis.cu). All enqueue on
-// h->stream and return the launch status. run_idx (device) selects element
-// *run_idx of a sequence (y, truth, resvar); NULL means element 0.
+// Launchers (letkf_kernels.cu / letkf_analysis.cu). All enqueue on h->stream.
+// run_idx (device) selects element *run_idx of a sequence (y, truth, resvar);
+// NULL means element 0. y, truth, mean, spread and noise are concatenated over
+// the instances in instance order.
 cudaError_t lk_launch_obs(letkf_ctx *h, const void *y, const long long *run_idx);
 cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread);
 cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise);
-cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar, const long long *run_idx);
+cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
+                               const long long *run_idx);
 cudaError_t lk_launch_tick(letkf_ctx *h);
+cudaError_t lk_setup_analysis(letkf_ctx *h);
+int lk_num_tile_shapes();
+void lk_tile_shape(int s, int *ti, int *tj);
+int lk_width_class(int m);          // 0: m <= 16, 1: m <= 32, 2: m <= 64
 
 // ---------------------------------------------------------------------------
 // Device helpers

@@ -53,6 +53,12 @@ _SIGS = {
     "letkf_stats": [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)],
     "letkf_analyze_noalloc": [POINTER(letkf_config), c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_char_p, ctypes.c_size_t],
+    "letkf_create_batch": [POINTER(letkf_config), c_int32, c_void_p, POINTER(c_void_p)],
+    "letkf_query_instance": [c_void_p, c_int32, POINTER(c_int32), POINTER(c_int32),
+                             POINTER(c_int32), POINTER(c_int32)],
+    "letkf_tile_shape": [c_int32, POINTER(c_int32), POINTER(c_int32)],
+    "letkf_set_tile_shape": [c_void_p, c_int32, c_int32],
+    "letkf_autotune": [c_void_p, c_void_p, c_int32, POINTER(c_int32), POINTER(ctypes.c_float)],
 }
 
 _lib = None
@@ -104,6 +110,48 @@ def letkf_create(cfg: letkf_config, stream_ptr: int) -> c_void_p:
     h = c_void_p()
     _check(lib().letkf_create(byref(cfg), c_void_p(stream_ptr), byref(h)), None)
     return h
+
+
+def letkf_create_batch(cfgs, stream_ptr: int) -> c_void_p:
+    arr = (letkf_config * len(cfgs))(*cfgs)
+    h = c_void_p()
+    _check(lib().letkf_create_batch(arr, len(cfgs), c_void_p(stream_ptr), byref(h)), None)
+    return h
+
+
+def letkf_query_instance(h, i: int):
+    """(n_pts, p, m, n_inst) of instance i."""
+    n, p, m, k = c_int32(), c_int32(), c_int32(), c_int32()
+    _check(lib().letkf_query_instance(h, i, byref(n), byref(p), byref(m), byref(k)), h)
+    return n.value, p.value, m.value, k.value
+
+
+def letkf_tile_shape(shape: int):
+    a, b = c_int32(), c_int32()
+    _check(lib().letkf_tile_shape(shape, byref(a), byref(b)), None)
+    return a.value, b.value
+
+
+def tile_shapes() -> list:
+    """All compiled analysis tile shapes (nodes per CTA side)."""
+    out = []
+    while True:
+        a, b = c_int32(), c_int32()
+        if lib().letkf_tile_shape(len(out), byref(a), byref(b)) != LETKF_OK:
+            return out
+        out.append((a.value, b.value))
+
+
+def letkf_set_tile_shape(h, width_class: int, shape: int) -> None:
+    _check(lib().letkf_set_tile_shape(h, width_class, shape), h)
+
+
+def letkf_autotune(h, y, reps: int = 3):
+    """Times every tile shape per width class; returns ([shape] * 3, [us] * 3)."""
+    shapes = (c_int32 * 3)()
+    us = (ctypes.c_float * 3)()
+    _check(lib().letkf_autotune(h, _ptr(y), reps, shapes, us), h)
+    return list(shapes), list(us)
 
 
 def letkf_destroy(h) -> None:
@@ -177,51 +225,77 @@ def letkf_last_error(h=None) -> str:
 # ---------------------------------------------------------------------------
 # Handle object
 # ---------------------------------------------------------------------------
-class Letkf:
-    """One LETKF instance on one GPU, on its own CUDA stream.
+def make_config(subap_mask, m: int, window: int, taper: int = 1, loc_len: float = 0.0,
+                rho: float = 1.0, sigma2: float = 0.01, a_ar1: float = 1.0,
+                noise_std: float = 0.0, precision: int = 0, fp64_kappa: float = 300.0,
+                seed: int = 0, bank=None, max_sweeps: int = 0):
+    """A letkf_config plus the numpy arrays its pointers refer to (keep both alive)."""
+    mask = np.ascontiguousarray(subap_mask, dtype=np.uint8)
+    bank = None if bank is None else np.ascontiguousarray(bank, dtype=np.float32)
+    cfg = letkf_config()
+    cfg.nsub = mask.shape[0]
+    cfg.subap_mask = mask.ctypes.data
+    cfg.m, cfg.window, cfg.taper, cfg.loc_len = m, window, taper, loc_len
+    cfg.rho, cfg.sigma2, cfg.a_ar1, cfg.noise_std = rho, sigma2, a_ar1, noise_std
+    cfg.precision, cfg.fp64_kappa, cfg.seed = precision, fp64_kappa, seed
+    if bank is not None:
+        cfg.noise_bank = bank.ctypes.data
+        cfg.bank_B, cfg.bank_G = bank.shape[0], bank.shape[1]
+    cfg.max_sweeps = max_sweeps
+    return cfg, (mask, bank)
 
-    Tensor arguments are CUDA tensors of the handle's dtype (float32 when
-    precision = 0, float64 when precision = 1), contiguous, in the layouts of
-    include/letkf.h. Calls order the handle's stream after torch's current
-    stream on entry and torch's current stream after the handle's on exit, so
-    they compose with ordinary torch code.
+
+def workload_config(w, bank=None, **kw):
+    from .synth import pupil_subap_mask
+    args = dict(m=w.m, window=w.window, taper=w.taper, loc_len=w.loc_len, rho=w.rho,
+                sigma2=w.sigma2, a_ar1=w.a_ar1, noise_std=w.noise_std, precision=w.precision,
+                seed=w.seeds[2], bank=bank)
+    args.update(kw)
+    return make_config(pupil_subap_mask(w.nsub, w.obscuration, w.square), **args)
+
+
+class Letkf:
+    """One or more LETKF instances on one GPU, on the handle's own CUDA stream.
+
+    Tensor arguments are contiguous CUDA tensors of the handle's dtype (float32
+    when precision = 0, float64 when precision = 1) in the layouts of
+    include/letkf.h: the ensemble is [n_pts, 2, m] for one instance and the flat
+    concatenation of the instances' blocks for a batch. Calls order the
+    handle's stream after torch's current stream on entry and torch's current
+    stream after the handle's on exit, so they compose with ordinary torch code.
     """
 
-    def __init__(self, subap_mask, m: int, window: int, taper: int = 1, loc_len: float = 0.0,
-                 rho: float = 1.0, sigma2: float = 0.01, a_ar1: float = 1.0,
-                 noise_std: float = 0.0, precision: int = 0, fp64_kappa: float = 300.0,
-                 seed: int = 0, bank=None, max_sweeps: int = 0, stream=None):
+    def __init__(self, subap_mask=None, m: int = 0, window: int = 0, stream=None,
+                 _configs=None, **kw):
         import torch
         self._torch = torch
         if not torch.cuda.is_available():
             raise RuntimeError("Letkf needs a CUDA GPU; there is no CPU implementation")
         self.stream = stream if stream is not None else torch.cuda.Stream()
-        mask = np.ascontiguousarray(subap_mask, dtype=np.uint8)
-        self._bank = None if bank is None else np.ascontiguousarray(bank, dtype=np.float32)
-        cfg = letkf_config()
-        cfg.nsub = mask.shape[0]
-        cfg.subap_mask = mask.ctypes.data
-        cfg.m, cfg.window, cfg.taper, cfg.loc_len = m, window, taper, loc_len
-        cfg.rho, cfg.sigma2, cfg.a_ar1, cfg.noise_std = rho, sigma2, a_ar1, noise_std
-        cfg.precision, cfg.fp64_kappa, cfg.seed = precision, fp64_kappa, seed
-        if self._bank is not None:
-            cfg.noise_bank = self._bank.ctypes.data
-            cfg.bank_B, cfg.bank_G = self._bank.shape[0], self._bank.shape[1]
-        cfg.max_sweeps = max_sweeps
-        self.h = letkf_create(cfg, self.stream.cuda_stream)
+        if _configs is None:
+            _configs = [make_config(subap_mask, m, window, **kw)]
+        self._keep = [k for _, k in _configs]
+        cfgs = [c for c, _ in _configs]
+        if len(cfgs) == 1:
+            self.h = letkf_create(cfgs[0], self.stream.cuda_stream)
+        else:
+            self.h = letkf_create_batch(cfgs, self.stream.cuda_stream)
         self.n_pts, self.p, self.m = letkf_query(self.h)
-        self.dtype = torch.float32 if precision == 0 else torch.float64
-        self.precision = precision
+        self.instances = [letkf_query_instance(self.h, i)[:3] for i in range(len(cfgs))]
+        self.n_inst = len(cfgs)
+        self.precision = cfgs[0].precision
+        self.dtype = torch.float32 if self.precision == 0 else torch.float64
+        self.state_numel = sum(2 * n * mm for n, _, mm in self.instances)
 
     @classmethod
-    def from_workload(cls, w, bank=None, **kw):
-        from .synth import pupil_subap_mask
-        mask = pupil_subap_mask(w.nsub, w.obscuration, w.square)
-        args = dict(m=w.m, window=w.window, taper=w.taper, loc_len=w.loc_len, rho=w.rho,
-                    sigma2=w.sigma2, a_ar1=w.a_ar1, noise_std=w.noise_std,
-                    precision=w.precision, seed=w.seeds[2], bank=bank)
-        args.update(kw)
-        return cls(mask, **args)
+    def from_workload(cls, w, bank=None, stream=None, **kw):
+        return cls(stream=stream, _configs=[workload_config(w, bank, **kw)])
+
+    @classmethod
+    def batch(cls, workloads, banks, stream=None, **kw):
+        """One handle for many instances (workloads[i] with noise bank banks[i])."""
+        return cls(stream=stream,
+                   _configs=[workload_config(w, b, **kw) for w, b in zip(workloads, banks)])
 
     # -- stream ordering ---------------------------------------------------
     def _enter(self):
@@ -240,6 +314,19 @@ class Letkf:
             raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
         return t
 
+    @property
+    def state_shape(self):
+        return (self.n_pts, 2, self.m) if self.n_inst == 1 else (self.state_numel,)
+
+    def split_state(self, X):
+        """Per-instance [n_pts_i, 2, m_i] views of a (flat) batch ensemble."""
+        out, off = [], 0
+        flat = X.reshape(-1)
+        for n, _, mm in self.instances:
+            out.append(flat[off:off + 2 * n * mm].view(n, 2, mm))
+            off += 2 * n * mm
+        return out
+
     # -- API -----------------------------------------------------------------
     def points(self):
         return letkf_query_points(self.h, self.n_pts)
@@ -249,19 +336,20 @@ class Letkf:
 
     def set_state(self, X):
         self._enter()
-        letkf_set_state(self.h, self._t(X, (self.n_pts, 2, self.m)))
+        letkf_set_state(self.h, self._t(X, self.state_shape))
         self._leave()
 
     def get_state(self):
-        X = self.new(self.n_pts, 2, self.m)
+        X = self.new(*self.state_shape)
         self._enter()
         letkf_get_state(self.h, X)
         self._leave()
         return X
 
     def forecast(self, noise=None):
+        shape = (self.n_pts, self.m) if self.n_inst == 1 else (sum(n * mm for n, _, mm in self.instances),)
         self._enter()
-        letkf_forecast(self.h, self._t(noise, (self.n_pts, self.m)))
+        letkf_forecast(self.h, self._t(noise, shape))
         self._leave()
 
     def analyze(self, y, mean=None, spread=None, outputs: bool = True):
@@ -277,7 +365,7 @@ class Letkf:
 
     def residual(self, truth, resvar=None):
         if resvar is None:
-            resvar = self._torch.zeros(1, dtype=self._torch.float64, device="cuda")
+            resvar = self._torch.zeros(self.n_inst, dtype=self._torch.float64, device="cuda")
         self._enter()
         letkf_residual(self.h, self._t(truth, (self.n_pts,)), resvar)
         self._leave()
@@ -292,11 +380,21 @@ class Letkf:
             if truth_seq.shape[0] < frames:
                 raise ValueError("truth_seq shorter than frames")
             if resvar is None:
-                resvar = self._torch.zeros(frames, dtype=self._torch.float64, device="cuda")
+                shape = (frames,) if self.n_inst == 1 else (frames, self.n_inst)
+                resvar = self._torch.zeros(*shape, dtype=self._torch.float64, device="cuda")
         self._enter()
         letkf_run(self.h, frames, y_seq, truth_seq, resvar, use_graph)
         self._leave()
         return resvar
+
+    def autotune(self, y, reps: int = 3):
+        self._enter()
+        out = letkf_autotune(self.h, self._t(y, (self.p,)), reps)
+        self._leave()
+        return out
+
+    def set_tile_shape(self, width_class: int, shape: int):
+        letkf_set_tile_shape(self.h, width_class, shape)
 
     def sync(self):
         letkf_sync(self.h)

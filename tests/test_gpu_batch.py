@@ -1,0 +1,120 @@
+"""Many AO instances of different sizes in one handle: per-instance parity with
+the oracle, equality with the same instances run one handle each, and tile
+shapes (autotuned or forced) leaving the arithmetic unchanged."""
+import functools
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1408_7069_gb300 import synth, workloads as W  # noqa: E402
+from paper_1408_7069_gb300 import letkf as L  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+BATCH = [
+    replace(W.TEL_16M, name="b0", nsub=20, m=24, window=5, seeds=(101, 102, 103)),
+    replace(W.TEL_16M, name="b1", nsub=12, m=10, window=3, rho=1.05, seeds=(111, 112, 113)),
+    replace(W.ELT_80X80, name="b2", nsub=28, m=32, window=7, seeds=(121, 122, 123)),
+    replace(W.TEL_16M, name="b3", nsub=16, m=16, window=7, obscuration=0.0, seeds=(131, 132, 133)),
+]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+@functools.lru_cache(maxsize=None)
+def inputs(frames):
+    out = []
+    for w in BATCH:
+        inp = synth.make_loop_inputs(w, frames=frames)
+        geom = oracle.build_geometry(inp.subap_mask, w.window, w.taper, w.loc_len)
+        out.append((inp, geom))
+    return out
+
+
+def test_batch_teacher_forced_parity_per_instance():
+    ins = inputs(4)
+    f = L.Letkf.batch(BATCH, [i.bank for i, _ in ins])
+    assert f.n_inst == len(BATCH)
+    X0 = np.concatenate([i.X0.astype(np.float32).ravel() for i, _ in ins])
+    y = np.concatenate([i.slopes[2].astype(np.float32) for i, _ in ins])
+    f.set_state(torch.from_numpy(X0).cuda())
+    mean, spread = f.analyze(torch.from_numpy(y).cuda())
+    f.sync()
+    Xs = [x.cpu().numpy() for x in f.split_state(f.get_state())]
+    row = 0
+    for (inp, geom), w, Xa in zip(ins, BATCH, Xs):
+        Xb = inp.X0.astype(np.float32).astype(np.float64)
+        rXa, rmean, rspread = oracle.analysis(geom, Xb, inp.slopes[2].astype(np.float32)
+                                              .astype(np.float64), w.sigma2, w.rho)
+        n = geom.n_pts
+        assert rel(mean[row:row + n].cpu().numpy(), rmean) <= 1e-4, w.name
+        assert rel(spread[row:row + n].cpu().numpy(), rspread) <= 1e-3, w.name
+        row += n
+    f.close()
+
+
+def _run_batch(frames, tile=None, autotune=False):
+    ins = inputs(frames)
+    f = L.Letkf.batch(BATCH, [i.bank for i, _ in ins])
+    X0 = np.concatenate([i.X0.astype(np.float32).ravel() for i, _ in ins])
+    y = torch.from_numpy(np.concatenate([i.slopes.astype(np.float32) for i, _ in ins], 1)).cuda()
+    t = torch.from_numpy(np.concatenate([i.truth.astype(np.float32) for i, _ in ins], 1)).cuda()
+    f.set_state(torch.from_numpy(X0).cuda())
+    if tile is not None:
+        for cls in (0, 1):
+            f.set_tile_shape(cls, tile)
+    if autotune:
+        shapes, us = f.autotune(y[0].contiguous(), reps=2)
+        assert all(0 <= s < len(L.tile_shapes()) for s in shapes)
+    rv = f.run(frames, y, t, use_graph=True)
+    f.sync()
+    X = f.get_state().cpu().numpy()
+    f.close()
+    return X, rv.cpu().numpy()
+
+
+def test_batch_equals_separate_handles_bitwise():
+    frames = 6
+    Xb, rvb = _run_batch(frames)
+    ins = inputs(frames)
+    parts, rvs = [], []
+    for (inp, _), w in zip(ins, BATCH):
+        f = L.Letkf.from_workload(w, bank=inp.bank)
+        f.set_state(torch.from_numpy(inp.X0.astype(np.float32)).cuda())
+        rv = f.run(frames, torch.from_numpy(inp.slopes.astype(np.float32)).cuda(),
+                   torch.from_numpy(inp.truth.astype(np.float32)).cuda(), use_graph=True)
+        f.sync()
+        parts.append(f.get_state().cpu().numpy().ravel())
+        rvs.append(rv.cpu().numpy())
+        f.close()
+    assert np.array_equal(Xb, np.concatenate(parts))
+    assert np.array_equal(rvb, np.stack(rvs, 1))
+
+
+def test_tile_shapes_and_autotune_leave_results_unchanged():
+    frames = 4
+    ref, _ = _run_batch(frames)
+    for s in range(len(L.tile_shapes())):
+        X, _ = _run_batch(frames, tile=s)
+        assert np.array_equal(X, ref), s
+    X, _ = _run_batch(frames, autotune=True)
+    assert np.array_equal(X, ref)
+
+
+def test_batch_closed_loop_matches_oracle_per_instance():
+    frames = 10
+    ins = inputs(frames)
+    _, rv = _run_batch(frames)
+    for k, ((inp, geom), w) in enumerate(zip(ins, BATCH)):
+        rv_ref, _, _ = oracle.closed_loop(
+            geom, inp.truth.astype(np.float32).astype(np.float64),
+            inp.slopes.astype(np.float32).astype(np.float64), inp.bank, w.m, w.sigma2, w.rho,
+            w.a_ar1, w.noise_std, w.seeds[2], frames,
+            X0=inp.X0.astype(np.float32).astype(np.float64), batched=True)
+        assert np.max(np.abs(rv[:, k] - rv_ref) / rv_ref) <= 1e-3, w.name
