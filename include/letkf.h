@@ -67,7 +67,7 @@ typedef enum {
 typedef struct {
   int32_t nsub;                /* subapertures per side; nodes (nsub+1)^2. 1..1024 */
   const uint8_t *subap_mask;   /* host [nsub*nsub] row-major, nonzero = valid; copied */
-  int32_t m;                   /* ensemble size, 2..32 */
+  int32_t m;                   /* ensemble size, 2..64 (2..32 when precision = 1) */
   int32_t window;              /* localization window: w x w subapertures, odd or even, 1..31 */
   int32_t taper;               /* 0 = box (tau = 1), 1 = Gaspari-Cohn tau on R^-1 */
   double loc_len;              /* Gaspari-Cohn half-support c in pitches; <= 0 -> w / 4 */
@@ -158,7 +158,8 @@ letkf_status letkf_run(letkf_t h, int32_t frames, const void *y_seq_dev, const v
  * memory once; the best shape depends on the window, the ensemble size and the
  * mix of instances. letkf_tile_shape describes compiled shape number `shape`
  * (0 .. count-1; LETKF_ERR_ARG beyond). Instances are grouped in width classes
- * by ensemble size: 0 for m <= 16, 1 for m <= 32. letkf_set_tile_shape selects
+ * by ensemble size: 0 for m <= 16, 1 for m <= 32, 2 for m <= 64 (one node per
+ * warp pair, fixed shape 2 = 2 x 2 nodes, no FP64 fallback). letkf_set_tile_shape selects
  * a shape for one class; letkf_autotune times every shape for every class
  * present on the handle's current ensemble with slopes y_dev (reps timed
  * analyses each, state restored afterwards), keeps the fastest and writes the

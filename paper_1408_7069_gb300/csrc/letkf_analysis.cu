@@ -572,6 +572,303 @@ __global__ void __launch_bounds__(LIST_WARPS * 32)
       I.basis + (size_t)pid * MP * MP);
 }
 
+// ---------------------------------------------------------------------------
+// Ensembles of 33..64 members: one node per warp pair (64 threads), lane L of
+// the pair holds column L of the 64-wide padded problem. Rotation partners in
+// the same warp are exchanged by shuffles, partners in the other warp through
+// shared memory under a 64-thread named barrier. FP32 only.
+// ---------------------------------------------------------------------------
+constexpr int P64_TI = 2, P64_TJ = 2;           // nodes per CTA: 4 (8 warps)
+constexpr int P64_LDA = 68;                      // A staging row stride
+constexpr int P64_SCR = 64 * 68;                 // per-node scratch floats (>= 64*65+192, 64*66)
+
+__host__ __device__ inline size_t p64_smem_bytes(int w) {
+  const size_t ncell = (size_t)(P64_TI + w - 1) * (P64_TJ + w - 1);
+  size_t off = align16(ncell * 2 * 64 * sizeof(float));
+  off = align16(off + ncell * 2 * sizeof(float));
+  off = align16(off + (size_t)w * w * sizeof(float));
+  return off + (size_t)P64_TI * P64_TJ * (P64_SCR + 8) * sizeof(float);
+}
+
+__device__ __forceinline__ void pair_bar(int id) {
+  asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+// Sum over the 64 threads of a pair; red: 2 floats of the pair's scratch.
+__device__ __forceinline__ float pair_sum(float v, float *red, int half, int bar) {
+  v = lk_warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[half] = v;
+  pair_bar(bar);
+  const float s = red[0] + red[1];
+  pair_bar(bar);
+  return s;
+}
+
+__device__ void analyze_node64(const float *__restrict__ win, const float *__restrict__ dwin,
+                               int stride, const float *__restrict__ tap, int w, int m,
+                               float alpha, float tol, int max_sweeps, float *__restrict__ xrow,
+                               float *__restrict__ mean_out, float *__restrict__ spread_out,
+                               float *__restrict__ scr, int *__restrict__ counters,
+                               float *__restrict__ U, int half, int bar) {
+  constexpr int MP = 64;
+  const int lane = threadIdx.x & 31;
+  const int L = half * 32 + lane;
+  float *red = scr + P64_SCR;                   // 8 floats after the node's scratch
+  const bool mem = L < m;
+  // ---- Gram row L ----
+  float b[MP];
+#pragma unroll
+  for (int k = 0; k < MP; ++k) b[k] = 0.f;
+  float diag = 0.f, cd = 0.f;
+  for (int ds = 0; ds < w; ++ds)
+    for (int dt = 0; dt < w; ++dt) {
+      const int cell = ds * stride + dt;
+      const float tw = tap[ds * w + dt];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float *yv = win + (size_t)cell * 2 * MP + c * MP;
+        const float yl = yv[L];
+        const float cy = tw * yl;
+        diag = fmaf(cy, yl, diag);
+        cd = fmaf(cy, dwin[cell * 2 + c], cd);
+#pragma unroll
+        for (int k = 0; k < MP; k += 4) {
+          const float4 y4 = *reinterpret_cast<const float4 *>(yv + k);
+          b[k] = fmaf(cy, y4.x, b[k]);
+          b[k + 1] = fmaf(cy, y4.y, b[k + 1]);
+          b[k + 2] = fmaf(cy, y4.z, b[k + 2]);
+          b[k + 3] = fmaf(cy, y4.w, b[k + 3]);
+        }
+      }
+    }
+  const float dval = mem ? alpha : 1.f;
+#pragma unroll
+  for (int k = 0; k < MP; ++k)
+    if (k == L) b[k] += dval;
+  // ---- B = A U0 ----
+#pragma unroll
+  for (int k = 0; k < MP; k += 4)
+    *reinterpret_cast<float4 *>(scr + L * P64_LDA + k) = make_float4(b[k], b[k + 1], b[k + 2], b[k + 3]);
+  pair_bar(bar);
+  {
+    float u[MP];
+#pragma unroll
+    for (int k = 0; k < MP; ++k) u[k] = U[k * MP + L];
+#pragma unroll
+    for (int i = 0; i < MP; ++i) {
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < MP; k += 4) {
+        const float4 a4 = *reinterpret_cast<const float4 *>(scr + i * P64_LDA + k);
+        s0 = fmaf(a4.x, u[k], s0);
+        s1 = fmaf(a4.y, u[k + 1], s1);
+        s0 = fmaf(a4.z, u[k + 2], s0);
+        s1 = fmaf(a4.w, u[k + 3], s1);
+      }
+      b[i] = s0 + s1;
+    }
+  }
+  pair_bar(bar);
+  // ---- one-sided Jacobi with scaled rotations (see jacobi_fast_f32) ----
+  const float tol2 = tol * tol;
+  int sweep = 0;
+  bool converged = false;
+  float *xb = scr;                              // exchange rows: [64][66]
+  for (; sweep < max_sweeps; ++sweep) {
+    float nrm = dot4<MP, float>(b, b);
+    float d = 1.f;
+    int rotated = 0;
+    for (int t = 1; t < MP; ++t) {
+      float pb[MP];
+      float pd, pn;
+      if (t < 32) {
+#pragma unroll
+        for (int k = 0; k < MP; ++k) pb[k] = __shfl_xor_sync(FULL, b[k], t);
+        pd = __shfl_xor_sync(FULL, d, t);
+        pn = __shfl_xor_sync(FULL, nrm, t);
+      } else {
+        float *row = xb + L * 66;
+#pragma unroll
+        for (int k = 0; k < MP; k += 2) *reinterpret_cast<float2 *>(row + k) = make_float2(b[k], b[k + 1]);
+        row[64] = d;
+        row[65] = nrm;
+        pair_bar(bar);
+        const float *prow = xb + (L ^ t) * 66;
+#pragma unroll
+        for (int k = 0; k < MP; k += 2) {
+          const float2 v2 = *reinterpret_cast<const float2 *>(prow + k);
+          pb[k] = v2.x;
+          pb[k + 1] = v2.y;
+        }
+        pd = prow[64];
+        pn = prow[65];
+        pair_bar(bar);
+      }
+      const float dot = d * pd * dot4<MP, float>(b, pb);
+      const bool isp = L < (L ^ t);
+      const float app = isp ? nrm : pn;
+      const float aqq = isp ? pn : nrm;
+      float tr = 0.f, cs = 1.f;
+      if (dot * dot > tol2 * app * aqq) {
+        const float zeta = __fdividef(aqq - app, 2.f * dot);
+        const float az = fabsf(zeta);
+        tr = az > 1e15f ? __fdividef(0.5f, zeta)
+                        : copysignf(__fdividef(1.f, az + __fsqrt_rn(fmaf(zeta, zeta, 1.f))), zeta);
+        cs = rsqrtf(fmaf(tr, tr, 1.f));
+        rotated = 1;
+      }
+      const float coef = (isp ? -tr : tr) * __fdividef(pd, d);
+#pragma unroll
+      for (int k = 0; k < MP; ++k) b[k] = fmaf(coef, pb[k], b[k]);
+      d *= cs;
+      nrm = isp ? fmaf(-tr, dot, app) : fmaf(tr, dot, aqq);
+    }
+#pragma unroll
+    for (int k = 0; k < MP; ++k) b[k] *= d;
+    const float any = pair_sum(__any_sync(FULL, rotated) ? 1.f : 0.f, red, half, bar);
+    if (any == 0.f) {
+      converged = true;
+      break;
+    }
+  }
+  if (L == 0) {
+    atomicMax(&counters[2], converged ? sweep + 1 : sweep);
+    atomicAdd(&counters[3], converged ? sweep + 1 : sweep);
+    if (!converged) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
+  }
+  const float nrm = dot4<MP, float>(b, b);
+  const float lam = nrm > 0.f ? sqrtf(nrm) : 1.f;
+  const float inv = 1.f / lam;
+#pragma unroll
+  for (int k = 0; k < MP; ++k) b[k] *= inv;      // eigenvector column L
+  // ---- transform and apply ----
+  float *vt = scr;                               // vt[i*65+j] = V[i][j]
+  float *vec = scr + 64 * 65;                    // [3][64]
+  const float x0 = mem ? xrow[L] : 0.f;
+  const float x1 = mem ? xrow[m + L] : 0.f;
+  const float inv_m = 1.f / float(m);
+  const float xb0 = pair_sum(x0, red, half, bar) * inv_m;
+  const float xb1 = pair_sum(x1, red, half, bar) * inv_m;
+  const float xp0 = mem ? x0 - xb0 : 0.f;
+  const float xp1 = mem ? x1 - xb1 : 0.f;
+  vec[L] = cd;
+  vec[MP + L] = xp0;
+  vec[2 * MP + L] = xp1;
+#pragma unroll
+  for (int k = 0; k < MP; ++k) vt[k * 65 + L] = b[k];
+  pair_bar(bar);
+  float u = 0.f, g0 = 0.f, g1 = 0.f;
+#pragma unroll
+  for (int k = 0; k < MP; ++k) {
+    u = fmaf(b[k], vec[k], u);
+    g0 = fmaf(b[k], vec[MP + k], g0);
+    g1 = fmaf(b[k], vec[2 * MP + k], g1);
+  }
+  const float z = u / lam;
+  const float P0 = pair_sum(g0 * z, red, half, bar);
+  const float P1 = pair_sum(g1 * z, red, half, bar);
+  const float sroot = mem ? sqrtf(float(m - 1) / lam) : 0.f;
+  vec[MP + L] = g0 * sroot;
+  vec[2 * MP + L] = g1 * sroot;
+  pair_bar(bar);
+  float q0 = 0.f, q1 = 0.f;
+  {
+    const float *vr = vt + L * 65;
+#pragma unroll
+    for (int j = 0; j < MP; ++j) {
+      q0 = fmaf(vr[j], vec[MP + j], q0);
+      q1 = fmaf(vr[j], vec[2 * MP + j], q1);
+    }
+  }
+  const float xa0 = xb0 + P0 + q0;
+  const float xa1 = xb1 + P1 + q1;
+  if (mem) {
+    xrow[L] = xa0;
+    xrow[m + L] = xa1;
+  }
+  const float mu0 = pair_sum(mem ? xa0 : 0.f, red, half, bar) * inv_m;
+  const float mu1 = pair_sum(mem ? xa1 : 0.f, red, half, bar) * inv_m;
+  const float e0 = mem ? xa0 - mu0 : 0.f;
+  const float e1 = mem ? xa1 - mu1 : 0.f;
+  const float sp0 = sqrtf(pair_sum(e0 * e0, red, half, bar) / float(m - 1));
+  const float sp1 = sqrtf(pair_sum(e1 * e1, red, half, bar) / float(m - 1));
+  if (L == 0) {
+    if (mean_out) {
+      mean_out[0] = mu0;
+      mean_out[1] = mu1;
+    }
+    if (spread_out) {
+      spread_out[0] = sp0;
+      spread_out[1] = sp1;
+    }
+    if (!isfinite(mu0) || !isfinite(mu1) || !isfinite(sp0) || !isfinite(sp1))
+      atomicOr(&counters[0], LK_BIT_NONFINITE);
+  }
+  // ---- eigenbasis for the next analysis (identity if non-finite) ----
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < MP; ++k) ok = ok && isfinite(b[k]);
+  const float okall = pair_sum(ok ? 0.f : 1.f, red, half, bar);
+#pragma unroll
+  for (int k = 0; k < MP; ++k) U[k * MP + L] = okall == 0.f ? b[k] : (k == L ? 1.f : 0.f);
+}
+
+__global__ void __launch_bounds__(P64_TI *P64_TJ * 64, 1)
+    analysis_tile64_kernel(const LkInst *__restrict__ insts, const LkTile *__restrict__ tiles,
+                           float *__restrict__ mean, float *__restrict__ spread, float tol,
+                           int max_sweeps, int *__restrict__ counters) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const LkTile tl = tiles[blockIdx.x];
+  const LkInst &I = insts[tl.inst];
+  const int w = I.w;
+  const int HJ = P64_TJ + w - 1;
+  const size_t ncell = (size_t)(P64_TI + w - 1) * HJ;
+  float *halo = reinterpret_cast<float *>(smem);
+  size_t off = align16(ncell * 2 * 64 * sizeof(float));
+  float *dh = reinterpret_cast<float *>(smem + off);
+  off = align16(off + ncell * 2 * sizeof(float));
+  float *tap = reinterpret_cast<float *>(smem + off);
+  off = align16(off + (size_t)w * w * sizeof(float));
+  float *scr = reinterpret_cast<float *>(smem + off);
+  stage_tile<64, float, float, P64_TI, P64_TJ>(I, tl.i0, tl.j0, halo, dh, tap);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  const int node = warp >> 1, half = warp & 1;
+  const int ti = node / P64_TJ, tj = node - (node / P64_TJ) * P64_TJ;
+  const int i = tl.i0 + ti, j = tl.j0 + tj;
+  if (i > I.nsub || j > I.nsub) return;          // both warps of the pair leave together
+  const int pid = I.pid_map[i * (I.nsub + 1) + j];
+  if (pid < 0) return;
+  const int cell = ti * HJ + tj;
+  const int m = I.m;
+  analyze_node64(halo + (size_t)cell * 2 * 64, dh + cell * 2, HJ, tap, w, m, float(I.alpha), tol,
+                 max_sweeps, static_cast<float *>(I.X) + (size_t)pid * 2 * m,
+                 mean ? mean + 2 * (I.node_off + pid) : nullptr,
+                 spread ? spread + 2 * (I.node_off + pid) : nullptr,
+                 scr + (size_t)node * (P64_SCR + 8), counters, I.basis + (size_t)pid * 64 * 64,
+                 half, 1 + node);
+}
+
+cudaError_t launch_class64(letkf_ctx *h, void *mean, void *spread) {
+  if (h->n_tiles[2] == 0) return cudaSuccess;
+  int wmax = 1;
+  for (const LkInst &I : h->inst)
+    if (I.mp == 64) wmax = I.w > wmax ? I.w : wmax;
+  analysis_tile64_kernel<<<h->n_tiles[2], P64_TI * P64_TJ * 64, p64_smem_bytes(wmax), h->stream>>>(
+      h->d_inst, h->tiles[2], (float *)mean, (float *)spread, (float)h->tol32, h->max_sweeps,
+      h->counters);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_class64(letkf_ctx *h) {
+  int wmax = 0;
+  for (const LkInst &I : h->inst)
+    if (I.mp == 64) wmax = I.w > wmax ? I.w : wmax;
+  if (wmax == 0) return cudaSuccess;
+  return cudaFuncSetAttribute(analysis_tile64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)p64_smem_bytes(wmax));
+}
+
 template <int MP, typename S, typename T, int TI, int TJ>
 cudaError_t launch_tile_shape(letkf_ctx *h, int cls, void *mean, void *spread, T tol, T kthr) {
   size_t need = 0;
@@ -680,6 +977,7 @@ int lk_width_class(int m) { return m <= 16 ? 0 : (m <= 32 ? 1 : 2); }
 cudaError_t lk_setup_analysis(letkf_ctx *h) {
   cudaError_t e = setup_class<16>(h);
   if (e == cudaSuccess) e = setup_class<32>(h);
+  if (e == cudaSuccess) e = setup_class64(h);
   return e;
 }
 
@@ -687,6 +985,7 @@ cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread) {
   cudaError_t e = cudaMemsetAsync(h->counters + 1, 0, 7 * sizeof(int), h->stream);
   if (e == cudaSuccess) e = launch_class<16>(h, 0, mean, spread);
   if (e == cudaSuccess) e = launch_class<32>(h, 1, mean, spread);
+  if (e == cudaSuccess) e = launch_class64(h, mean, spread);
   return e;
 }
 

@@ -86,7 +86,9 @@ struct DeviceGuard {
 letkf_status check_config(const letkf_config &c) {
   if (c.nsub < 1 || c.nsub > 1024) return fail(nullptr, LETKF_ERR_ARG, "nsub must be in 1..1024");
   if (!c.subap_mask) return fail(nullptr, LETKF_ERR_ARG, "subap_mask is NULL");
-  if (c.m < 2 || c.m > 32) return fail(nullptr, LETKF_ERR_ARG, "m must be in 2..32");
+  if (c.m < 2 || c.m > 64) return fail(nullptr, LETKF_ERR_ARG, "m must be in 2..64");
+  if (c.precision == 1 && c.m > 32)
+    return fail(nullptr, LETKF_ERR_ARG, "m must be in 2..32 with precision 1");
   if (c.window < 1 || c.window > 31) return fail(nullptr, LETKF_ERR_ARG, "window must be in 1..31");
   if (c.taper != 0 && c.taper != 1) return fail(nullptr, LETKF_ERR_ARG, "taper must be 0 or 1");
   if (!(c.rho > 0) || !(c.sigma2 > 0) || !isfinite(c.rho) || !isfinite(c.sigma2))
@@ -224,6 +226,7 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   h->max_sweeps = cfgs[0].max_sweeps > 0 ? cfgs[0].max_sweeps : 20;
   h->fp64_kappa = cfgs[0].fp64_kappa;
   h->n_inst = n;
+  h->tile_shape[2] = 2;               // 33..64 members: fixed 2 x 2 node tiles (warp pair per node)
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     delete h;
     return fail(nullptr, LETKF_ERR_CUDA, "no CUDA device");
@@ -247,7 +250,7 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
     I.m = c.m;
     I.w = c.window;
     I.h = c.window / 2;
-    I.mp = c.m <= 16 ? 16 : 32;
+    I.mp = c.m <= 16 ? 16 : (c.m <= 32 ? 32 : 64);
     I.n_pts = (int)geo[k].pts.size();
     I.n_sap = (int)geo[k].saps.size();
     I.p = 2 * I.n_sap;
@@ -550,6 +553,8 @@ letkf_status letkf_set_tile_shape(letkf_t h, int32_t width_class, int32_t shape)
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
   if (width_class < 0 || width_class > 2 || shape < 0 || shape >= lk_num_tile_shapes())
     return fail(h, LETKF_ERR_ARG, "width class or tile shape out of range");
+  if (width_class == 2 && shape != 2)
+    return fail(h, LETKF_ERR_ARG, "ensembles of 33..64 members use tile shape 2 (2 x 2) only");
   DeviceGuard dg(h->device);
   LK_CUDA(h, cudaStreamSynchronize(h->stream));
   h->tile_shape[width_class] = shape;
@@ -586,7 +591,7 @@ letkf_status letkf_autotune(letkf_t h, const void *y_dev, int32_t reps, int32_t 
   for (int cls = 0; cls < 3 && e == cudaSuccess && st == LETKF_OK; ++cls) {
     if (shapes_out) shapes_out[cls] = h->tile_shape[cls];
     if (us_out) us_out[cls] = 0.f;
-    if (h->n_tiles[cls] == 0) continue;
+    if (h->n_tiles[cls] == 0 || cls == 2) continue;
     int best = h->tile_shape[cls];
     float best_ms = 1e30f;
     for (int s = 0; s < ns && e == cudaSuccess && st == LETKF_OK; ++s) {

@@ -53,7 +53,7 @@ def _cfg(mask, **kw):
     return c
 
 
-@pytest.mark.parametrize("bad", [dict(m=1), dict(m=33), dict(window=0), dict(window=32),
+@pytest.mark.parametrize("bad", [dict(m=1), dict(m=65), dict(m=33, precision=1), dict(window=0), dict(window=32),
                                  dict(taper=2), dict(rho=0.0), dict(sigma2=-1.0),
                                  dict(precision=3), dict(nsub=0), dict(rho=float("nan"))])
 def test_create_rejects_bad_arguments(built, bad):

@@ -118,3 +118,58 @@ def test_batch_closed_loop_matches_oracle_per_instance():
             w.a_ar1, w.noise_std, w.seeds[2], frames,
             X0=inp.X0.astype(np.float32).astype(np.float64), batched=True)
         assert np.max(np.abs(rv[:, k] - rv_ref) / rv_ref) <= 1e-3, w.name
+
+
+WIDE = [replace(W.ELT_80X80, name="w48", nsub=16, m=48, window=7, seeds=(141, 142, 143)),
+        replace(W.TEL_16M, name="w40", nsub=12, m=40, window=5, seeds=(151, 152, 153))]
+
+
+@pytest.mark.parametrize("w", WIDE, ids=[w.name for w in WIDE])
+def test_wide_ensemble_matches_oracle(w):
+    """33..64 members (one node per warp pair, FP32 only) on steady-state loop
+    backgrounds (the prior-draw transient needs the FP64 path, which this width
+    class does not have)."""
+    inp = synth.make_loop_inputs(w, frames=10)
+    geom = oracle.build_geometry(inp.subap_mask, w.window, w.taper, w.loc_len)
+    X = inp.X0.copy()
+    for k in range(8):
+        Xa, _, _ = oracle.analysis_batched(geom, X, inp.slopes[k], w.sigma2, w.rho)
+        X = oracle.forecast(Xa, oracle.bank_noise(inp.bank, geom.points, w.m, w.seeds[2], k,
+                                                  w.noise_std), w.a_ar1)
+    Xb = X.astype(np.float32)
+    y = inp.slopes[8].astype(np.float32)
+    rXa, rmean, rspread = oracle.analysis(geom, Xb.astype(np.float64), y.astype(np.float64),
+                                          w.sigma2, w.rho)
+    f = L.Letkf.from_workload(w, bank=inp.bank)
+    f.set_state(torch.from_numpy(Xb).cuda())
+    mean, spread = f.analyze(torch.from_numpy(y).cuda())
+    f.sync()
+    Xa = f.get_state().cpu().numpy().astype(np.float64)
+    assert rel(mean.cpu().numpy(), rmean) <= 1e-4
+    assert rel(spread.cpu().numpy(), rspread) <= 1e-3
+    an = Xa - Xa.mean(-1, keepdims=True)
+    ar = rXa - rXa.mean(-1, keepdims=True)
+    assert rel(an, ar) <= 1e-3
+    f.close()
+
+
+def test_mixed_batch_with_wide_ensembles_equals_separate_handles():
+    ws = [BATCH[0], WIDE[0], BATCH[1], WIDE[1]]
+    ins = [synth.make_loop_inputs(w, frames=5) for w in ws]
+    f = L.Letkf.batch(ws, [i.bank for i in ins])
+    X0 = np.concatenate([i.X0.astype(np.float32).ravel() for i in ins])
+    y = torch.from_numpy(np.concatenate([i.slopes.astype(np.float32) for i in ins], 1)).cuda()
+    f.set_state(torch.from_numpy(X0).cuda())
+    f.run(5, y, use_graph=True)
+    f.sync()
+    Xb = f.get_state().cpu().numpy()
+    f.close()
+    parts = []
+    for w, inp in zip(ws, ins):
+        g = L.Letkf.from_workload(w, bank=inp.bank)
+        g.set_state(torch.from_numpy(inp.X0.astype(np.float32)).cuda())
+        g.run(5, torch.from_numpy(inp.slopes.astype(np.float32)).cuda(), use_graph=False)
+        g.sync()
+        parts.append(g.get_state().cpu().numpy().ravel())
+        g.close()
+    assert np.array_equal(Xb, np.concatenate(parts))
