@@ -162,7 +162,9 @@ letkf_status letkf_run(letkf_t h, int32_t frames, const void *y_seq_dev, const v
  * warp pair, fixed shape 2 = 2 x 2 nodes, no FP64 fallback). letkf_set_tile_shape selects
  * a shape for one class; letkf_autotune times every shape for every class
  * present on the handle's current ensemble with slopes y_dev (reps timed
- * analyses each, state restored afterwards), keeps the fastest and writes the
+ * analyses of that class's nodes each, state restored afterwards; tune on a
+ * loop state, not on a fresh prior draw whose nodes mostly take the FP64
+ * path), keeps the fastest and writes the
  * choices to shapes_out[3] and their analysis time in microseconds to us_out[3]
  * (either may be NULL). Both synchronise; choices may be cached by the caller
  * and restored with letkf_set_tile_shape. */

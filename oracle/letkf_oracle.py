@@ -52,6 +52,9 @@ class Geometry:
     D1: scipy.sparse.csr_matrix   # float64 [p, n_pts] Fried slope operator (4 nonzeros per row)
     win_idx: list                 # per point: int array of slope indices into y
     win_tau: list                 # per point: float64 taper of each slope
+    win_dist: list = None         # per point: node-to-subaperture-centre distance (pitches)
+    taper: int = 0
+    loc_len: float = 0.0          # Gaspari-Cohn half-support actually used
 
     @property
     def n_pts(self) -> int:
@@ -74,6 +77,20 @@ def gaspari_cohn(z):
     zb = z[b]
     out[b] = (zb**5 / 12.0 - 0.5 * zb**4 + 0.625 * zb**3 + (5.0 / 3.0) * zb**2
               - 5.0 * zb + 4.0 - (2.0 / 3.0) / zb)
+    return out
+
+
+def gaspari_cohn_deriv(z):
+    """d/dz of gaspari_cohn (differentiating its two polynomial pieces)."""
+    z = np.abs(np.asarray(z, dtype=np.float64))
+    out = np.zeros_like(z)
+    a = z <= 1.0
+    b = (z > 1.0) & (z < 2.0)
+    za = z[a]
+    out[a] = -1.25 * za**4 + 2.0 * za**3 + 1.875 * za**2 - (10.0 / 3.0) * za
+    zb = z[b]
+    out[b] = (5.0 / 12.0) * zb**4 - 2.0 * zb**3 + 1.875 * zb**2 + (10.0 / 3.0) * zb - 5.0 \
+        + (2.0 / 3.0) / zb**2
     return out
 
 
@@ -118,9 +135,9 @@ def build_geometry(subap_mask, window: int, taper: int = 0, loc_len: float = 0.0
     D1 = D1.tocsr()
     h = window // 2
     c = loc_len if loc_len > 0 else window / 4.0
-    win_idx, win_tau = [], []
+    win_idx, win_tau, win_dist = [], [], []
     for (i, j) in points:
-        idx, tau = [], []
+        idx, tau, dist_l = [], [], []
         for s in range(i - h, i - h + window):
             for t in range(j - h, j - h + window):
                 if 0 <= s < nsub and 0 <= t < nsub and sm[s, t]:
@@ -132,9 +149,12 @@ def build_geometry(subap_mask, window: int, taper: int = 0, loc_len: float = 0.0
                         tk = 1.0
                     idx += [k, n_sap + k]
                     tau += [tk, tk]
+                    dd = math.hypot(s + 0.5 - i, t + 0.5 - j)
+                    dist_l += [dd, dd]
         win_idx.append(np.array(idx, int))
         win_tau.append(np.array(tau, float))
-    return Geometry(nsub, sm, points, subaps, D1, win_idx, win_tau)
+        win_dist.append(np.array(dist_l, float))
+    return Geometry(nsub, sm, points, subaps, D1, win_idx, win_tau, win_dist, taper, c)
 
 
 # ---------------------------------------------------------------------------
@@ -304,3 +324,110 @@ def closed_loop(geom: Geometry, truth, slopes, bank, m: int, sigma2: float, rho:
         v = bank_noise(bank, geom.points, m, seed, k, noise_scale)
         X = forecast(Xa, v, a)
     return resvar, X, np.array(means)
+
+
+# ---------------------------------------------------------------------------
+# Reverse mode of the closed loop (gradient of the mean residual variance)
+# ---------------------------------------------------------------------------
+
+
+def analysis_adjoint(geom: Geometry, Xb, y, sigma2: float, rho: float, Xa_bar):
+    """Adjoint of one analysis (Section 4.2) at background Xb and slopes y.
+
+    Xa_bar [n_pts, 2, m]: gradient of a scalar with respect to the analysis
+    ensemble. Returns (Xb_bar [n_pts, 2, m], d/drho, d/dsigma2, d/dL) of that
+    scalar, L the Gaspari-Cohn half-support. Per node, with c_j = tau_j/sigma2,
+    A = (m-1)/rho I + sum_j c_j y_j y_j^T, b = sum_j c_j d_j y_j,
+    wbar = A^-1 b, W = sqrt(m-1) A^-1/2 and Xa_r = xbar_r + X'_r (wbar 1^T + W):
+      Xa_r -> xbar_r, X'_r, wbar, W;
+      wbar -> b_bar = A^-1 wbar_bar, A_bar -= b_bar wbar^T;
+      W -> A_bar += sqrt(m-1) Q (F o (Q^T W_bar Q)) Q^T, F_pq the divided
+           difference of lambda^-1/2, -1/(sqrt(l_p) sqrt(l_q) (sqrt(l_p) + sqrt(l_q)));
+      A, b -> y_j, d_j, c_j, (m-1)/rho; then the slopes back to the nodes
+      through D1 and the anomaly / mean split (Section 3.1).
+    """
+    Xb = np.asarray(Xb, dtype=np.float64)
+    n_pts, _, m = Xb.shape
+    xbar, Xp, Yb, ybar = observe(geom, Xb)
+    d = np.asarray(y, dtype=np.float64) - ybar
+    Xp_bar = np.zeros_like(Xb)                 # adjoint of the anomalies X'
+    xbar_bar = np.zeros((n_pts, 2))
+    Yb_bar = np.zeros_like(Yb)
+    d_bar = np.zeros_like(d)
+    alpha = (m - 1) / rho
+    g_alpha = g_s2 = g_L = 0.0
+    one = np.ones(m)
+    for g in range(n_pts):
+        idx = geom.win_idx[g]
+        tau = geom.win_tau[g]
+        cw = tau / sigma2
+        Yl = Yb[idx]
+        dl = d[idx]
+        A = alpha * np.eye(m) + (Yl.T * cw) @ Yl
+        bvec = Yl.T @ (cw * dl)
+        lam, Q = np.linalg.eigh(A)
+        wbar = Q @ ((Q.T @ bvec) / lam)
+        W = np.sqrt(m - 1) * (Q / np.sqrt(lam)) @ Q.T
+        G = Xa_bar[g]                           # [2, m]
+        ssum = G @ one                          # [2]
+        xbar_bar[g] += ssum
+        Xp_bar[g] += np.outer(ssum, wbar) + G @ W.T
+        wbar_bar = Xp[g].T @ ssum
+        W_bar = Xp[g].T @ G
+        b_bar = Q @ ((Q.T @ wbar_bar) / lam)
+        A_bar = -np.outer(b_bar, wbar)
+        rl = np.sqrt(lam)
+        F = -1.0 / (np.outer(rl, rl) * (rl[:, None] + rl[None, :]))
+        A_bar += np.sqrt(m - 1) * Q @ (F * (Q.T @ W_bar @ Q)) @ Q.T
+        As = 0.5 * (A_bar + A_bar.T)
+        g_alpha += np.trace(As)
+        Yb_bar[idx] += 2.0 * cw[:, None] * (Yl @ As) + np.outer(cw * dl, b_bar)
+        yb = Yl @ b_bar
+        d_bar[idx] += cw * yb
+        c_bar = np.einsum("jm,mn,jn->j", Yl, As, Yl) + dl * yb
+        g_s2 += np.sum(c_bar * (-cw / sigma2))
+        if geom.taper == 1:
+            z = geom.win_dist[g] / geom.loc_len
+            dtau = gaspari_cohn_deriv(z) * (-z / geom.loc_len)
+            g_L += np.sum(c_bar * dtau / sigma2)
+    # slopes -> anomalies / means of the phi_{k-1} row (Yb = D1 X'_1, ybar = D1 xbar_1)
+    Xp_bar[:, 1, :] += geom.D1.T @ Yb_bar
+    xbar_bar[:, 1] += -(geom.D1.T @ d_bar)
+    # X' = X - xbar 1^T, xbar = mean
+    Xb_bar = Xp_bar - Xp_bar.mean(axis=-1, keepdims=True) + xbar_bar[..., None] / m
+    g_rho = g_alpha * (-(m - 1) / rho**2)
+    return Xb_bar, g_rho, g_s2, g_L
+
+
+def residual_variance_grad(truth_k, X):
+    """d/dX of residual_variance(truth_k, X)."""
+    n_pts, _, m = X.shape
+    r = truth_k - X[:, 0, :].mean(axis=-1)
+    r = r - r.mean()
+    G = np.zeros_like(X)
+    G[:, 0, :] = (-2.0 / (n_pts * m)) * r[:, None]
+    return G
+
+
+def closed_loop_grad(geom: Geometry, truth, slopes, bank, m: int, sigma2: float, rho: float,
+                     a: float, noise_scale: float, seed: int, frames: int, X0):
+    """J = mean over the frames of the residual variance of the prediction
+    (Section 2.1, Eq. Crit_Opt) and its gradient with respect to (rho, sigma2,
+    L), by reverse mode through the analyses and AR(1) forecasts, from X0."""
+    X = np.array(X0, dtype=np.float64)
+    Xs, J = [], 0.0
+    for k in range(frames):
+        Xs.append(X)
+        J += residual_variance(truth[k], X)
+        Xa, _, _ = analysis(geom, X, slopes[k], sigma2, rho)
+        X = forecast(Xa, bank_noise(bank, geom.points, m, seed, k, noise_scale), a)
+    J /= frames
+    grad = np.zeros(3)
+    lam_next = np.zeros_like(X)                 # adjoint of X_{k+1}
+    for k in range(frames - 1, -1, -1):
+        Xa_bar = np.zeros_like(X)
+        Xa_bar[:, 0, :] = a * lam_next[:, 0, :] + lam_next[:, 1, :]
+        Xb_bar, gr, gs, gl = analysis_adjoint(geom, Xs[k], slopes[k], sigma2, rho, Xa_bar)
+        grad += (gr, gs, gl)
+        lam_next = Xb_bar + residual_variance_grad(truth[k], Xs[k]) / frames
+    return J, grad, lam_next

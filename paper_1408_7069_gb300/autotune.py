@@ -1,0 +1,66 @@
+"""Tile-shape autotuning with a JSON cache.
+
+The analysis runs one CTA per tile of nodes; which of the compiled tile shapes
+is fastest depends on the windows, ensemble sizes and instance mix. `tune()`
+times every shape per width class through ``letkf_autotune`` on the handle's
+current ensemble and caches the choice under a key made of the GPU name and
+the instances' (nsub, m, window) triples; later handles with the same key reuse
+it through ``letkf_set_tile_shape``.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+from . import letkf as L
+
+
+def cache_path() -> str:
+    return os.environ.get("LETKF_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "letkf_gb300",
+                                       "tiles.json"))
+
+
+def signature(gpu_name: str, shapes) -> str:
+    """Cache key: GPU name and the sorted (nsub, m, window) of the instances."""
+    body = json.dumps([gpu_name, sorted(tuple(s) for s in shapes)])
+    return hashlib.sha1(body.encode()).hexdigest()
+
+
+def tune(f: "L.Letkf", y, shapes, reps: int = 3, path: str | None = None,
+         refresh: bool = False) -> dict:
+    """Select tile shapes for handle ``f`` (cached or timed). ``shapes``: the
+    (nsub, m, window) of every instance. Returns the record used."""
+    import torch
+    path = path or cache_path()
+    key = signature(torch.cuda.get_device_name(), shapes)
+    cache = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as fh:
+                cache = json.load(fh)
+        except (OSError, ValueError):
+            cache = {}
+    rec = None if refresh else cache.get(key)
+    if rec is not None:
+        for cls, s in enumerate(rec["shapes"]):
+            if f.instances and any(_cls(m) == cls for _, _, m in f.instances):
+                f.set_tile_shape(cls, s)
+        rec = dict(rec, cached=True)
+        return rec
+    chosen, us = f.autotune(y, reps=reps)
+    rec = {"shapes": chosen, "us": us, "tiles": [L.letkf_tile_shape(s) for s in chosen],
+           "cached": False}
+    cache[key] = {k: v for k, v in rec.items() if k != "cached"}
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as fh:
+            json.dump(cache, fh, indent=1)
+    except OSError:
+        pass
+    return rec
+
+
+def _cls(m: int) -> int:
+    return 0 if m <= 16 else (1 if m <= 32 else 2)

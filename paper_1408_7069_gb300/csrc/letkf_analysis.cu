@@ -981,6 +981,14 @@ cudaError_t lk_setup_analysis(letkf_ctx *h) {
   return e;
 }
 
+cudaError_t lk_launch_analysis_class(letkf_ctx *h, int cls, void *mean, void *spread) {
+  cudaError_t e = cudaMemsetAsync(h->counters + 1, 0, 7 * sizeof(int), h->stream);
+  if (e != cudaSuccess) return e;
+  if (cls == 0) return launch_class<16>(h, 0, mean, spread);
+  if (cls == 1) return launch_class<32>(h, 1, mean, spread);
+  return launch_class64(h, mean, spread);
+}
+
 cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread) {
   cudaError_t e = cudaMemsetAsync(h->counters + 1, 0, 7 * sizeof(int), h->stream);
   if (e == cudaSuccess) e = launch_class<16>(h, 0, mean, spread);

@@ -606,7 +606,7 @@ letkf_status letkf_autotune(letkf_t h, const void *y_dev, int32_t reps, int32_t 
                               h->stream);
         if (e == cudaSuccess) e = lk_launch_obs(h, y_dev, nullptr);
         if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-        if (e == cudaSuccess) e = lk_launch_analysis(h, nullptr, nullptr);
+        if (e == cudaSuccess) e = lk_launch_analysis_class(h, cls, nullptr, nullptr);
         if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;

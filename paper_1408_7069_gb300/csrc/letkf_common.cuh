@@ -109,6 +109,7 @@ struct letkf_ctx {
 // the instances in instance order.
 cudaError_t lk_launch_obs(letkf_ctx *h, const void *y, const long long *run_idx);
 cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread);
+cudaError_t lk_launch_analysis_class(letkf_ctx *h, int cls, void *mean, void *spread);
 cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise);
 cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
                                const long long *run_idx);
