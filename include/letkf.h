@@ -115,7 +115,10 @@ letkf_status letkf_query_instance(letkf_t h, int32_t i, int32_t *n_pts, int32_t 
  * valid window slopes per node [n_pts] (p_l, Section 4.2's p_d). Either may be NULL. */
 letkf_status letkf_query_points(letkf_t h, int32_t *ij_host, int32_t *window_slopes_host);
 
-/* Copy the ensemble [n_pts][2][m] (real) from / into device memory. */
+/* Copy the ensemble [n_pts][2][m] (real) from / into device memory.
+ * letkf_set_state also resets every node's stored eigenbasis (the starting
+ * point of the next FP32 eigensolve) to the identity, so the analyses that
+ * follow depend on the new ensemble only. */
 letkf_status letkf_get_state(letkf_t h, void *X_dev);
 letkf_status letkf_set_state(letkf_t h, const void *X_dev);
 
@@ -152,6 +155,45 @@ letkf_status letkf_residual(letkf_t h, const void *truth_dev, double *resvar_dev
  * noise bank for every instance. */
 letkf_status letkf_run(letkf_t h, int32_t frames, const void *y_seq_dev, const void *truth_seq_dev,
                        double *resvar_dev, int32_t use_graph);
+
+/* Change instance i's inflation rho, slope noise variance sigma2 and taper
+ * half-support loc_len (<= 0: window / 4) in place (Section 4.2: A = (m-1)/rho I
+ * + Yb^T R^-1 Yb with R^-1 = diag(tau_j / sigma2)); the next analysis uses them.
+ * LETKF_ERR_ARG unless rho, sigma2 > 0 and all are finite. Synchronises. */
+letkf_status letkf_set_params(letkf_t h, int32_t i, double rho, double sigma2, double loc_len);
+
+/* Set the forecast counter: the next forecast with bank noise draws the noise
+ * of frame `frame` (>= 0) and later ones follow on. A new handle starts at 0.
+ * Synchronises. */
+letkf_status letkf_set_frame(letkf_t h, int64_t frame);
+
+/* Reverse mode of the closed loop. J = mean over `frames` frames of the
+ * residual variance of the prediction (Section 2.1 Eq. Crit_Opt, as in
+ * letkf_residual), each frame run as in letkf_run (residual of the current
+ * prediction, analysis of y_seq[k] by Section 4.2, forecast of Section 3.1.2
+ * with bank noise) from the handle's current ensemble, eigenbases and frame
+ * counter; and grad = (dJ/drho, dJ/dsigma2, dJ/dL), L the Gaspari-Cohn
+ * half-support of the taper (cfg.loc_len, or window / 4 when that is <= 0; the
+ * L component is 0 without the taper). The analysis is differentiated through
+ * its eigendecomposition with divided differences of lambda^-1/2 written in a
+ * form exact for equal eigenvalues, so windows with fewer slopes than m - 1
+ * (exactly degenerate eigenvalues) need no special case. The backward pass
+ * recomputes each node's eigenbasis from the one its forward analysis stored
+ * (FP32), and in FP64 for the nodes that the FP64 fallback takes.
+ * y_seq_dev: device [frames][p] real; truth_seq_dev: device [frames][n_pts] real.
+ * ckpt_every: frames per segment; the forward keeps the ensemble and bases at
+ *   the start of every segment and the backward recomputes one segment at a
+ *   time (device memory ~ (frames / ckpt_every + ckpt_every) states); <= 0 or
+ *   >= frames keeps every frame (no recomputation).
+ * J_out, grad_out: host double[1] and double[3], either may be NULL.
+ * Single-instance handles with m <= 32 and a noise bank only (LETKF_ERR_ARG /
+ * LETKF_ERR_STATE otherwise). On return the handle holds the state letkf_run
+ * would leave after the same frames. With a non-default stream the whole
+ * computation is captured once into a CUDA graph (rebuilt when the sequence
+ * pointers, frames or ckpt_every change) and replayed. Synchronises. The
+ * result is bitwise reproducible for the same inputs. */
+letkf_status letkf_grad(letkf_t h, int32_t frames, const void *y_seq_dev, const void *truth_seq_dev,
+                        int32_t ckpt_every, double *J_out, double *grad_out);
 
 /* Analysis tile shapes. The analysis runs one CTA per tile of tile_i x tile_j
  * nodes (one warp per node) and stages the tile's window halo in shared

@@ -29,7 +29,7 @@
 #include <mutex>
 #include <type_traits>
 
-#include "letkf_common.cuh"
+#include "letkf_device.cuh"
 
 // Tile shapes (nodes per CTA side) the autotuner chooses from; each divides
 // LK_TILE_MAX so the padded grid covers every tile's halo.
@@ -39,10 +39,6 @@ constexpr int LK_NUM_SHAPES = 4;
 namespace {
 
 constexpr int LIST_WARPS = 4;
-constexpr unsigned FULL = 0xffffffffu;
-
-__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-
 // Per-warp scratch: V staging [MP][MP+1] + 3 vectors, or A staging [MP][MP+4].
 template <int MP, typename T>
 __host__ __device__ constexpr size_t scratch_elems() {
@@ -72,140 +68,6 @@ __host__ __device__ size_t list_warp_bytes(int w) {
   const size_t wc = (size_t)w * w;
   return align16(wc * 2 * MP * sizeof(float)) + align16(wc * 2 * sizeof(float)) +
          align16(wc * sizeof(double)) + scratch_elems<MP, double>() * sizeof(double);
-}
-
-__device__ __forceinline__ void ld4(const float *p, float &a, float &b, float &c, float &d) {
-  const float4 v = *reinterpret_cast<const float4 *>(p);
-  a = v.x; b = v.y; c = v.z; d = v.w;
-}
-__device__ __forceinline__ void ld4(const float *p, double &a, double &b, double &c, double &d) {
-  const float4 v = *reinterpret_cast<const float4 *>(p);
-  a = v.x; b = v.y; c = v.z; d = v.w;
-}
-__device__ __forceinline__ void ld4(const double *p, double &a, double &b, double &c, double &d) {
-  const double2 u = *reinterpret_cast<const double2 *>(p);
-  const double2 v = *reinterpret_cast<const double2 *>(p + 2);
-  a = u.x; b = u.y; c = v.x; d = v.y;
-}
-
-__device__ __forceinline__ float lk_rsqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double lk_rsqrt(double x) { return rsqrt(x); }
-
-// Dot product of two register columns with four independent FMA chains (the
-// grouping is the same on both lanes of a pair, so both get the same bits).
-template <int MP, typename T>
-__device__ __forceinline__ T dot4(const T (&a)[MP], const T (&b)[MP]) {
-  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-#pragma unroll
-  for (int k = 0; k < MP; k += 4) {
-    s0 = fma(a[k], b[k], s0);
-    s1 = fma(a[k + 1], b[k + 1], s1);
-    s2 = fma(a[k + 2], b[k + 2], s2);
-    s3 = fma(a[k + 3], b[k + 3], s3);
-  }
-  return (s0 + s1) + (s2 + s3);
-}
-
-// Row `lane` of A = (m-1)/rho I + sum_j c_j y_j y_j^T (identity on the padding),
-// plus (C d)_lane and G_lane,lane. win / dwin: the node's window in shared memory,
-// cell (ds, dt) at row stride `stride` cells.
-template <int MP, typename S, typename T>
-__device__ __forceinline__ void gram(const S *__restrict__ win, const S *__restrict__ dwin,
-                                     int stride, const T *__restrict__ tap, int w, int m, T alpha,
-                                     T (&b)[MP], T &diag, T &cd) {
-  const int lane = threadIdx.x & 31;
-  const bool col = lane < MP;
-#pragma unroll
-  for (int k = 0; k < MP; ++k) b[k] = T(0);
-  diag = T(0);
-  cd = T(0);
-  for (int ds = 0; ds < w; ++ds) {
-    for (int dt = 0; dt < w; ++dt) {
-      const int cell = ds * stride + dt;
-      const S *cy2 = win + (size_t)cell * 2 * MP;
-      const T tw = tap[ds * w + dt];
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const S *yv = cy2 + c * MP;
-        const T yl = col ? T(yv[lane]) : T(0);
-        const T cy = tw * yl;
-        diag = fma(cy, yl, diag);
-        cd = fma(cy, T(dwin[cell * 2 + c]), cd);
-#pragma unroll
-        for (int k = 0; k < MP; k += 4) {
-          T y0, y1, y2, y3;
-          ld4(yv + k, y0, y1, y2, y3);
-          b[k] = fma(cy, y0, b[k]);
-          b[k + 1] = fma(cy, y1, b[k + 1]);
-          b[k + 2] = fma(cy, y2, b[k + 2]);
-          b[k + 3] = fma(cy, y3, b[k + 3]);
-        }
-      }
-    }
-  }
-  const T dval = lane < m ? alpha : T(1);
-#pragma unroll
-  for (int k = 0; k < MP; ++k)
-    if (k == lane) b[k] += dval;
-}
-
-// One Hestenes rotation step for pair (lane, lane ^ t) on column b (and v when
-// ACCUM). nrm = |b|^2 of this lane's column. Returns whether it rotated.
-template <int MP, typename T, bool ACCUM>
-__device__ __forceinline__ int jacobi_step(T (&b)[MP], T (&v)[MP], T &nrm, int t, T tol) {
-  const int lane = threadIdx.x & 31;
-  T pb[MP];
-#pragma unroll
-  for (int k = 0; k < MP; ++k) pb[k] = __shfl_xor_sync(FULL, b[k], t);
-  const T dot = dot4<MP, T>(b, pb);
-  const T pn = __shfl_xor_sync(FULL, nrm, t);
-  const bool isp = lane < (lane ^ t);  // this lane holds column p of the pair (p < q)
-  const T app = isp ? nrm : pn;
-  const T aqq = isp ? pn : nrm;
-  T cs = T(1), sn = T(0), tr = T(0);
-  int rot = 0;
-  if (fabs(dot) > tol * sqrt(app * aqq)) {
-    const T zeta = (aqq - app) / (T(2) * dot);
-    const T az = fabs(zeta);
-    tr = az > T(1e15) ? T(0.5) / zeta : copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
-    cs = lk_rsqrt(T(1) + tr * tr);
-    sn = cs * tr;
-    rot = 1;
-  }
-  const T sg = isp ? -sn : sn;  // p' = c p - s q ; q' = s p + c q
-#pragma unroll
-  for (int k = 0; k < MP; ++k) b[k] = fma(sg, pb[k], cs * b[k]);
-  nrm = isp ? (app - tr * dot) : (aqq + tr * dot);
-  if (ACCUM) {
-#pragma unroll
-    for (int k = 0; k < MP; ++k) pb[k] = __shfl_xor_sync(FULL, v[k], t);
-#pragma unroll
-    for (int k = 0; k < MP; ++k) v[k] = fma(sg, pb[k], cs * v[k]);
-  }
-  return rot;
-}
-
-// Sweeps until a full sweep makes no rotation. Records the sweep count and a
-// non-convergence flag.
-template <int MP, typename T, bool ACCUM>
-__device__ __forceinline__ void jacobi(T (&b)[MP], T (&v)[MP], T tol, int max_sweeps,
-                                       int *__restrict__ counters) {
-  int sweep = 0;
-  bool converged = false;
-  for (; sweep < max_sweeps; ++sweep) {
-    T nrm = dot4<MP, T>(b, b);
-    int rotated = 0;
-    for (int t = 1; t < MP; ++t) rotated |= jacobi_step<MP, T, ACCUM>(b, v, nrm, t, tol);
-    if (!__any_sync(FULL, rotated)) {
-      converged = true;
-      break;
-    }
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&counters[2], converged ? sweep + 1 : sweep);
-    atomicAdd(&counters[3], converged ? sweep + 1 : sweep);
-    if (!converged) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
-  }
 }
 
 // FP32 one-sided Jacobi on B alone with scaled ("fast") rotations: the true

@@ -62,6 +62,7 @@ letkf_status upload(letkf_ctx *h, void *dst, const void *src, size_t bytes) {
 
 void release(letkf_ctx *h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  lk_adjoint_release(h);
   void *bufs[] = {h->X,          h->Ybp,      h->dp,       h->taper,    h->pid_map,
                   h->pts,        h->saps,     h->bank,     h->basis,    h->counters,
                   h->worklist,   h->frame,    h->partial,  h->d_inst,   h->obs_items,
@@ -110,6 +111,25 @@ struct HostInst {
   std::vector<double> taper;
 };
 
+// Taper weights tau / sigma2 by window offset: subaperture (s, t) = (i - h + ds, j - h + dt)
+// has its centre at (ds - h + 0.5, dt - h + 0.5) pitches from node (i, j).
+void taper_table(const letkf_config &c, std::vector<double> &tap) {
+  const int w = c.window, hw = w / 2;
+  const double cl = c.loc_len > 0 ? c.loc_len : w / 4.0;
+  tap.resize((size_t)w * w);
+  for (int ds = 0; ds < w; ++ds)
+    for (int dt = 0; dt < w; ++dt) {
+      const double tau = c.taper == 1 ? gaspari_cohn(hypot(ds - hw + 0.5, dt - hw + 0.5) / cl) : 1.0;
+      tap[(size_t)ds * w + dt] = tau / c.sigma2;
+    }
+}
+
+letkf_status upload_taper(letkf_ctx *h, const LkInst &I, const std::vector<double> &tap) {
+  if (h->precision) return upload(h, (void *)I.taper, tap.data(), tap.size() * sizeof(double));
+  std::vector<float> t32(tap.begin(), tap.end());
+  return upload(h, (void *)I.taper, t32.data(), t32.size() * sizeof(float));
+}
+
 void build_geometry(const letkf_config &c, HostInst &g) {
   const int ns = c.nsub, nn = ns + 1, w = c.window, hw = w / 2;
   g.pid.assign((size_t)nn * nn, -1);
@@ -136,15 +156,7 @@ void build_geometry(const letkf_config &c, HostInst &g) {
         if (s >= 0 && s < ns && t >= 0 && t < ns && c.subap_mask[(size_t)s * ns + t]) cnt += 2;
     g.wslopes[k] = cnt;
   }
-  // taper weights tau / sigma2 by window offset: subaperture (s, t) = (i - h + ds, j - h + dt)
-  // has its centre at (ds - h + 0.5, dt - h + 0.5) pitches from node (i, j)
-  const double cl = c.loc_len > 0 ? c.loc_len : w / 4.0;
-  g.taper.resize((size_t)w * w);
-  for (int ds = 0; ds < w; ++ds)
-    for (int dt = 0; dt < w; ++dt) {
-      const double tau = c.taper == 1 ? gaspari_cohn(hypot(ds - hw + 0.5, dt - hw + 0.5) / cl) : 1.0;
-      g.taper[(size_t)ds * w + dt] = tau / c.sigma2;
-    }
+  taper_table(c, g.taper);
 }
 
 int padded_grid(int nsub, int w) {
@@ -189,6 +201,7 @@ letkf_status build_tiles(letkf_ctx *h, int cls, const std::vector<std::vector<in
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
   }
+  lk_adjoint_release(h);   // its graph holds the old tile list
   return upload(h, h->tiles[cls], tl.data(), tl.size() * sizeof(LkTile));
 }
 
@@ -217,9 +230,12 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   }
   letkf_ctx *h = new (std::nothrow) letkf_ctx();
   if (!h) return fail(nullptr, LETKF_ERR_NOMEM, "host allocation failed");
-  h->cfg = cfgs[0];
-  h->cfg.subap_mask = nullptr;
-  h->cfg.noise_bank = nullptr;
+  h->cfgs.assign(cfgs, cfgs + n);
+  for (letkf_config &c : h->cfgs) {
+    c.subap_mask = nullptr;
+    c.noise_bank = nullptr;
+  }
+  h->cfg = h->cfgs[0];
   h->stream = (cudaStream_t)stream;
   h->precision = cfgs[0].precision;
   h->rsz = h->precision ? sizeof(double) : sizeof(float);
@@ -319,12 +335,7 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
     I.pts = h->pts + o_pts;
     I.saps = h->saps + o_sap;
     I.basis = h->basis + o_basis;
-    if (h->precision) {
-      LK_TRY(upload(h, (void *)I.taper, G.taper.data(), G.taper.size() * sizeof(double)));
-    } else {
-      std::vector<float> t32(G.taper.begin(), G.taper.end());
-      LK_TRY(upload(h, (void *)I.taper, t32.data(), t32.size() * sizeof(float)));
-    }
+    LK_TRY(upload_taper(h, I, G.taper));
     LK_TRY(upload(h, (void *)I.pid_map, G.pid.data(), G.pid.size() * sizeof(int)));
     LK_TRY(upload(h, (void *)I.pts, G.pts.data(), G.pts.size() * sizeof(int2)));
     LK_TRY(upload(h, (void *)I.saps, G.saps.data(), G.saps.size() * sizeof(int2)));
@@ -461,6 +472,7 @@ letkf_status letkf_set_state(letkf_t h, const void *X_dev) {
   DeviceGuard dg(h->device);
   LK_CUDA(h, cudaMemcpyAsync(h->X, X_dev, h->state_total * h->rsz, cudaMemcpyDeviceToDevice,
                              h->stream));
+  LK_CUDA(h, lk_launch_basis_reset(h));
   return LETKF_OK;
 }
 
@@ -536,6 +548,39 @@ letkf_status letkf_run(letkf_t h, int32_t frames, const void *y_seq_dev, const v
     }
   }
   h->frame_host += frames;
+  return LETKF_OK;
+}
+
+letkf_status letkf_set_params(letkf_t h, int32_t i, double rho, double sigma2, double loc_len) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (i < 0 || i >= h->n_inst) return fail(h, LETKF_ERR_ARG, "no such instance");
+  if (!(rho > 0) || !(sigma2 > 0) || !isfinite(rho) || !isfinite(sigma2) || !isfinite(loc_len))
+    return fail(h, LETKF_ERR_ARG, "rho and sigma2 must be finite and > 0, loc_len finite");
+  DeviceGuard dg(h->device);
+  LK_CUDA(h, cudaStreamSynchronize(h->stream));
+  letkf_config &c = h->cfgs[i];
+  c.rho = rho;
+  c.sigma2 = sigma2;
+  c.loc_len = loc_len;
+  if (i == 0) h->cfg = c;
+  LkInst &I = h->inst[i];
+  I.alpha = (c.m - 1) / rho;
+  std::vector<double> tap;
+  taper_table(c, tap);
+  letkf_status st = upload_taper(h, I, tap);
+  if (st == LETKF_OK) st = upload(h, h->d_inst + i, &I, sizeof(LkInst));
+  lk_adjoint_release(h);   // its graph holds rho and sigma2 as kernel arguments
+  return st;
+}
+
+letkf_status letkf_set_frame(letkf_t h, int64_t frame) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (frame < 0) return fail(h, LETKF_ERR_ARG, "frame < 0");
+  DeviceGuard dg(h->device);
+  LK_CUDA(h, cudaStreamSynchronize(h->stream));
+  const long long f = frame;
+  LK_CUDA(h, cudaMemcpy(h->frame, &f, sizeof(long long), cudaMemcpyHostToDevice));
+  h->frame_host = frame;
   return LETKF_OK;
 }
 

@@ -58,8 +58,11 @@ struct LkTile {             // one analysis CTA: instance, tile origin (node coo
   int inst, i0, j0, cost;
 };
 
+struct LkAdjWork;           // reverse-mode workspace (letkf_adjoint.cu)
+
 struct letkf_ctx {
   letkf_config cfg;         // first instance's config (host pointers cleared)
+  std::vector<letkf_config> cfgs;   // every instance's config (host pointers cleared)
   cudaStream_t stream = nullptr;
   int device = 0;
   int precision = 0;
@@ -100,6 +103,8 @@ struct letkf_ctx {
   const void *graph_y = nullptr, *graph_truth = nullptr;
   const double *graph_resvar = nullptr;
 
+  LkAdjWork *adj = nullptr;         // letkf_grad buffers and graph, built on first use
+
   std::string err;
 };
 
@@ -114,10 +119,12 @@ cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise);
 cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
                                const long long *run_idx);
 cudaError_t lk_launch_tick(letkf_ctx *h);
+cudaError_t lk_launch_basis_reset(letkf_ctx *h);   // warm-start eigenbases -> identity
 cudaError_t lk_setup_analysis(letkf_ctx *h);
 int lk_num_tile_shapes();
 void lk_tile_shape(int s, int *ti, int *tj);
 int lk_width_class(int m);          // 0: m <= 16, 1: m <= 32, 2: m <= 64
+void lk_adjoint_release(letkf_ctx *h);  // frees the letkf_grad workspace (and its graph)
 
 // ---------------------------------------------------------------------------
 // Device helpers

@@ -163,6 +163,17 @@ __global__ void residual_final_kernel(const LkInst *__restrict__ insts,
   }
 }
 
+// Every node's warm-start eigenbasis back to the identity (grid.y = instance).
+__global__ void basis_reset_kernel(const LkInst *__restrict__ insts) {
+  const LkInst &I = insts[blockIdx.y];
+  const long long mp = I.mp, n = (long long)I.n_pts * mp * mp;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % (mp * mp);
+    I.basis[e] = (r / mp == r % mp) ? 1.f : 0.f;
+  }
+}
+
 __global__ void tick_kernel(long long *frame) {
   frame[0] += 1;
   frame[1] += 1;
@@ -211,6 +222,11 @@ cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
   if (e != cudaSuccess) return e;
   residual_final_kernel<<<h->n_inst, 32, 0, h->stream>>>(h->d_inst, h->partial, LK_RES_BLOCKS,
                                                          h->n_inst, run_idx, resvar);
+  return cudaGetLastError();
+}
+
+cudaError_t lk_launch_basis_reset(letkf_ctx *h) {
+  basis_reset_kernel<<<dim3(152, h->n_inst), 256, 0, h->stream>>>(h->d_inst);
   return cudaGetLastError();
 }
 

@@ -59,6 +59,10 @@ _SIGS = {
     "letkf_tile_shape": [c_int32, POINTER(c_int32), POINTER(c_int32)],
     "letkf_set_tile_shape": [c_void_p, c_int32, c_int32],
     "letkf_autotune": [c_void_p, c_void_p, c_int32, POINTER(c_int32), POINTER(ctypes.c_float)],
+    "letkf_set_params": [c_void_p, c_int32, c_double, c_double, c_double],
+    "letkf_set_frame": [c_void_p, ctypes.c_int64],
+    "letkf_grad": [c_void_p, c_int32, c_void_p, c_void_p, c_int32, POINTER(c_double),
+                   POINTER(c_double)],
 }
 
 _lib = None
@@ -194,6 +198,23 @@ def letkf_residual(h, truth, resvar) -> None:
 def letkf_run(h, frames: int, y_seq, truth_seq=None, resvar=None, use_graph: bool = True) -> None:
     _check(lib().letkf_run(h, int(frames), _ptr(y_seq), _ptr(truth_seq), _ptr(resvar),
                            1 if use_graph else 0), h)
+
+
+def letkf_set_params(h, i: int, rho: float, sigma2: float, loc_len: float) -> None:
+    _check(lib().letkf_set_params(h, int(i), float(rho), float(sigma2), float(loc_len)), h)
+
+
+def letkf_set_frame(h, frame: int) -> None:
+    _check(lib().letkf_set_frame(h, int(frame)), h)
+
+
+def letkf_grad(h, frames: int, y_seq, truth_seq, ckpt_every: int = 0):
+    """(J, array([dJ/drho, dJ/dsigma2, dJ/dL])) of the closed loop over `frames` frames."""
+    J = c_double()
+    g = (c_double * 3)()
+    _check(lib().letkf_grad(h, int(frames), _ptr(y_seq), _ptr(truth_seq), int(ckpt_every),
+                            byref(J), g), h)
+    return J.value, np.array(g[:], dtype=np.float64)
 
 
 def letkf_sync(h) -> None:
@@ -387,6 +408,26 @@ class Letkf:
         self._leave()
         return resvar
 
+    def set_params(self, rho: float, sigma2: float, loc_len: float, instance: int = 0):
+        letkf_set_params(self.h, instance, rho, sigma2, loc_len)
+
+    def set_frame(self, frame: int):
+        letkf_set_frame(self.h, frame)
+
+    def grad(self, frames: int, y_seq, truth_seq, ckpt_every: int = 0):
+        """Mean residual variance J over `frames` closed-loop frames from the
+        current state and its gradient (dJ/drho, dJ/dsigma2, dJ/dL)."""
+        if self.n_inst != 1:
+            raise ValueError("grad takes a single-instance handle")
+        self._t(y_seq, (y_seq.shape[0], self.p))
+        self._t(truth_seq, (truth_seq.shape[0], self.n_pts))
+        if y_seq.shape[0] < frames or truth_seq.shape[0] < frames:
+            raise ValueError("sequences shorter than frames")
+        self._enter()
+        out = letkf_grad(self.h, frames, y_seq, truth_seq, ckpt_every)
+        self._leave()
+        return out
+
     def autotune(self, y, reps: int = 3):
         self._enter()
         out = letkf_autotune(self.h, self._t(y, (self.p,)), reps)
@@ -412,3 +453,51 @@ class Letkf:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Autograd
+# ---------------------------------------------------------------------------
+def _loss_function():
+    import torch
+
+    class LetkfLoss(torch.autograd.Function):
+        """J(rho, sigma2, L): mean residual variance of the closed loop over
+        `frames` frames on handle `f`, started from ensemble X0 at noise frame
+        `frame0` (Section 2.1 Eq. Crit_Opt). rho, sigma2 and L are scalar
+        tensors; backward returns dJ/drho, dJ/dsigma2, dJ/dL from the
+        library's reverse mode (letkf_grad). The handle's parameters, state
+        and frame counter are set by every call."""
+
+        @staticmethod
+        def forward(ctx, rho, sigma2, L, f, X0, y_seq, truth_seq, frames, ckpt_every=20,
+                    frame0=0):
+            f.set_params(float(rho), float(sigma2), float(L))
+            f.set_state(X0)
+            f.set_frame(frame0)
+            J, g = f.grad(frames, y_seq, truth_seq, ckpt_every)
+            ctx.save_for_backward(torch.as_tensor(g, dtype=torch.float64))
+            ctx.like = (rho, sigma2, L)
+            return torch.tensor(J, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (g,) = ctx.saved_tensors
+            gJ = gJ.detach().to(torch.float64).cpu()
+            out = [(gJ * g[i]).to(dtype=t.dtype, device=t.device) if torch.is_tensor(t) else None
+                   for i, t in enumerate(ctx.like)]
+            return (*out, None, None, None, None, None, None, None)
+
+    return LetkfLoss
+
+
+_LOSS = None
+
+
+def letkf_loss(rho, sigma2, L, f, X0, y_seq, truth_seq, frames: int, ckpt_every: int = 20,
+               frame0: int = 0):
+    """Differentiable J(rho, sigma2, L) (see LetkfLoss)."""
+    global _LOSS
+    if _LOSS is None:
+        _LOSS = _loss_function()
+    return _LOSS.apply(rho, sigma2, L, f, X0, y_seq, truth_seq, frames, ckpt_every, frame0)

@@ -81,3 +81,6 @@ def test_null_handle_calls_fail_cleanly(built):
     assert built.letkf_analyze(None, None, None, None) == 1
     assert built.letkf_forecast(None, None) == 1
     assert built.letkf_sync(None) == 1
+    assert built.letkf_set_params(None, 0, 1.0, 1.0, 1.0) == 1
+    assert built.letkf_set_frame(None, 0) == 1
+    assert built.letkf_grad(None, 1, None, None, 0, None, None) == 1
