@@ -34,7 +34,7 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "analysis_tile_kernel_elt80.md"
 def parse_args(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -43,6 +43,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 48-instance batched measurement")
     ap.add_argument("--batched-steps", type=int, default=100)
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the reverse-mode (letkf_grad) measurement")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -103,7 +105,7 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -187,6 +189,85 @@ def batched_arm(torch, L, K, Wm):
            "launch": "one CUDA-graph replay per frame covering all 48 instances"}
     f.close()
     return out
+
+
+# --------------------------------------------------------------------------- reverse mode
+def adjoint_arm(torch, L, reps: int = 3):
+    """Gradient of the mean residual variance over 200 closed-loop frames of the
+    16 m system (32x32, m = 24, 5x5 Gaspari-Cohn window) with respect to rho,
+    sigma2 and L, by letkf_grad with a checkpoint every 20 frames, against the
+    6 forward runs of 200 frames that central differences of the 3 parameters
+    need. Returns the 'adjoint' object of the JSON line."""
+    import numpy as np
+    from paper_1408_7069_gb300 import synth, workloads as W
+    w = W.ADJ_16M
+    frames, ckpt = w.frames, 20
+    inp = synth.make_loop_inputs(w, frames=frames)
+    f = L.Letkf.from_workload(w, bank=inp.bank)
+    y = torch.from_numpy(inp.slopes[:frames].astype(np.float32)).cuda()
+    t = torch.from_numpy(inp.truth[:frames].astype(np.float32)).cuda()
+    X0 = torch.from_numpy(inp.X0.astype(np.float32)).cuda()
+    Ll = w.loc_len if w.loc_len > 0 else w.window / 4.0
+    theta = np.array([w.rho, w.sigma2, Ll])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def grad_once():
+        f.set_state(X0)
+        f.set_frame(0)
+        torch.cuda.synchronize()
+        e0.record(f.stream)
+        J, g = f.grad(frames, y, t, ckpt)
+        e1.record(f.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), J, g
+
+    grad_once()                                   # builds the workspace and the CUDA graph
+    runs = [grad_once() for _ in range(reps)]
+    grad_ms = sorted(r[0] for r in runs)[len(runs) // 2]
+    J, g = runs[0][1], runs[0][2]
+
+    def forward_once(th):
+        f.set_params(*th)
+        f.set_state(X0)
+        f.set_frame(0)
+        torch.cuda.synchronize()
+        e0.record(f.stream)
+        rv = f.run(frames, y, t, use_graph=True)
+        Jv = float(rv.mean().item())
+        e1.record(f.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), Jv
+
+    forward_once(theta)
+    fd_ms = 0.0
+    for k in range(3):
+        for s in (1, -1):
+            th = theta.copy()
+            th[k] *= 1 + s * 1e-4
+            fd_ms += forward_once(th)[0]
+    f.close()
+    # the same gradient on an FP64 handle: J over 200 frames is rough in the
+    # parameters, so this shows how far the FP32 trajectory's gradient moves
+    from dataclasses import replace
+    c = lambda a: torch.from_numpy(np.asarray(a).astype(np.float32).astype(np.float64)).cuda()  # noqa: E731
+    f64 = L.Letkf.from_workload(replace(w, precision=1), bank=inp.bank)
+    f64.set_state(c(inp.X0))
+    torch.cuda.synchronize()
+    e0.record(f64.stream)
+    J64, g64 = f64.grad(frames, c(inp.slopes[:frames]), c(inp.truth[:frames]), ckpt)
+    e1.record(f64.stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    f64.close()
+    rel = lambda a, b: float(abs(a - b) / abs(b))  # noqa: E731
+    return {"workload": w.name, "frames": frames, "ckpt_every": ckpt, "n_pts": int(f.n_pts),
+            "J": J, "grad": {"rho": g[0], "sigma2": g[1], "L": g[2]},
+            "grad_ms": grad_ms, "fd6_forward_ms": fd_ms, "grad_vs_fd6_time": grad_ms / fd_ms,
+            "fp64_handle": {"J": J64, "grad": {"rho": g64[0], "sigma2": g64[1], "L": g64[2]},
+                            "ms": ms64, "rel_J": rel(J, J64),
+                            "rel_grad": [rel(g[k], g64[k]) for k in range(3)]},
+            "launch": "letkf_grad: forward, segment recomputation and backward in one CUDA graph",
+            "fd_launch": "6 x letkf_run of 200 frames (one graph replay per frame)"}
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -320,6 +401,10 @@ def gpu_arm(args):
         for k in range(Wm):
             frame(k)
     L.letkf_sync(h)
+    torch.cuda.synchronize()
+    # tile shape per width class from the autotuner, on the loop state after warm-up
+    from paper_1408_7069_gb300 import autotune
+    tune = autotune.tune(f, y[Wm].contiguous(), [(w.nsub, w.m, w.window)], reps=3)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -407,6 +492,7 @@ def gpu_arm(args):
         "config": {"workload": w.name, "nsub": w.nsub, "m": w.m, "window": w.window,
                    "taper": "gaspari-cohn", "n_pts": f.n_pts, "p": f.p,
                    "fp64_fallback_kappa": 300.0, "parallelism": f"replicas x{world}",
+                   "tile_shape": tune.get("tiles"),
                    "l2": "flushed between timed frames (256 MiB write, outside the frame events)",
                    "step": "residual + observation + local analysis + forecast, per-frame launches"},
         "p50_us": 1e3 * percentile(frame_ms, 50), "p99_us": 1e3 * percentile(frame_ms, 99),
@@ -426,6 +512,8 @@ def gpu_arm(args):
     }
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_arm(torch, L, args.batched_steps, Wm)
+    if rank == 0 and not args.no_adjoint:
+        line["adjoint"] = adjoint_arm(torch, L)
     if rank == 0:
         line["clocks"] = clk.summary()
         if world == 1 and not args.no_cpu_baseline:

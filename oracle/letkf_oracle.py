@@ -307,12 +307,12 @@ def residual_variance(truth_k, X):
 
 def closed_loop(geom: Geometry, truth, slopes, bank, m: int, sigma2: float, rho: float,
                 a: float, noise_scale: float, seed: int, frames: int, X0=None,
-                batched: bool = False):
+                batched: bool = False, frame0: int = 0):
     """Run the loop: at frame k record the residual of the prediction X_{k/k-1},
-    analyse y_k, forecast with the bank noise of frame k. Without X0 the first
-    prediction ensemble is all zeros (Section 3.1). ``batched`` uses the stacked
-    form of the analysis. Returns (resvar [frames], final X, per-frame
-    analysis means)."""
+    analyse y_k, forecast with the bank noise of frame frame0 + k. Without X0
+    the first prediction ensemble is all zeros (Section 3.1). ``batched`` uses
+    the stacked form of the analysis. Returns (resvar [frames], final X,
+    per-frame analysis means)."""
     X = np.zeros((geom.n_pts, 2, m)) if X0 is None else np.array(X0, dtype=np.float64)
     resvar = np.empty(frames)
     means = []
@@ -321,7 +321,7 @@ def closed_loop(geom: Geometry, truth, slopes, bank, m: int, sigma2: float, rho:
         resvar[k] = residual_variance(truth[k], X)
         Xa, mean, _ = ana(geom, X, slopes[k], sigma2, rho)
         means.append(mean)
-        v = bank_noise(bank, geom.points, m, seed, k, noise_scale)
+        v = bank_noise(bank, geom.points, m, seed, frame0 + k, noise_scale)
         X = forecast(Xa, v, a)
     return resvar, X, np.array(means)
 
@@ -410,17 +410,19 @@ def residual_variance_grad(truth_k, X):
 
 
 def closed_loop_grad(geom: Geometry, truth, slopes, bank, m: int, sigma2: float, rho: float,
-                     a: float, noise_scale: float, seed: int, frames: int, X0):
+                     a: float, noise_scale: float, seed: int, frames: int, X0,
+                     frame0: int = 0):
     """J = mean over the frames of the residual variance of the prediction
     (Section 2.1, Eq. Crit_Opt) and its gradient with respect to (rho, sigma2,
-    L), by reverse mode through the analyses and AR(1) forecasts, from X0."""
+    L), by reverse mode through the analyses and AR(1) forecasts, from X0; the
+    forecast after frame k draws the bank noise of frame frame0 + k."""
     X = np.array(X0, dtype=np.float64)
     Xs, J = [], 0.0
     for k in range(frames):
         Xs.append(X)
         J += residual_variance(truth[k], X)
         Xa, _, _ = analysis(geom, X, slopes[k], sigma2, rho)
-        X = forecast(Xa, bank_noise(bank, geom.points, m, seed, k, noise_scale), a)
+        X = forecast(Xa, bank_noise(bank, geom.points, m, seed, frame0 + k, noise_scale), a)
     J /= frames
     grad = np.zeros(3)
     lam_next = np.zeros_like(X)                 # adjoint of X_{k+1}

@@ -22,9 +22,14 @@ def cache_path() -> str:
                                        "tiles.json"))
 
 
+# Bumped whenever the analysis kernels change, so that cached choices are retimed.
+KERNEL_REVISION = 2
+
+
 def signature(gpu_name: str, shapes) -> str:
-    """Cache key: GPU name and the sorted (nsub, m, window) of the instances."""
-    body = json.dumps([gpu_name, sorted(tuple(s) for s in shapes)])
+    """Cache key: GPU name, kernel revision and the sorted (nsub, m, window) of
+    the instances."""
+    body = json.dumps([gpu_name, KERNEL_REVISION, sorted(tuple(s) for s in shapes)])
     return hashlib.sha1(body.encode()).hexdigest()
 
 

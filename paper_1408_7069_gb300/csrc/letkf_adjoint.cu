@@ -832,6 +832,12 @@ extern "C" letkf_status letkf_grad(letkf_t h, int32_t frames, const void *y_seq_
                            cudaMemcpyHostToDevice));
   }
   LK_ACUDA(h, setup_kernels(h));
+  // the forward analyses keep every node's eigenbasis for the backward pass
+  struct KeepBasis {
+    letkf_ctx *h;
+    ~KeepBasis() { h->keep_basis = 0; }
+  } keep{h};
+  h->keep_basis = 1;
   if (h->stream) {
     if (!W->graph || W->graph_y != y_seq_dev || W->graph_truth != truth_seq_dev) {
       if (W->graph) {

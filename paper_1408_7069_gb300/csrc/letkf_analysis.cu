@@ -779,7 +779,8 @@ cudaError_t launch_class(letkf_ctx *h, int cls, void *mean, void *spread) {
   if (h->precision == 1)
     return launch_tile<MP, double, double>(h, cls, mean, spread, h->tol64, 0.0);
   const float kthr = h->fp64_kappa > 0 ? (float)h->fp64_kappa : 0.f;
-  cudaError_t e = launch_tile<MP, float, float>(h, cls, mean, spread, (float)h->tol32, kthr);
+  cudaError_t e = MP == 32 ? lk_launch_pair(h, cls, mean, spread, (float)h->tol32, kthr)
+                           : launch_tile<MP, float, float>(h, cls, mean, spread, (float)h->tol32, kthr);
   if (e != cudaSuccess || kthr <= 0.f) return e;
   return launch_list<MP>(h, cls, mean, spread);
 }
@@ -812,6 +813,7 @@ cudaError_t setup_class(letkf_ctx *h) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(analysis_list_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(LIST_WARPS * list_warp_bytes<MP>(wmax)));
+  if (e == cudaSuccess && MP == 32) e = lk_setup_pair(h);
   return e;
 }
 

@@ -69,6 +69,7 @@ struct letkf_ctx {
   size_t rsz = 4;           // bytes of the real type
   double tol32 = 4e-6, tol64 = 1e-13, fp64_kappa = 300;
   int max_sweeps = 20;
+  int keep_basis = 0;               // store every node's eigenbasis (reverse mode needs it)
 
   int n_inst = 0;
   std::vector<LkInst> inst;         // host copies of the descriptors
@@ -121,6 +122,9 @@ cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
 cudaError_t lk_launch_tick(letkf_ctx *h);
 cudaError_t lk_launch_basis_reset(letkf_ctx *h);   // warm-start eigenbases -> identity
 cudaError_t lk_setup_analysis(letkf_ctx *h);
+// FP32 analysis of the 17..32-member class, two nodes per warp (letkf_pair.cu).
+cudaError_t lk_launch_pair(letkf_ctx *h, int cls, void *mean, void *spread, float tol, float kthr);
+cudaError_t lk_setup_pair(letkf_ctx *h);
 int lk_num_tile_shapes();
 void lk_tile_shape(int s, int *ti, int *tj);
 int lk_width_class(int m);          // 0: m <= 16, 1: m <= 32, 2: m <= 64

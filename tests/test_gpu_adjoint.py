@@ -199,3 +199,37 @@ def test_grad_rejects_unsupported_handles():
     with pytest.raises(ValueError):
         b.grad(3, y, t)
     b.close()
+
+
+def _golden(name):
+    import os
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split(None, 1)
+                out[k] = float(v)
+    return out
+
+
+def test_fp64_gradient_over_200_frames_matches_oracle_golden():
+    """The 16 m system over 200 frames from the prior draw (checkpoint every 20
+    frames) on an FP64 handle against the oracle's reverse mode, stored by
+    tests/golden/make_adjoint_golden.py. Over this horizon J is rough in the
+    parameters, so FP32 trajectories give gradients that differ by percents;
+    the FP64 path must agree to rounding."""
+    g0 = _golden("adjoint_16m_200f.txt")
+    w = replace(W.ADJ_16M, precision=1)
+    frames = W.ADJ_16M.frames
+    inp = synth.make_loop_inputs(w, frames=frames)
+    c = lambda a: np.asarray(a).astype(np.float32).astype(np.float64)  # noqa: E731
+    f = L.Letkf.from_workload(w, bank=inp.bank)
+    f.set_state(torch.from_numpy(c(inp.X0)).cuda())
+    J, g = f.grad(frames, torch.from_numpy(c(inp.slopes[:frames])).cuda(),
+                  torch.from_numpy(c(inp.truth[:frames])).cuda(), 20)
+    f.sync()
+    f.close()
+    assert J == pytest.approx(g0["J"], rel=1e-9)
+    for k, name in enumerate(("dJ_drho", "dJ_dsigma2", "dJ_dL")):
+        assert g[k] == pytest.approx(g0[name], rel=1e-7), name
