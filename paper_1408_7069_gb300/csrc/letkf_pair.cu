@@ -28,6 +28,7 @@
 // kappa_hat = 1 + rho tr(G)/(m-1) bounds the condition number before the
 // eigensolve; nodes above the threshold are queued for the FP64 list kernel.
 #include <math.h>
+#include <stdint.h>
 
 #include "letkf_device.cuh"
 
@@ -37,7 +38,7 @@ namespace {
 
 constexpr int PMP = 32;               // padded width of the node problem
 constexpr int CELLF = 2 * PMP + 4;    // floats per halo cell: +4 shifts banks between neighbours
-constexpr int NODE_SCR = PMP * 36 + 4 * PMP + 2 * PMP + 4;  // floats of scratch per node
+constexpr int NODE_SCR = 3 * PMP + 4;  // floats of scratch per node (C d, X'_0, X'_1)
 
 // Shared-memory layout of one CTA (bytes).
 struct PairLayout {
@@ -91,10 +92,15 @@ __device__ __forceinline__ int pair_round(float2 (&P)[16], float2 (&Q)[16], floa
   const float t = (x >= 0.f ? y : -y) / (fabsf(x) + h);
   const float cr = rsqrtf(fmaf(t, t, 1.f));
   const bool rot = !frozen && !idle && dot * dot > tol2 * nP * nQ;
-  const float c = rot ? cr : ((idle && !frozen) ? 0.f : 1.f);
-  const float s = rot ? cr * t : ((idle && !frozen) ? 1.f : 0.f);
-  const float nP2 = rot ? fmaf(-t, dot, nP) : ((idle && !frozen) ? nQ : nP);
-  const float nQ2 = rot ? fmaf(t, dot, nQ) : ((idle && !frozen) ? nP : nQ);
+  const bool swp = idle && !frozen;
+  // P' = c P - s Q, Q' = s P + c Q: exact for the swap (c = 0, s = 1) and for no
+  // rotation (c = 1, s = 0). A three-shear form would save one packed FMA per
+  // element pair but its swap leaks rounding of the larger column into the
+  // smaller one, which stalls convergence when their norms differ by kappa.
+  const float c = rot ? cr : (swp ? 0.f : 1.f);
+  const float s = rot ? cr * t : (swp ? 1.f : 0.f);
+  const float nP2 = rot ? fmaf(-t, dot, nP) : (swp ? nQ : nP);
+  const float nQ2 = rot ? fmaf(t, dot, nQ) : (swp ? nP : nQ);
   const float2 cc = f2(c), ms = f2(-s), ps = f2(s);
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
@@ -117,6 +123,27 @@ __device__ __forceinline__ void shfl_cols(float2 (&X)[16], int src) {
 
 __device__ __forceinline__ float norm16(const float2 (&a)[16]) { return dot16(a, a); }
 
+// Sum of v over the 16 lanes of a node, scattered: on return v[0] of lane i
+// holds element i (members 2i, 2i+1) of the sum. Recursive halving: at offset
+// o a lane keeps the half selected by bit o of its index and adds the partner's
+// copy of that half.
+__device__ __forceinline__ float2 reduce_scatter16(float2 (&v)[16], int li) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    const bool b = (li & o) != 0;
+#pragma unroll
+    for (int e = 0; e < o; ++e) {
+      const float2 lo = v[e], hi = v[e + o];
+      const float2 keep = b ? hi : lo;
+      float2 send = b ? lo : hi;
+      send.x = __shfl_xor_sync(FULL, send.x, o);
+      send.y = __shfl_xor_sync(FULL, send.y, o);
+      v[e] = make_float2(keep.x + send.x, keep.y + send.y);
+    }
+  }
+  return v[0];
+}
+
 // Stages the tile's halo (slope anomalies and innovations) and the taper table.
 template <int TI, int TJ>
 __device__ __forceinline__ void stage_pair_tile(const LkInst &I, int i0, int j0, float *halo,
@@ -127,7 +154,17 @@ __device__ __forceinline__ void stage_pair_tile(const LkInst &I, int i0, int j0,
   const float *Ybp = static_cast<const float *>(I.Ybp);
   const float *dp = static_cast<const float *>(I.dp);
   const float *taper = static_cast<const float *>(I.taper);
-  for (int e = threadIdx.x; e < ncell * CELLF; e += blockDim.x) {
+  if (m == PMP && (reinterpret_cast<uintptr_t>(Ybp) & 15) == 0) {
+    // a cell's two slope rows are 64 contiguous floats in the grid: float4 copies
+    for (int e4 = threadIdx.x; e4 < ncell * 16; e4 += blockDim.x) {
+      const int cell = e4 >> 4, q = e4 & 15;
+      const int hi = cell / HJ, hj = cell - hi * HJ;
+      const size_t src = (size_t)(i0 + hi) * I.gs_cols + (j0 + hj);
+      reinterpret_cast<float4 *>(halo + (size_t)cell * CELLF)[q] =
+          reinterpret_cast<const float4 *>(Ybp + src * 2 * PMP)[q];
+    }
+  } else {
+    for (int e = threadIdx.x; e < ncell * CELLF; e += blockDim.x) {
     const int cell = e / CELLF;
     const int r = e - cell * CELLF;
     float v = 0.f;
@@ -139,6 +176,7 @@ __device__ __forceinline__ void stage_pair_tile(const LkInst &I, int i0, int j0,
       if (mm < m) v = Ybp[(src * 2 + c) * m + mm];
     }
     halo[e] = v;
+    }
   }
   for (int e = threadIdx.x; e < ncell * 2; e += blockDim.x) {
     const int cell = e >> 1;
@@ -301,11 +339,9 @@ __global__ void __launch_bounds__(TI *TJ * 16)
     }
   }
   // ---- transform and apply (Section 4.2): Xa_r = xbar_r + X'_r wbar + X'_r W ----
-  float *Vt = scr;                      // [32][36]: column j of V at Vt + 36 j
-  float *vcd = scr + PMP * 36;          // C d
+  float *vcd = scr;                     // C d
   float *vx0 = vcd + PMP;               // X'_0
   float *vx1 = vx0 + PMP;               // X'_1
-  float *hh01 = vx1 + PMP;              // [32] float2 (h0_j, h1_j)
   float *xrow = active ? static_cast<float *>(I.X) + (size_t)pid * 2 * m : nullptr;
   const int m0 = 2 * li, m1 = 2 * li + 1;
   const float x00 = (active && m0 < m) ? xrow[m0] : 0.f;
@@ -320,13 +356,6 @@ __global__ void __launch_bounds__(TI *TJ * 16)
       make_float2(m0 < m ? x00 - xb0 : 0.f, m1 < m ? x01 - xb0 : 0.f);
   reinterpret_cast<float2 *>(vx1)[li] =
       make_float2(m0 < m ? x10 - xb1 : 0.f, m1 < m ? x11 - xb1 : 0.f);
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    reinterpret_cast<float4 *>(Vt + 36 * m0)[k] =
-        make_float4(P[2 * k].x, P[2 * k].y, P[2 * k + 1].x, P[2 * k + 1].y);
-    reinterpret_cast<float4 *>(Vt + 36 * m1)[k] =
-        make_float4(Q[2 * k].x, Q[2 * k].y, Q[2 * k + 1].x, Q[2 * k + 1].y);
-  }
   __syncwarp();
   // projections of C d and of the two anomaly rows on this lane's eigenvectors
   float2 uP = f2(0.f), uQ = f2(0.f), a0P = f2(0.f), a0Q = f2(0.f), a1P = f2(0.f), a1Q = f2(0.f);
@@ -348,19 +377,20 @@ __global__ void __launch_bounds__(TI *TJ * 16)
   const float w0 = half_sum(gP0 * zP + gQ0 * zQ);          // X'_0 wbar
   const float w1 = half_sum(gP1 * zP + gQ1 * zQ);          // X'_1 wbar
   const float rP = sqrtf(float(m - 1) / lP), rQ = sqrtf(float(m - 1) / lQ);
-  reinterpret_cast<float4 *>(hh01)[li] = make_float4(gP0 * rP, gP1 * rP, gQ0 * rQ, gQ1 * rQ);
-  __syncwarp();
-  // (X'_r W)[i] = sum_j V[i][j] h_r,j for members m0, m1
-  float q00 = 0.f, q01 = 0.f, q10 = 0.f, q11 = 0.f;
-#pragma unroll 8
-  for (int j = 0; j < PMP; ++j) {
-    const float2 v = reinterpret_cast<const float2 *>(Vt + 36 * j)[li];
-    const float2 hv = reinterpret_cast<const float2 *>(hh01)[j];
-    q00 = fmaf(v.x, hv.x, q00);
-    q01 = fmaf(v.y, hv.x, q01);
-    q10 = fmaf(v.x, hv.y, q10);
-    q11 = fmaf(v.y, hv.y, q11);
+  // X'_r W = sum_j h_r,j v_j^T with h_r,j = (X'_r v_j) sqrt((m-1)/lambda_j): this
+  // lane's two terms, summed over the node's lanes and scattered by member
+  float2 v0[16], v1[16];
+  {
+    const float2 hP0 = f2(gP0 * rP), hQ0 = f2(gQ0 * rQ), hP1 = f2(gP1 * rP), hQ1 = f2(gQ1 * rQ);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      v0[k] = fma2(hP0, P[k], mul2(hQ0, Q[k]));
+      v1[k] = fma2(hP1, P[k], mul2(hQ1, Q[k]));
+    }
   }
+  const float2 q0 = reduce_scatter16(v0, li);
+  const float2 q1 = reduce_scatter16(v1, li);
+  const float q00 = q0.x, q01 = q0.y, q10 = q1.x, q11 = q1.y;
   const float xa00 = xb0 + w0 + q00, xa01 = xb0 + w0 + q01;
   const float xa10 = xb1 + w1 + q10, xa11 = xb1 + w1 + q11;
   if (active) {
