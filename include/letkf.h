@@ -196,12 +196,13 @@ letkf_status letkf_grad(letkf_t h, int32_t frames, const void *y_seq_dev, const 
                         int32_t ckpt_every, double *J_out, double *grad_out);
 
 /* Analysis tile shapes. The analysis runs one CTA per tile of tile_i x tile_j
- * nodes (one warp per node) and stages the tile's window halo in shared
+ * nodes (4, 2 or 1 nodes per warp for m <= 16, <= 32 and larger; FP64 handles
+ * one node per warp) and stages the tile's window halo in shared
  * memory once; the best shape depends on the window, the ensemble size and the
  * mix of instances. letkf_tile_shape describes compiled shape number `shape`
  * (0 .. count-1; LETKF_ERR_ARG beyond). Instances are grouped in width classes
  * by ensemble size: 0 for m <= 16, 1 for m <= 32, 2 for m <= 64 (one node per
- * warp pair, fixed shape 2 = 2 x 2 nodes, no FP64 fallback). letkf_set_tile_shape selects
+ * warp, tiles of at most 8 nodes, no FP64 fallback). letkf_set_tile_shape selects
  * a shape for one class; letkf_autotune times every shape for every class
  * present on the handle's current ensemble with slopes y_dev (reps timed
  * analyses of that class's nodes each, state restored afterwards; tune on a

@@ -70,63 +70,6 @@ __host__ __device__ size_t list_warp_bytes(int w) {
          align16(wc * sizeof(double)) + scratch_elems<MP, double>() * sizeof(double);
 }
 
-// FP32 one-sided Jacobi on B alone with scaled ("fast") rotations: the true
-// column is d * beta, so a rotation updates beta with one FMA per element,
-//   beta_p <- beta_p - t (d_q / d_p) beta_q,   beta_q <- beta_q + t (d_p / d_q) beta_p,
-// and multiplies both scales by cos. Columns are rescaled (beta <- d beta, d = 1)
-// at the start of every sweep, which bounds their growth to (1/cos)^(MP-1).
-// The convergence test is the same as jacobi(): cos(b_p, b_q) <= tol.
-template <int MP>
-__device__ __forceinline__ void jacobi_fast_f32(float (&b)[MP], float tol, int max_sweeps,
-                                                int *__restrict__ counters) {
-  const int lane = threadIdx.x & 31;
-  const float tol2 = tol * tol;
-  int sweep = 0;
-  bool converged = false;
-  for (; sweep < max_sweeps; ++sweep) {
-    float nrm = dot4<MP, float>(b, b);   // true squared norm of this lane's column
-    float d = 1.f;                        // scale: true column = d * b
-    int rotated = 0;
-    for (int t = 1; t < MP; ++t) {
-      float pb[MP];
-#pragma unroll
-      for (int k = 0; k < MP; ++k) pb[k] = __shfl_xor_sync(FULL, b[k], t);
-      const float pd = __shfl_xor_sync(FULL, d, t);
-      const float pn = __shfl_xor_sync(FULL, nrm, t);
-      const float dot = d * pd * dot4<MP, float>(b, pb);   // true b_p . b_q
-      const bool isp = lane < (lane ^ t);
-      const float app = isp ? nrm : pn;
-      const float aqq = isp ? pn : nrm;
-      float tr = 0.f, cs = 1.f;
-      if (dot * dot > tol2 * app * aqq) {
-        const float zeta = __fdividef(aqq - app, 2.f * dot);
-        const float az = fabsf(zeta);
-        tr = az > 1e15f ? __fdividef(0.5f, zeta)
-                        : copysignf(__fdividef(1.f, az + __fsqrt_rn(fmaf(zeta, zeta, 1.f))), zeta);
-        cs = rsqrtf(fmaf(tr, tr, 1.f));
-        rotated = 1;
-      }
-      // own' = own -/+ t (d_partner / d_own) partner
-      const float coef = (isp ? -tr : tr) * __fdividef(pd, d);
-#pragma unroll
-      for (int k = 0; k < MP; ++k) b[k] = fmaf(coef, pb[k], b[k]);
-      d *= cs;
-      nrm = isp ? fmaf(-tr, dot, app) : fmaf(tr, dot, aqq);
-    }
-#pragma unroll
-    for (int k = 0; k < MP; ++k) b[k] *= d;
-    if (!__any_sync(FULL, rotated)) {
-      converged = true;
-      break;
-    }
-  }
-  if (lane == 0) {
-    atomicMax(&counters[2], converged ? sweep + 1 : sweep);
-    atomicAdd(&counters[3], converged ? sweep + 1 : sweep);
-    if (!converged) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
-  }
-}
-
 // wbar, W from the eigenpairs (lane j: eigenvector column v, eigenvalue lam) and
 // the update of the node's two rows; writes Xa, the mean and the spread.
 template <int MP, typename S, typename T>
@@ -245,70 +188,6 @@ __device__ __forceinline__ void analyze_node_accum(const S *__restrict__ win,
   if (U) store_basis<MP, T>(v, U);
 }
 
-// FP32 analysis of one node from its stored eigenbasis U (see the file comment).
-// Nodes whose kappa_hat exceeds kappa_thr (> 0) are queued for FP64 instead.
-template <int MP>
-__device__ __forceinline__ void analyze_node_f32(const float *__restrict__ win,
-                                                 const float *__restrict__ dwin, int stride,
-                                                 const float *__restrict__ tap, int w, int m,
-                                                 float alpha, float tol, int max_sweeps,
-                                                 float *__restrict__ xrow,
-                                                 float *__restrict__ mean_out,
-                                                 float *__restrict__ spread_out,
-                                                 float *__restrict__ scr,
-                                                 int *__restrict__ counters, float kappa_thr,
-                                                 int *__restrict__ queue_len, int pid,
-                                                 float *__restrict__ U,
-                                                 int2 *__restrict__ worklist, int inst) {
-  const int lane = threadIdx.x & 31;
-  const bool col = lane < MP;
-  float b[MP], diag, cd;
-  gram<MP, float, float>(win, dwin, stride, tap, w, m, alpha, b, diag, cd);
-  if (kappa_thr > 0.f) {
-    const float trg = lk_warp_sum(diag);
-    if (1.f + trg / alpha > kappa_thr) {
-      if (lane == 0) {
-        worklist[atomicAdd(queue_len, 1)] = make_int2(inst, pid);
-        atomicAdd(&counters[1], 1);
-      }
-      return;
-    }
-  }
-  // B = A U0: stage the rows of A, each lane multiplies A by its basis column.
-  constexpr int LDA = MP + 4;
-  if (col) {
-#pragma unroll
-    for (int k = 0; k < MP; k += 4)
-      *reinterpret_cast<float4 *>(scr + lane * LDA + k) = make_float4(b[k], b[k + 1], b[k + 2], b[k + 3]);
-  }
-  float u[MP];
-#pragma unroll
-  for (int k = 0; k < MP; ++k) u[k] = col ? U[k * MP + lane] : 0.f;
-  __syncwarp();
-#pragma unroll
-  for (int i = 0; i < MP; ++i) {
-    float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-    for (int k = 0; k < MP; k += 4) {
-      const float4 a4 = *reinterpret_cast<const float4 *>(scr + i * LDA + k);
-      s0 = fmaf(a4.x, u[k], s0);
-      s1 = fmaf(a4.y, u[k + 1], s1);
-      s0 = fmaf(a4.z, u[k + 2], s0);
-      s1 = fmaf(a4.w, u[k + 3], s1);
-    }
-    b[i] = s0 + s1;
-  }
-  jacobi_fast_f32<MP>(b, tol, max_sweeps, counters);
-  const float nrm = dot4<MP, float>(b, b);
-  const float lam = (col && nrm > 0.f) ? sqrtf(nrm) : 1.f;
-  const float inv = 1.f / lam;
-#pragma unroll
-  for (int k = 0; k < MP; ++k) b[k] *= inv;            // eigenvector column
-  transform_apply<MP, float, float>(b, lam, cd, m, xrow, mean_out, spread_out, scr, counters);
-  store_basis<MP, float>(b, U);
-}
-
-
 // Stages a tile's halo (slope anomalies and innovations of the padded grid)
 // and the taper table in shared memory.
 template <int MP, typename S, typename T, int TI, int TJ>
@@ -367,18 +246,8 @@ __global__ void __launch_bounds__(TI *TJ * 32)
   S *mo = mean ? mean + 2 * (I.node_off + pid) : nullptr;
   S *so = spread ? spread + 2 * (I.node_off + pid) : nullptr;
   T *wscr = scr + (size_t)warp * scratch_elems<MP, T>();
-  if constexpr (std::is_same<T, float>::value) {
-    const int queue = kappa_thr > 0.f ? 1 : 0;
-    int *slot = queue ? &counters[4 + (MP == 16 ? 0 : 1)] : nullptr;
-    analyze_node_f32<MP>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m, float(I.alpha),
-                         tol, max_sweeps, xrow, mo, so, wscr, counters, kappa_thr,
-                         reinterpret_cast<int *>(slot), pid, I.basis + (size_t)pid * MP * MP,
-                         worklist, tl.inst);
-  } else {
-    analyze_node_accum<MP, S, T>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m,
-                                 T(I.alpha), tol, max_sweeps, xrow, mo, so, wscr, counters,
-                                 nullptr);
-  }
+  analyze_node_accum<MP, S, T>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m,
+                               T(I.alpha), tol, max_sweeps, xrow, mo, so, wscr, counters, nullptr);
 }
 
 // FP64 re-analysis of the queued nodes (FP32 handles): one warp per node,
@@ -434,303 +303,6 @@ __global__ void __launch_bounds__(LIST_WARPS * 32)
       I.basis + (size_t)pid * MP * MP);
 }
 
-// ---------------------------------------------------------------------------
-// Ensembles of 33..64 members: one node per warp pair (64 threads), lane L of
-// the pair holds column L of the 64-wide padded problem. Rotation partners in
-// the same warp are exchanged by shuffles, partners in the other warp through
-// shared memory under a 64-thread named barrier. FP32 only.
-// ---------------------------------------------------------------------------
-constexpr int P64_TI = 2, P64_TJ = 2;           // nodes per CTA: 4 (8 warps)
-constexpr int P64_LDA = 68;                      // A staging row stride
-constexpr int P64_SCR = 64 * 68;                 // per-node scratch floats (>= 64*65+192, 64*66)
-
-__host__ __device__ inline size_t p64_smem_bytes(int w) {
-  const size_t ncell = (size_t)(P64_TI + w - 1) * (P64_TJ + w - 1);
-  size_t off = align16(ncell * 2 * 64 * sizeof(float));
-  off = align16(off + ncell * 2 * sizeof(float));
-  off = align16(off + (size_t)w * w * sizeof(float));
-  return off + (size_t)P64_TI * P64_TJ * (P64_SCR + 8) * sizeof(float);
-}
-
-__device__ __forceinline__ void pair_bar(int id) {
-  asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
-}
-
-// Sum over the 64 threads of a pair; red: 2 floats of the pair's scratch.
-__device__ __forceinline__ float pair_sum(float v, float *red, int half, int bar) {
-  v = lk_warp_sum(v);
-  if ((threadIdx.x & 31) == 0) red[half] = v;
-  pair_bar(bar);
-  const float s = red[0] + red[1];
-  pair_bar(bar);
-  return s;
-}
-
-__device__ void analyze_node64(const float *__restrict__ win, const float *__restrict__ dwin,
-                               int stride, const float *__restrict__ tap, int w, int m,
-                               float alpha, float tol, int max_sweeps, float *__restrict__ xrow,
-                               float *__restrict__ mean_out, float *__restrict__ spread_out,
-                               float *__restrict__ scr, int *__restrict__ counters,
-                               float *__restrict__ U, int half, int bar) {
-  constexpr int MP = 64;
-  const int lane = threadIdx.x & 31;
-  const int L = half * 32 + lane;
-  float *red = scr + P64_SCR;                   // 8 floats after the node's scratch
-  const bool mem = L < m;
-  // ---- Gram row L ----
-  float b[MP];
-#pragma unroll
-  for (int k = 0; k < MP; ++k) b[k] = 0.f;
-  float diag = 0.f, cd = 0.f;
-  for (int ds = 0; ds < w; ++ds)
-    for (int dt = 0; dt < w; ++dt) {
-      const int cell = ds * stride + dt;
-      const float tw = tap[ds * w + dt];
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const float *yv = win + (size_t)cell * 2 * MP + c * MP;
-        const float yl = yv[L];
-        const float cy = tw * yl;
-        diag = fmaf(cy, yl, diag);
-        cd = fmaf(cy, dwin[cell * 2 + c], cd);
-#pragma unroll
-        for (int k = 0; k < MP; k += 4) {
-          const float4 y4 = *reinterpret_cast<const float4 *>(yv + k);
-          b[k] = fmaf(cy, y4.x, b[k]);
-          b[k + 1] = fmaf(cy, y4.y, b[k + 1]);
-          b[k + 2] = fmaf(cy, y4.z, b[k + 2]);
-          b[k + 3] = fmaf(cy, y4.w, b[k + 3]);
-        }
-      }
-    }
-  const float dval = mem ? alpha : 1.f;
-#pragma unroll
-  for (int k = 0; k < MP; ++k)
-    if (k == L) b[k] += dval;
-  // ---- B = A U0 ----
-#pragma unroll
-  for (int k = 0; k < MP; k += 4)
-    *reinterpret_cast<float4 *>(scr + L * P64_LDA + k) = make_float4(b[k], b[k + 1], b[k + 2], b[k + 3]);
-  pair_bar(bar);
-  {
-    float u[MP];
-#pragma unroll
-    for (int k = 0; k < MP; ++k) u[k] = U[k * MP + L];
-#pragma unroll
-    for (int i = 0; i < MP; ++i) {
-      float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-      for (int k = 0; k < MP; k += 4) {
-        const float4 a4 = *reinterpret_cast<const float4 *>(scr + i * P64_LDA + k);
-        s0 = fmaf(a4.x, u[k], s0);
-        s1 = fmaf(a4.y, u[k + 1], s1);
-        s0 = fmaf(a4.z, u[k + 2], s0);
-        s1 = fmaf(a4.w, u[k + 3], s1);
-      }
-      b[i] = s0 + s1;
-    }
-  }
-  pair_bar(bar);
-  // ---- one-sided Jacobi with scaled rotations (see jacobi_fast_f32) ----
-  const float tol2 = tol * tol;
-  int sweep = 0;
-  bool converged = false;
-  float *xb = scr;                              // exchange rows: [64][66]
-  for (; sweep < max_sweeps; ++sweep) {
-    float nrm = dot4<MP, float>(b, b);
-    float d = 1.f;
-    int rotated = 0;
-    for (int t = 1; t < MP; ++t) {
-      float pb[MP];
-      float pd, pn;
-      if (t < 32) {
-#pragma unroll
-        for (int k = 0; k < MP; ++k) pb[k] = __shfl_xor_sync(FULL, b[k], t);
-        pd = __shfl_xor_sync(FULL, d, t);
-        pn = __shfl_xor_sync(FULL, nrm, t);
-      } else {
-        float *row = xb + L * 66;
-#pragma unroll
-        for (int k = 0; k < MP; k += 2) *reinterpret_cast<float2 *>(row + k) = make_float2(b[k], b[k + 1]);
-        row[64] = d;
-        row[65] = nrm;
-        pair_bar(bar);
-        const float *prow = xb + (L ^ t) * 66;
-#pragma unroll
-        for (int k = 0; k < MP; k += 2) {
-          const float2 v2 = *reinterpret_cast<const float2 *>(prow + k);
-          pb[k] = v2.x;
-          pb[k + 1] = v2.y;
-        }
-        pd = prow[64];
-        pn = prow[65];
-        pair_bar(bar);
-      }
-      const float dot = d * pd * dot4<MP, float>(b, pb);
-      const bool isp = L < (L ^ t);
-      const float app = isp ? nrm : pn;
-      const float aqq = isp ? pn : nrm;
-      float tr = 0.f, cs = 1.f;
-      if (dot * dot > tol2 * app * aqq) {
-        const float zeta = __fdividef(aqq - app, 2.f * dot);
-        const float az = fabsf(zeta);
-        tr = az > 1e15f ? __fdividef(0.5f, zeta)
-                        : copysignf(__fdividef(1.f, az + __fsqrt_rn(fmaf(zeta, zeta, 1.f))), zeta);
-        cs = rsqrtf(fmaf(tr, tr, 1.f));
-        rotated = 1;
-      }
-      const float coef = (isp ? -tr : tr) * __fdividef(pd, d);
-#pragma unroll
-      for (int k = 0; k < MP; ++k) b[k] = fmaf(coef, pb[k], b[k]);
-      d *= cs;
-      nrm = isp ? fmaf(-tr, dot, app) : fmaf(tr, dot, aqq);
-    }
-#pragma unroll
-    for (int k = 0; k < MP; ++k) b[k] *= d;
-    const float any = pair_sum(__any_sync(FULL, rotated) ? 1.f : 0.f, red, half, bar);
-    if (any == 0.f) {
-      converged = true;
-      break;
-    }
-  }
-  if (L == 0) {
-    atomicMax(&counters[2], converged ? sweep + 1 : sweep);
-    atomicAdd(&counters[3], converged ? sweep + 1 : sweep);
-    if (!converged) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
-  }
-  const float nrm = dot4<MP, float>(b, b);
-  const float lam = nrm > 0.f ? sqrtf(nrm) : 1.f;
-  const float inv = 1.f / lam;
-#pragma unroll
-  for (int k = 0; k < MP; ++k) b[k] *= inv;      // eigenvector column L
-  // ---- transform and apply ----
-  float *vt = scr;                               // vt[i*65+j] = V[i][j]
-  float *vec = scr + 64 * 65;                    // [3][64]
-  const float x0 = mem ? xrow[L] : 0.f;
-  const float x1 = mem ? xrow[m + L] : 0.f;
-  const float inv_m = 1.f / float(m);
-  const float xb0 = pair_sum(x0, red, half, bar) * inv_m;
-  const float xb1 = pair_sum(x1, red, half, bar) * inv_m;
-  const float xp0 = mem ? x0 - xb0 : 0.f;
-  const float xp1 = mem ? x1 - xb1 : 0.f;
-  vec[L] = cd;
-  vec[MP + L] = xp0;
-  vec[2 * MP + L] = xp1;
-#pragma unroll
-  for (int k = 0; k < MP; ++k) vt[k * 65 + L] = b[k];
-  pair_bar(bar);
-  float u = 0.f, g0 = 0.f, g1 = 0.f;
-#pragma unroll
-  for (int k = 0; k < MP; ++k) {
-    u = fmaf(b[k], vec[k], u);
-    g0 = fmaf(b[k], vec[MP + k], g0);
-    g1 = fmaf(b[k], vec[2 * MP + k], g1);
-  }
-  const float z = u / lam;
-  const float P0 = pair_sum(g0 * z, red, half, bar);
-  const float P1 = pair_sum(g1 * z, red, half, bar);
-  const float sroot = mem ? sqrtf(float(m - 1) / lam) : 0.f;
-  vec[MP + L] = g0 * sroot;
-  vec[2 * MP + L] = g1 * sroot;
-  pair_bar(bar);
-  float q0 = 0.f, q1 = 0.f;
-  {
-    const float *vr = vt + L * 65;
-#pragma unroll
-    for (int j = 0; j < MP; ++j) {
-      q0 = fmaf(vr[j], vec[MP + j], q0);
-      q1 = fmaf(vr[j], vec[2 * MP + j], q1);
-    }
-  }
-  const float xa0 = xb0 + P0 + q0;
-  const float xa1 = xb1 + P1 + q1;
-  if (mem) {
-    xrow[L] = xa0;
-    xrow[m + L] = xa1;
-  }
-  const float mu0 = pair_sum(mem ? xa0 : 0.f, red, half, bar) * inv_m;
-  const float mu1 = pair_sum(mem ? xa1 : 0.f, red, half, bar) * inv_m;
-  const float e0 = mem ? xa0 - mu0 : 0.f;
-  const float e1 = mem ? xa1 - mu1 : 0.f;
-  const float sp0 = sqrtf(pair_sum(e0 * e0, red, half, bar) / float(m - 1));
-  const float sp1 = sqrtf(pair_sum(e1 * e1, red, half, bar) / float(m - 1));
-  if (L == 0) {
-    if (mean_out) {
-      mean_out[0] = mu0;
-      mean_out[1] = mu1;
-    }
-    if (spread_out) {
-      spread_out[0] = sp0;
-      spread_out[1] = sp1;
-    }
-    if (!isfinite(mu0) || !isfinite(mu1) || !isfinite(sp0) || !isfinite(sp1))
-      atomicOr(&counters[0], LK_BIT_NONFINITE);
-  }
-  // ---- eigenbasis for the next analysis (identity if non-finite) ----
-  bool ok = true;
-#pragma unroll
-  for (int k = 0; k < MP; ++k) ok = ok && isfinite(b[k]);
-  const float okall = pair_sum(ok ? 0.f : 1.f, red, half, bar);
-#pragma unroll
-  for (int k = 0; k < MP; ++k) U[k * MP + L] = okall == 0.f ? b[k] : (k == L ? 1.f : 0.f);
-}
-
-__global__ void __launch_bounds__(P64_TI *P64_TJ * 64, 1)
-    analysis_tile64_kernel(const LkInst *__restrict__ insts, const LkTile *__restrict__ tiles,
-                           float *__restrict__ mean, float *__restrict__ spread, float tol,
-                           int max_sweeps, int *__restrict__ counters) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const LkTile tl = tiles[blockIdx.x];
-  const LkInst &I = insts[tl.inst];
-  const int w = I.w;
-  const int HJ = P64_TJ + w - 1;
-  const size_t ncell = (size_t)(P64_TI + w - 1) * HJ;
-  float *halo = reinterpret_cast<float *>(smem);
-  size_t off = align16(ncell * 2 * 64 * sizeof(float));
-  float *dh = reinterpret_cast<float *>(smem + off);
-  off = align16(off + ncell * 2 * sizeof(float));
-  float *tap = reinterpret_cast<float *>(smem + off);
-  off = align16(off + (size_t)w * w * sizeof(float));
-  float *scr = reinterpret_cast<float *>(smem + off);
-  stage_tile<64, float, float, P64_TI, P64_TJ>(I, tl.i0, tl.j0, halo, dh, tap);
-  __syncthreads();
-  const int warp = threadIdx.x >> 5;
-  const int node = warp >> 1, half = warp & 1;
-  const int ti = node / P64_TJ, tj = node - (node / P64_TJ) * P64_TJ;
-  const int i = tl.i0 + ti, j = tl.j0 + tj;
-  if (i > I.nsub || j > I.nsub) return;          // both warps of the pair leave together
-  const int pid = I.pid_map[i * (I.nsub + 1) + j];
-  if (pid < 0) return;
-  const int cell = ti * HJ + tj;
-  const int m = I.m;
-  analyze_node64(halo + (size_t)cell * 2 * 64, dh + cell * 2, HJ, tap, w, m, float(I.alpha), tol,
-                 max_sweeps, static_cast<float *>(I.X) + (size_t)pid * 2 * m,
-                 mean ? mean + 2 * (I.node_off + pid) : nullptr,
-                 spread ? spread + 2 * (I.node_off + pid) : nullptr,
-                 scr + (size_t)node * (P64_SCR + 8), counters, I.basis + (size_t)pid * 64 * 64,
-                 half, 1 + node);
-}
-
-cudaError_t launch_class64(letkf_ctx *h, void *mean, void *spread) {
-  if (h->n_tiles[2] == 0) return cudaSuccess;
-  int wmax = 1;
-  for (const LkInst &I : h->inst)
-    if (I.mp == 64) wmax = I.w > wmax ? I.w : wmax;
-  analysis_tile64_kernel<<<h->n_tiles[2], P64_TI * P64_TJ * 64, p64_smem_bytes(wmax), h->stream>>>(
-      h->d_inst, h->tiles[2], (float *)mean, (float *)spread, (float)h->tol32, h->max_sweeps,
-      h->counters);
-  return cudaGetLastError();
-}
-
-cudaError_t setup_class64(letkf_ctx *h) {
-  int wmax = 0;
-  for (const LkInst &I : h->inst)
-    if (I.mp == 64) wmax = I.w > wmax ? I.w : wmax;
-  if (wmax == 0) return cudaSuccess;
-  return cudaFuncSetAttribute(analysis_tile64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)p64_smem_bytes(wmax));
-}
-
 template <int MP, typename S, typename T, int TI, int TJ>
 cudaError_t launch_tile_shape(letkf_ctx *h, int cls, void *mean, void *spread, T tol, T kthr) {
   size_t need = 0;
@@ -773,15 +345,16 @@ cudaError_t launch_list(letkf_ctx *h, int cls, void *mean, void *spread) {
   return cudaGetLastError();
 }
 
+// One width class: FP64 handles run the tile kernel; FP32 handles the
+// two-columns-per-lane kernel (letkf_pair.cu), then, for MP <= 32, the FP64
+// re-analysis of the nodes it queued.
 template <int MP>
 cudaError_t launch_class(letkf_ctx *h, int cls, void *mean, void *spread) {
   if (h->n_tiles[cls] == 0) return cudaSuccess;
   if (h->precision == 1)
     return launch_tile<MP, double, double>(h, cls, mean, spread, h->tol64, 0.0);
-  const float kthr = h->fp64_kappa > 0 ? (float)h->fp64_kappa : 0.f;
-  cudaError_t e = MP == 32 ? lk_launch_pair(h, cls, mean, spread, (float)h->tol32, kthr)
-                           : launch_tile<MP, float, float>(h, cls, mean, spread, (float)h->tol32, kthr);
-  if (e != cudaSuccess || kthr <= 0.f) return e;
+  cudaError_t e = lk_launch_pair(h, cls, mean, spread);
+  if (e != cudaSuccess || h->fp64_kappa <= 0 || MP > 32) return e;
   return launch_list<MP>(h, cls, mean, spread);
 }
 
@@ -806,14 +379,9 @@ cudaError_t setup_class(letkf_ctx *h) {
 #undef LK_SET
     return e;
   }
-#define LK_SET(id, ti, tj) \
-  if (e == cudaSuccess) e = set_smem<MP, float, float, ti, tj>(wmax);
-  LK_FOR_SHAPES(LK_SET)
-#undef LK_SET
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(analysis_list_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(LIST_WARPS * list_warp_bytes<MP>(wmax)));
-  if (e == cudaSuccess && MP == 32) e = lk_setup_pair(h);
   return e;
 }
 
@@ -841,7 +409,7 @@ int lk_width_class(int m) { return m <= 16 ? 0 : (m <= 32 ? 1 : 2); }
 cudaError_t lk_setup_analysis(letkf_ctx *h) {
   cudaError_t e = setup_class<16>(h);
   if (e == cudaSuccess) e = setup_class<32>(h);
-  if (e == cudaSuccess) e = setup_class64(h);
+  if (e == cudaSuccess) e = lk_setup_pair(h);
   return e;
 }
 
@@ -850,14 +418,14 @@ cudaError_t lk_launch_analysis_class(letkf_ctx *h, int cls, void *mean, void *sp
   if (e != cudaSuccess) return e;
   if (cls == 0) return launch_class<16>(h, 0, mean, spread);
   if (cls == 1) return launch_class<32>(h, 1, mean, spread);
-  return launch_class64(h, mean, spread);
+  return h->n_tiles[2] ? lk_launch_pair(h, 2, mean, spread) : cudaSuccess;
 }
 
 cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread) {
   cudaError_t e = cudaMemsetAsync(h->counters + 1, 0, 7 * sizeof(int), h->stream);
   if (e == cudaSuccess) e = launch_class<16>(h, 0, mean, spread);
   if (e == cudaSuccess) e = launch_class<32>(h, 1, mean, spread);
-  if (e == cudaSuccess) e = launch_class64(h, mean, spread);
+  if (e == cudaSuccess && h->n_tiles[2]) e = lk_launch_pair(h, 2, mean, spread);
   return e;
 }
 

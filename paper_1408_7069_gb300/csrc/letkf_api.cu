@@ -190,8 +190,13 @@ letkf_status build_tiles(letkf_ctx *h, int cls, const std::vector<std::vector<in
         if (any) tl.push_back(LkTile{k, i0, j0, (int)(cost * I.mp * I.mp / 32)});
       }
   }
-  std::stable_sort(tl.begin(), tl.end(),
-                   [](const LkTile &a, const LkTile &b) { return a.cost > b.cost; });
+  // class 2 runs as two launches (MP = 64, then MP = 48): group by width first
+  auto wide = [h](const LkTile &t) { return h->inst[t.inst].mp == 64; };
+  std::stable_sort(tl.begin(), tl.end(), [&](const LkTile &a, const LkTile &b) {
+    if (wide(a) != wide(b)) return wide(a);
+    return a.cost > b.cost;
+  });
+  h->tile_split[cls] = (int)std::count_if(tl.begin(), tl.end(), wide);
   if (h->tiles[cls]) cudaFree(h->tiles[cls]);
   h->tiles[cls] = nullptr;
   letkf_status st = dalloc(h, &h->tiles[cls], tl.size() * sizeof(LkTile));
@@ -242,7 +247,6 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   h->max_sweeps = cfgs[0].max_sweeps > 0 ? cfgs[0].max_sweeps : 20;
   h->fp64_kappa = cfgs[0].fp64_kappa;
   h->n_inst = n;
-  h->tile_shape[2] = 2;               // 33..64 members: fixed 2 x 2 node tiles (warp pair per node)
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     delete h;
     return fail(nullptr, LETKF_ERR_CUDA, "no CUDA device");
@@ -266,7 +270,7 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
     I.m = c.m;
     I.w = c.window;
     I.h = c.window / 2;
-    I.mp = c.m <= 16 ? 16 : (c.m <= 32 ? 32 : 64);
+    I.mp = c.m <= 16 ? 16 : (c.m <= 32 ? 32 : (c.m <= 48 ? 48 : 64));
     I.n_pts = (int)geo[k].pts.size();
     I.n_sap = (int)geo[k].saps.size();
     I.p = 2 * I.n_sap;
@@ -598,8 +602,8 @@ letkf_status letkf_set_tile_shape(letkf_t h, int32_t width_class, int32_t shape)
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
   if (width_class < 0 || width_class > 2 || shape < 0 || shape >= lk_num_tile_shapes())
     return fail(h, LETKF_ERR_ARG, "width class or tile shape out of range");
-  if (width_class == 2 && shape != 2)
-    return fail(h, LETKF_ERR_ARG, "ensembles of 33..64 members use tile shape 2 (2 x 2) only");
+  if (!lk_pair_shape_ok(width_class, shape))
+    return fail(h, LETKF_ERR_ARG, "ensembles of 33..64 members take tiles of at most 8 nodes");
   DeviceGuard dg(h->device);
   LK_CUDA(h, cudaStreamSynchronize(h->stream));
   h->tile_shape[width_class] = shape;
@@ -636,10 +640,11 @@ letkf_status letkf_autotune(letkf_t h, const void *y_dev, int32_t reps, int32_t 
   for (int cls = 0; cls < 3 && e == cudaSuccess && st == LETKF_OK; ++cls) {
     if (shapes_out) shapes_out[cls] = h->tile_shape[cls];
     if (us_out) us_out[cls] = 0.f;
-    if (h->n_tiles[cls] == 0 || cls == 2) continue;
+    if (h->n_tiles[cls] == 0) continue;
     int best = h->tile_shape[cls];
     float best_ms = 1e30f;
     for (int s = 0; s < ns && e == cudaSuccess && st == LETKF_OK; ++s) {
+      if (!lk_pair_shape_ok(cls, s)) continue;
       h->tile_shape[cls] = s;
       st = rebuild_tiles(h, cls);
       float total = 0.f;

@@ -31,7 +31,7 @@ constexpr int LK_RES_BLOCKS = 128;
 // float (precision 0) or double (precision 1).
 struct LkInst {
   int nsub, m, w, h;        // h = w / 2
-  int mp;                   // padded ensemble width of the kernels (16, 32 or 64)
+  int mp;                   // padded ensemble width of the kernels (16, 32, 48 or 64)
   int n_pts, n_sap, p;
   int gs_rows, gs_cols;     // padded subaperture grid: cell (s+h, t+h) holds subap (s, t)
   const int *pid_map;       // [(nsub+1)^2] node -> point id or -1
@@ -83,6 +83,7 @@ struct letkf_ctx {
   LkTile *tiles[3] = {nullptr, nullptr, nullptr};   // per width class 16 / 32 / 64
   int n_tiles[3] = {0, 0, 0};
   int tile_shape[3] = {0, 0, 0};    // index into the compiled tile shapes, per class
+  int tile_split[3] = {0, 0, 0};    // class 2: leading tiles of MP = 64 instances (MP = 48 after)
   std::vector<LkTile> tiles_host[3];
 
   // device buffers (single allocations sliced per instance)
@@ -122,9 +123,10 @@ cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
 cudaError_t lk_launch_tick(letkf_ctx *h);
 cudaError_t lk_launch_basis_reset(letkf_ctx *h);   // warm-start eigenbases -> identity
 cudaError_t lk_setup_analysis(letkf_ctx *h);
-// FP32 analysis of the 17..32-member class, two nodes per warp (letkf_pair.cu).
-cudaError_t lk_launch_pair(letkf_ctx *h, int cls, void *mean, void *spread, float tol, float kthr);
+// FP32 analysis of width class cls, two columns per lane (letkf_pair.cu).
+cudaError_t lk_launch_pair(letkf_ctx *h, int cls, void *mean, void *spread);
 cudaError_t lk_setup_pair(letkf_ctx *h);
+bool lk_pair_shape_ok(int cls, int shape);   // class 2 (one node per warp): at most 8 nodes per tile
 int lk_num_tile_shapes();
 void lk_tile_shape(int s, int *ti, int *tj);
 int lk_width_class(int m);          // 0: m <= 16, 1: m <= 32, 2: m <= 64

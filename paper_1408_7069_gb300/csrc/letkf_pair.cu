@@ -1,32 +1,35 @@
-// FP32 local analysis for ensembles of 17..32 members (Section 4.2 with
-// Section 3.1 and Appendix A), two nodes per warp.
+// FP32 local analysis (Section 4.2 with Section 3.1 and Appendix A) with two
+// columns of the node problem per lane.
 //
-// Lanes 16h .. 16h+15 of a warp serve node h of the pair. Lane i of a node
-// holds two columns of the node's 32-column problem (padded with identity
-// columns above m): on entry rows 2i and 2i+1 of
+// The node problem is padded to MP = 16, 32, 48 or 64 columns (identity on the
+// padding). A node is served by LPN = MP/2 lanes: 4 nodes per warp for MP = 16,
+// 2 for MP = 32, 1 for MP = 48 (lanes 24..31 idle) and 64. Lane i of a node
+// holds two columns, on entry rows 2i and 2i+1 of
 //   A = (m-1)/rho I + sum_j tau_j/sigma2 Yb_j Yb_j^T     (symmetric, so also columns),
-// as 16 float2 each, so that packed FP32 FMAs (two lanes of arithmetic per
+// as MP/2 float2 each, so that packed FP32 FMAs (two lanes of arithmetic per
 // instruction) do the Gram, the rotations and the dot products.
 //
 // Eigensolve: one-sided (Hestenes) Jacobi on the columns of B = A, which
 // converge to V diag(lambda) (|A v| = lambda for A > 0). A sweep visits all
-// 496 column pairs in 32 rounds of the odd-even transposition network: in an
-// even round lane i rotates its own pair (positions 2i, 2i+1); in an odd round
-// it rotates positions (2i+1, 2i+2), where position 2i+2 came from lane i+1.
-// After each rotation the two columns trade positions (the network's swap),
-// so between rounds every lane passes exactly one column to a neighbour: the Q
-// column down after an even round, the P column up after an odd round. One
-// shuffle moves 32 values per pair visit, half of what a lane-per-column
-// layout needs. The end slot of an odd round (positions 31 and 0, held by lane
-// 15) does not rotate; it swaps its columns (an exact 90-degree rotation, the
-// sign being irrelevant), which keeps the register roles of every lane the same.
-// A rotation is applied as P' = c P - s Q, Q' = s P + c Q, exact for c = 1,
-// s = 0 (no rotation) and for the swap. A node whose sweep made no rotation is
-// converged and freezes (its lanes shuffle from themselves), so its result does
-// not depend on the node that shares its warp.
+// MP (MP-1)/2 column pairs in MP rounds of the odd-even transposition network:
+// in an even round lane i rotates its own pair (positions 2i, 2i+1); in an odd
+// round it rotates positions (2i+1, 2i+2), where position 2i+2 came from lane
+// i+1. After each rotation the two columns trade positions (the network's
+// swap), so between rounds every lane passes exactly one column to a
+// neighbour: the Q column down after an even round, the P column up after an
+// odd round. One shuffle moves MP values per pair visit, half of what a
+// lane-per-column layout needs. The end slot of an odd round (positions MP-1
+// and 0, held by the node's last lane) does not rotate; it swaps its columns
+// (an exact 90-degree rotation, the sign being irrelevant), which keeps the
+// register roles of every lane the same. A rotation is applied as
+// P' = c P - s Q, Q' = s P + c Q, exact for c = 1, s = 0 (no rotation) and for
+// the swap. A node whose sweep made no rotation is converged and freezes (its
+// lanes shuffle from themselves), so its result does not depend on the nodes
+// that share its warp.
 //
-// kappa_hat = 1 + rho tr(G)/(m-1) bounds the condition number before the
-// eigensolve; nodes above the threshold are queued for the FP64 list kernel.
+// For MP <= 32, kappa_hat = 1 + rho tr(G)/(m-1) bounds the condition number
+// before the eigensolve; nodes above the threshold are queued for the FP64
+// list kernel. Wider problems have no FP64 fallback.
 #include <math.h>
 #include <stdint.h>
 
@@ -36,22 +39,29 @@
 
 namespace {
 
-constexpr int PMP = 32;               // padded width of the node problem
-constexpr int CELLF = 2 * PMP + 4;    // floats per halo cell: +4 shifts banks between neighbours
-constexpr int NODE_SCR = 3 * PMP + 4;  // floats of scratch per node (C d, X'_0, X'_1)
+template <int MP>
+struct PairCfg {
+  static constexpr int LPN = MP / 2;                      // lanes per node
+  static constexpr int NPW = MP <= 32 ? 32 / LPN : 1;     // nodes per warp
+  static constexpr int GL = NPW > 1 ? LPN : 32;           // lanes of a node's group (power of 2)
+  static constexpr int K2 = MP / 2;                       // float2 per column
+  static constexpr int CELLF = 2 * MP + 4;                // floats per halo cell (+4: bank shift)
+  static constexpr int NODE_SCR = 3 * MP + 4;             // scratch floats per node
+};
 
 // Shared-memory layout of one CTA (bytes).
 struct PairLayout {
   size_t dh, tap, scr, total;
 };
-template <int TI, int TJ>
+template <int MP, int TI, int TJ>
 __host__ __device__ PairLayout pair_layout(int w) {
+  using C = PairCfg<MP>;
   PairLayout L;
   const size_t ncell = (size_t)(TI + w - 1) * (TJ + w - 1);
-  L.dh = align16(ncell * CELLF * sizeof(float));
+  L.dh = align16(ncell * C::CELLF * sizeof(float));
   L.tap = align16(L.dh + ncell * 2 * sizeof(float));
   L.scr = align16(L.tap + (size_t)w * w * sizeof(float));
-  L.total = L.scr + (size_t)TI * TJ * NODE_SCR * sizeof(float);
+  L.total = L.scr + (size_t)TI * TJ * C::NODE_SCR * sizeof(float);
   return L;
 }
 
@@ -59,17 +69,19 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
-// Sum over the 16 lanes of a node.
-__device__ __forceinline__ float half_sum(float v) {
+// Sum over the lanes of a node's group (idle lanes contribute zero).
+template <int GL>
+__device__ __forceinline__ float group_sum(float v) {
 #pragma unroll
-  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  for (int o = GL / 2; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
   return v;
 }
 
-__device__ __forceinline__ float dot16(const float2 (&a)[16], const float2 (&b)[16]) {
+template <int K2>
+__device__ __forceinline__ float dotk(const float2 (&a)[K2], const float2 (&b)[K2]) {
   float2 s0 = f2(0.f), s1 = f2(0.f), s2 = f2(0.f), s3 = f2(0.f);
 #pragma unroll
-  for (int k = 0; k < 16; k += 4) {
+  for (int k = 0; k < K2; k += 4) {
     s0 = fma2(a[k], b[k], s0);
     s1 = fma2(a[k + 1], b[k + 1], s1);
     s2 = fma2(a[k + 2], b[k + 2], s2);
@@ -81,10 +93,11 @@ __device__ __forceinline__ float dot16(const float2 (&a)[16], const float2 (&b)[
 // One round on this lane's pair (P, Q) with tracked squared norms. `idle`:
 // the end slot of an odd round, which swaps instead of rotating. Returns
 // whether the pair was rotated.
-__device__ __forceinline__ int pair_round(float2 (&P)[16], float2 (&Q)[16], float &nP, float &nQ,
+template <int K2>
+__device__ __forceinline__ int pair_round(float2 (&P)[K2], float2 (&Q)[K2], float &nP, float &nQ,
                                           float tol2, bool idle, bool frozen) {
-  const float dot = dot16(P, Q);
-  // tan(theta) for the rotation that makes the pair orthogonal, with
+  const float dot = dotk<K2>(P, Q);
+  // tan(theta) of the rotation that makes the pair orthogonal, with
   // x = |q|^2 - |p|^2, y = 2 p.q: t = sign(x) y / (|x| + sqrt(x^2 + y^2)), |theta| <= pi/4
   const float x = nQ - nP, y = 2.f * dot;
   const float h2 = fmaf(x, x, y * y);
@@ -103,7 +116,7 @@ __device__ __forceinline__ int pair_round(float2 (&P)[16], float2 (&Q)[16], floa
   const float nQ2 = rot ? fmaf(t, dot, nQ) : (swp ? nP : nQ);
   const float2 cc = f2(c), ms = f2(-s), ps = f2(s);
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
+  for (int k = 0; k < K2; ++k) {
     const float2 p = P[k], q = Q[k];
     P[k] = fma2(cc, p, mul2(ms, q));
     Q[k] = fma2(cc, q, mul2(ps, p));
@@ -113,23 +126,22 @@ __device__ __forceinline__ int pair_round(float2 (&P)[16], float2 (&Q)[16], floa
   return rot ? 1 : 0;
 }
 
-__device__ __forceinline__ void shfl_cols(float2 (&X)[16], int src) {
+template <int K2>
+__device__ __forceinline__ void shfl_cols(float2 (&X)[K2], int src) {
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
+  for (int k = 0; k < K2; ++k) {
     X[k].x = __shfl_sync(FULL, X[k].x, src);
     X[k].y = __shfl_sync(FULL, X[k].y, src);
   }
 }
 
-__device__ __forceinline__ float norm16(const float2 (&a)[16]) { return dot16(a, a); }
-
-// Sum of v over the 16 lanes of a node, scattered: on return v[0] of lane i
-// holds element i (members 2i, 2i+1) of the sum. Recursive halving: at offset
-// o a lane keeps the half selected by bit o of its index and adds the partner's
-// copy of that half.
-__device__ __forceinline__ float2 reduce_scatter16(float2 (&v)[16], int li) {
+// Sum of v over the GL lanes of a group, scattered: on return v[0] of lane i
+// (i < GL) holds element i of the sum. Recursive halving: at offset o a lane
+// keeps the half selected by bit o of its index and adds the partner's copy.
+template <int GL>
+__device__ __forceinline__ float2 reduce_scatter(float2 (&v)[GL], int li) {
 #pragma unroll
-  for (int o = 8; o > 0; o >>= 1) {
+  for (int o = GL / 2; o > 0; o >>= 1) {
     const bool b = (li & o) != 0;
 #pragma unroll
     for (int e = 0; e < o; ++e) {
@@ -145,96 +157,102 @@ __device__ __forceinline__ float2 reduce_scatter16(float2 (&v)[16], int li) {
 }
 
 // Stages the tile's halo (slope anomalies and innovations) and the taper table.
-template <int TI, int TJ>
+template <int MP, int TI, int TJ>
 __device__ __forceinline__ void stage_pair_tile(const LkInst &I, int i0, int j0, float *halo,
                                                 float *dh, float *tap) {
+  using C = PairCfg<MP>;
   const int w = I.w, m = I.m;
   const int HJ = TJ + w - 1;
   const int ncell = (TI + w - 1) * HJ;
   const float *Ybp = static_cast<const float *>(I.Ybp);
   const float *dp = static_cast<const float *>(I.dp);
   const float *taper = static_cast<const float *>(I.taper);
-  if (m == PMP && (reinterpret_cast<uintptr_t>(Ybp) & 15) == 0) {
-    // a cell's two slope rows are 64 contiguous floats in the grid: float4 copies
-    for (int e4 = threadIdx.x; e4 < ncell * 16; e4 += blockDim.x) {
-      const int cell = e4 >> 4, q = e4 & 15;
+  if (m == MP && (reinterpret_cast<uintptr_t>(Ybp) & 15) == 0) {
+    // a cell's two slope rows are 2 MP contiguous floats in the grid: float4 copies
+    constexpr int Q4 = MP / 2;
+    for (int e4 = threadIdx.x; e4 < ncell * Q4; e4 += blockDim.x) {
+      const int cell = e4 / Q4, q = e4 - cell * Q4;
       const int hi = cell / HJ, hj = cell - hi * HJ;
       const size_t src = (size_t)(i0 + hi) * I.gs_cols + (j0 + hj);
-      reinterpret_cast<float4 *>(halo + (size_t)cell * CELLF)[q] =
-          reinterpret_cast<const float4 *>(Ybp + src * 2 * PMP)[q];
+      reinterpret_cast<float4 *>(halo + (size_t)cell * C::CELLF)[q] =
+          reinterpret_cast<const float4 *>(Ybp + src * 2 * MP)[q];
     }
   } else {
-    for (int e = threadIdx.x; e < ncell * CELLF; e += blockDim.x) {
-    const int cell = e / CELLF;
-    const int r = e - cell * CELLF;
-    float v = 0.f;
-    if (r < 2 * PMP) {
-      const int c = r / PMP;
-      const int mm = r - c * PMP;
-      const int hi = cell / HJ, hj = cell - (cell / HJ) * HJ;
-      const size_t src = (size_t)(i0 + hi) * I.gs_cols + (j0 + hj);
-      if (mm < m) v = Ybp[(src * 2 + c) * m + mm];
-    }
-    halo[e] = v;
+    for (int e = threadIdx.x; e < ncell * C::CELLF; e += blockDim.x) {
+      const int cell = e / C::CELLF;
+      const int r = e - cell * C::CELLF;
+      float v = 0.f;
+      if (r < 2 * MP) {
+        const int c = r / MP;
+        const int mm = r - c * MP;
+        const int hi = cell / HJ, hj = cell - hi * HJ;
+        const size_t src = (size_t)(i0 + hi) * I.gs_cols + (j0 + hj);
+        if (mm < m) v = Ybp[(src * 2 + c) * m + mm];
+      }
+      halo[e] = v;
     }
   }
   for (int e = threadIdx.x; e < ncell * 2; e += blockDim.x) {
     const int cell = e >> 1;
-    const int hi = cell / HJ, hj = cell - (cell / HJ) * HJ;
+    const int hi = cell / HJ, hj = cell - hi * HJ;
     const size_t src = (size_t)(i0 + hi) * I.gs_cols + (j0 + hj);
     dh[e] = dp[src * 2 + (e & 1)];
   }
   for (int e = threadIdx.x; e < w * w; e += blockDim.x) tap[e] = taper[e];
 }
 
-// One CTA per tile of TI x TJ nodes of one instance; warp w serves nodes 2w
-// and 2w+1 of the tile (row-major).
-// Register cap: 128 per thread, so that 16 warps (32 nodes) fit on an SM.
-template <int TI, int TJ>
-__global__ void __launch_bounds__(TI *TJ * 16)
+// One CTA per tile of TI x TJ nodes of one instance; the nodes of the tile are
+// taken in row-major order, NPW per warp. `queue`: FP64 worklist counter slot
+// (MP <= 32), NULL for no fallback.
+template <int MP, int TI, int TJ>
+__global__ void __launch_bounds__(TI *TJ * 32 / PairCfg<MP>::NPW)
     analysis_pair_kernel(const LkInst *__restrict__ insts, const LkTile *__restrict__ tiles,
                          float *__restrict__ mean, float *__restrict__ spread, float tol,
                          int max_sweeps, float kappa_thr, int *__restrict__ counters,
-                         int2 *__restrict__ worklist, int keep_basis) {
+                         int *__restrict__ queue, int2 *__restrict__ worklist, int keep_basis) {
+  using C = PairCfg<MP>;
+  constexpr int K2 = C::K2, LPN = C::LPN, GL = C::GL;
   extern __shared__ __align__(16) unsigned char smem[];
   const LkTile tl = tiles[blockIdx.x];
   const LkInst &I = insts[tl.inst];
   const int w = I.w, m = I.m;
-  const PairLayout Ly = pair_layout<TI, TJ>(w);
+  const PairLayout Ly = pair_layout<MP, TI, TJ>(w);
   const int HJ = TJ + w - 1;
   float *halo = reinterpret_cast<float *>(smem);
   float *dh = reinterpret_cast<float *>(smem + Ly.dh);
   float *tap = reinterpret_cast<float *>(smem + Ly.tap);
-  stage_pair_tile<TI, TJ>(I, tl.i0, tl.j0, halo, dh, tap);
+  stage_pair_tile<MP, TI, TJ>(I, tl.i0, tl.j0, halo, dh, tap);
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
-  const int hh = lane >> 4, li = lane & 15;
-  const int node = (threadIdx.x >> 5) * 2 + hh;            // node of the tile
+  const int grp = lane / GL, li = lane - grp * GL;    // node of the warp, lane within the node
+  const bool live = li < LPN;                        // lanes 24..31 idle when MP = 48
+  const int node = (threadIdx.x >> 5) * C::NPW + grp;  // node of the tile
   const int ti = node / TJ, tj = node - (node / TJ) * TJ;
   const int gi = tl.i0 + ti, gj = tl.j0 + tj;
   int pid = -1;
   if (gi <= I.nsub && gj <= I.nsub) pid = I.pid_map[gi * (I.nsub + 1) + gj];
-  float *scr = reinterpret_cast<float *>(smem + Ly.scr) + (size_t)node * NODE_SCR;
+  float *scr = reinterpret_cast<float *>(smem + Ly.scr) + (size_t)node * C::NODE_SCR;
 
   // ---- Gram: rows 2li and 2li+1 of A, C d, diagonal of G ----
-  float2 P[16], Q[16];
+  float2 P[K2], Q[K2];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
+  for (int k = 0; k < K2; ++k) {
     P[k] = f2(0.f);
     Q[k] = f2(0.f);
   }
   float diag = 0.f, cd0 = 0.f, cd1 = 0.f;
-  const float *hwin = halo + (size_t)(ti * HJ + tj) * CELLF;
+  const float *hwin = halo + (size_t)(ti * HJ + tj) * C::CELLF;
   const float *dwin = dh + (size_t)(ti * HJ + tj) * 2;
+  const int lr = live ? li : 0;                      // idle lanes read row pair 0, then drop it
   for (int ds = 0; ds < w; ++ds) {
     for (int dt = 0; dt < w; ++dt) {
       const int cell = ds * HJ + dt;
       const float tw = tap[ds * w + dt];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const float *yv = hwin + (size_t)cell * CELLF + c * PMP;
-        const float2 yl = reinterpret_cast<const float2 *>(yv)[li];
+        const float *yv = hwin + (size_t)cell * C::CELLF + c * MP;
+        const float2 yl = reinterpret_cast<const float2 *>(yv)[lr];
         const float cy0 = tw * yl.x, cy1 = tw * yl.y;
         diag = fmaf(cy0, yl.x, fmaf(cy1, yl.y, diag));
         const float dj = dwin[cell * 2 + c];
@@ -242,7 +260,7 @@ __global__ void __launch_bounds__(TI *TJ * 16)
         cd1 = fmaf(cy1, dj, cd1);
         const float2 c0 = f2(cy0), c1 = f2(cy1);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < K2 / 2; ++k) {
           const float4 y4 = reinterpret_cast<const float4 *>(yv)[k];
           const float2 ya = make_float2(y4.x, y4.y), yb = make_float2(y4.z, y4.w);
           P[2 * k] = fma2(c0, ya, P[2 * k]);
@@ -253,55 +271,66 @@ __global__ void __launch_bounds__(TI *TJ * 16)
       }
     }
   }
+  if (!live) diag = cd0 = cd1 = 0.f;
   const float alpha = float(I.alpha);
   bool active = pid >= 0;
-  if (kappa_thr > 0.f) {
-    const float trg = half_sum(diag);
+  if (queue) {
+    const float trg = group_sum<GL>(diag);
     if (active && 1.f + trg / alpha > kappa_thr) {
       if (li == 0) {
-        worklist[atomicAdd(&counters[4 + 1], 1)] = make_int2(tl.inst, pid);
+        worklist[atomicAdd(queue, 1)] = make_int2(tl.inst, pid);
         atomicAdd(&counters[1], 1);
       }
       active = false;
     }
   }
-  // (m-1)/rho on the diagonal, 1 on the padding; inactive nodes get the identity
+  // (m-1)/rho on the diagonal, 1 on the padding; inactive nodes and idle lanes
+  // get identity columns
+  const bool own = active && live;
   const float dP = (2 * li < m) ? alpha : 1.f, dQ = (2 * li + 1 < m) ? alpha : 1.f;
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    if (!active) {
+  for (int k = 0; k < K2; ++k) {
+    if (!own) {
       P[k] = f2(0.f);
       Q[k] = f2(0.f);
     }
     if (k == li) {
-      P[k].x = active ? P[k].x + dP : 1.f;
-      Q[k].y = active ? Q[k].y + dQ : 1.f;
+      P[k].x = own ? P[k].x + dP : 1.f;
+      Q[k].y = own ? Q[k].y + dQ : 1.f;
     }
+  }
+  if (!live) {                                       // unit columns, never touched again
+    P[0].x = 1.f;
+    Q[0].y = 1.f;
   }
 
   // ---- Jacobi sweeps ----
   const float tol2 = tol * tol;
-  const int up = (lane & 16) | ((li + 1) & 15), dn = (lane & 16) | ((li + 15) & 15);
+  const int base = grp * GL;
+  const int up = live ? base + (li + 1) % LPN : lane;
+  const int dn = live ? base + (li + LPN - 1) % LPN : lane;
   bool conv = !active;
   int sweeps = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (__all_sync(FULL, conv)) break;
-    float nP = norm16(P), nQ = norm16(Q);
+    float nP = dotk<K2>(P, P), nQ = dotk<K2>(Q, Q);
     int rotated = 0;
-    const int su = conv ? lane : up, sd = conv ? lane : dn;
+    const bool frz = conv || !live;
+    const int su = frz ? lane : up, sd = frz ? lane : dn;
 #pragma unroll 1
-    for (int r = 0; r < 16; ++r) {
-      rotated |= pair_round(P, Q, nP, nQ, tol2, false, conv);
-      shfl_cols(Q, su);
+    for (int r = 0; r < MP / 2; ++r) {
+      rotated |= pair_round<K2>(P, Q, nP, nQ, tol2, false, frz);
+      shfl_cols<K2>(Q, su);
       nQ = __shfl_sync(FULL, nQ, su);
-      rotated |= pair_round(P, Q, nP, nQ, tol2, li == 15, conv);
-      shfl_cols(P, sd);
+      rotated |= pair_round<K2>(P, Q, nP, nQ, tol2, li == LPN - 1, frz);
+      shfl_cols<K2>(P, sd);
       nP = __shfl_sync(FULL, nP, sd);
     }
     const unsigned any = __ballot_sync(FULL, rotated);
+    const unsigned gmask = (GL == 32) ? 0xffffffffu : (((1u << GL) - 1u) << base);
     if (!conv) {
       sweeps = sweep + 1;
-      if (((any >> (16 * hh)) & 0xffffu) == 0u) conv = true;
+      if ((any & gmask) == 0u) conv = true;
     }
   }
   if (active && li == 0) {
@@ -311,56 +340,55 @@ __global__ void __launch_bounds__(TI *TJ * 16)
   }
 
   // ---- eigenpairs: lambda = |b|, v = b / lambda ----
-  const float lP = sqrtf(norm16(P)), lQ = sqrtf(norm16(Q));
+  const float lP = sqrtf(dotk<K2>(P, P)), lQ = sqrtf(dotk<K2>(Q, Q));
   {
     const float iP = 1.f / lP, iQ = 1.f / lQ;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < K2; ++k) {
       P[k] = mul2(f2(iP), P[k]);
       Q[k] = mul2(f2(iQ), Q[k]);
     }
   }
-
   // ---- eigenbasis for the reverse mode: U[k][2li], U[k][2li+1] ----
-  if (keep_basis && active) {
+  if (keep_basis && active && live) {
     bool ok = true;
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < K2; ++k)
       ok = ok && isfinite(P[k].x) && isfinite(P[k].y) && isfinite(Q[k].x) && isfinite(Q[k].y);
-    float *U = I.basis + (size_t)pid * PMP * PMP;
+    float *U = I.basis + (size_t)pid * MP * MP;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const float2 r0 = ok ? make_float2(P[k].x, Q[k].x)
-                           : make_float2(k == li ? 1.f : 0.f, 0.f);
-      const float2 r1 = ok ? make_float2(P[k].y, Q[k].y)
-                           : make_float2(0.f, k == li ? 1.f : 0.f);
-      reinterpret_cast<float2 *>(U + (2 * k) * PMP)[li] = r0;
-      reinterpret_cast<float2 *>(U + (2 * k + 1) * PMP)[li] = r1;
+    for (int k = 0; k < K2; ++k) {
+      const float2 r0 = ok ? make_float2(P[k].x, Q[k].x) : make_float2(k == li ? 1.f : 0.f, 0.f);
+      const float2 r1 = ok ? make_float2(P[k].y, Q[k].y) : make_float2(0.f, k == li ? 1.f : 0.f);
+      reinterpret_cast<float2 *>(U + (2 * k) * MP)[li] = r0;
+      reinterpret_cast<float2 *>(U + (2 * k + 1) * MP)[li] = r1;
     }
   }
+
   // ---- transform and apply (Section 4.2): Xa_r = xbar_r + X'_r wbar + X'_r W ----
   float *vcd = scr;                     // C d
-  float *vx0 = vcd + PMP;               // X'_0
-  float *vx1 = vx0 + PMP;               // X'_1
+  float *vx0 = vcd + MP;                // X'_0
+  float *vx1 = vx0 + MP;                // X'_1
   float *xrow = active ? static_cast<float *>(I.X) + (size_t)pid * 2 * m : nullptr;
   const int m0 = 2 * li, m1 = 2 * li + 1;
-  const float x00 = (active && m0 < m) ? xrow[m0] : 0.f;
-  const float x01 = (active && m1 < m) ? xrow[m1] : 0.f;
-  const float x10 = (active && m0 < m) ? xrow[m + m0] : 0.f;
-  const float x11 = (active && m1 < m) ? xrow[m + m1] : 0.f;
+  const bool in0 = live && m0 < m, in1 = live && m1 < m;
+  const float x00 = (active && in0) ? xrow[m0] : 0.f;
+  const float x01 = (active && in1) ? xrow[m1] : 0.f;
+  const float x10 = (active && in0) ? xrow[m + m0] : 0.f;
+  const float x11 = (active && in1) ? xrow[m + m1] : 0.f;
   const float inv_m = 1.f / float(m);
-  const float xb0 = half_sum(x00 + x01) * inv_m;
-  const float xb1 = half_sum(x10 + x11) * inv_m;
-  reinterpret_cast<float2 *>(vcd)[li] = make_float2(cd0, cd1);
-  reinterpret_cast<float2 *>(vx0)[li] =
-      make_float2(m0 < m ? x00 - xb0 : 0.f, m1 < m ? x01 - xb0 : 0.f);
-  reinterpret_cast<float2 *>(vx1)[li] =
-      make_float2(m0 < m ? x10 - xb1 : 0.f, m1 < m ? x11 - xb1 : 0.f);
+  const float xb0 = group_sum<GL>(x00 + x01) * inv_m;
+  const float xb1 = group_sum<GL>(x10 + x11) * inv_m;
+  if (live) {
+    reinterpret_cast<float2 *>(vcd)[li] = make_float2(cd0, cd1);
+    reinterpret_cast<float2 *>(vx0)[li] = make_float2(in0 ? x00 - xb0 : 0.f, in1 ? x01 - xb0 : 0.f);
+    reinterpret_cast<float2 *>(vx1)[li] = make_float2(in0 ? x10 - xb1 : 0.f, in1 ? x11 - xb1 : 0.f);
+  }
   __syncwarp();
   // projections of C d and of the two anomaly rows on this lane's eigenvectors
   float2 uP = f2(0.f), uQ = f2(0.f), a0P = f2(0.f), a0Q = f2(0.f), a1P = f2(0.f), a1Q = f2(0.f);
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
+  for (int k = 0; k < K2; ++k) {
     const float2 cdv = reinterpret_cast<const float2 *>(vcd)[k];
     const float2 x0v = reinterpret_cast<const float2 *>(vx0)[k];
     const float2 x1v = reinterpret_cast<const float2 *>(vx1)[k];
@@ -371,46 +399,50 @@ __global__ void __launch_bounds__(TI *TJ * 16)
     a1P = fma2(P[k], x1v, a1P);
     a1Q = fma2(Q[k], x1v, a1Q);
   }
-  const float gP0 = a0P.x + a0P.y, gQ0 = a0Q.x + a0Q.y;
-  const float gP1 = a1P.x + a1P.y, gQ1 = a1Q.x + a1Q.y;
+  const float gP0 = live ? a0P.x + a0P.y : 0.f, gQ0 = live ? a0Q.x + a0Q.y : 0.f;
+  const float gP1 = live ? a1P.x + a1P.y : 0.f, gQ1 = live ? a1Q.x + a1Q.y : 0.f;
   const float zP = (uP.x + uP.y) / lP, zQ = (uQ.x + uQ.y) / lQ;
-  const float w0 = half_sum(gP0 * zP + gQ0 * zQ);          // X'_0 wbar
-  const float w1 = half_sum(gP1 * zP + gQ1 * zQ);          // X'_1 wbar
+  const float w0 = group_sum<GL>(gP0 * zP + gQ0 * zQ);    // X'_0 wbar
+  const float w1 = group_sum<GL>(gP1 * zP + gQ1 * zQ);    // X'_1 wbar
   const float rP = sqrtf(float(m - 1) / lP), rQ = sqrtf(float(m - 1) / lQ);
   // X'_r W = sum_j h_r,j v_j^T with h_r,j = (X'_r v_j) sqrt((m-1)/lambda_j): this
   // lane's two terms, summed over the node's lanes and scattered by member
-  float2 v0[16], v1[16];
+  float2 v0[GL], v1[GL];
   {
     const float2 hP0 = f2(gP0 * rP), hQ0 = f2(gQ0 * rQ), hP1 = f2(gP1 * rP), hQ1 = f2(gQ1 * rQ);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      v0[k] = fma2(hP0, P[k], mul2(hQ0, Q[k]));
-      v1[k] = fma2(hP1, P[k], mul2(hQ1, Q[k]));
+    for (int k = 0; k < GL; ++k) {
+      if (k < K2) {
+        v0[k] = fma2(hP0, P[k], mul2(hQ0, Q[k]));
+        v1[k] = fma2(hP1, P[k], mul2(hQ1, Q[k]));
+      } else {
+        v0[k] = f2(0.f);
+        v1[k] = f2(0.f);
+      }
     }
   }
-  const float2 q0 = reduce_scatter16(v0, li);
-  const float2 q1 = reduce_scatter16(v1, li);
-  const float q00 = q0.x, q01 = q0.y, q10 = q1.x, q11 = q1.y;
-  const float xa00 = xb0 + w0 + q00, xa01 = xb0 + w0 + q01;
-  const float xa10 = xb1 + w1 + q10, xa11 = xb1 + w1 + q11;
+  const float2 q0 = reduce_scatter<GL>(v0, li);
+  const float2 q1 = reduce_scatter<GL>(v1, li);
+  const float xa00 = xb0 + w0 + q0.x, xa01 = xb0 + w0 + q0.y;
+  const float xa10 = xb1 + w1 + q1.x, xa11 = xb1 + w1 + q1.y;
   if (active) {
-    if (m0 < m) {
+    if (in0) {
       xrow[m0] = xa00;
       xrow[m + m0] = xa10;
     }
-    if (m1 < m) {
+    if (in1) {
       xrow[m1] = xa01;
       xrow[m + m1] = xa11;
     }
   }
-  const float e00 = m0 < m ? xa00 : 0.f, e01 = m1 < m ? xa01 : 0.f;
-  const float e10 = m0 < m ? xa10 : 0.f, e11 = m1 < m ? xa11 : 0.f;
-  const float mu0 = half_sum(e00 + e01) * inv_m;
-  const float mu1 = half_sum(e10 + e11) * inv_m;
-  const float d00 = m0 < m ? xa00 - mu0 : 0.f, d01 = m1 < m ? xa01 - mu0 : 0.f;
-  const float d10 = m0 < m ? xa10 - mu1 : 0.f, d11 = m1 < m ? xa11 - mu1 : 0.f;
-  const float sp0 = sqrtf(half_sum(d00 * d00 + d01 * d01) / float(m - 1));
-  const float sp1 = sqrtf(half_sum(d10 * d10 + d11 * d11) / float(m - 1));
+  const float e00 = in0 ? xa00 : 0.f, e01 = in1 ? xa01 : 0.f;
+  const float e10 = in0 ? xa10 : 0.f, e11 = in1 ? xa11 : 0.f;
+  const float mu0 = group_sum<GL>(e00 + e01) * inv_m;
+  const float mu1 = group_sum<GL>(e10 + e11) * inv_m;
+  const float d00 = in0 ? xa00 - mu0 : 0.f, d01 = in1 ? xa01 - mu0 : 0.f;
+  const float d10 = in0 ? xa10 - mu1 : 0.f, d11 = in1 ? xa11 - mu1 : 0.f;
+  const float sp0 = sqrtf(group_sum<GL>(d00 * d00 + d01 * d01) / float(m - 1));
+  const float sp1 = sqrtf(group_sum<GL>(d10 * d10 + d11 * d11) / float(m - 1));
   if (active && li == 0) {
     const long long row = I.node_off + pid;
     if (mean) {
@@ -426,49 +458,100 @@ __global__ void __launch_bounds__(TI *TJ * 16)
   }
 }
 
-template <int TI, int TJ>
-cudaError_t launch_shape(letkf_ctx *h, int cls, float *mean, float *spread, float tol, float kthr) {
+// Wide problems (one node per warp) take tiles of at most 8 nodes: a 16-warp
+// CTA would leave fewer registers per thread than the two columns need.
+template <int MP, int TI, int TJ>
+constexpr bool shape_ok() {
+  return PairCfg<MP>::NPW > 1 || TI * TJ <= 8;
+}
+
+template <int MP, int TI, int TJ>
+cudaError_t launch_shape(letkf_ctx *h, const LkTile *tiles, int n_tiles, float *mean,
+                         float *spread, float kthr, int *queue, int2 *worklist) {
+  if (n_tiles == 0) return cudaSuccess;
+  if constexpr (!shape_ok<MP, TI, TJ>()) {
+    return cudaErrorInvalidConfiguration;
+  } else {
   size_t need = 0;
   for (const LkInst &I : h->inst)
-    if (I.mp == PMP) {
-      const size_t b = pair_layout<TI, TJ>(I.w).total;
+    if (I.mp == MP) {
+      const size_t b = pair_layout<MP, TI, TJ>(I.w).total;
       need = b > need ? b : need;
     }
-  analysis_pair_kernel<TI, TJ><<<h->n_tiles[cls], TI * TJ * 16, need, h->stream>>>(
-      h->d_inst, h->tiles[cls], mean, spread, tol, h->max_sweeps, kthr, h->counters,
-      h->worklist + (size_t)cls * h->n_pts_total, h->keep_basis);
+  analysis_pair_kernel<MP, TI, TJ><<<n_tiles, TI * TJ * 32 / PairCfg<MP>::NPW, need, h->stream>>>(
+      h->d_inst, tiles, mean, spread, (float)h->tol32, h->max_sweeps, kthr, h->counters, queue,
+      worklist, h->keep_basis);
   return cudaGetLastError();
+  }
 }
 
-template <int TI, int TJ>
-cudaError_t set_shape_smem(int w) {
-  return cudaFuncSetAttribute(analysis_pair_kernel<TI, TJ>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)pair_layout<TI, TJ>(w).total);
-}
-
-}  // namespace
-
-cudaError_t lk_launch_pair(letkf_ctx *h, int cls, void *mean, void *spread, float tol, float kthr) {
+template <int MP>
+cudaError_t launch_mp(letkf_ctx *h, int cls, const LkTile *tiles, int n_tiles, float *mean,
+                      float *spread) {
+  const float kthr = h->fp64_kappa > 0 ? (float)h->fp64_kappa : 0.f;
+  int *queue = (MP <= 32 && kthr > 0.f) ? h->counters + 4 + cls : nullptr;
+  int2 *wl = h->worklist + (size_t)cls * h->n_pts_total;
   switch (h->tile_shape[cls]) {
 #define LK_CASE(id, ti, tj) \
   case id:                  \
-    return launch_shape<ti, tj>(h, cls, (float *)mean, (float *)spread, tol, kthr);
+    return launch_shape<MP, ti, tj>(h, tiles, n_tiles, mean, spread, kthr, queue, wl);
     LK_PAIR_SHAPES(LK_CASE)
 #undef LK_CASE
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t lk_setup_pair(letkf_ctx *h) {
+template <int MP, int TI, int TJ>
+cudaError_t set_shape_smem(int w) {
+  if constexpr (!shape_ok<MP, TI, TJ>()) {
+    return cudaSuccess;
+  } else {
+    return cudaFuncSetAttribute(analysis_pair_kernel<MP, TI, TJ>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pair_layout<MP, TI, TJ>(w).total);
+  }
+}
+
+template <int MP>
+cudaError_t setup_mp(letkf_ctx *h) {
   int wmax = 0;
   for (const LkInst &I : h->inst)
-    if (I.mp == PMP) wmax = I.w > wmax ? I.w : wmax;
-  if (wmax == 0 || h->precision != 0) return cudaSuccess;
+    if (I.mp == MP) wmax = I.w > wmax ? I.w : wmax;
+  if (wmax == 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
 #define LK_SET(id, ti, tj) \
-  if (e == cudaSuccess) e = set_shape_smem<ti, tj>(wmax);
+  if (e == cudaSuccess) e = set_shape_smem<MP, ti, tj>(wmax);
   LK_PAIR_SHAPES(LK_SET)
 #undef LK_SET
+  return e;
+}
+
+}  // namespace
+
+// Class 0: MP = 16; class 1: MP = 32; class 2: tiles of MP = 64 instances first
+// (tile_split of them), then MP = 48.
+cudaError_t lk_launch_pair(letkf_ctx *h, int cls, void *mean, void *spread) {
+  float *mo = static_cast<float *>(mean), *so = static_cast<float *>(spread);
+  if (cls == 0) return launch_mp<16>(h, 0, h->tiles[0], h->n_tiles[0], mo, so);
+  if (cls == 1) return launch_mp<32>(h, 1, h->tiles[1], h->n_tiles[1], mo, so);
+  const int split = h->tile_split[2];
+  cudaError_t e = launch_mp<64>(h, 2, h->tiles[2], split, mo, so);
+  if (e == cudaSuccess)
+    e = launch_mp<48>(h, 2, h->tiles[2] + split, h->n_tiles[2] - split, mo, so);
+  return e;
+}
+
+bool lk_pair_shape_ok(int cls, int shape) {
+  int ti, tj;
+  lk_tile_shape(shape, &ti, &tj);
+  return cls < 2 || ti * tj <= 8;
+}
+
+cudaError_t lk_setup_pair(letkf_ctx *h) {
+  if (h->precision != 0) return cudaSuccess;
+  cudaError_t e = setup_mp<16>(h);
+  if (e == cudaSuccess) e = setup_mp<32>(h);
+  if (e == cudaSuccess) e = setup_mp<48>(h);
+  if (e == cudaSuccess) e = setup_mp<64>(h);
   return e;
 }

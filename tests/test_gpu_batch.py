@@ -121,12 +121,13 @@ def test_batch_closed_loop_matches_oracle_per_instance():
 
 
 WIDE = [replace(W.ELT_80X80, name="w48", nsub=16, m=48, window=7, seeds=(141, 142, 143)),
-        replace(W.TEL_16M, name="w40", nsub=12, m=40, window=5, seeds=(151, 152, 153))]
+        replace(W.TEL_16M, name="w40", nsub=12, m=40, window=5, seeds=(151, 152, 153)),
+        replace(W.TEL_16M, name="w60", nsub=10, m=60, window=5, seeds=(161, 162, 163))]
 
 
 @pytest.mark.parametrize("w", WIDE, ids=[w.name for w in WIDE])
 def test_wide_ensemble_matches_oracle(w):
-    """33..64 members (one node per warp pair, FP32 only) on steady-state loop
+    """33..64 members (one node per warp, padded to 48 or 64 columns, FP32 only) on steady-state loop
     backgrounds (the prior-draw transient needs the FP64 path, which this width
     class does not have)."""
     inp = synth.make_loop_inputs(w, frames=10)
@@ -173,3 +174,31 @@ def test_mixed_batch_with_wide_ensembles_equals_separate_handles():
         parts.append(g.get_state().cpu().numpy().ravel())
         g.close()
     assert np.array_equal(Xb, np.concatenate(parts))
+
+
+def test_wide_tile_shapes_leave_results_unchanged():
+    """Instances padded to 48 and to 64 columns in one handle (two launches of
+    the wide class): every allowed tile shape gives the same bits, and tiles
+    of more than 8 nodes are refused for this class."""
+    ws = [WIDE[0], WIDE[2], WIDE[1]]
+    ins = [synth.make_loop_inputs(w, frames=4) for w in ws]
+    X0 = np.concatenate([i.X0.astype(np.float32).ravel() for i in ins])
+    y = torch.from_numpy(np.concatenate([i.slopes.astype(np.float32) for i in ins], 1)).cuda()
+    ref = None
+    for shape in range(len(L.tile_shapes())):
+        f = L.Letkf.batch(ws, [i.bank for i in ins])
+        ti, tj = L.tile_shapes()[shape]
+        if ti * tj > 8:
+            with pytest.raises(L.LetkfError, match="LETKF_ERR_ARG"):
+                f.set_tile_shape(2, shape)
+            f.close()
+            continue
+        f.set_tile_shape(2, shape)
+        f.set_state(torch.from_numpy(X0).cuda())
+        f.run(4, y, use_graph=False)
+        f.sync()
+        X = f.get_state().cpu().numpy()
+        f.close()
+        if ref is None:
+            ref = X
+        assert np.array_equal(X, ref), shape
