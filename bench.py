@@ -28,7 +28,7 @@ METRIC = "LETKF frames/s and p50/p99 µs/frame at 80×80 subaps k=32; grad time 
 UNIT = "frames/s"
 L2_FLUSH_BYTES = 256 << 20
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "analysis_tile_kernel_elt80.md")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "analysis_pair_kernel_elt80.md")
 
 
 def parse_args(argv=None):
@@ -502,7 +502,7 @@ def gpu_arm(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": profile_traffic(),
-                     "kernel": "letkf_analyze (observation + analysis tile + FP64 list kernels)",
+                     "kernel": "letkf_analyze (observation + analysis_pair_kernel + FP64 list kernels)",
                      "flops_per_launch": flops,
                      "launch_us": 1e6 * ana_mean_s},
         "gpu_launches": launches_per_frame * K,
