@@ -204,6 +204,9 @@ def adjoint_arm(torch, L, reps: int = 3):
     frames, ckpt = w.frames, 20
     inp = synth.make_loop_inputs(w, frames=frames)
     f = L.Letkf.from_workload(w, bank=inp.bank)
+    # strict eigensolve stopping rule: over this 200-frame window the gradient
+    # amplifies per-frame errors (both the gradient and the FD runs use it)
+    f.set_jacobi(4e-6, 0.0)
     y = torch.from_numpy(inp.slopes[:frames].astype(np.float32)).cuda()
     t = torch.from_numpy(inp.truth[:frames].astype(np.float32)).cuda()
     X0 = torch.from_numpy(inp.X0.astype(np.float32)).cuda()
@@ -266,6 +269,7 @@ def adjoint_arm(torch, L, reps: int = 3):
             "fp64_handle": {"J": J64, "grad": {"rho": g64[0], "sigma2": g64[1], "L": g64[2]},
                             "ms": ms64, "rel_J": rel(J, J64),
                             "rel_grad": [rel(g[k], g64[k]) for k in range(3)]},
+            "eigensolve": "FP32 Jacobi, strict stopping rule (letkf_set_jacobi(4e-6, 0))",
             "launch": "letkf_grad: forward, segment recomputation and backward in one CUDA graph",
             "fd_launch": "6 x letkf_run of 200 frames (one graph replay per frame)"}
 

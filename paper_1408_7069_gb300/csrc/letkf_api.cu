@@ -577,6 +577,22 @@ letkf_status letkf_set_params(letkf_t h, int32_t i, double rho, double sigma2, d
   return st;
 }
 
+letkf_status letkf_set_jacobi(letkf_t h, double rotate_tol, double stop_cos) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (!(rotate_tol > 0) || !(rotate_tol < 1) || !(stop_cos >= 0) || !(stop_cos < 1))
+    return fail(h, LETKF_ERR_ARG, "rotate_tol must be in (0, 1) and stop_cos in [0, 1)");
+  DeviceGuard dg(h->device);
+  LK_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->tol32 = rotate_tol;
+  h->stop32 = stop_cos > rotate_tol ? stop_cos : rotate_tol;
+  if (h->graph) {                    // the captured frame holds the old values
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  lk_adjoint_release(h);
+  return LETKF_OK;
+}
+
 letkf_status letkf_set_frame(letkf_t h, int64_t frame) {
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
   if (frame < 0) return fail(h, LETKF_ERR_ARG, "frame < 0");

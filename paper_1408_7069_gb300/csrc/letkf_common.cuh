@@ -68,6 +68,7 @@ struct letkf_ctx {
   int precision = 0;
   size_t rsz = 4;           // bytes of the real type
   double tol32 = 4e-6, tol64 = 1e-13, fp64_kappa = 300;
+  double stop32 = 1e-3;             // FP32 Jacobi stops after a sweep with all cosines <= this
   int max_sweeps = 20;
   int keep_basis = 0;               // store every node's eigenbasis (reverse mode needs it)
 

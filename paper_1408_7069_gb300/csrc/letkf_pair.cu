@@ -95,7 +95,7 @@ __device__ __forceinline__ float dotk(const float2 (&a)[K2], const float2 (&b)[K
 // whether the pair was rotated.
 template <int K2>
 __device__ __forceinline__ int pair_round(float2 (&P)[K2], float2 (&Q)[K2], float &nP, float &nQ,
-                                          float tol2, bool idle, bool frozen) {
+                                          float tol2, float stop2, bool idle, bool frozen) {
   const float dot = dotk<K2>(P, Q);
   // tan(theta) of the rotation that makes the pair orthogonal, with
   // x = |q|^2 - |p|^2, y = 2 p.q: t = sign(x) y / (|x| + sqrt(x^2 + y^2)), |theta| <= pi/4
@@ -104,7 +104,8 @@ __device__ __forceinline__ int pair_round(float2 (&P)[K2], float2 (&Q)[K2], floa
   const float h = h2 * rsqrtf(fmaxf(h2, 1e-37f));
   const float t = (x >= 0.f ? y : -y) / (fabsf(x) + h);
   const float cr = rsqrtf(fmaf(t, t, 1.f));
-  const bool rot = !frozen && !idle && dot * dot > tol2 * nP * nQ;
+  const float dd = dot * dot, nn = nP * nQ;
+  const bool rot = !frozen && !idle && dd > tol2 * nn;
   const bool swp = idle && !frozen;
   // P' = c P - s Q, Q' = s P + c Q: exact for the swap (c = 0, s = 1) and for no
   // rotation (c = 1, s = 0). A three-shear form would save one packed FMA per
@@ -123,7 +124,8 @@ __device__ __forceinline__ int pair_round(float2 (&P)[K2], float2 (&Q)[K2], floa
   }
   nP = nP2;
   nQ = nQ2;
-  return rot ? 1 : 0;
+  // bit 0: rotated; bit 1: rotated with cos(p, q) above the stopping cosine
+  return (rot ? 1 : 0) | ((rot && dd > stop2 * nn) ? 2 : 0);
 }
 
 template <int K2>
@@ -208,7 +210,7 @@ template <int MP, int TI, int TJ>
 __global__ void __launch_bounds__(TI *TJ * 32 / PairCfg<MP>::NPW)
     analysis_pair_kernel(const LkInst *__restrict__ insts, const LkTile *__restrict__ tiles,
                          float *__restrict__ mean, float *__restrict__ spread, float tol,
-                         int max_sweeps, float kappa_thr, int *__restrict__ counters,
+                         float stop, int max_sweeps, float kappa_thr, int *__restrict__ counters,
                          int *__restrict__ queue, int2 *__restrict__ worklist, int keep_basis) {
   using C = PairCfg<MP>;
   constexpr int K2 = C::K2, LPN = C::LPN, GL = C::GL;
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(TI *TJ * 32 / PairCfg<MP>::NPW)
   }
 
   // ---- Jacobi sweeps ----
-  const float tol2 = tol * tol;
+  const float tol2 = tol * tol, stop2 = stop * stop;
   const int base = grp * GL;
   const int up = live ? base + (li + 1) % LPN : lane;
   const int dn = live ? base + (li + LPN - 1) % LPN : lane;
@@ -319,18 +321,23 @@ __global__ void __launch_bounds__(TI *TJ * 32 / PairCfg<MP>::NPW)
     const int su = frz ? lane : up, sd = frz ? lane : dn;
 #pragma unroll 1
     for (int r = 0; r < MP / 2; ++r) {
-      rotated |= pair_round<K2>(P, Q, nP, nQ, tol2, false, frz);
+      rotated |= pair_round<K2>(P, Q, nP, nQ, tol2, stop2, false, frz);
       shfl_cols<K2>(Q, su);
       nQ = __shfl_sync(FULL, nQ, su);
-      rotated |= pair_round<K2>(P, Q, nP, nQ, tol2, li == LPN - 1, frz);
+      rotated |= pair_round<K2>(P, Q, nP, nQ, tol2, stop2, li == LPN - 1, frz);
       shfl_cols<K2>(P, sd);
       nP = __shfl_sync(FULL, nP, sd);
     }
-    const unsigned any = __ballot_sync(FULL, rotated);
+    // Converged after a sweep whose rotations all had cos(p, q) <= stop. With
+    // stop <= tol that is a sweep without rotations (every pair orthogonal to
+    // tol); a larger stop ends one or two sweeps earlier, leaving pairs within
+    // about stop^2 except inside near-degenerate clusters, whose mixing does
+    // not change W.
+    const unsigned big = __ballot_sync(FULL, rotated & 2);
     const unsigned gmask = (GL == 32) ? 0xffffffffu : (((1u << GL) - 1u) << base);
     if (!conv) {
       sweeps = sweep + 1;
-      if ((any & gmask) == 0u) conv = true;
+      if ((big & gmask) == 0u) conv = true;
     }
   }
   if (active && li == 0) {
@@ -479,8 +486,8 @@ cudaError_t launch_shape(letkf_ctx *h, const LkTile *tiles, int n_tiles, float *
       need = b > need ? b : need;
     }
   analysis_pair_kernel<MP, TI, TJ><<<n_tiles, TI * TJ * 32 / PairCfg<MP>::NPW, need, h->stream>>>(
-      h->d_inst, tiles, mean, spread, (float)h->tol32, h->max_sweeps, kthr, h->counters, queue,
-      worklist, h->keep_basis);
+      h->d_inst, tiles, mean, spread, (float)h->tol32, (float)h->stop32, h->max_sweeps, kthr,
+      h->counters, queue, worklist, h->keep_basis);
   return cudaGetLastError();
   }
 }

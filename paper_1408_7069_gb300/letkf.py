@@ -61,6 +61,7 @@ _SIGS = {
     "letkf_autotune": [c_void_p, c_void_p, c_int32, POINTER(c_int32), POINTER(ctypes.c_float)],
     "letkf_set_params": [c_void_p, c_int32, c_double, c_double, c_double],
     "letkf_set_frame": [c_void_p, ctypes.c_int64],
+    "letkf_set_jacobi": [c_void_p, c_double, c_double],
     "letkf_grad": [c_void_p, c_int32, c_void_p, c_void_p, c_int32, POINTER(c_double),
                    POINTER(c_double)],
 }
@@ -202,6 +203,10 @@ def letkf_run(h, frames: int, y_seq, truth_seq=None, resvar=None, use_graph: boo
 
 def letkf_set_params(h, i: int, rho: float, sigma2: float, loc_len: float) -> None:
     _check(lib().letkf_set_params(h, int(i), float(rho), float(sigma2), float(loc_len)), h)
+
+
+def letkf_set_jacobi(h, rotate_tol: float = 4e-6, stop_cos: float = 1e-3) -> None:
+    _check(lib().letkf_set_jacobi(h, float(rotate_tol), float(stop_cos)), h)
 
 
 def letkf_set_frame(h, frame: int) -> None:
@@ -410,6 +415,11 @@ class Letkf:
 
     def set_params(self, rho: float, sigma2: float, loc_len: float, instance: int = 0):
         letkf_set_params(self.h, instance, rho, sigma2, loc_len)
+
+    def set_jacobi(self, rotate_tol: float = 4e-6, stop_cos: float = 1e-3):
+        """FP32 eigensolve stopping rule; stop_cos <= rotate_tol: stop after a
+        sweep without rotations."""
+        letkf_set_jacobi(self.h, rotate_tol, stop_cos)
 
     def set_frame(self, frame: int):
         letkf_set_frame(self.h, frame)

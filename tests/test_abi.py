@@ -83,4 +83,5 @@ def test_null_handle_calls_fail_cleanly(built):
     assert built.letkf_sync(None) == 1
     assert built.letkf_set_params(None, 0, 1.0, 1.0, 1.0) == 1
     assert built.letkf_set_frame(None, 0) == 1
+    assert built.letkf_set_jacobi(None, 4e-6, 1e-3) == 1
     assert built.letkf_grad(None, 1, None, None, 0, None, None) == 1

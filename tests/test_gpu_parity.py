@@ -165,9 +165,18 @@ def test_forecast_with_given_noise_and_residual():
     f.close()
 
 
-@pytest.mark.parametrize("w,frames", [(W.TOY_8X8, 100), (W.TEL_16M, 60)],
-                         ids=["toy-fp64-100f", "16m-fp32-60f"])
-def test_closed_loop_free_running(w, frames):
+@pytest.mark.parametrize("w,frames,strict", [(W.TOY_8X8, 100, False), (W.TEL_16M, 60, True),
+                                             (W.TEL_16M, 60, False)],
+                         ids=["toy-fp64-100f", "16m-fp32-60f-strict", "16m-fp32-60f"])
+def test_closed_loop_free_running(w, frames, strict):
+    """The closed loop against the oracle's, both started from the same prior
+    draw. The loop amplifies small perturbations: on the oracle itself a
+    relative change of 1e-6 (1e-5) in X0 moves J by up to 4.6e-4 (4.6e-3)
+    within 60 frames. So the FP32 trajectory is compared at 1e-3 with the
+    strict eigensolve stopping rule (per-frame anomaly error 9e-6), and with
+    the default rule (4e-5) at 1e-3 over the first 20 frames and, over the
+    whole run, at the level of that measured sensitivity. FP64 handles:
+    rounding only."""
     inp, geom = inputs(w, frames)
     dt = dtype_of(w)
     rv_ref, X_ref, _ = oracle.closed_loop(
@@ -175,19 +184,28 @@ def test_closed_loop_free_running(w, frames):
         inp.bank, w.m, w.sigma2, w.rho, w.a_ar1, w.noise_std, w.seeds[2], frames,
         X0=inp.X0.astype(dt).astype(np.float64), batched=True)
     f = Letkf.from_workload(w, bank=inp.bank)
+    if strict:
+        f.set_jacobi(4e-6, 0.0)
     f.set_state(torch.from_numpy(inp.X0.astype(dt)).cuda())
     y = torch.from_numpy(inp.slopes.astype(dt)).cuda()
     truth = torch.from_numpy(inp.truth.astype(dt)).cuda()
     rv = f.run(frames, y, truth, use_graph=True)
     f.sync()
     rv = rv.cpu().numpy()
-    tol = 1e-3 if w.precision == 0 else 1e-8
-    assert np.max(np.abs(rv - rv_ref) / rv_ref) <= tol, np.max(np.abs(rv - rv_ref) / rv_ref)
+    dev = np.abs(rv - rv_ref) / rv_ref
     # piston (and other barely damped unobservable modes) drift apart by rounding;
     # compare the piston-removed estimates, as the criterion does
     X = f.get_state().cpu().numpy().astype(np.float64)
-    assert rel(depiston(X.mean(-1)), depiston(X_ref.mean(-1))) <= tol
+    fin = rel(depiston(X.mean(-1)), depiston(X_ref.mean(-1)))
     f.close()
+    if w.precision == 1:
+        assert dev.max() <= 1e-8 and fin <= 1e-8, (dev.max(), fin)
+    elif strict:
+        assert dev.max() <= 1e-3 and fin <= 1e-3, (dev.max(), fin)
+    else:
+        late = abs(rv[20:].mean() - rv_ref[20:].mean()) / rv_ref[20:].mean()
+        assert dev[:20].max() <= 1e-3, dev[:20].max()
+        assert dev.max() <= 2e-2 and late <= 5e-3 and fin <= 5e-3, (dev.max(), late, fin)
 
 
 def depiston(mean):
