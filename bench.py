@@ -488,7 +488,7 @@ def gpu_arm(args):
     ana_mean_s = statistics.mean(ana_ms) / 1e3
     achieved = flops / ana_mean_s / 1e12
     fallback = 1 if f.precision == 0 else 0
-    launches_per_frame = 2 + (2 + fallback) + 2   # residual 2, observe + tile (+ FP64 list), forecast + tick
+    launches_per_frame = 1 + (2 + fallback) + 1   # residual, observe + pair (+ FP64 list), forecast
     line = {
         "metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": Wm, "ms_per_step": agg["ms_per_step"], "higher_is_better": True,

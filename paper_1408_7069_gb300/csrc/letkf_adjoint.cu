@@ -683,7 +683,6 @@ cudaError_t forward_frame(letkf_ctx *h, const void *y_seq, const void *truth_seq
     e = cudaMemcpyAsync(bk, h->basis, (size_t)I.n_pts * I.mp * I.mp * sizeof(float),
                         cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess && forecast) e = lk_launch_forecast(h, nullptr);
-  if (e == cudaSuccess && forecast) e = lk_launch_tick(h);
   return e;
 }
 

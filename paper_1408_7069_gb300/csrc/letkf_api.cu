@@ -65,7 +65,7 @@ void release(letkf_ctx *h) {
   lk_adjoint_release(h);
   void *bufs[] = {h->X,          h->Ybp,      h->dp,       h->taper,    h->pid_map,
                   h->pts,        h->saps,     h->bank,     h->basis,    h->counters,
-                  h->worklist,   h->frame,    h->partial,  h->d_inst,   h->obs_items,
+                  h->worklist,   h->frame,    h->partial,  h->tickets,  h->d_inst,   h->obs_items,
                   h->node_items, h->tiles[0], h->tiles[1], h->tiles[2]};
   for (void *p : bufs)
     if (p) cudaFree(p);
@@ -320,6 +320,7 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   LK_TRY(dalloc(h, &h->worklist, 3 * h->n_pts_total * sizeof(int2)));
   LK_TRY(dalloc(h, &h->frame, 2 * sizeof(long long)));
   LK_TRY(dalloc(h, &h->partial, (size_t)n * LK_RES_BLOCKS * sizeof(double2)));
+  LK_TRY(dalloc(h, &h->tickets, (size_t)(n + 1) * sizeof(int)));
   LK_TRY(dalloc(h, &h->d_inst, (size_t)n * sizeof(LkInst)));
   LK_TRY(dalloc(h, &h->obs_items, h->sap_total * sizeof(int2)));
   LK_TRY(dalloc(h, &h->node_items, h->n_pts_total * sizeof(int2)));
@@ -382,6 +383,7 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   if (e == cudaSuccess) e = cudaMemset(h->dp, 0, n_dp * h->rsz);
   if (e == cudaSuccess) e = cudaMemset(h->counters, 0, 8 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->frame, 0, 2 * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemset(h->tickets, 0, (size_t)(n + 1) * sizeof(int));
   if (e != cudaSuccess) LK_TRY(cuda_fail(h, e, "cudaMemset"));
   for (int cls = 0; cls < 3; ++cls) LK_TRY(build_tiles(h, cls, pids));
   e = lk_setup_analysis(h);
@@ -399,7 +401,6 @@ letkf_status enqueue_frame(letkf_ctx *h, const void *y_seq, const void *truth_se
   LK_CUDA(h, lk_launch_obs(h, y_seq, ridx));
   LK_CUDA(h, lk_launch_analysis(h, nullptr, nullptr));
   LK_CUDA(h, lk_launch_forecast(h, nullptr));
-  LK_CUDA(h, lk_launch_tick(h));
   return LETKF_OK;
 }
 
@@ -486,7 +487,6 @@ letkf_status letkf_forecast(letkf_t h, const void *noise_dev) {
     return fail(h, LETKF_ERR_STATE, "no noise given and an instance has no noise bank");
   DeviceGuard dg(h->device);
   LK_CUDA(h, lk_launch_forecast(h, noise_dev));
-  LK_CUDA(h, lk_launch_tick(h));
   h->frame_host += 1;
   return LETKF_OK;
 }

@@ -96,6 +96,7 @@ struct letkf_ctx {
   int2 *worklist = nullptr;         // [n_pts_total] (inst, point) queued for FP64
   long long *frame = nullptr;       // [0] forecast counter, [1] frame index within letkf_run
   double2 *partial = nullptr;       // [n_inst][LK_RES_BLOCKS] residual partial sums
+  int *tickets = nullptr;           // [n_inst + 1] last-CTA counters: residual per instance, forecast
 
   // host copies
   std::vector<int32_t> pts_host, wslopes_host;
@@ -118,10 +119,10 @@ struct letkf_ctx {
 cudaError_t lk_launch_obs(letkf_ctx *h, const void *y, const long long *run_idx);
 cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread);
 cudaError_t lk_launch_analysis_class(letkf_ctx *h, int cls, void *mean, void *spread);
+// The forecast also advances the forecast counter and the run index (frame[0..1]).
 cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise);
 cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
                                const long long *run_idx);
-cudaError_t lk_launch_tick(letkf_ctx *h);
 cudaError_t lk_launch_basis_reset(letkf_ctx *h);   // warm-start eigenbases -> identity
 cudaError_t lk_setup_analysis(letkf_ctx *h);
 // FP32 analysis of width class cls, two columns per lane (letkf_pair.cu).

@@ -67,18 +67,10 @@ __global__ void __launch_bounds__(256) obs_kernel(const LkInst *__restrict__ ins
   }
 }
 
-// One warp per (instance, node), lane = member: phi_{k+1} = a phi_k + v,
-// phi_k -> row 1 (Section 2.2, A1 = [[a I, 0], [I, 0]]; Section 3.1.2, Eq. Mem_pre).
-// v is the caller's noise, or a bank screen chosen per member by SplitMix64.
 template <typename S>
-__global__ void __launch_bounds__(256) forecast_kernel(const LkInst *__restrict__ insts,
-                                                       const int2 *__restrict__ items,
-                                                       long long n_items, const S *__restrict__ noise,
-                                                       const long long *__restrict__ frame) {
-  const long long wi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wi >= n_items) return;
-  const int2 it = items[wi];
+__device__ __forceinline__ void forecast_node(const LkInst *__restrict__ insts, int2 it, int lane,
+                                              const S *__restrict__ noise,
+                                              const long long *__restrict__ frame) {
   const LkInst &I = insts[it.x];
   const int gpt = it.y, m = I.m;
   S *row0 = static_cast<S *>(I.X) + (size_t)gpt * 2 * m;
@@ -103,63 +95,95 @@ __global__ void __launch_bounds__(256) forecast_kernel(const LkInst *__restrict_
   }
 }
 
+// One warp per (instance, node), lane = member: phi_{k+1} = a phi_k + v,
+// phi_k -> row 1 (Section 2.2, A1 = [[a I, 0], [I, 0]]; Section 3.1.2, Eq. Mem_pre).
+// v is the caller's noise, or a bank screen chosen per member by SplitMix64.
+template <typename S>
+__global__ void __launch_bounds__(256) forecast_kernel(const LkInst *__restrict__ insts,
+                                                       const int2 *__restrict__ items,
+                                                       long long n_items, const S *__restrict__ noise,
+                                                       long long *__restrict__ frame,
+                                                       int *__restrict__ ticket) {
+  const long long wi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wi < n_items) forecast_node<S>(insts, items[wi], lane, noise, frame);
+  // the last CTA to finish advances the forecast counter and the run index
+  // (every CTA has read the counter by then)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ticket, 1) == (int)gridDim.x - 1) {
+      frame[0] += 1;
+      frame[1] += 1;
+      *ticket = 0;
+    }
+  }
+}
+
 // Spatial variance of truth - mean(row 0) over one instance's nodes, piston
 // removed (Section 2.1, Eq. Crit_Opt; Section 5). Grid (LK_RES_BLOCKS, n_inst):
-// warp per node, FP64 partial sums per CTA; a second kernel adds the partials
-// of each instance in a fixed order.
+// thread per node, FP64 partial sums per CTA; the last CTA of an instance to
+// finish (ticket counter, reset by it) adds the partials in a fixed order.
 template <typename S>
-__global__ void __launch_bounds__(256) residual_partial_kernel(const LkInst *__restrict__ insts,
-                                                               long long n_pts_total,
-                                                               const S *__restrict__ truth,
-                                                               const long long *__restrict__ run_idx,
-                                                               double2 *__restrict__ partial) {
+__global__ void __launch_bounds__(256) residual_kernel(const LkInst *__restrict__ insts,
+                                                       long long n_pts_total,
+                                                       const S *__restrict__ truth,
+                                                       const long long *__restrict__ run_idx,
+                                                       double2 *__restrict__ partial,
+                                                       int *__restrict__ tickets, int n_inst,
+                                                       double *__restrict__ resvar) {
   const LkInst &I = insts[blockIdx.y];
   const long long k = run_idx ? *run_idx : 0;
-  truth += k * n_pts_total + I.node_off;
+  const S *tr = truth + k * n_pts_total + I.node_off;
   const S *X = static_cast<const S *>(I.X);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5, m = I.m;
+  const int m = I.m;
   double s1 = 0.0, s2 = 0.0;
-  for (int gpt = blockIdx.x * nw + wid; gpt < I.n_pts; gpt += gridDim.x * nw) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < I.n_pts; g += gridDim.x * blockDim.x) {
+    const S *row = X + (size_t)g * 2 * m;
     double x = 0.0;
-    for (int i = lane; i < m; i += 32) x += (double)X[(size_t)gpt * 2 * m + i];
-    const double r = (double)truth[gpt] - lk_warp_sum(x) / m;
+    for (int i = 0; i < m; ++i) x += (double)row[i];
+    const double r = (double)tr[g] - x / m;
     s1 += r;
     s2 += r * r;
   }
-  __shared__ double sh1[32], sh2[32];
+  s1 = lk_warp_sum(s1);
+  s2 = lk_warp_sum(s2);
+  __shared__ double sh1[8], sh2[8];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     sh1[wid] = s1;
     sh2[wid] = s2;
   }
   __syncthreads();
+  double2 *pp = partial + (size_t)blockIdx.y * gridDim.x;
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
-    for (int i = 0; i < nw; ++i) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
       a += sh1[i];
       b += sh2[i];
     }
-    partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = make_double2(a, b);
+    pp[blockIdx.x] = make_double2(a, b);
+    __threadfence();
+    last = atomicAdd(&tickets[blockIdx.y], 1) == (int)gridDim.x - 1;
   }
-}
-
-__global__ void residual_final_kernel(const LkInst *__restrict__ insts,
-                                      const double2 *__restrict__ partial, int nparts, int n_inst,
-                                      const long long *__restrict__ run_idx,
-                                      double *__restrict__ resvar) {
-  const int inst = blockIdx.x;
-  const long long k = run_idx ? *run_idx : 0;
-  double s1 = 0.0, s2 = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += 32) {
-    s1 += partial[(size_t)inst * nparts + i].x;
-    s2 += partial[(size_t)inst * nparts + i].y;
-  }
-  s1 = lk_warp_sum(s1);
-  s2 = lk_warp_sum(s2);
-  if (threadIdx.x == 0) {
-    const double n = insts[inst].n_pts;
-    const double mu = s1 / n;
-    resvar[k * n_inst + inst] = s2 / n - mu * mu;
+  __syncthreads();
+  if (last && threadIdx.x < 32) {
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) {
+      const double2 v = __ldcg(pp + i);
+      a += v.x;
+      b += v.y;
+    }
+    a = lk_warp_sum(a);
+    b = lk_warp_sum(b);
+    if (threadIdx.x == 0) {
+      const double n = I.n_pts;
+      const double mu = a / n;
+      resvar[k * n_inst + blockIdx.y] = b / n - mu * mu;
+      tickets[blockIdx.y] = 0;
+    }
   }
 }
 
@@ -174,10 +198,6 @@ __global__ void basis_reset_kernel(const LkInst *__restrict__ insts) {
   }
 }
 
-__global__ void tick_kernel(long long *frame) {
-  frame[0] += 1;
-  frame[1] += 1;
-}
 
 int warp_blocks(long long warps) { return (int)((warps * 32 + 255) / 256); }
 
@@ -199,13 +219,14 @@ cudaError_t lk_launch_obs(letkf_ctx *h, const void *y, const long long *run_idx)
 
 cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise) {
   const int blocks = warp_blocks(h->n_pts_total);
+  int *ticket = h->tickets + h->n_inst;
   if (h->precision == 1)
     forecast_kernel<double><<<blocks, 256, 0, h->stream>>>(h->d_inst, h->node_items,
                                                            h->n_pts_total, (const double *)noise,
-                                                           h->frame);
+                                                           h->frame, ticket);
   else
     forecast_kernel<float><<<blocks, 256, 0, h->stream>>>(h->d_inst, h->node_items, h->n_pts_total,
-                                                          (const float *)noise, h->frame);
+                                                          (const float *)noise, h->frame, ticket);
   return cudaGetLastError();
 }
 
@@ -213,15 +234,13 @@ cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
                                const long long *run_idx) {
   const dim3 grid(LK_RES_BLOCKS, h->n_inst);
   if (h->precision == 1)
-    residual_partial_kernel<double><<<grid, 256, 0, h->stream>>>(
-        h->d_inst, h->n_pts_total, (const double *)truth, run_idx, h->partial);
+    residual_kernel<double><<<grid, 256, 0, h->stream>>>(h->d_inst, h->n_pts_total,
+                                                         (const double *)truth, run_idx, h->partial,
+                                                         h->tickets, h->n_inst, resvar);
   else
-    residual_partial_kernel<float><<<grid, 256, 0, h->stream>>>(
-        h->d_inst, h->n_pts_total, (const float *)truth, run_idx, h->partial);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  residual_final_kernel<<<h->n_inst, 32, 0, h->stream>>>(h->d_inst, h->partial, LK_RES_BLOCKS,
-                                                         h->n_inst, run_idx, resvar);
+    residual_kernel<float><<<grid, 256, 0, h->stream>>>(h->d_inst, h->n_pts_total,
+                                                        (const float *)truth, run_idx, h->partial,
+                                                        h->tickets, h->n_inst, resvar);
   return cudaGetLastError();
 }
 
@@ -230,7 +249,3 @@ cudaError_t lk_launch_basis_reset(letkf_ctx *h) {
   return cudaGetLastError();
 }
 
-cudaError_t lk_launch_tick(letkf_ctx *h) {
-  tick_kernel<<<1, 1, 0, h->stream>>>(h->frame);
-  return cudaGetLastError();
-}
