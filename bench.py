@@ -458,27 +458,24 @@ def gpu_arm(args):
     L.letkf_sync(h)
     graph_fps = K / (g0.elapsed_time(g1) / 1e3)
 
-    # end to end through the public API with host buffers (pinned), one frame at a time
+    # end to end through the public API with host buffers: one letkf_step per
+    # frame (inputs copied in from host memory, analysis mean and residual
+    # copied out, synchronised), as a real-time controller calls it
     f.set_state(X0)
-    y_h = torch.from_numpy(inp.slopes.astype(np.float32)).pin_memory()
-    t_h = torch.from_numpy(inp.truth.astype(np.float32)).pin_memory()
-    y_d = torch.zeros(f.p, device="cuda")
-    t_d = torch.zeros(f.n_pts, device="cuda")
-    out_h = torch.zeros(K, f.n_pts, 2).pin_memory()
-    rv_h = torch.zeros(K, dtype=torch.float64).pin_memory()
+    y_np = np.ascontiguousarray(inp.slopes.astype(np.float32))
+    t_np = np.ascontiguousarray(inp.truth.astype(np.float32))
+    mean_h = np.empty((f.n_pts, 2), np.float32)
+    rv_h = np.empty(1, np.float64)
+    f.step(y_np[0], t_np[0], mean_h, rv_h)            # capture the frame graph
+    f.set_state(X0)
+    f.set_frame(0)
     torch.cuda.synchronize()
+    for k in range(Wm):
+        f.step(y_np[k], t_np[k], mean_h, rv_h)
     te0 = time.perf_counter()
-    with torch.cuda.stream(s):
-        for i in range(K):
-            k = Wm + i
-            y_d.copy_(y_h[k], non_blocking=True)
-            t_d.copy_(t_h[k], non_blocking=True)
-            L.letkf_residual(h, t_d, resvar[k:k + 1])
-            L.letkf_analyze(h, y_d, mean, spread)
-            L.letkf_forecast(h)
-            out_h[i].copy_(mean, non_blocking=True)
-            rv_h[i:i + 1].copy_(resvar[k:k + 1], non_blocking=True)
-            s.synchronize()
+    for i in range(K):
+        k = Wm + i
+        f.step(y_np[k], t_np[k], mean_h, rv_h)
     te = time.perf_counter() - te0
     L.letkf_sync(h)
     e2e_fps = K / te if world == 1 else combine(te, K, world, reduce_max)["value"]

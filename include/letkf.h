@@ -180,6 +180,18 @@ letkf_status letkf_set_jacobi(letkf_t h, double rotate_tol, double stop_cos);
  * Synchronises. */
 letkf_status letkf_set_frame(letkf_t h, int64_t frame);
 
+/* One closed-loop frame from host memory, for a real-time controller: copies
+ * y_host [p] (real) and, if not NULL, truth_host [n_pts] into pinned staging
+ * buffers the handle owns, runs the frame as letkf_run does (residual of the
+ * current prediction against truth, analysis of y, forecast with bank noise),
+ * waits for it, and copies the analysis mean [n_pts][2] (real) into mean_host
+ * and the residual variance (one double per instance) into resvar_host (either
+ * may be NULL; resvar_host only with truth_host). The frame runs as one CUDA
+ * graph (captured on the first call, per with/without truth) on a non-default
+ * stream. Requires a noise bank for every instance. Synchronises. */
+letkf_status letkf_step(letkf_t h, const void *y_host, const void *truth_host, void *mean_host,
+                        double *resvar_host);
+
 /* Reverse mode of the closed loop. J = mean over `frames` frames of the
  * residual variance of the prediction (Section 2.1 Eq. Crit_Opt, as in
  * letkf_residual), each frame run as in letkf_run (residual of the current

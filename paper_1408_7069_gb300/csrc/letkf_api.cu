@@ -60,9 +60,22 @@ letkf_status upload(letkf_ctx *h, void *dst, const void *src, size_t bytes) {
   return e == cudaSuccess ? LETKF_OK : cuda_fail(h, e, "cudaMemcpy");
 }
 
-void release(letkf_ctx *h) {
+// Drops every captured graph of the handle (they hold kernel arguments and
+// tile lists that a call is about to change).
+void drop_graphs(letkf_ctx *h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  for (cudaGraphExec_t &g : h->step_graph) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
   lk_adjoint_release(h);
+}
+
+void release(letkf_ctx *h) {
+  drop_graphs(h);
+  if (h->step_pin) cudaFreeHost(h->step_pin);
+  if (h->step_dev) cudaFree(h->step_dev);
   void *bufs[] = {h->X,          h->Ybp,      h->dp,       h->taper,    h->pid_map,
                   h->pts,        h->saps,     h->bank,     h->basis,    h->counters,
                   h->worklist,   h->frame,    h->partial,  h->tickets,  h->d_inst,   h->obs_items,
@@ -202,11 +215,7 @@ letkf_status build_tiles(letkf_ctx *h, int cls, const std::vector<std::vector<in
   letkf_status st = dalloc(h, &h->tiles[cls], tl.size() * sizeof(LkTile));
   if (st != LETKF_OK) return st;
   h->n_tiles[cls] = (int)tl.size();
-  if (h->graph) {
-    cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
-  }
-  lk_adjoint_release(h);   // its graph holds the old tile list
+  drop_graphs(h);          // they hold the old tile list
   return upload(h, h->tiles[cls], tl.data(), tl.size() * sizeof(LkTile));
 }
 
@@ -404,6 +413,30 @@ letkf_status enqueue_frame(letkf_ctx *h, const void *y_seq, const void *truth_se
   return LETKF_OK;
 }
 
+// One frame from the step staging buffers: upload, (residual), observation,
+// analysis (mean into staging), forecast, download.
+letkf_status enqueue_step(letkf_ctx *h, bool with_truth) {
+  unsigned char *yd = h->step_dev + h->step_off[0], *td = h->step_dev + h->step_off[1];
+  unsigned char *md = h->step_dev + h->step_off[2], *rd = h->step_dev + h->step_off[3];
+  unsigned char *yp = h->step_pin + h->step_off[0], *tp = h->step_pin + h->step_off[1];
+  unsigned char *mp = h->step_pin + h->step_off[2], *rp = h->step_pin + h->step_off[3];
+  LK_CUDA(h, cudaMemcpyAsync(yd, yp, h->p_total * h->rsz, cudaMemcpyHostToDevice, h->stream));
+  if (with_truth) {
+    LK_CUDA(h, cudaMemcpyAsync(td, tp, h->n_pts_total * h->rsz, cudaMemcpyHostToDevice,
+                               h->stream));
+    LK_CUDA(h, lk_launch_residual(h, td, reinterpret_cast<double *>(rd), nullptr));
+  }
+  LK_CUDA(h, lk_launch_obs(h, yd, nullptr));
+  LK_CUDA(h, lk_launch_analysis(h, md, nullptr));
+  LK_CUDA(h, lk_launch_forecast(h, nullptr));
+  LK_CUDA(h, cudaMemcpyAsync(mp, md, 2 * h->n_pts_total * h->rsz, cudaMemcpyDeviceToHost,
+                             h->stream));
+  if (with_truth)
+    LK_CUDA(h, cudaMemcpyAsync(rp, rd, h->n_inst * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+  return LETKF_OK;
+}
+
 bool all_have_banks(const letkf_ctx *h) {
   for (const LkInst &I : h->inst)
     if (!I.bank) return false;
@@ -573,7 +606,7 @@ letkf_status letkf_set_params(letkf_t h, int32_t i, double rho, double sigma2, d
   taper_table(c, tap);
   letkf_status st = upload_taper(h, I, tap);
   if (st == LETKF_OK) st = upload(h, h->d_inst + i, &I, sizeof(LkInst));
-  lk_adjoint_release(h);   // its graph holds rho and sigma2 as kernel arguments
+  drop_graphs(h);          // the reverse mode's graph holds rho and sigma2 as kernel arguments
   return st;
 }
 
@@ -585,11 +618,7 @@ letkf_status letkf_set_jacobi(letkf_t h, double rotate_tol, double stop_cos) {
   LK_CUDA(h, cudaStreamSynchronize(h->stream));
   h->tol32 = rotate_tol;
   h->stop32 = stop_cos > rotate_tol ? stop_cos : rotate_tol;
-  if (h->graph) {                    // the captured frame holds the old values
-    cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
-  }
-  lk_adjoint_release(h);
+  drop_graphs(h);                    // captured launches hold the old values
   return LETKF_OK;
 }
 
@@ -601,6 +630,62 @@ letkf_status letkf_set_frame(letkf_t h, int64_t frame) {
   const long long f = frame;
   LK_CUDA(h, cudaMemcpy(h->frame, &f, sizeof(long long), cudaMemcpyHostToDevice));
   h->frame_host = frame;
+  return LETKF_OK;
+}
+
+letkf_status letkf_step(letkf_t h, const void *y_host, const void *truth_host, void *mean_host,
+                        double *resvar_host) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (!y_host) return fail(h, LETKF_ERR_ARG, "y_host is NULL");
+  if (!all_have_banks(h))
+    return fail(h, LETKF_ERR_STATE, "letkf_step needs a noise bank for every instance");
+  DeviceGuard dg(h->device);
+  if (!h->step_pin) {
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    h->step_off[0] = 0;
+    h->step_off[1] = al(h->p_total * h->rsz);
+    h->step_off[2] = h->step_off[1] + al(h->n_pts_total * h->rsz);
+    h->step_off[3] = h->step_off[2] + al(2 * h->n_pts_total * h->rsz);
+    const size_t total = h->step_off[3] + al(h->n_inst * sizeof(double));
+    LK_CUDA(h, cudaMallocHost((void **)&h->step_pin, total));
+    cudaError_t e = cudaMalloc((void **)&h->step_dev, total);
+    if (e != cudaSuccess) {
+      cudaFreeHost(h->step_pin);
+      h->step_pin = nullptr;
+      return fail(h, LETKF_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+  }
+  const bool wt = truth_host != nullptr;
+  LK_CUDA(h, cudaStreamSynchronize(h->stream));    // staging is free again
+  memcpy(h->step_pin + h->step_off[0], y_host, h->p_total * h->rsz);
+  if (wt) memcpy(h->step_pin + h->step_off[1], truth_host, h->n_pts_total * h->rsz);
+  if (h->stream) {
+    cudaGraphExec_t &g = h->step_graph[wt ? 1 : 0];
+    if (!g) {
+      LK_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      letkf_status st = enqueue_step(h, wt);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+      if (st != LETKF_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&g, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    LK_CUDA(h, cudaGraphLaunch(g, h->stream));
+  } else {
+    letkf_status st = enqueue_step(h, wt);
+    if (st != LETKF_OK) return st;
+  }
+  LK_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->frame_host += 1;
+  if (mean_host)
+    memcpy(mean_host, h->step_pin + h->step_off[2], 2 * h->n_pts_total * h->rsz);
+  if (wt && resvar_host)
+    memcpy(resvar_host, h->step_pin + h->step_off[3], h->n_inst * sizeof(double));
   return LETKF_OK;
 }
 

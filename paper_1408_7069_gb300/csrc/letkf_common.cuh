@@ -109,6 +109,12 @@ struct letkf_ctx {
 
   LkAdjWork *adj = nullptr;         // letkf_grad buffers and graph, built on first use
 
+  // letkf_step: pinned staging and device copies of one frame's inputs and
+  // outputs (y, truth, mean, resvar), and its graphs without / with truth
+  unsigned char *step_pin = nullptr, *step_dev = nullptr;
+  size_t step_off[4] = {0, 0, 0, 0};
+  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+
   std::string err;
 };
 

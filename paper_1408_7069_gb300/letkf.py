@@ -62,6 +62,7 @@ _SIGS = {
     "letkf_set_params": [c_void_p, c_int32, c_double, c_double, c_double],
     "letkf_set_frame": [c_void_p, ctypes.c_int64],
     "letkf_set_jacobi": [c_void_p, c_double, c_double],
+    "letkf_step": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p],
     "letkf_grad": [c_void_p, c_int32, c_void_p, c_void_p, c_int32, POINTER(c_double),
                    POINTER(c_double)],
 }
@@ -203,6 +204,13 @@ def letkf_run(h, frames: int, y_seq, truth_seq=None, resvar=None, use_graph: boo
 
 def letkf_set_params(h, i: int, rho: float, sigma2: float, loc_len: float) -> None:
     _check(lib().letkf_set_params(h, int(i), float(rho), float(sigma2), float(loc_len)), h)
+
+
+def letkf_step(h, y_host, truth_host=None, mean_host=None, resvar_host=None) -> None:
+    """One frame from host (numpy) buffers; see include/letkf.h."""
+    ptr = lambda a: None if a is None else a.ctypes.data  # noqa: E731
+    _check(lib().letkf_step(h, ptr(y_host), ptr(truth_host), ptr(mean_host), ptr(resvar_host)),
+           h)
 
 
 def letkf_set_jacobi(h, rotate_tol: float = 4e-6, stop_cos: float = 1e-3) -> None:
@@ -415,6 +423,27 @@ class Letkf:
 
     def set_params(self, rho: float, sigma2: float, loc_len: float, instance: int = 0):
         letkf_set_params(self.h, instance, rho, sigma2, loc_len)
+
+    def step(self, y, truth=None, mean=None, resvar=None):
+        """One closed-loop frame from host memory (numpy arrays of the handle's
+        real type): returns the analysis mean [n_pts, 2] and, with truth, the
+        residual variance per instance."""
+        rt = np.float32 if self.precision == 0 else np.float64
+
+        def host(a, n):
+            if a is None:
+                return None
+            if not (isinstance(a, np.ndarray) and a.dtype == rt and a.flags.c_contiguous
+                    and a.size == n):
+                raise ValueError(f"expected a contiguous {np.dtype(rt).name} array of {n} values")
+            return a
+        y = host(y, self.p)
+        truth = host(truth, self.n_pts)
+        mean = host(mean, 2 * self.n_pts) if mean is not None else np.empty((self.n_pts, 2), rt)
+        if truth is not None and resvar is None:
+            resvar = np.empty(self.n_inst, np.float64)
+        letkf_step(self.h, y, truth, mean, resvar)
+        return mean, resvar
 
     def set_jacobi(self, rotate_tol: float = 4e-6, stop_cos: float = 1e-3):
         """FP32 eigensolve stopping rule; stop_cos <= rotate_tol: stop after a

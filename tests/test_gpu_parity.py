@@ -300,3 +300,33 @@ def test_nonfinite_slopes_are_reported_and_handle_survives():
     f.analyze(torch.from_numpy(inp.slopes[0].astype(np.float32)).cuda())
     f.sync()
     f.close()
+
+
+def test_step_from_host_buffers_equals_run():
+    """letkf_step (host buffers, one graph per frame) runs the same frames as
+    letkf_run: same residuals, same final ensemble, and the returned analysis
+    mean of row 0 is the member mean of the forecast's row 1."""
+    w, frames = W.TEL_16M, 6
+    inp, _ = inputs(w, frames)
+    y = inp.slopes[:frames].astype(np.float32)
+    t = inp.truth[:frames].astype(np.float32)
+    a = Letkf.from_workload(w, bank=inp.bank)
+    a.set_state(torch.from_numpy(inp.X0.astype(np.float32)).cuda())
+    rv = a.run(frames, torch.from_numpy(y).cuda(), torch.from_numpy(t).cuda(), use_graph=True)
+    a.sync()
+    Xa = a.get_state().cpu().numpy()
+    b = Letkf.from_workload(w, bank=inp.bank)
+    b.set_state(torch.from_numpy(inp.X0.astype(np.float32)).cuda())
+    rvs = []
+    for k in range(frames):
+        mean, r = b.step(np.ascontiguousarray(y[k]), np.ascontiguousarray(t[k]))
+        rvs.append(r[0])
+        Xk = b.get_state().cpu().numpy()
+        assert np.allclose(mean[:, 0], Xk[:, 1, :].mean(-1), rtol=1e-5, atol=1e-6)
+    b.sync()
+    assert np.array_equal(np.array(rvs), rv.cpu().numpy())
+    assert np.array_equal(b.get_state().cpu().numpy(), Xa)
+    with pytest.raises(ValueError):
+        b.step(y[0].astype(np.float64))
+    a.close()
+    b.close()
