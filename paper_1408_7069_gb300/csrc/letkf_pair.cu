@@ -77,17 +77,20 @@ __device__ __forceinline__ float group_sum(float v) {
   return v;
 }
 
+// Dot product of two MP-element columns with eight independent packed chains.
 template <int K2>
 __device__ __forceinline__ float dotk(const float2 (&a)[K2], const float2 (&b)[K2]) {
-  float2 s0 = f2(0.f), s1 = f2(0.f), s2 = f2(0.f), s3 = f2(0.f);
+  constexpr int NC = K2 >= 8 ? 8 : K2;
+  float2 s[NC];
 #pragma unroll
-  for (int k = 0; k < K2; k += 4) {
-    s0 = fma2(a[k], b[k], s0);
-    s1 = fma2(a[k + 1], b[k + 1], s1);
-    s2 = fma2(a[k + 2], b[k + 2], s2);
-    s3 = fma2(a[k + 3], b[k + 3], s3);
-  }
-  return ((s0.x + s0.y) + (s1.x + s1.y)) + ((s2.x + s2.y) + (s3.x + s3.y));
+  for (int c = 0; c < NC; ++c) s[c] = mul2(a[c], b[c]);
+#pragma unroll
+  for (int k = NC; k < K2; ++k) s[k % NC] = fma2(a[k], b[k], s[k % NC]);
+#pragma unroll
+  for (int w = NC / 2; w > 0; w >>= 1)
+#pragma unroll
+    for (int c = 0; c < w; ++c) s[c] = make_float2(s[c].x + s[c + w].x, s[c].y + s[c + w].y);
+  return s[0].x + s[0].y;
 }
 
 // One round on this lane's pair (P, Q) with tracked squared norms. `idle`:
@@ -102,7 +105,8 @@ __device__ __forceinline__ int pair_round(float2 (&P)[K2], float2 (&Q)[K2], floa
   const float x = nQ - nP, y = 2.f * dot;
   const float h2 = fmaf(x, x, y * y);
   const float h = h2 * rsqrtf(fmaxf(h2, 1e-37f));
-  const float t = (x >= 0.f ? y : -y) / (fabsf(x) + h);
+  // (a fast divide: c and s both follow from t, so the rotation stays orthogonal)
+  const float t = __fdividef(x >= 0.f ? y : -y, fabsf(x) + h);
   const float cr = rsqrtf(fmaf(t, t, 1.f));
   const float dd = dot * dot, nn = nP * nQ;
   const bool rot = !frozen && !idle && dd > tol2 * nn;
@@ -206,8 +210,16 @@ __device__ __forceinline__ void stage_pair_tile(const LkInst &I, int i0, int j0,
 // One CTA per tile of TI x TJ nodes of one instance; the nodes of the tile are
 // taken in row-major order, NPW per warp. `queue`: FP64 worklist counter slot
 // (MP <= 32), NULL for no fallback.
+// Threads per CTA, and CTAs per SM to budget registers for: 128 per thread
+// for MP <= 32 (16 warps per SM), whatever the wide problems need otherwise.
 template <int MP, int TI, int TJ>
-__global__ void __launch_bounds__(TI *TJ * 32 / PairCfg<MP>::NPW)
+struct PairLaunch {
+  static constexpr int threads = TI * TJ * 32 / PairCfg<MP>::NPW;
+  static constexpr int min_ctas = MP <= 32 ? 65536 / (threads * 128) : 1;
+};
+
+template <int MP, int TI, int TJ>
+__global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP, TI, TJ>::min_ctas)
     analysis_pair_kernel(const LkInst *__restrict__ insts, const LkTile *__restrict__ tiles,
                          float *__restrict__ mean, float *__restrict__ spread, float tol,
                          float stop, int max_sweeps, float kappa_thr, int *__restrict__ counters,
@@ -319,7 +331,7 @@ __global__ void __launch_bounds__(TI *TJ * 32 / PairCfg<MP>::NPW)
     int rotated = 0;
     const bool frz = conv || !live;
     const int su = frz ? lane : up, sd = frz ? lane : dn;
-#pragma unroll 1
+#pragma unroll 2
     for (int r = 0; r < MP / 2; ++r) {
       rotated |= pair_round<K2>(P, Q, nP, nQ, tol2, stop2, false, frz);
       shfl_cols<K2>(Q, su);
