@@ -100,14 +100,17 @@ template <int K2>
 __device__ __forceinline__ int pair_round(float2 (&P)[K2], float2 (&Q)[K2], float &nP, float &nQ,
                                           float tol2, float stop2, bool idle, bool frozen) {
   const float dot = dotk<K2>(P, Q);
-  // tan(theta) of the rotation that makes the pair orthogonal, with
-  // x = |q|^2 - |p|^2, y = 2 p.q: t = sign(x) y / (|x| + sqrt(x^2 + y^2)), |theta| <= pi/4
+  // The rotation that makes the pair orthogonal, |theta| <= pi/4, from
+  // x = |q|^2 - |p|^2, y = 2 p.q and h = sqrt(x^2 + y^2): cos 2theta = |x|/h,
+  // sin 2theta = sign(x) y / h, c = sqrt((1 + cos 2theta)/2) >= 1/sqrt(2),
+  // s = sin 2theta / (2c), t = s / c. Two reciprocal square roots, no divide.
   const float x = nQ - nP, y = 2.f * dot;
-  const float h2 = fmaf(x, x, y * y);
-  const float h = h2 * rsqrtf(fmaxf(h2, 1e-37f));
-  // (a fast divide: c and s both follow from t, so the rotation stays orthogonal)
-  const float t = __fdividef(x >= 0.f ? y : -y, fabsf(x) + h);
-  const float cr = rsqrtf(fmaf(t, t, 1.f));
+  const float rh = rsqrtf(fmaxf(fmaf(x, x, y * y), 1e-37f));
+  const float c2 = fmaf(0.5f * fabsf(x), rh, 0.5f);
+  const float rc = rsqrtf(c2);
+  const float cr = c2 * rc;
+  const float sr = (x >= 0.f ? y : -y) * (0.5f * rh) * rc;
+  const float t = sr * rc;
   const float dd = dot * dot, nn = nP * nQ;
   const bool rot = !frozen && !idle && dd > tol2 * nn;
   const bool swp = idle && !frozen;
@@ -116,7 +119,7 @@ __device__ __forceinline__ int pair_round(float2 (&P)[K2], float2 (&Q)[K2], floa
   // element pair but its swap leaks rounding of the larger column into the
   // smaller one, which stalls convergence when their norms differ by kappa.
   const float c = rot ? cr : (swp ? 0.f : 1.f);
-  const float s = rot ? cr * t : (swp ? 1.f : 0.f);
+  const float s = rot ? sr : (swp ? 1.f : 0.f);
   const float nP2 = rot ? fmaf(-t, dot, nP) : (swp ? nQ : nP);
   const float nQ2 = rot ? fmaf(t, dot, nQ) : (swp ? nP : nQ);
   const float2 cc = f2(c), ms = f2(-s), ps = f2(s);

