@@ -1,6 +1,8 @@
 // Per-frame kernels around the analysis, over every instance of a handle:
 // observation of the background ensemble (means, slope anomalies,
 // innovations), the AR(1) forecast, the residual criterion and the frame counter.
+#include <stdint.h>
+
 #include "letkf_common.cuh"
 
 namespace {
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(256) forecast_kernel(const LkInst *__restrict_
 // thread per node, FP64 partial sums per CTA; the last CTA of an instance to
 // finish (ticket counter, reset by it) adds the partials in a fixed order.
 template <typename S>
-__global__ void __launch_bounds__(256) residual_kernel(const LkInst *__restrict__ insts,
+__global__ void __launch_bounds__(64) residual_kernel(const LkInst *__restrict__ insts,
                                                        long long n_pts_total,
                                                        const S *__restrict__ truth,
                                                        const long long *__restrict__ run_idx,
@@ -137,18 +139,32 @@ __global__ void __launch_bounds__(256) residual_kernel(const LkInst *__restrict_
   const S *tr = truth + k * n_pts_total + I.node_off;
   const S *X = static_cast<const S *>(I.X);
   const int m = I.m;
+  const double inv_m = 1.0 / m;
+  const bool vec = sizeof(S) == 4 && (m & 3) == 0 &&
+                   (reinterpret_cast<uintptr_t>(X) & 15) == 0;
   double s1 = 0.0, s2 = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < I.n_pts; g += gridDim.x * blockDim.x) {
     const S *row = X + (size_t)g * 2 * m;
     double x = 0.0;
-    for (int i = 0; i < m; ++i) x += (double)row[i];
-    const double r = (double)tr[g] - x / m;
+    if (vec) {
+      const float4 *r4 = reinterpret_cast<const float4 *>(row);
+      double a = 0.0, b = 0.0;
+      for (int i = 0; i < m / 4; ++i) {
+        const float4 v = r4[i];
+        a += (double)v.x + (double)v.y;
+        b += (double)v.z + (double)v.w;
+      }
+      x = a + b;
+    } else {
+      for (int i = 0; i < m; ++i) x += (double)row[i];
+    }
+    const double r = (double)tr[g] - x * inv_m;
     s1 += r;
     s2 += r * r;
   }
   s1 = lk_warp_sum(s1);
   s2 = lk_warp_sum(s2);
-  __shared__ double sh1[8], sh2[8];
+  __shared__ double sh1[2], sh2[2];
   __shared__ int last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
@@ -234,11 +250,11 @@ cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
                                const long long *run_idx) {
   const dim3 grid(LK_RES_BLOCKS, h->n_inst);
   if (h->precision == 1)
-    residual_kernel<double><<<grid, 256, 0, h->stream>>>(h->d_inst, h->n_pts_total,
+    residual_kernel<double><<<grid, 64, 0, h->stream>>>(h->d_inst, h->n_pts_total,
                                                          (const double *)truth, run_idx, h->partial,
                                                          h->tickets, h->n_inst, resvar);
   else
-    residual_kernel<float><<<grid, 256, 0, h->stream>>>(h->d_inst, h->n_pts_total,
+    residual_kernel<float><<<grid, 64, 0, h->stream>>>(h->d_inst, h->n_pts_total,
                                                         (const float *)truth, run_idx, h->partial,
                                                         h->tickets, h->n_inst, resvar);
   return cudaGetLastError();
