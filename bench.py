@@ -43,6 +43,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 48-instance batched measurement")
     ap.add_argument("--batched-steps", type=int, default=100)
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the 8x8 FP64 and 16 m FP32 measurements")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the reverse-mode (letkf_grad) measurement")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
@@ -188,6 +190,56 @@ def batched_arm(torch, L, K, Wm):
            "l2": "working set above L2 (ensembles, anomalies and eigenbases of 48 instances)",
            "launch": "one CUDA-graph replay per frame covering all 48 instances"}
     f.close()
+    return out
+
+
+# --------------------------------------------------------------------------- smaller configs
+def small_configs_arm(torch, L, K: int = 500, Wm: int = 20):
+    """The 8x8 FP64 system and the 16 m FP32 system: per-frame CUDA events
+    (launches as in the main measurement, L2 not flushed: both fit in L2) and
+    one CUDA-graph replay per frame. Returns the 'configs' object of the JSON line."""
+    import numpy as np
+    from paper_1408_7069_gb300 import synth, workloads as W
+    out = {}
+    for w in (W.TOY_8X8, W.TEL_16M):
+        rt = np.float32 if w.precision == 0 else np.float64
+        inp = synth.make_loop_inputs(w, frames=Wm + K + 1)
+        f = L.Letkf.from_workload(w, bank=inp.bank)
+        X0 = torch.from_numpy(inp.X0.astype(rt)).cuda()
+        y = torch.from_numpy(inp.slopes.astype(rt)).cuda()
+        t = torch.from_numpy(inp.truth.astype(rt)).cuda()
+        rv = torch.zeros(Wm + K + 1, dtype=torch.float64, device="cuda")
+        h, s = f.h, f.stream
+        f.set_state(X0)
+        f.run(Wm, y, t, use_graph=False)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            for i in range(K):
+                k = Wm + i
+                ev[i][0].record(s)
+                L.letkf_residual(h, t[k], rv[k:k + 1])
+                L.letkf_analyze(h, y[k], None, None)
+                L.letkf_forecast(h)
+                ev[i][1].record(s)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        f.set_state(X0)
+        L.letkf_run(h, Wm, y, t, rv, True)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        g0.record(s)
+        L.letkf_run(h, K, y, t, rv, True)
+        g1.record(s)
+        torch.cuda.synchronize()
+        f.sync()
+        out[w.name] = {"n_pts": int(f.n_pts), "m": w.m, "window": w.window,
+                       "dtype": "f32" if w.precision == 0 else "f64",
+                       "frames_per_s": K / (sum(ms) / 1e3), "p50_us": 1e3 * percentile(ms, 50),
+                       "p99_us": 1e3 * percentile(ms, 99),
+                       "graph_frames_per_s": K / (g0.elapsed_time(g1) / 1e3)}
+        f.close()
     return out
 
 
@@ -513,6 +565,8 @@ def gpu_arm(args):
     }
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_arm(torch, L, args.batched_steps, Wm)
+    if rank == 0 and not args.no_small:
+        line["configs"] = small_configs_arm(torch, L)
     if rank == 0 and not args.no_adjoint:
         line["adjoint"] = adjoint_arm(torch, L)
     if rank == 0:

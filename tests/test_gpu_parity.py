@@ -84,8 +84,10 @@ def test_analysis_teacher_forced(w, k):
 
 def test_fp64_fallback_matches_oracle_and_counts_points():
     """Prior-draw background (kappa ~ 1e4): with every node routed to the FP64
-    eigensolve the FP32 tolerances hold; the FP32-only path is further off at
-    this conditioning, which is what the kappa_hat rule is for."""
+    path (threshold just above 1) the FP32 tolerances hold and the nodes are
+    counted; the FP32-only path is further off (its mean solve A^-1 C d
+    carries the FP32 Gram's rounding times kappa), which is what the
+    kappa_hat rule is for."""
     w = W.TEL_16M
     inp, geom = inputs(w, 8)
     Xb_r = inp.X0.astype(np.float32)
