@@ -94,8 +94,9 @@ struct AdjArgs {
 
 // Adjoint of one node's analysis. T = float: FP32 handle, warm start from the
 // frame's stored eigenbasis U0 and B-only Jacobi, nodes above kappa_thr queued.
-// T = double: identity start with accumulated eigenvectors; with `list` the
-// nodes are taken from the FP64 queue.
+// T = double: accumulated eigenvectors, started from the identity (FP64
+// handles) or, with `list` (the FP64 queue of an FP32 handle), from the FP32
+// basis U0 the forward pair kernel stored for the queued node.
 template <int MP, typename S, typename T>
 __global__ void __launch_bounds__(ADJ_WARPS * 32)
     adjoint_node_kernel(const LkInst *__restrict__ insts, const int2 *__restrict__ list,
@@ -188,8 +189,12 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
     __syncwarp();
     jacobi<MP, T, false>(b, v, tol, a.max_sweeps, a.counters);
   } else {
+    if (U0) {
+      warm_basis<MP, T>(b, v, U0 + (size_t)pid * MP * MP, Ms, Vs);
+    } else {
 #pragma unroll
-    for (int k = 0; k < MP; ++k) v[k] = (k == lane) ? T(1) : T(0);
+      for (int k = 0; k < MP; ++k) v[k] = (k == lane) ? T(1) : T(0);
+    }
     jacobi<MP, T, true>(b, v, tol, a.max_sweeps, a.counters);
   }
   const T nrm = dot4<MP, T>(b, b);
@@ -570,7 +575,7 @@ cudaError_t launch_nodes(letkf_ctx *h, LkAdjWork *W, const float *U0, const AdjA
   if (e != cudaSuccess || kthr <= 0.f) return e;
   adjoint_node_kernel<MP, float, double>
       <<<blocks, ADJ_WARPS * 32, node_smem<MP, float, double>(I), h->stream>>>(
-          h->d_inst, W->queue, W->queue_len, nullptr, 0.f, nullptr, nullptr, h->tol64, a);
+          h->d_inst, W->queue, W->queue_len, U0, 0.f, nullptr, nullptr, h->tol64, a);
   return cudaGetLastError();
 }
 

@@ -14,15 +14,12 @@
 //   weights  wbar = V Lambda^-1 V^T C d,  W = V ((m-1) Lambda^-1)^(1/2) V^T
 //   apply    Xa_r = xbar_r + X'_r wbar + X'_r W for the node's two rows
 //
-// FP32 nodes start from the eigenbasis the node had in the previous analysis
-// (V0, kept per node): the transform W maps member space along A's own
-// eigenvectors, so the next frame's matrix is nearly diagonal in that basis
-// and the sweep converges in a few sweeps. They iterate on B only and recover
-// V as the normalised columns of B (B = V Lambda at convergence).
-// kappa_hat = 1 + rho tr(G)/(m-1) bounds the condition number of A before the
-// eigensolve (its eigenvalues lie in [(m-1)/rho, (m-1)/rho + tr G]); in FP32 mode
-// nodes above the threshold are queued and redone in FP64 by a second kernel,
-// which accumulates V explicitly.
+// FP32 handles run the analysis in letkf_pair.cu (two columns per lane). Nodes
+// whose kappa_hat = 1 + rho tr(G)/(m-1) exceeds the threshold still take that
+// FP32 eigensolve, but their mean solve wbar = A^-1 C d would amplify the FP32
+// Gram's rounding by kappa: they are queued, and the list kernel here redoes
+// them in FP64 (Gram and sweep), the sweep started from the FP32 eigenbasis.
+// FP64 handles run the tile kernel below (one warp per node, accumulated V).
 #include <math.h>
 #include <stdio.h>
 
@@ -38,7 +35,7 @@ constexpr int LK_NUM_SHAPES = 4;
 
 namespace {
 
-constexpr int LIST_WARPS = 4;
+constexpr int LIST_WARPS = 1;
 // Per-warp scratch: V staging [MP][MP+1] + 3 vectors, or A staging [MP][MP+4].
 template <int MP, typename T>
 __host__ __device__ constexpr size_t scratch_elems() {
@@ -62,12 +59,19 @@ __host__ __device__ TileLayout tile_layout(int w) {
   return L;
 }
 
-// Shared-memory layout of one warp of the FP64 list kernel.
+// Shared-memory layout of one warp of the FP64 list kernel: window, innovations,
+// taper, then the scratch of A and V staging ([MP][MP+1] each, FP64), reused
+// by transform_apply.
+template <int MP>
+__host__ __device__ constexpr size_t refine_scratch_elems() {
+  return 2 * (size_t)MP * (MP + 1) > scratch_elems<MP, double>() ? 2 * (size_t)MP * (MP + 1)
+                                                                  : scratch_elems<MP, double>();
+}
 template <int MP>
 __host__ __device__ size_t list_warp_bytes(int w) {
   const size_t wc = (size_t)w * w;
   return align16(wc * 2 * MP * sizeof(float)) + align16(wc * 2 * sizeof(float)) +
-         align16(wc * sizeof(double)) + scratch_elems<MP, double>() * sizeof(double);
+         align16(wc * sizeof(double)) + refine_scratch_elems<MP>() * sizeof(double);
 }
 
 // wbar, W from the eigenpairs (lane j: eigenvector column v, eigenvalue lam) and
@@ -108,7 +112,10 @@ __device__ __forceinline__ void transform_apply(const T (&v)[MP], T lam, T cd, i
   const T z = u / lam;
   const T P0 = lk_warp_sum(g0 * z);           // X'_0 wbar
   const T P1 = lk_warp_sum(g1 * z);
-  const T sroot = mem ? sqrt(T(m - 1) / lam) : T(0);
+  // every eigenvector gets its root: a warm-started sweep leaves the padding's
+  // unit eigenvectors (lambda = 1) in arbitrary columns, and their projections
+  // g0, g1 of the zero-padded anomalies are exactly zero
+  const T sroot = col ? sqrt(T(m - 1) / lam) : T(0);
   __syncwarp();
   if (col) {
     vec[MP + lane] = g0 * sroot;
@@ -250,8 +257,36 @@ __global__ void __launch_bounds__(TI *TJ * 32)
                                T(I.alpha), tol, max_sweeps, xrow, mo, so, wscr, counters, nullptr);
 }
 
-// FP64 re-analysis of the queued nodes (FP32 handles): one warp per node,
-// window staged per warp from the padded grid.
+// FP64 analysis of one node whose kappa_hat sent it here (FP32 handles), one
+// warp, lane = column. A and C d are formed in FP64 from the node's window and
+// the FP64 sweep of the tile kernel (accumulated V) is started from the FP32
+// eigenbasis the pair kernel stored for the node instead of the identity:
+// V is made orthonormal in FP64 and the sweep starts from B = A V (warm_basis).
+// V diagonalises A up to O(eps32 kappa), so the quadratically convergent sweeps
+// end after two or three (the last one rotates nothing) instead of the eight
+// to ten of a cold start.
+// The result is the FP64 analysis: the same eigenpairs, hence the same wbar and
+// W up to FP64 rounding, written as by the pair kernel.
+template <int MP>
+__device__ __forceinline__ void warm_node(const float *__restrict__ win,
+                                          const float *__restrict__ dwin,
+                                          const double *__restrict__ tap, int w, int m,
+                                          double alpha, double tol, int max_sweeps,
+                                          float *__restrict__ xrow, float *__restrict__ mean_out,
+                                          float *__restrict__ spread_out, double *__restrict__ scr,
+                                          const float *__restrict__ U, int *__restrict__ counters) {
+  const int lane = threadIdx.x & 31;
+  double b[MP], diag, cd, v[MP];
+  gram<MP, float, double>(win, dwin, w, tap, w, m, alpha, b, diag, cd);
+  warm_basis<MP, double>(b, v, U, scr, scr + MP * (MP + 1));
+  jacobi<MP, double, true>(b, v, tol, max_sweeps, counters);
+  const double nrm = dot4<MP, double>(b, b);
+  const double lam = (lane < MP && nrm > 0.0) ? sqrt(nrm) : 1.0;   // |A v_j| = lambda_j
+  transform_apply<MP, float, double>(v, lam, cd, m, xrow, mean_out, spread_out, scr, counters);
+}
+
+// The queued nodes (FP32 handles): one warp per node, window staged per warp
+// from the padded grid, then warm_node.
 template <int MP>
 __global__ void __launch_bounds__(LIST_WARPS * 32)
     analysis_list_kernel(const LkInst *__restrict__ insts, const int2 *__restrict__ worklist,
@@ -295,12 +330,11 @@ __global__ void __launch_bounds__(LIST_WARPS * 32)
   }
   for (int e = lane; e < wc; e += 32) tap[e] = (double)taper[e];
   __syncwarp();
-  analyze_node_accum<MP, float, double>(
-      win, dwin, w, tap, w, m, I.alpha, tol, max_sweeps,
-      static_cast<float *>(I.X) + (size_t)pid * 2 * m,
-      mean ? mean + 2 * (I.node_off + pid) : nullptr,
-      spread ? spread + 2 * (I.node_off + pid) : nullptr, scr, counters,
-      I.basis + (size_t)pid * MP * MP);
+  warm_node<MP>(win, dwin, tap, w, m, I.alpha, tol, max_sweeps,
+                static_cast<float *>(I.X) + (size_t)pid * 2 * m,
+                mean ? mean + 2 * (I.node_off + pid) : nullptr,
+                spread ? spread + 2 * (I.node_off + pid) : nullptr, scr,
+                I.basis + (size_t)pid * MP * MP, counters);
 }
 
 template <int MP, typename S, typename T, int TI, int TJ>

@@ -122,6 +122,52 @@ __device__ __forceinline__ int jacobi_step(T (&b)[MP], T (&v)[MP], T &nrm, int t
   return rot;
 }
 
+// Start of an accumulated FP64 sweep from a stored FP32 eigenbasis U
+// (row-major MP x MP, lane = column) instead of the identity. One Newton-Schulz
+// step V <- V (3 I - V^T V) / 2 makes the columns orthonormal to FP64 rounding
+// (it squares their orthogonality error), then b = A v_lane. On entry b holds
+// row lane of the symmetric A; As and Vs are [MP][MP+1] warp scratch.
+template <int MP, typename T>
+__device__ __forceinline__ void warm_basis(T (&b)[MP], T (&v)[MP], const float *__restrict__ U,
+                                           T *__restrict__ As, T *__restrict__ Vs) {
+  constexpr int LD = MP + 1;
+  const int lane = threadIdx.x & 31;
+  const bool col = lane < MP;
+#pragma unroll
+  for (int k = 0; k < MP; ++k) v[k] = col ? T(U[k * MP + lane]) : T(0);
+  __syncwarp();
+  if (col) {
+#pragma unroll
+    for (int k = 0; k < MP; ++k) {
+      As[k * LD + lane] = b[k];
+      Vs[k * LD + lane] = v[k];
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < MP; ++i) {                  // b <- V^T v_lane
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < MP; ++k) acc = fma(Vs[k * LD + i], v[k], acc);
+    b[i] = acc;
+  }
+#pragma unroll
+  for (int k = 0; k < MP; ++k) {                  // v_lane <- 1.5 v_lane - 0.5 V b
+    T acc = T(0);
+#pragma unroll
+    for (int i = 0; i < MP; ++i) acc = fma(Vs[k * LD + i], b[i], acc);
+    v[k] = fma(T(-0.5), acc, T(1.5) * v[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < MP; ++k) {                  // b <- A v_lane
+    T acc = T(0);
+#pragma unroll
+    for (int i = 0; i < MP; ++i) acc = fma(As[k * LD + i], v[i], acc);
+    b[k] = acc;
+  }
+  __syncwarp();
+}
+
 // Sweeps until a full sweep makes no rotation. Records the sweep count and a
 // non-convergence flag.
 template <int MP, typename T, bool ACCUM>

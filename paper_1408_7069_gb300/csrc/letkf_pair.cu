@@ -290,7 +290,11 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
   }
   if (!live) diag = cd0 = cd1 = 0.f;
   const float alpha = float(I.alpha);
-  bool active = pid >= 0;
+  const bool active = pid >= 0;
+  // kappa_hat above the threshold: the node's mean solve needs the FP64 Gram.
+  // It still takes this FP32 eigensolve, whose basis is stored as the start of
+  // the FP64 list kernel's sweep; X is left alone and the node is queued.
+  bool queued = false;
   if (queue) {
     const float trg = group_sum<GL>(diag);
     if (active && 1.f + trg / alpha > kappa_thr) {
@@ -298,7 +302,7 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
         worklist[atomicAdd(queue, 1)] = make_int2(tl.inst, pid);
         atomicAdd(&counters[1], 1);
       }
-      active = false;
+      queued = true;
     }
   }
   // (m-1)/rho on the diagonal, 1 on the padding; inactive nodes and idle lanes
@@ -371,8 +375,8 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
       Q[k] = mul2(f2(iQ), Q[k]);
     }
   }
-  // ---- eigenbasis for the reverse mode: U[k][2li], U[k][2li+1] ----
-  if (keep_basis && active && live) {
+  // ---- eigenbasis for the reverse mode and for queued nodes: U[k][2li], U[k][2li+1] ----
+  if ((keep_basis || queued) && active && live) {
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < K2; ++k)
@@ -391,13 +395,14 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
   float *vcd = scr;                     // C d
   float *vx0 = vcd + MP;                // X'_0
   float *vx1 = vx0 + MP;                // X'_1
-  float *xrow = active ? static_cast<float *>(I.X) + (size_t)pid * 2 * m : nullptr;
+  const bool wr = active && !queued;
+  float *xrow = wr ? static_cast<float *>(I.X) + (size_t)pid * 2 * m : nullptr;
   const int m0 = 2 * li, m1 = 2 * li + 1;
   const bool in0 = live && m0 < m, in1 = live && m1 < m;
-  const float x00 = (active && in0) ? xrow[m0] : 0.f;
-  const float x01 = (active && in1) ? xrow[m1] : 0.f;
-  const float x10 = (active && in0) ? xrow[m + m0] : 0.f;
-  const float x11 = (active && in1) ? xrow[m + m1] : 0.f;
+  const float x00 = (wr && in0) ? xrow[m0] : 0.f;
+  const float x01 = (wr && in1) ? xrow[m1] : 0.f;
+  const float x10 = (wr && in0) ? xrow[m + m0] : 0.f;
+  const float x11 = (wr && in1) ? xrow[m + m1] : 0.f;
   const float inv_m = 1.f / float(m);
   const float xb0 = group_sum<GL>(x00 + x01) * inv_m;
   const float xb1 = group_sum<GL>(x10 + x11) * inv_m;
@@ -447,7 +452,7 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
   const float2 q1 = reduce_scatter<GL>(v1, li);
   const float xa00 = xb0 + w0 + q0.x, xa01 = xb0 + w0 + q0.y;
   const float xa10 = xb1 + w1 + q1.x, xa11 = xb1 + w1 + q1.y;
-  if (active) {
+  if (wr) {
     if (in0) {
       xrow[m0] = xa00;
       xrow[m + m0] = xa10;
@@ -465,7 +470,7 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
   const float d10 = in0 ? xa10 - mu1 : 0.f, d11 = in1 ? xa11 - mu1 : 0.f;
   const float sp0 = sqrtf(group_sum<GL>(d00 * d00 + d01 * d01) / float(m - 1));
   const float sp1 = sqrtf(group_sum<GL>(d10 * d10 + d11 * d11) / float(m - 1));
-  if (active && li == 0) {
+  if (wr && li == 0) {
     const long long row = I.node_off + pid;
     if (mean) {
       mean[2 * row] = mu0;
