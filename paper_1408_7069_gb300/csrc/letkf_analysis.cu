@@ -36,6 +36,20 @@ constexpr int LK_NUM_SHAPES = 4;
 namespace {
 
 constexpr int LIST_WARPS = 1;
+constexpr int LIST_CTAS_PER_SM = 8;
+
+// SM count of a device, cached (read once per device).
+int lk_sm_count(int device) {
+  static int cache[64] = {0};
+  const int d = device >= 0 && device < 64 ? device : 0;
+  if (cache[d] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0)
+      n = 1;
+    cache[d] = n;
+  }
+  return cache[d];
+}
 // Per-warp scratch: V staging [MP][MP+1] + 3 vectors, or A staging [MP][MP+4].
 template <int MP, typename T>
 __host__ __device__ constexpr size_t scratch_elems() {
@@ -286,7 +300,9 @@ __device__ __forceinline__ void warm_node(const float *__restrict__ win,
 }
 
 // The queued nodes (FP32 handles): one warp per node, window staged per warp
-// from the padded grid, then warm_node.
+// from the padded grid, then warm_node. A fixed grid of a few CTAs per SM walks
+// the queue, so that the launch costs little when the queue is empty (the
+// steady state).
 template <int MP>
 __global__ void __launch_bounds__(LIST_WARPS * 32)
     analysis_list_kernel(const LkInst *__restrict__ insts, const int2 *__restrict__ worklist,
@@ -295,46 +311,48 @@ __global__ void __launch_bounds__(LIST_WARPS * 32)
                          int *__restrict__ counters, int wmax) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int idx = blockIdx.x * LIST_WARPS + warp;
-  if (idx >= *queue_len) return;
-  const int2 it = worklist[idx];
-  const LkInst &I = insts[it.x];
-  const int w = I.w, wc = w * w, m = I.m;
-  // every warp's region has the size for the class's widest window, whatever
-  // the window of the instance it serves
-  unsigned char *base = smem + (size_t)warp * list_warp_bytes<MP>(wmax);
-  float *win = reinterpret_cast<float *>(base);
-  float *dwin = reinterpret_cast<float *>(base + align16((size_t)wc * 2 * MP * sizeof(float)));
-  double *tap = reinterpret_cast<double *>(base + align16((size_t)wc * 2 * MP * sizeof(float)) +
-                                           align16((size_t)wc * 2 * sizeof(float)));
-  double *scr = tap + align16((size_t)wc * sizeof(double)) / sizeof(double);
-  const int pid = it.y;
-  const int2 ij = I.pts[pid];
-  const float *Ybp = static_cast<const float *>(I.Ybp);
-  const float *dp = static_cast<const float *>(I.dp);
-  const float *taper = static_cast<const float *>(I.taper);
-  for (int e = lane; e < wc * 2 * MP; e += 32) {
-    const int cell = e / (2 * MP);
-    const int r = e - cell * 2 * MP;
-    const int c = r / MP;
-    const int mm = r - c * MP;
-    const int ds = cell / w, dt = cell - (cell / w) * w;
-    const size_t src = (size_t)(ij.x + ds) * I.gs_cols + (ij.y + dt);
-    win[e] = mm < m ? Ybp[(src * 2 + c) * m + mm] : 0.f;
+  const int qn = *queue_len;
+  for (int idx = blockIdx.x * LIST_WARPS + warp; idx < qn; idx += gridDim.x * LIST_WARPS) {
+    const int2 it = worklist[idx];
+    const LkInst &I = insts[it.x];
+    const int w = I.w, wc = w * w, m = I.m;
+    // every warp's region has the size for the class's widest window, whatever
+    // the window of the instance it serves
+    unsigned char *base = smem + (size_t)warp * list_warp_bytes<MP>(wmax);
+    float *win = reinterpret_cast<float *>(base);
+    float *dwin = reinterpret_cast<float *>(base + align16((size_t)wc * 2 * MP * sizeof(float)));
+    double *tap = reinterpret_cast<double *>(base + align16((size_t)wc * 2 * MP * sizeof(float)) +
+                                             align16((size_t)wc * 2 * sizeof(float)));
+    double *scr = tap + align16((size_t)wc * sizeof(double)) / sizeof(double);
+    const int pid = it.y;
+    const int2 ij = I.pts[pid];
+    const float *Ybp = static_cast<const float *>(I.Ybp);
+    const float *dp = static_cast<const float *>(I.dp);
+    const float *taper = static_cast<const float *>(I.taper);
+    for (int e = lane; e < wc * 2 * MP; e += 32) {
+      const int cell = e / (2 * MP);
+      const int r = e - cell * 2 * MP;
+      const int c = r / MP;
+      const int mm = r - c * MP;
+      const int ds = cell / w, dt = cell - (cell / w) * w;
+      const size_t src = (size_t)(ij.x + ds) * I.gs_cols + (ij.y + dt);
+      win[e] = mm < m ? Ybp[(src * 2 + c) * m + mm] : 0.f;
+    }
+    for (int e = lane; e < wc * 2; e += 32) {
+      const int cell = e >> 1;
+      const int ds = cell / w, dt = cell - (cell / w) * w;
+      const size_t src = (size_t)(ij.x + ds) * I.gs_cols + (ij.y + dt);
+      dwin[e] = dp[src * 2 + (e & 1)];
+    }
+    for (int e = lane; e < wc; e += 32) tap[e] = (double)taper[e];
+    __syncwarp();
+    warm_node<MP>(win, dwin, tap, w, m, I.alpha, tol, max_sweeps,
+                  static_cast<float *>(I.X) + (size_t)pid * 2 * m,
+                  mean ? mean + 2 * (I.node_off + pid) : nullptr,
+                  spread ? spread + 2 * (I.node_off + pid) : nullptr, scr,
+                  I.basis + (size_t)pid * MP * MP, counters);
+    __syncwarp();
   }
-  for (int e = lane; e < wc * 2; e += 32) {
-    const int cell = e >> 1;
-    const int ds = cell / w, dt = cell - (cell / w) * w;
-    const size_t src = (size_t)(ij.x + ds) * I.gs_cols + (ij.y + dt);
-    dwin[e] = dp[src * 2 + (e & 1)];
-  }
-  for (int e = lane; e < wc; e += 32) tap[e] = (double)taper[e];
-  __syncwarp();
-  warm_node<MP>(win, dwin, tap, w, m, I.alpha, tol, max_sweeps,
-                static_cast<float *>(I.X) + (size_t)pid * 2 * m,
-                mean ? mean + 2 * (I.node_off + pid) : nullptr,
-                spread ? spread + 2 * (I.node_off + pid) : nullptr, scr,
-                I.basis + (size_t)pid * MP * MP, counters);
 }
 
 template <int MP, typename S, typename T, int TI, int TJ>
@@ -372,7 +390,9 @@ cudaError_t launch_list(letkf_ctx *h, int cls, void *mean, void *spread) {
   long long n = 0;
   for (const LkInst &I : h->inst)
     if (I.mp == MP) n += I.n_pts;
-  const int blocks = (int)((n + LIST_WARPS - 1) / LIST_WARPS);
+  const long long want = (n + LIST_WARPS - 1) / LIST_WARPS;
+  const long long cap = (long long)LIST_CTAS_PER_SM * lk_sm_count(h->device);
+  const int blocks = (int)(want < cap ? want : cap);
   analysis_list_kernel<MP><<<blocks, LIST_WARPS * 32, bytes, h->stream>>>(
       h->d_inst, h->worklist + (size_t)cls * h->n_pts_total, h->counters + 4 + cls, (float *)mean,
       (float *)spread, h->tol64, h->max_sweeps, h->counters, wmax);
