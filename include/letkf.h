@@ -138,7 +138,11 @@ letkf_status letkf_forecast(letkf_t h, const void *noise_dev);
  * W = Q ((m-1) Lambda^-1)^(1/2) Q^T, X_a = xbar + X_b' (wbar 1^T + W).
  * y_dev: device [p] real. mean_dev, spread_dev: device [n_pts][2] real or
  * NULL; spread is the sample standard deviation over members (m - 1). The
- * ensemble is replaced by the analysis. */
+ * ensemble is replaced by the analysis.
+ * FP32 handles: a node whose kappa_hat = 1 + rho tr(C Yb_l) / (m - 1), an upper
+ * bound on the condition number of A, exceeds fp64_kappa is analysed in FP64
+ * (Gram and accumulated Jacobi sweep, started from the node's FP32 eigenbasis)
+ * and written back in FP32. */
 letkf_status letkf_analyze(letkf_t h, const void *y_dev, void *mean_dev, void *spread_dev);
 
 /* Loop criterion (Section 2.1 Eq. Crit_Opt; Section 5): spatial variance over
@@ -247,7 +251,8 @@ letkf_status letkf_sync(letkf_t h);
 
 /* Counters of the last analysis, host pointers (any may be NULL): nodes that
  * took the FP64 fallback, the largest and the total number of Jacobi sweeps
- * over the nodes. Synchronises. */
+ * over the nodes (a node of the FP64 fallback counts the sweeps of its FP32
+ * and of its FP64 eigensolve). Synchronises. */
 letkf_status letkf_stats(letkf_t h, int32_t *fp64_points, int32_t *max_sweeps,
                          int32_t *total_sweeps);
 
