@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
 #pragma unroll
       for (int k = 0; k < MP; ++k) v[k] = (k == lane) ? T(1) : T(0);
     }
-    jacobi<MP, T, true>(b, v, tol, a.max_sweeps, a.counters);
+    jacobi<MP, T, true>(b, v, tol, a.max_sweeps, a.counters, U0 ? T(LK_WARM_STOP64) : T(0));
   }
   const T nrm = dot4<MP, T>(b, b);
   const T lam = (col && nrm > T(0)) ? sqrt(nrm) : T(1);   // |A v_j| = lambda_j

@@ -277,8 +277,8 @@ __global__ void __launch_bounds__(TI *TJ * 32)
 // eigenbasis the pair kernel stored for the node instead of the identity:
 // V is made orthonormal in FP64 and the sweep starts from B = A V (warm_basis).
 // V diagonalises A up to O(eps32 kappa), so the quadratically convergent sweeps
-// end after two or three (the last one rotates nothing) instead of the eight
-// to ten of a cold start.
+// stop after two or three (at the first sweep whose cosines all stay below
+// LK_WARM_STOP64) instead of the eight to ten of a cold start.
 // The result is the FP64 analysis: the same eigenpairs, hence the same wbar and
 // W up to FP64 rounding, written as by the pair kernel.
 template <int MP>
@@ -293,7 +293,7 @@ __device__ __forceinline__ void warm_node(const float *__restrict__ win,
   double b[MP], diag, cd, v[MP];
   gram<MP, float, double>(win, dwin, w, tap, w, m, alpha, b, diag, cd);
   warm_basis<MP, double>(b, v, U, scr, scr + MP * (MP + 1));
-  jacobi<MP, double, true>(b, v, tol, max_sweeps, counters);
+  jacobi<MP, double, true>(b, v, tol, max_sweeps, counters, LK_WARM_STOP64);
   const double nrm = dot4<MP, double>(b, b);
   const double lam = (lane < MP && nrm > 0.0) ? sqrt(nrm) : 1.0;   // |A v_j| = lambda_j
   transform_apply<MP, float, double>(v, lam, cd, m, xrow, mean_out, spread_out, scr, counters);

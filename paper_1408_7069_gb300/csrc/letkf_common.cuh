@@ -25,6 +25,10 @@ constexpr int LK_TILE_J = 4;
 constexpr int LK_TILE_MAX = 8;
 // CTAs of the residual reduction per instance (fixed, so the sum order is fixed).
 constexpr int LK_RES_BLOCKS = 128;
+// Stop cosine of the FP64 sweeps that start from a stored FP32 eigenbasis
+// (queued nodes of FP32 handles): the next sweep would rotate by about its
+// square, far below what the FP32 outputs resolve.
+constexpr double LK_WARM_STOP64 = 1e-8;
 
 // One AO instance, as the kernels see it (device pointers, by-value copy in a
 // device array). The real type of X, Yb, d, y, truth, taper and the outputs is

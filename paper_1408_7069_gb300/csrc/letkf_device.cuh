@@ -87,9 +87,11 @@ __device__ __forceinline__ void gram(const S *__restrict__ win, const S *__restr
 }
 
 // One Hestenes rotation step for pair (lane, lane ^ t) on column b (and v when
-// ACCUM). nrm = |b|^2 of this lane's column. Returns whether it rotated.
+// ACCUM). nrm = |b|^2 of this lane's column. Returns bit 0: it rotated (cosine
+// above tol), bit 1: the cosine was above stop.
 template <int MP, typename T, bool ACCUM>
-__device__ __forceinline__ int jacobi_step(T (&b)[MP], T (&v)[MP], T &nrm, int t, T tol) {
+__device__ __forceinline__ int jacobi_step(T (&b)[MP], T (&v)[MP], T &nrm, int t, T tol,
+                                           T stop) {
   const int lane = threadIdx.x & 31;
   T pb[MP];
 #pragma unroll
@@ -101,13 +103,14 @@ __device__ __forceinline__ int jacobi_step(T (&b)[MP], T (&v)[MP], T &nrm, int t
   const T aqq = isp ? pn : nrm;
   T cs = T(1), sn = T(0), tr = T(0);
   int rot = 0;
-  if (fabs(dot) > tol * sqrt(app * aqq)) {
+  const T scale = sqrt(app * aqq);
+  if (fabs(dot) > tol * scale) {
     const T zeta = (aqq - app) / (T(2) * dot);
     const T az = fabs(zeta);
     tr = az > T(1e15) ? T(0.5) / zeta : copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
     cs = lk_rsqrt(T(1) + tr * tr);
     sn = cs * tr;
-    rot = 1;
+    rot = fabs(dot) > stop * scale ? 3 : 1;
   }
   const T sg = isp ? -sn : sn;  // p' = c p - s q ; q' = s p + c q
 #pragma unroll
@@ -168,18 +171,22 @@ __device__ __forceinline__ void warm_basis(T (&b)[MP], T (&v)[MP], const float *
   __syncwarp();
 }
 
-// Sweeps until a full sweep makes no rotation. Records the sweep count and a
-// non-convergence flag.
+// Sweeps until a full sweep makes no rotation or, with stop > 0, until a sweep
+// whose rotations all had cosines <= stop (sweeps converge quadratically, so
+// the next one would rotate by about stop^2, except inside clusters of nearly
+// equal eigenvalues, whose mixing leaves functions of A unchanged). Records
+// the sweep count and a non-convergence flag.
 template <int MP, typename T, bool ACCUM>
 __device__ __forceinline__ void jacobi(T (&b)[MP], T (&v)[MP], T tol, int max_sweeps,
-                                       int *__restrict__ counters) {
+                                       int *__restrict__ counters, T stop = T(0)) {
   int sweep = 0;
   bool converged = false;
+  if (stop < tol) stop = tol;
   for (; sweep < max_sweeps; ++sweep) {
     T nrm = dot4<MP, T>(b, b);
     int rotated = 0;
-    for (int t = 1; t < MP; ++t) rotated |= jacobi_step<MP, T, ACCUM>(b, v, nrm, t, tol);
-    if (!__any_sync(FULL, rotated)) {
+    for (int t = 1; t < MP; ++t) rotated |= jacobi_step<MP, T, ACCUM>(b, v, nrm, t, tol, stop);
+    if (!__any_sync(FULL, rotated & 2)) {
       converged = true;
       break;
     }
