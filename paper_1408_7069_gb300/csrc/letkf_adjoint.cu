@@ -59,7 +59,7 @@ struct LkAdjWork {
   double *ybar = nullptr;           // [gs_rows*gs_cols][2][m] slope adjoints (padded grid)
   double *dbar = nullptr;           // [gs_rows*gs_cols][2]
   double *theta = nullptr;          // [n_pts][3] per-node (rho, sigma2, L) partials
-  double *acc = nullptr;            // [4] accumulated gradient, [3] = mean residual piston
+  double *acc = nullptr;            // [5]: [0..2] accumulated gradient, [3] the frame's residual piston, [4] scratch
   double *dtap = nullptr;           // [w*w] d(tau/sigma2)/dL
   int2 *queue = nullptr;            // [n_pts] nodes redone in FP64
   int *queue_len = nullptr;
@@ -367,7 +367,9 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
 }
 
 // Warp per valid subaperture (s, t): sums the slope adjoints the nodes whose
-// window holds (s, t) wrote, in a fixed order, into the padded grid.
+// window holds (s, t) wrote, in a fixed order (node row, then column), into the
+// padded grid. The candidate nodes are looked up 32 at a time, one per lane,
+// so that the loads of their adjoints do not wait on one another.
 __global__ void __launch_bounds__(256)
     adjoint_subap_kernel(const LkInst *__restrict__ insts, const double *__restrict__ ybw,
                          const double *__restrict__ dbw, double *__restrict__ ybar,
@@ -379,20 +381,30 @@ __global__ void __launch_bounds__(256)
   const int2 st = I.saps[q];
   const int w = I.w, wc = w * w, m = I.m, nn = I.nsub + 1;
   const bool mem = lane < m;
+  const int i0 = st.x + I.h - w + 1, j0 = st.y + I.h - w + 1;
   double y0 = 0, y1 = 0, d0 = 0, d1 = 0;
-  for (int i = st.x + I.h - w + 1; i <= st.x + I.h; ++i) {
-    if (i < 0 || i >= nn) continue;
-    for (int j = st.y + I.h - w + 1; j <= st.y + I.h; ++j) {
-      if (j < 0 || j >= nn) continue;
-      const int pid = I.pid_map[i * nn + j];
-      if (pid < 0) continue;
-      const size_t cell = (size_t)pid * wc + (size_t)(st.x - i + I.h) * w + (st.y - j + I.h);
-      if (mem) {
-        y0 += ybw[(cell * 2 + 0) * m + lane];
-        y1 += ybw[(cell * 2 + 1) * m + lane];
+  for (int c0 = 0; c0 < wc; c0 += 32) {
+    // lane: candidate node c0 + lane of the w x w block of nodes, row-major
+    long long cell = -1;
+    const int c = c0 + lane;
+    if (c < wc) {
+      const int i = i0 + c / w, j = j0 + c % w;
+      if (i >= 0 && i < nn && j >= 0 && j < nn) {
+        const int pid = I.pid_map[i * nn + j];
+        if (pid >= 0) cell = (long long)pid * wc + (long long)(st.x - i + I.h) * w + (st.y - j + I.h);
       }
-      d0 += dbw[cell * 2 + 0];
-      d1 += dbw[cell * 2 + 1];
+    }
+    const int nc = wc - c0 < 32 ? wc - c0 : 32;
+#pragma unroll 4
+    for (int u = 0; u < nc; ++u) {
+      const long long cu = __shfl_sync(FULL, cell, u);
+      if (cu < 0) continue;
+      if (mem) {
+        y0 += ybw[(cu * 2 + 0) * m + lane];
+        y1 += ybw[(cu * 2 + 1) * m + lane];
+      }
+      d0 += dbw[cu * 2 + 0];
+      d1 += dbw[cu * 2 + 1];
     }
   }
   const size_t g = (size_t)(st.x + I.h) * I.gs_cols + (st.y + I.h);
@@ -403,31 +415,6 @@ __global__ void __launch_bounds__(256)
   if (lane == 0) {
     dbar[g * 2 + 0] = d0;
     dbar[g * 2 + 1] = d1;
-  }
-}
-
-// Mean over nodes of truth - mean(row 0): the piston of the residual. One CTA,
-// fixed summation order.
-template <typename S>
-__global__ void __launch_bounds__(1024) resmean_kernel(const LkInst *__restrict__ insts,
-                                                       const S *__restrict__ truth,
-                                                       double *__restrict__ ebar) {
-  const LkInst &I = insts[0];
-  const S *X = static_cast<const S *>(I.X);
-  double s = 0;
-  for (int g = threadIdx.x; g < I.n_pts; g += blockDim.x) {
-    double mu = 0;
-    for (int i = 0; i < I.m; ++i) mu += double(X[(size_t)g * 2 * I.m + i]);
-    s += double(truth[g]) - mu / I.m;
-  }
-  __shared__ double sh[32];
-  s = lk_warp_sum(s);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-    s = lk_warp_sum(s);
-    if (threadIdx.x == 0) ebar[0] = s / I.n_pts;
   }
 }
 
@@ -629,7 +616,7 @@ letkf_status ensure_work(letkf_ctx *h, int frames, int ckpt) {
   if (e == cudaSuccess) e = walloc(&W->ybar, cells * 2 * I.m * sizeof(double));
   if (e == cudaSuccess) e = walloc(&W->dbar, cells * 2 * sizeof(double));
   if (e == cudaSuccess) e = walloc(&W->theta, (size_t)I.n_pts * 3 * sizeof(double));
-  if (e == cudaSuccess) e = walloc(&W->acc, 4 * sizeof(double));
+  if (e == cudaSuccess) e = walloc(&W->acc, 5 * sizeof(double));
   if (e == cudaSuccess) e = walloc(&W->dtap, wc * sizeof(double));
   if (e == cudaSuccess) e = walloc(&W->queue, (size_t)I.n_pts * sizeof(int2));
   if (e == cudaSuccess) e = walloc(&W->queue_len, sizeof(int));
@@ -720,15 +707,14 @@ cudaError_t backward_frame(letkf_ctx *h, LkAdjWork *W, const void *y_k, const vo
   adjoint_subap_kernel<<<(I.n_sap * 32 + 255) / 256, 256, 0, h->stream>>>(h->d_inst, W->ybw,
                                                                          W->dbw, W->ybar, W->dbar);
   const int blocks = (int)(((long long)I.n_pts * 32 + 255) / 256);
+  // the piston of the frame's residual (acc[3]; its variance goes to acc[4])
+  e = lk_launch_residual(h, truth_k, W->acc + 4, nullptr, W->acc + 3);
+  if (e != cudaSuccess) return e;
   if (h->precision == 1) {
-    resmean_kernel<double><<<1, 1024, 0, h->stream>>>(h->d_inst, (const double *)truth_k,
-                                                      W->acc + 3);
     adjoint_gather_kernel<double><<<blocks, 256, 0, h->stream>>>(
         h->d_inst, W->xp_bar, W->xbar_bar, W->ybar, W->dbar, (const double *)truth_k, W->acc + 3,
         crit_scale, lam_out);
   } else {
-    resmean_kernel<float><<<1, 1024, 0, h->stream>>>(h->d_inst, (const float *)truth_k,
-                                                     W->acc + 3);
     adjoint_gather_kernel<float><<<blocks, 256, 0, h->stream>>>(
         h->d_inst, W->xp_bar, W->xbar_bar, W->ybar, W->dbar, (const float *)truth_k, W->acc + 3,
         crit_scale, lam_out);
@@ -761,7 +747,7 @@ letkf_status enqueue_grad(letkf_ctx *h, int frames, const void *y_seq, const voi
   // ---- backward ----
   LK_ACUDA(h, cudaMemsetAsync(W->lam[0], 0, (size_t)I.n_pts * 2 * I.m * sizeof(double),
                               h->stream));
-  LK_ACUDA(h, cudaMemsetAsync(W->acc, 0, 4 * sizeof(double), h->stream));
+  LK_ACUDA(h, cudaMemsetAsync(W->acc, 0, 5 * sizeof(double), h->stream));
   int cur = 0;
   for (int seg = W->n_seg - 1; seg >= 0; --seg) {
     const int s = seg * C, e = (s + C < frames) ? s + C : frames;

@@ -132,7 +132,7 @@ cudaError_t lk_launch_analysis_class(letkf_ctx *h, int cls, void *mean, void *sp
 // The forecast also advances the forecast counter and the run index (frame[0..1]).
 cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise);
 cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
-                               const long long *run_idx);
+                               const long long *run_idx, double *piston = nullptr);
 cudaError_t lk_launch_basis_reset(letkf_ctx *h);   // warm-start eigenbases -> identity
 cudaError_t lk_setup_analysis(letkf_ctx *h);
 // FP32 analysis of width class cls, two columns per lane (letkf_pair.cu).

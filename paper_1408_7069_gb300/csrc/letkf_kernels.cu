@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(256) forecast_kernel(const LkInst *__restrict_
 // Spatial variance of truth - mean(row 0) over one instance's nodes, piston
 // removed (Section 2.1, Eq. Crit_Opt; Section 5). Grid (LK_RES_BLOCKS, n_inst):
 // thread per node, FP64 partial sums per CTA; the last CTA of an instance to
-// finish (ticket counter, reset by it) adds the partials in a fixed order.
+// finish (ticket counter, reset by it) adds the partials in a fixed order and
+// writes the variance and, when piston is given, the piston (the mean).
 template <typename S>
 __global__ void __launch_bounds__(64) residual_kernel(const LkInst *__restrict__ insts,
                                                        long long n_pts_total,
@@ -133,7 +134,8 @@ __global__ void __launch_bounds__(64) residual_kernel(const LkInst *__restrict__
                                                        const long long *__restrict__ run_idx,
                                                        double2 *__restrict__ partial,
                                                        int *__restrict__ tickets, int n_inst,
-                                                       double *__restrict__ resvar) {
+                                                       double *__restrict__ resvar,
+                                                       double *__restrict__ piston) {
   const LkInst &I = insts[blockIdx.y];
   const long long k = run_idx ? *run_idx : 0;
   const S *tr = truth + k * n_pts_total + I.node_off;
@@ -198,6 +200,7 @@ __global__ void __launch_bounds__(64) residual_kernel(const LkInst *__restrict__
       const double n = I.n_pts;
       const double mu = a / n;
       resvar[k * n_inst + blockIdx.y] = b / n - mu * mu;
+      if (piston) piston[k * n_inst + blockIdx.y] = mu;
       tickets[blockIdx.y] = 0;
     }
   }
@@ -247,16 +250,16 @@ cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise) {
 }
 
 cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
-                               const long long *run_idx) {
+                               const long long *run_idx, double *piston) {
   const dim3 grid(LK_RES_BLOCKS, h->n_inst);
   if (h->precision == 1)
     residual_kernel<double><<<grid, 64, 0, h->stream>>>(h->d_inst, h->n_pts_total,
                                                          (const double *)truth, run_idx, h->partial,
-                                                         h->tickets, h->n_inst, resvar);
+                                                         h->tickets, h->n_inst, resvar, piston);
   else
     residual_kernel<float><<<grid, 64, 0, h->stream>>>(h->d_inst, h->n_pts_total,
                                                         (const float *)truth, run_idx, h->partial,
-                                                        h->tickets, h->n_inst, resvar);
+                                                        h->tickets, h->n_inst, resvar, piston);
   return cudaGetLastError();
 }
 
