@@ -336,6 +336,9 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
   const double alpha_bar = double(lk_warp_sum(dg));   // d/d((m-1)/rho) = tr(A_bar)
 
   // ---- window slopes: y_bar_j = 2 c_j A_bar y_j + c_j d_j b_bar, d_bar_j, c_bar_j ----
+  // sum_j c_bar_j c_j and sum_j c_bar_j dc_j/dL, accumulated in FP64 (their
+  // terms cancel strongly over the window); dc_j/dsigma2 = -c_j / sigma2 is
+  // applied once per node
   const T bbl = col ? V(S_BB)[lane] : T(0);
   double gs2 = 0, gL = 0;
   double *yb_out = a.ybw + (size_t)pid * wc * 2 * m;
@@ -354,14 +357,14 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
       const T yay = lk_warp_sum(yl * ay);
       if (mem) yb_out[((size_t)cell * 2 + c) * m + lane] = double(T(2) * cj * ay + cj * dj * bbl);
       if (lane == 0) db_out[cell * 2 + c] = double(cj * yb);
-      const double cbar = double(yay) + double(dj) * double(yb);
-      gs2 = fma(cbar, -double(cj) / a.sigma2, gs2);
+      const double cbar = double(fma(dj, yb, yay));
+      gs2 = fma(cbar, double(cj), gs2);
       gL = fma(cbar, dtap[cell], gL);
     }
   }
   if (lane == 0) {
     a.theta[(size_t)pid * 3 + 0] = alpha_bar * (-(m - 1) / (a.rho * a.rho));
-    a.theta[(size_t)pid * 3 + 1] = gs2;
+    a.theta[(size_t)pid * 3 + 1] = -gs2 / a.sigma2;
     a.theta[(size_t)pid * 3 + 2] = gL;
   }
 }
