@@ -149,14 +149,18 @@ __global__ void __launch_bounds__(64) residual_kernel(const LkInst *__restrict__
     const S *row = X + (size_t)g * 2 * m;
     double x = 0.0;
     if (vec) {
+      // FP32 storage: the member sum in FP32 (four chains; its rounding is far
+      // below the FP32 state's own), the residual and its moments in FP64
       const float4 *r4 = reinterpret_cast<const float4 *>(row);
-      double a = 0.0, b = 0.0;
+      float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
       for (int i = 0; i < m / 4; ++i) {
         const float4 v = r4[i];
-        a += (double)v.x + (double)v.y;
-        b += (double)v.z + (double)v.w;
+        a += v.x;
+        b += v.y;
+        c += v.z;
+        d += v.w;
       }
-      x = a + b;
+      x = (double)((a + b) + (c + d));
     } else {
       for (int i = 0; i < m; ++i) x += (double)row[i];
     }
