@@ -192,7 +192,10 @@ letkf_status letkf_set_frame(letkf_t h, int64_t frame);
  * and the residual variance (one double per instance) into resvar_host (either
  * may be NULL; resvar_host only with truth_host). The frame runs as one CUDA
  * graph (captured on the first call, per with/without truth) on a non-default
- * stream. Requires a noise bank for every instance. Synchronises. */
+ * stream. Requires a noise bank for every instance. It returns once the
+ * outputs are in host memory; the frame's forecast may still be running on
+ * the handle's stream then, and every later call on the handle is ordered
+ * after it. On the legacy default stream it synchronises the stream. */
 letkf_status letkf_step(letkf_t h, const void *y_host, const void *truth_host, void *mean_host,
                         double *resvar_host);
 

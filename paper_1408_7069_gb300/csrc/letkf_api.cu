@@ -74,6 +74,9 @@ void drop_graphs(letkf_ctx *h) {
 
 void release(letkf_ctx *h) {
   drop_graphs(h);
+  for (cudaEvent_t ev : {h->ev_fork, h->ev_join, h->ev_out})
+    if (ev) cudaEventDestroy(ev);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->step_pin) cudaFreeHost(h->step_pin);
   if (h->step_dev) cudaFree(h->step_dev);
   void *bufs[] = {h->X,          h->Ybp,      h->dp,       h->taper,    h->pid_map,
@@ -333,6 +336,13 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   LK_TRY(dalloc(h, &h->d_inst, (size_t)n * sizeof(LkInst)));
   LK_TRY(dalloc(h, &h->obs_items, h->sap_total * sizeof(int2)));
   LK_TRY(dalloc(h, &h->node_items, h->n_pts_total * sizeof(int2)));
+  if (h->stream) {
+    cudaError_t es = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+    if (es == cudaSuccess) es = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (es == cudaSuccess) es = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    if (es == cudaSuccess) es = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+    if (es != cudaSuccess) LK_TRY(cuda_fail(h, es, "stream / event creation"));
+  }
   // ---- slice buffers, upload tables ----
   size_t o_ybp = 0, o_dp = 0, o_tap = 0, o_pid = 0, o_basis = 0, o_bank = 0, o_pts = 0, o_sap = 0;
   std::vector<int2> obs_items, node_items;
@@ -403,37 +413,61 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   return LETKF_OK;
 }
 
+// Residual and observation of a frame. Both read the prediction ensemble
+// only, so with a side stream the residual runs beside the observation kernel
+// and rejoins before the analysis overwrites the ensemble.
+letkf_status enqueue_head(letkf_ctx *h, const void *y, const void *truth, double *resvar,
+                          const long long *ridx) {
+  const bool res = truth && resvar;
+  const bool fork = res && h->side && h->stream;
+  if (fork) {
+    LK_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+    LK_CUDA(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    LK_CUDA(h, lk_launch_residual_on(h, h->side, truth, resvar, ridx, nullptr));
+    LK_CUDA(h, cudaEventRecord(h->ev_join, h->side));
+  } else if (res) {
+    LK_CUDA(h, lk_launch_residual(h, truth, resvar, ridx));
+  }
+  LK_CUDA(h, lk_launch_obs(h, y, ridx));
+  if (fork) LK_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+  return LETKF_OK;
+}
+
 letkf_status enqueue_frame(letkf_ctx *h, const void *y_seq, const void *truth_seq,
                            double *resvar) {
   const long long *ridx = h->frame + 1;
-  if (truth_seq && resvar) LK_CUDA(h, lk_launch_residual(h, truth_seq, resvar, ridx));
-  LK_CUDA(h, lk_launch_obs(h, y_seq, ridx));
+  letkf_status st = enqueue_head(h, y_seq, truth_seq, resvar, ridx);
+  if (st != LETKF_OK) return st;
   LK_CUDA(h, lk_launch_analysis(h, nullptr, nullptr));
   LK_CUDA(h, lk_launch_forecast(h, nullptr));
   return LETKF_OK;
 }
 
-// One frame from the step staging buffers: upload, (residual), observation,
-// analysis (mean into staging), forecast, download.
+// One frame from the step staging buffers: upload, (residual beside the)
+// observation, analysis (mean into staging), download, then the forecast.
+// ev_out is recorded after the downloads (an event node of the step graph),
+// so that the caller can return its outputs while the forecast still runs.
 letkf_status enqueue_step(letkf_ctx *h, bool with_truth) {
   unsigned char *yd = h->step_dev + h->step_off[0], *td = h->step_dev + h->step_off[1];
   unsigned char *md = h->step_dev + h->step_off[2], *rd = h->step_dev + h->step_off[3];
   unsigned char *yp = h->step_pin + h->step_off[0], *tp = h->step_pin + h->step_off[1];
   unsigned char *mp = h->step_pin + h->step_off[2], *rp = h->step_pin + h->step_off[3];
-  LK_CUDA(h, cudaMemcpyAsync(yd, yp, h->p_total * h->rsz, cudaMemcpyHostToDevice, h->stream));
-  if (with_truth) {
+  if (with_truth)
     LK_CUDA(h, cudaMemcpyAsync(td, tp, h->n_pts_total * h->rsz, cudaMemcpyHostToDevice,
                                h->stream));
-    LK_CUDA(h, lk_launch_residual(h, td, reinterpret_cast<double *>(rd), nullptr));
-  }
-  LK_CUDA(h, lk_launch_obs(h, yd, nullptr));
+  LK_CUDA(h, cudaMemcpyAsync(yd, yp, h->p_total * h->rsz, cudaMemcpyHostToDevice, h->stream));
+  letkf_status st = enqueue_head(h, yd, with_truth ? td : nullptr,
+                                 with_truth ? reinterpret_cast<double *>(rd) : nullptr, nullptr);
+  if (st != LETKF_OK) return st;
   LK_CUDA(h, lk_launch_analysis(h, md, nullptr));
-  LK_CUDA(h, lk_launch_forecast(h, nullptr));
   LK_CUDA(h, cudaMemcpyAsync(mp, md, 2 * h->n_pts_total * h->rsz, cudaMemcpyDeviceToHost,
                              h->stream));
   if (with_truth)
     LK_CUDA(h, cudaMemcpyAsync(rp, rd, h->n_inst * sizeof(double), cudaMemcpyDeviceToHost,
                                h->stream));
+  if (h->ev_out)
+    LK_CUDA(h, cudaEventRecordWithFlags(h->ev_out, h->stream, cudaEventRecordExternal));
+  LK_CUDA(h, lk_launch_forecast(h, nullptr));
   return LETKF_OK;
 }
 
@@ -656,7 +690,9 @@ letkf_status letkf_step(letkf_t h, const void *y_host, const void *truth_host, v
     }
   }
   const bool wt = truth_host != nullptr;
-  LK_CUDA(h, cudaStreamSynchronize(h->stream));    // staging is free again
+  // the staging is free once the previous step's downloads are done (its
+  // forecast may still run: the next graph is ordered after it on the stream)
+  LK_CUDA(h, h->ev_out ? cudaEventSynchronize(h->ev_out) : cudaStreamSynchronize(h->stream));
   memcpy(h->step_pin + h->step_off[0], y_host, h->p_total * h->rsz);
   if (wt) memcpy(h->step_pin + h->step_off[1], truth_host, h->n_pts_total * h->rsz);
   if (h->stream) {
@@ -680,7 +716,7 @@ letkf_status letkf_step(letkf_t h, const void *y_host, const void *truth_host, v
     letkf_status st = enqueue_step(h, wt);
     if (st != LETKF_OK) return st;
   }
-  LK_CUDA(h, cudaStreamSynchronize(h->stream));
+  LK_CUDA(h, h->ev_out ? cudaEventSynchronize(h->ev_out) : cudaStreamSynchronize(h->stream));
   h->frame_host += 1;
   if (mean_host)
     memcpy(mean_host, h->step_pin + h->step_off[2], 2 * h->n_pts_total * h->rsz);

@@ -119,6 +119,12 @@ struct letkf_ctx {
   size_t step_off[4] = {0, 0, 0, 0};
   cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
 
+  // Second stream of a handle on a user stream: the residual runs on it beside
+  // the observation kernel (fork / join events); ev_out marks a step's
+  // downloads, so that letkf_step returns while its forecast still runs.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr;
+
   std::string err;
 };
 
@@ -133,6 +139,9 @@ cudaError_t lk_launch_analysis_class(letkf_ctx *h, int cls, void *mean, void *sp
 cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise);
 cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
                                const long long *run_idx, double *piston = nullptr);
+// The same on another stream of the handle's device.
+cudaError_t lk_launch_residual_on(letkf_ctx *h, cudaStream_t stream, const void *truth,
+                                  double *resvar, const long long *run_idx, double *piston);
 cudaError_t lk_launch_basis_reset(letkf_ctx *h);   // warm-start eigenbases -> identity
 cudaError_t lk_setup_analysis(letkf_ctx *h);
 // FP32 analysis of width class cls, two columns per lane (letkf_pair.cu).

@@ -255,13 +255,18 @@ cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise) {
 
 cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
                                const long long *run_idx, double *piston) {
+  return lk_launch_residual_on(h, h->stream, truth, resvar, run_idx, piston);
+}
+
+cudaError_t lk_launch_residual_on(letkf_ctx *h, cudaStream_t stream, const void *truth,
+                                  double *resvar, const long long *run_idx, double *piston) {
   const dim3 grid(LK_RES_BLOCKS, h->n_inst);
   if (h->precision == 1)
-    residual_kernel<double><<<grid, 64, 0, h->stream>>>(h->d_inst, h->n_pts_total,
+    residual_kernel<double><<<grid, 64, 0, stream>>>(h->d_inst, h->n_pts_total,
                                                          (const double *)truth, run_idx, h->partial,
                                                          h->tickets, h->n_inst, resvar, piston);
   else
-    residual_kernel<float><<<grid, 64, 0, h->stream>>>(h->d_inst, h->n_pts_total,
+    residual_kernel<float><<<grid, 64, 0, stream>>>(h->d_inst, h->n_pts_total,
                                                         (const float *)truth, run_idx, h->partial,
                                                         h->tickets, h->n_inst, resvar, piston);
   return cudaGetLastError();
