@@ -220,6 +220,8 @@ def small_configs_arm(torch, L, K: int = 500, Wm: int = 20):
         h, s = f.h, f.stream
         f.set_state(X0)
         f.run(Wm, y, t, use_graph=False)
+        from paper_1408_7069_gb300 import autotune
+        tune = autotune.tune(f, y[Wm].contiguous(), [(w.nsub, w.m, w.window)], reps=3)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(K)]
         torch.cuda.synchronize()
@@ -244,6 +246,7 @@ def small_configs_arm(torch, L, K: int = 500, Wm: int = 20):
         f.sync()
         out[w.name] = {"n_pts": int(f.n_pts), "m": w.m, "window": w.window,
                        "dtype": "f32" if w.precision == 0 else "f64",
+                       "tile_shape": tune.get("tiles"),
                        "frames_per_s": K / (sum(ms) / 1e3), "p50_us": 1e3 * percentile(ms, 50),
                        "p99_us": 1e3 * percentile(ms, 99),
                        "graph_frames_per_s": K / (g0.elapsed_time(g1) / 1e3)}

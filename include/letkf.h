@@ -234,8 +234,11 @@ letkf_status letkf_grad(letkf_t h, int32_t frames, const void *y_seq_dev, const 
  * mix of instances. letkf_tile_shape describes compiled shape number `shape`
  * (0 .. count-1; LETKF_ERR_ARG beyond). Instances are grouped in width classes
  * by ensemble size: 0 for m <= 16, 1 for m <= 32, 2 for m <= 64 (one node per
- * warp, tiles of at most 8 nodes, no FP64 fallback). letkf_set_tile_shape selects
- * a shape for one class; letkf_autotune times every shape for every class
+ * warp, tiles of at most 8 nodes, no FP64 fallback). On FP32 handles a tile
+ * holds whole warps of nodes (a multiple of 4 nodes in class 0, of 2 in class
+ * 1); a shape a class cannot take gives LETKF_ERR_ARG. New FP32 handles start
+ * at shape 0 (2 x 4), FP64 handles at one node per tile. letkf_set_tile_shape
+ * selects a shape for one class; letkf_autotune times every allowed shape for every class
  * present on the handle's current ensemble with slopes y_dev (reps timed
  * analyses of that class's nodes each, state restored afterwards; tune on a
  * loop state, not on a fresh prior draw whose nodes mostly take the FP64

@@ -28,11 +28,6 @@
 
 #include "letkf_device.cuh"
 
-// Tile shapes (nodes per CTA side) the autotuner chooses from; each divides
-// LK_TILE_MAX so the padded grid covers every tile's halo.
-#define LK_FOR_SHAPES(X) X(0, 2, 4) X(1, 4, 4) X(2, 2, 2) X(3, 1, 8)
-constexpr int LK_NUM_SHAPES = 4;
-
 namespace {
 
 constexpr int LIST_WARPS = 1;

@@ -255,6 +255,8 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   h->cfg = h->cfgs[0];
   h->stream = (cudaStream_t)stream;
   h->precision = cfgs[0].precision;
+  if (h->precision == 1)
+    for (int &t : h->tile_shape) t = LK_SHAPE_FP64_DEFAULT;
   h->rsz = h->precision ? sizeof(double) : sizeof(float);
   h->max_sweeps = cfgs[0].max_sweeps > 0 ? cfgs[0].max_sweeps : 20;
   h->fp64_kappa = cfgs[0].fp64_kappa;
@@ -739,8 +741,10 @@ letkf_status letkf_set_tile_shape(letkf_t h, int32_t width_class, int32_t shape)
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
   if (width_class < 0 || width_class > 2 || shape < 0 || shape >= lk_num_tile_shapes())
     return fail(h, LETKF_ERR_ARG, "width class or tile shape out of range");
-  if (!lk_pair_shape_ok(width_class, shape))
-    return fail(h, LETKF_ERR_ARG, "ensembles of 33..64 members take tiles of at most 8 nodes");
+  if (!lk_shape_ok(h, width_class, shape))
+    return fail(h, LETKF_ERR_ARG,
+                "FP32 tiles hold whole warps of nodes (4 per warp for m <= 16, 2 for m <= 32) "
+                "and ensembles of 33..64 members at most 8 nodes");
   DeviceGuard dg(h->device);
   LK_CUDA(h, cudaStreamSynchronize(h->stream));
   h->tile_shape[width_class] = shape;
@@ -781,7 +785,7 @@ letkf_status letkf_autotune(letkf_t h, const void *y_dev, int32_t reps, int32_t 
     int best = h->tile_shape[cls];
     float best_ms = 1e30f;
     for (int s = 0; s < ns && e == cudaSuccess && st == LETKF_OK; ++s) {
-      if (!lk_pair_shape_ok(cls, s)) continue;
+      if (!lk_shape_ok(h, cls, s)) continue;
       h->tile_shape[cls] = s;
       st = rebuild_tiles(h, cls);
       float total = 0.f;

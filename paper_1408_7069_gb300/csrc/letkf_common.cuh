@@ -23,6 +23,14 @@ constexpr int LK_TILE_J = 4;
 // Padding of the slope-anomaly grid: tiles up to this many nodes per side keep
 // their halo in bounds.
 constexpr int LK_TILE_MAX = 8;
+// The compiled analysis tile shapes (id, TI, TJ: nodes per CTA side), for the
+// FP32 pair kernel and the FP64 tile kernel alike; letkf_tile_shape enumerates
+// them. Each side divides LK_TILE_MAX, so the padded grid covers every halo.
+#define LK_FOR_SHAPES(X) X(0, 2, 4) X(1, 4, 4) X(2, 2, 2) X(3, 1, 8) X(4, 1, 2) X(5, 1, 1)
+constexpr int LK_NUM_SHAPES = 6;
+// Default shape of FP64 handles: one node per CTA, which spreads the nodes
+// over the most SMs (their FP64 rate, not the halo reuse, bounds the analysis).
+constexpr int LK_SHAPE_FP64_DEFAULT = 5;
 // CTAs of the residual reduction per instance (fixed, so the sum order is fixed).
 constexpr int LK_RES_BLOCKS = 128;
 // Stop cosine of the FP64 sweeps that start from a stored FP32 eigenbasis
@@ -147,7 +155,10 @@ cudaError_t lk_setup_analysis(letkf_ctx *h);
 // FP32 analysis of width class cls, two columns per lane (letkf_pair.cu).
 cudaError_t lk_launch_pair(letkf_ctx *h, int cls, void *mean, void *spread);
 cudaError_t lk_setup_pair(letkf_ctx *h);
-bool lk_pair_shape_ok(int cls, int shape);   // class 2 (one node per warp): at most 8 nodes per tile
+// Whether width class cls of the handle can take tile shape `shape`: FP32
+// handles need whole warps of nodes and, in class 2 (one node per warp), at
+// most 8 nodes per tile.
+bool lk_shape_ok(const letkf_ctx *h, int cls, int shape);
 int lk_num_tile_shapes();
 void lk_tile_shape(int s, int *ti, int *tj);
 int lk_width_class(int m);          // 0: m <= 16, 1: m <= 32, 2: m <= 64

@@ -35,8 +35,6 @@
 
 #include "letkf_device.cuh"
 
-#define LK_PAIR_SHAPES(X) X(0, 2, 4) X(1, 4, 4) X(2, 2, 2) X(3, 1, 8)
-
 namespace {
 
 template <int MP>
@@ -485,11 +483,12 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
   }
 }
 
-// Wide problems (one node per warp) take tiles of at most 8 nodes: a 16-warp
-// CTA would leave fewer registers per thread than the two columns need.
+// A tile fills whole warps (its node count is a multiple of the nodes per
+// warp), and wide problems (one node per warp) take tiles of at most 8 nodes:
+// a 16-warp CTA would leave fewer registers per thread than the two columns need.
 template <int MP, int TI, int TJ>
 constexpr bool shape_ok() {
-  return PairCfg<MP>::NPW > 1 || TI * TJ <= 8;
+  return (TI * TJ) % PairCfg<MP>::NPW == 0 && (PairCfg<MP>::NPW > 1 || TI * TJ <= 8);
 }
 
 template <int MP, int TI, int TJ>
@@ -522,7 +521,7 @@ cudaError_t launch_mp(letkf_ctx *h, int cls, const LkTile *tiles, int n_tiles, f
 #define LK_CASE(id, ti, tj) \
   case id:                  \
     return launch_shape<MP, ti, tj>(h, tiles, n_tiles, mean, spread, kthr, queue, wl);
-    LK_PAIR_SHAPES(LK_CASE)
+    LK_FOR_SHAPES(LK_CASE)
 #undef LK_CASE
   }
   return cudaErrorInvalidValue;
@@ -548,7 +547,7 @@ cudaError_t setup_mp(letkf_ctx *h) {
   cudaError_t e = cudaSuccess;
 #define LK_SET(id, ti, tj) \
   if (e == cudaSuccess) e = set_shape_smem<MP, ti, tj>(wmax);
-  LK_PAIR_SHAPES(LK_SET)
+  LK_FOR_SHAPES(LK_SET)
 #undef LK_SET
   return e;
 }
@@ -568,10 +567,15 @@ cudaError_t lk_launch_pair(letkf_ctx *h, int cls, void *mean, void *spread) {
   return e;
 }
 
-bool lk_pair_shape_ok(int cls, int shape) {
+bool lk_shape_ok(const letkf_ctx *h, int cls, int shape) {
   int ti, tj;
   lk_tile_shape(shape, &ti, &tj);
-  return cls < 2 || ti * tj <= 8;
+  if (h->precision == 1) return true;     // FP64 tile kernel: one warp per node
+  switch (cls) {
+    case 0: return (ti * tj) % PairCfg<16>::NPW == 0;
+    case 1: return (ti * tj) % PairCfg<32>::NPW == 0;
+    default: return ti * tj <= 8;
+  }
 }
 
 cudaError_t lk_setup_pair(letkf_ctx *h) {

@@ -67,8 +67,13 @@ def _run_batch(frames, tile=None, autotune=False):
     t = torch.from_numpy(np.concatenate([i.truth.astype(np.float32) for i, _ in ins], 1)).cuda()
     f.set_state(torch.from_numpy(X0).cuda())
     if tile is not None:
-        for cls in (0, 1):
-            f.set_tile_shape(cls, tile)
+        ti, tj = L.tile_shapes()[tile]
+        for cls, per_warp in ((0, 4), (1, 2)):       # nodes per warp of the FP32 kernel
+            if (ti * tj) % per_warp == 0:
+                f.set_tile_shape(cls, tile)
+            else:                                     # a tile must fill whole warps
+                with pytest.raises(L.LetkfError, match="LETKF_ERR_ARG"):
+                    f.set_tile_shape(cls, tile)
     if autotune:
         shapes, us = f.autotune(y[0].contiguous(), reps=2)
         assert all(0 <= s < len(L.tile_shapes()) for s in shapes)
