@@ -69,7 +69,9 @@ struct LkAdjWork {
 
 namespace {
 
-constexpr int ADJ_WARPS = 4;
+// One warp per CTA: the node kernels are bound by their SM's FP64 and dependency
+// latency, so the nodes are spread over as many SMs as possible.
+constexpr int ADJ_WARPS = 1;
 
 // Per-warp vector slots in shared memory (MP elements each).
 enum { S_LAM, S_B, S_XP0, S_XP1, S_G0, S_G1, S_Z, S_WB, S_GX0, S_GX1, S_H0, S_H1, S_WBB, S_Q, S_BB,
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
 // window holds (s, t) wrote, in a fixed order (node row, then column), into the
 // padded grid. The candidate nodes are looked up 32 at a time, one per lane,
 // so that the loads of their adjoints do not wait on one another.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(LK_WARP_CTA)
     adjoint_subap_kernel(const LkInst *__restrict__ insts, const double *__restrict__ ybw,
                          const double *__restrict__ dbw, double *__restrict__ ybar,
                          double *__restrict__ dbar) {
@@ -426,7 +428,7 @@ __global__ void __launch_bounds__(256)
 // the criterion's gradient, then the adjoint of the forecast
 // x_{k+1} = A1 x_{k/k} + v (row 0 <- a row 0 + row 1, row 1 <- 0).
 template <typename S>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(LK_WARP_CTA)
     adjoint_gather_kernel(const LkInst *__restrict__ insts, const double *__restrict__ xp_bar,
                           const double *__restrict__ xbar_bar, const double *__restrict__ ybar,
                           const double *__restrict__ dbar, const S *__restrict__ truth,
@@ -707,18 +709,18 @@ cudaError_t backward_frame(letkf_ctx *h, LkAdjWork *W, const void *y_k, const vo
   e = I.mp == 16 ? launch_nodes<16>(h, W, bk, a) : launch_nodes<32>(h, W, bk, a);
   if (e != cudaSuccess) return e;
   theta_reduce_kernel<<<1, 256, 0, h->stream>>>(W->theta, I.n_pts, W->acc);
-  adjoint_subap_kernel<<<(I.n_sap * 32 + 255) / 256, 256, 0, h->stream>>>(h->d_inst, W->ybw,
-                                                                         W->dbw, W->ybar, W->dbar);
-  const int blocks = (int)(((long long)I.n_pts * 32 + 255) / 256);
+  adjoint_subap_kernel<<<(I.n_sap * 32 + LK_WARP_CTA - 1) / LK_WARP_CTA, LK_WARP_CTA, 0,
+                         h->stream>>>(h->d_inst, W->ybw, W->dbw, W->ybar, W->dbar);
+  const int blocks = (int)(((long long)I.n_pts * 32 + LK_WARP_CTA - 1) / LK_WARP_CTA);
   // the piston of the frame's residual (acc[3]; its variance goes to acc[4])
   e = lk_launch_residual(h, truth_k, W->acc + 4, nullptr, W->acc + 3);
   if (e != cudaSuccess) return e;
   if (h->precision == 1) {
-    adjoint_gather_kernel<double><<<blocks, 256, 0, h->stream>>>(
+    adjoint_gather_kernel<double><<<blocks, LK_WARP_CTA, 0, h->stream>>>(
         h->d_inst, W->xp_bar, W->xbar_bar, W->ybar, W->dbar, (const double *)truth_k, W->acc + 3,
         crit_scale, lam_out);
   } else {
-    adjoint_gather_kernel<float><<<blocks, 256, 0, h->stream>>>(
+    adjoint_gather_kernel<float><<<blocks, LK_WARP_CTA, 0, h->stream>>>(
         h->d_inst, W->xp_bar, W->xbar_bar, W->ybar, W->dbar, (const float *)truth_k, W->acc + 3,
         crit_scale, lam_out);
   }

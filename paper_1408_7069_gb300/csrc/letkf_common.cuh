@@ -33,6 +33,9 @@ constexpr int LK_NUM_SHAPES = 6;
 constexpr int LK_SHAPE_FP64_DEFAULT = 5;
 // CTAs of the residual reduction per instance (fixed, so the sum order is fixed).
 constexpr int LK_RES_BLOCKS = 128;
+// Threads per CTA of the warp-per-item kernels (observation, forecast, reverse
+// gathers): small CTAs spread a 16 m system's few hundred items over all SMs.
+constexpr int LK_WARP_CTA = 64;
 // Stop cosine of the FP64 sweeps that start from a stored FP32 eigenbasis
 // (queued nodes of FP32 handles): the next sweep would rotate by about its
 // square, far below what the FP32 outputs resolve.

@@ -13,7 +13,7 @@ namespace {
 // (Appendix B) into the padded grid cell (s+h, t+h), and the innovation
 // d = y - D1 xbar (Section 3.1.1, with the correction known exactly).
 template <typename S>
-__global__ void __launch_bounds__(256) obs_kernel(const LkInst *__restrict__ insts,
+__global__ void __launch_bounds__(LK_WARP_CTA) obs_kernel(const LkInst *__restrict__ insts,
                                                   const int2 *__restrict__ items, long long n_items,
                                                   long long p_total, const S *__restrict__ y,
                                                   const long long *__restrict__ run_idx,
@@ -101,7 +101,7 @@ __device__ __forceinline__ void forecast_node(const LkInst *__restrict__ insts, 
 // phi_k -> row 1 (Section 2.2, A1 = [[a I, 0], [I, 0]]; Section 3.1.2, Eq. Mem_pre).
 // v is the caller's noise, or a bank screen chosen per member by SplitMix64.
 template <typename S>
-__global__ void __launch_bounds__(256) forecast_kernel(const LkInst *__restrict__ insts,
+__global__ void __launch_bounds__(LK_WARP_CTA) forecast_kernel(const LkInst *__restrict__ insts,
                                                        const int2 *__restrict__ items,
                                                        long long n_items, const S *__restrict__ noise,
                                                        long long *__restrict__ frame,
@@ -222,7 +222,9 @@ __global__ void basis_reset_kernel(const LkInst *__restrict__ insts) {
 }
 
 
-int warp_blocks(long long warps) { return (int)((warps * 32 + 255) / 256); }
+int warp_blocks(long long warps) {
+  return (int)((warps * 32 + LK_WARP_CTA - 1) / LK_WARP_CTA);
+}
 
 }  // namespace
 
@@ -230,11 +232,11 @@ cudaError_t lk_launch_obs(letkf_ctx *h, const void *y, const long long *run_idx)
   if (h->sap_total == 0) return cudaSuccess;
   const int blocks = warp_blocks(h->sap_total);
   if (h->precision == 1)
-    obs_kernel<double><<<blocks, 256, 0, h->stream>>>(h->d_inst, h->obs_items, h->sap_total,
+    obs_kernel<double><<<blocks, LK_WARP_CTA, 0, h->stream>>>(h->d_inst, h->obs_items, h->sap_total,
                                                       h->p_total, (const double *)y, run_idx,
                                                       h->counters);
   else
-    obs_kernel<float><<<blocks, 256, 0, h->stream>>>(h->d_inst, h->obs_items, h->sap_total,
+    obs_kernel<float><<<blocks, LK_WARP_CTA, 0, h->stream>>>(h->d_inst, h->obs_items, h->sap_total,
                                                      h->p_total, (const float *)y, run_idx,
                                                      h->counters);
   return cudaGetLastError();
@@ -244,11 +246,11 @@ cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise) {
   const int blocks = warp_blocks(h->n_pts_total);
   int *ticket = h->tickets + h->n_inst;
   if (h->precision == 1)
-    forecast_kernel<double><<<blocks, 256, 0, h->stream>>>(h->d_inst, h->node_items,
+    forecast_kernel<double><<<blocks, LK_WARP_CTA, 0, h->stream>>>(h->d_inst, h->node_items,
                                                            h->n_pts_total, (const double *)noise,
                                                            h->frame, ticket);
   else
-    forecast_kernel<float><<<blocks, 256, 0, h->stream>>>(h->d_inst, h->node_items, h->n_pts_total,
+    forecast_kernel<float><<<blocks, LK_WARP_CTA, 0, h->stream>>>(h->d_inst, h->node_items, h->n_pts_total,
                                                           (const float *)noise, h->frame, ticket);
   return cudaGetLastError();
 }
