@@ -70,6 +70,20 @@ def percentile(xs, q):
     return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
 
 
+def make_reduce_max(world: int, device: str):
+    """Max over the ranks of a per-rank float (all_reduce MAX of a one-element
+    FP64 tensor on `device`: "cuda" under NCCL, "cpu" under gloo)."""
+    def reduce_max(x: float) -> float:
+        if world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+    return reduce_max
+
+
 def combine(total_s_local: float, steps: int, world: int, reduce_max) -> dict:
     """Whole-job throughput: every rank processes `steps` frames of its own
     instance; the job time is the slowest rank's."""
@@ -499,13 +513,7 @@ def gpu_arm(args):
     ana_ms = [e[1].elapsed_time(e[2]) for e in ev]
     total_s = sum(frame_ms) / 1e3
 
-    def reduce_max(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
-
+    reduce_max = make_reduce_max(world, "cuda")
     agg = combine(total_s, K, world, reduce_max)
 
     # graph-captured loop over the same frames (state resident in L2, no flush)
