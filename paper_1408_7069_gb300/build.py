@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libletkf.so")
-SOURCES = ["letkf_api.cu", "letkf_kernels.cu", "letkf_analysis.cu", "letkf_adjoint.cu", "letkf_pair.cu"]
+SOURCES = ["letkf_api.cu", "letkf_kernels.cu", "letkf_analysis.cu", "letkf_adjoint.cu", "letkf_pair.cu",
+           "letkf_node64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -400,11 +400,10 @@ cudaError_t launch_list(letkf_ctx *h, int cls, void *mean, void *spread) {
 template <int MP>
 cudaError_t launch_class(letkf_ctx *h, int cls, void *mean, void *spread) {
   if (h->n_tiles[cls] == 0) return cudaSuccess;
-  if (h->precision == 1)
-    return launch_tile<MP, double, double>(h, cls, mean, spread, h->tol64, 0.0);
+  if (h->precision == 1) return lk_launch_node64(h, cls, mean, spread);
   cudaError_t e = lk_launch_pair(h, cls, mean, spread);
   if (e != cudaSuccess || h->fp64_kappa <= 0 || MP > 32) return e;
-  return launch_list<MP>(h, cls, mean, spread);
+  return lk_launch_list64(h, cls, mean, spread);
 }
 
 template <int MP, typename S, typename T, int TI, int TJ>

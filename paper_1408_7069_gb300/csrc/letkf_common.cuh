@@ -158,6 +158,12 @@ cudaError_t lk_setup_analysis(letkf_ctx *h);
 // FP32 analysis of width class cls, two columns per lane (letkf_pair.cu).
 cudaError_t lk_launch_pair(letkf_ctx *h, int cls, void *mean, void *spread);
 cudaError_t lk_setup_pair(letkf_ctx *h);
+// FP64 analysis with one CTA of four warps per node (letkf_node64.cu): every
+// node of width class cls (0: MP 16, 1: MP 32) of an FP64 handle, or the nodes
+// the pair kernel queued in class cls of an FP32 handle.
+cudaError_t lk_launch_node64(letkf_ctx *h, int cls, void *mean, void *spread);
+cudaError_t lk_launch_list64(letkf_ctx *h, int cls, void *mean, void *spread);
+
 // Whether width class cls of the handle can take tile shape `shape`: FP32
 // handles need whole warps of nodes and, in class 2 (one node per warp), at
 // most 8 nodes per tile.
