@@ -227,24 +227,25 @@ letkf_status letkf_step(letkf_t h, const void *y_host, const void *truth_host, v
 letkf_status letkf_grad(letkf_t h, int32_t frames, const void *y_seq_dev, const void *truth_seq_dev,
                         int32_t ckpt_every, double *J_out, double *grad_out);
 
-/* Analysis tile shapes. The analysis runs one CTA per tile of tile_i x tile_j
- * nodes (4, 2 or 1 nodes per warp for m <= 16, <= 32 and larger; FP64 handles
- * one node per warp) and stages the tile's window halo in shared
- * memory once; the best shape depends on the window, the ensemble size and the
+/* Analysis tile shapes. On FP32 handles the analysis runs one CTA per tile of
+ * tile_i x tile_j nodes (4, 2 or 1 nodes per warp for m <= 16, <= 32 and
+ * larger) and stages the tile's window halo in shared memory once (FP64
+ * handles run one CTA of four warps per node and ignore the shapes); the best shape depends on the window, the ensemble size and the
  * mix of instances. letkf_tile_shape describes compiled shape number `shape`
  * (0 .. count-1; LETKF_ERR_ARG beyond). Instances are grouped in width classes
  * by ensemble size: 0 for m <= 16, 1 for m <= 32, 2 for m <= 64 (one node per
  * warp, tiles of at most 8 nodes, no FP64 fallback). On FP32 handles a tile
  * holds whole warps of nodes (a multiple of 4 nodes in class 0, of 2 in class
- * 1); a shape a class cannot take gives LETKF_ERR_ARG. New FP32 handles start
- * at shape 0 (2 x 4), FP64 handles at one node per tile. letkf_set_tile_shape
+ * 1); a shape a class cannot take gives LETKF_ERR_ARG. New handles start at
+ * shape 0 (2 x 4). letkf_set_tile_shape
  * selects a shape for one class; letkf_autotune times every allowed shape for every class
  * present on the handle's current ensemble with slopes y_dev (reps timed
  * analyses of that class's nodes each, state restored afterwards; tune on a
  * loop state, not on a fresh prior draw whose nodes mostly take the FP64
  * path), keeps the fastest and writes the
  * choices to shapes_out[3] and their analysis time in microseconds to us_out[3]
- * (either may be NULL). Both synchronise; choices may be cached by the caller
+ * (either may be NULL; on FP64 handles it times nothing, returns the current
+ * shapes and zero times). Both synchronise; choices may be cached by the caller
  * and restored with letkf_set_tile_shape. */
 letkf_status letkf_tile_shape(int32_t shape, int32_t *tile_i, int32_t *tile_j);
 letkf_status letkf_set_tile_shape(letkf_t h, int32_t width_class, int32_t shape);

@@ -1,25 +1,26 @@
-// Local ensemble transform analysis (Section 4.2 with Section 3.1 and Appendix A).
+// Local ensemble transform analysis (Section 4.2 with Section 3.1 and Appendix A):
+// the per-width-class dispatch of letkf_analyze, and the allocation-free
+// analysis of letkf_analyze_noalloc.
 //
-// One warp analyses one node. A CTA owns a tile of LK_TILE_I x LK_TILE_J nodes
-// and stages the (tile + window - 1)^2 halo of slope anomalies and innovations
-// in shared memory once; every warp then reads its own w x w window from it.
-//
-// Per node, with lane l standing for member / column l of the m x m problem
-// (zero-padded to MP = 16 or 32 columns, identity on the padding):
+// Per node, with column l of the m x m problem zero-padded to MP = 16 or 32
+// columns (identity on the padding):
 //   Gram     A = (m-1)/rho I + sum_j tau_j/sigma2 Yb_j Yb_j^T,  C d = sum_j tau_j/sigma2 d_j Yb_j
 //   EVD      one-sided (Hestenes) Jacobi on the columns of B = A V0: rotations J make
-//            the columns of B J orthogonal, so A (V0 J) = (V0 J) Lambda. Pairs follow
-//            the xor tournament (step t pairs column l with l ^ t: a perfect matching
-//            for every t in 1..MP-1, all pairs once per sweep).
+//            the columns of B J orthogonal, so A (V0 J) = (V0 J) Lambda
 //   weights  wbar = V Lambda^-1 V^T C d,  W = V ((m-1) Lambda^-1)^(1/2) V^T
 //   apply    Xa_r = xbar_r + X'_r wbar + X'_r W for the node's two rows
 //
 // FP32 handles run the analysis in letkf_pair.cu (two columns per lane). Nodes
 // whose kappa_hat = 1 + rho tr(G)/(m-1) exceeds the threshold still take that
 // FP32 eigensolve, but their mean solve wbar = A^-1 C d would amplify the FP32
-// Gram's rounding by kappa: they are queued, and the list kernel here redoes
-// them in FP64 (Gram and sweep), the sweep started from the FP32 eigenbasis.
-// FP64 handles run the tile kernel below (one warp per node, accumulated V).
+// Gram's rounding by kappa: they are queued and redone in FP64 (Gram and
+// sweep, started from the FP32 eigenbasis) by letkf_node64.cu, which also
+// analyses every node of FP64 handles (one CTA of four warps per node).
+//
+// The allocation-free analysis below keeps the earlier tile layout: one warp
+// per node (lane = column, eigenvectors accumulated from the identity, pairs
+// by the xor tournament: step t pairs column l with l ^ t), a CTA per tile of
+// nodes staging the tile's window halo in shared memory once.
 #include <math.h>
 #include <stdio.h>
 
@@ -30,21 +31,6 @@
 
 namespace {
 
-constexpr int LIST_WARPS = 1;
-constexpr int LIST_CTAS_PER_SM = 8;
-
-// SM count of a device, cached (read once per device).
-int lk_sm_count(int device) {
-  static int cache[64] = {0};
-  const int d = device >= 0 && device < 64 ? device : 0;
-  if (cache[d] == 0) {
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0)
-      n = 1;
-    cache[d] = n;
-  }
-  return cache[d];
-}
 // Per-warp scratch: V staging [MP][MP+1] + 3 vectors, or A staging [MP][MP+4].
 template <int MP, typename T>
 __host__ __device__ constexpr size_t scratch_elems() {
@@ -66,21 +52,6 @@ __host__ __device__ TileLayout tile_layout(int w) {
   L.scr = align16(L.tap + (size_t)w * w * sizeof(T));
   L.total = L.scr + (size_t)TI * TJ * scratch_elems<MP, T>() * sizeof(T);
   return L;
-}
-
-// Shared-memory layout of one warp of the FP64 list kernel: window, innovations,
-// taper, then the scratch of A and V staging ([MP][MP+1] each, FP64), reused
-// by transform_apply.
-template <int MP>
-__host__ __device__ constexpr size_t refine_scratch_elems() {
-  return 2 * (size_t)MP * (MP + 1) > scratch_elems<MP, double>() ? 2 * (size_t)MP * (MP + 1)
-                                                                  : scratch_elems<MP, double>();
-}
-template <int MP>
-__host__ __device__ size_t list_warp_bytes(int w) {
-  const size_t wc = (size_t)w * w;
-  return align16(wc * 2 * MP * sizeof(float)) + align16(wc * 2 * sizeof(float)) +
-         align16(wc * sizeof(double)) + refine_scratch_elems<MP>() * sizeof(double);
 }
 
 // wbar, W from the eigenpairs (lane j: eigenvector column v, eigenvalue lam) and
@@ -232,171 +203,9 @@ __device__ __forceinline__ void stage_tile(const LkInst &I, int i0, int j0, S *h
   for (int e = threadIdx.x; e < w * w; e += blockDim.x) tap[e] = T(taper[e]);
 }
 
-// One CTA per tile of TI x TJ nodes of one instance, one warp per node.
-template <int MP, typename S, typename T, int TI, int TJ>
-__global__ void __launch_bounds__(TI *TJ * 32)
-    analysis_tile_kernel(const LkInst *__restrict__ insts, const LkTile *__restrict__ tiles,
-                         S *__restrict__ mean, S *__restrict__ spread, T tol, int max_sweeps,
-                         T kappa_thr, int *__restrict__ counters, int2 *__restrict__ worklist) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const LkTile tl = tiles[blockIdx.x];
-  const LkInst &I = insts[tl.inst];
-  const int w = I.w;
-  const TileLayout L = tile_layout<MP, S, T, TI, TJ>(w);
-  const int HJ = TJ + w - 1;
-  S *halo = reinterpret_cast<S *>(smem + L.halo);
-  S *dh = reinterpret_cast<S *>(smem + L.dh);
-  T *tap = reinterpret_cast<T *>(smem + L.tap);
-  T *scr = reinterpret_cast<T *>(smem + L.scr);
-  stage_tile<MP, S, T, TI, TJ>(I, tl.i0, tl.j0, halo, dh, tap);
-  __syncthreads();
-  const int warp = threadIdx.x >> 5;
-  const int ti = warp / TJ, tj = warp - (warp / TJ) * TJ;
-  const int i = tl.i0 + ti, j = tl.j0 + tj;
-  if (i > I.nsub || j > I.nsub) return;
-  const int pid = I.pid_map[i * (I.nsub + 1) + j];
-  if (pid < 0) return;
-  const int off = ti * HJ + tj;
-  const int m = I.m;
-  S *xrow = static_cast<S *>(I.X) + (size_t)pid * 2 * m;
-  S *mo = mean ? mean + 2 * (I.node_off + pid) : nullptr;
-  S *so = spread ? spread + 2 * (I.node_off + pid) : nullptr;
-  T *wscr = scr + (size_t)warp * scratch_elems<MP, T>();
-  analyze_node_accum<MP, S, T>(halo + (size_t)off * 2 * MP, dh + off * 2, HJ, tap, w, m,
-                               T(I.alpha), tol, max_sweeps, xrow, mo, so, wscr, counters, nullptr);
-}
-
-// FP64 analysis of one node whose kappa_hat sent it here (FP32 handles), one
-// warp, lane = column. A and C d are formed in FP64 from the node's window and
-// the FP64 sweep of the tile kernel (accumulated V) is started from the FP32
-// eigenbasis the pair kernel stored for the node instead of the identity:
-// V is made orthonormal in FP64 and the sweep starts from B = A V (warm_basis).
-// V diagonalises A up to O(eps32 kappa), so the quadratically convergent sweeps
-// stop after two or three (at the first sweep whose cosines all stay below
-// LK_WARM_STOP64) instead of the eight to ten of a cold start.
-// The result is the FP64 analysis: the same eigenpairs, hence the same wbar and
-// W up to FP64 rounding, written as by the pair kernel.
-template <int MP>
-__device__ __forceinline__ void warm_node(const float *__restrict__ win,
-                                          const float *__restrict__ dwin,
-                                          const double *__restrict__ tap, int w, int m,
-                                          double alpha, double tol, int max_sweeps,
-                                          float *__restrict__ xrow, float *__restrict__ mean_out,
-                                          float *__restrict__ spread_out, double *__restrict__ scr,
-                                          const float *__restrict__ U, int *__restrict__ counters) {
-  const int lane = threadIdx.x & 31;
-  double b[MP], diag, cd, v[MP];
-  gram<MP, float, double>(win, dwin, w, tap, w, m, alpha, b, diag, cd);
-  warm_basis<MP, double>(b, v, U, scr, scr + MP * (MP + 1));
-  jacobi<MP, double, true>(b, v, tol, max_sweeps, counters, LK_WARM_STOP64);
-  const double nrm = dot4<MP, double>(b, b);
-  const double lam = (lane < MP && nrm > 0.0) ? sqrt(nrm) : 1.0;   // |A v_j| = lambda_j
-  transform_apply<MP, float, double>(v, lam, cd, m, xrow, mean_out, spread_out, scr, counters);
-}
-
-// The queued nodes (FP32 handles): one warp per node, window staged per warp
-// from the padded grid, then warm_node. A fixed grid of a few CTAs per SM walks
-// the queue, so that the launch costs little when the queue is empty (the
-// steady state).
-template <int MP>
-__global__ void __launch_bounds__(LIST_WARPS * 32)
-    analysis_list_kernel(const LkInst *__restrict__ insts, const int2 *__restrict__ worklist,
-                         const int *__restrict__ queue_len, float *__restrict__ mean,
-                         float *__restrict__ spread, double tol, int max_sweeps,
-                         int *__restrict__ counters, int wmax) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int qn = *queue_len;
-  for (int idx = blockIdx.x * LIST_WARPS + warp; idx < qn; idx += gridDim.x * LIST_WARPS) {
-    const int2 it = worklist[idx];
-    const LkInst &I = insts[it.x];
-    const int w = I.w, wc = w * w, m = I.m;
-    // every warp's region has the size for the class's widest window, whatever
-    // the window of the instance it serves
-    unsigned char *base = smem + (size_t)warp * list_warp_bytes<MP>(wmax);
-    float *win = reinterpret_cast<float *>(base);
-    float *dwin = reinterpret_cast<float *>(base + align16((size_t)wc * 2 * MP * sizeof(float)));
-    double *tap = reinterpret_cast<double *>(base + align16((size_t)wc * 2 * MP * sizeof(float)) +
-                                             align16((size_t)wc * 2 * sizeof(float)));
-    double *scr = tap + align16((size_t)wc * sizeof(double)) / sizeof(double);
-    const int pid = it.y;
-    const int2 ij = I.pts[pid];
-    const float *Ybp = static_cast<const float *>(I.Ybp);
-    const float *dp = static_cast<const float *>(I.dp);
-    const float *taper = static_cast<const float *>(I.taper);
-    for (int e = lane; e < wc * 2 * MP; e += 32) {
-      const int cell = e / (2 * MP);
-      const int r = e - cell * 2 * MP;
-      const int c = r / MP;
-      const int mm = r - c * MP;
-      const int ds = cell / w, dt = cell - (cell / w) * w;
-      const size_t src = (size_t)(ij.x + ds) * I.gs_cols + (ij.y + dt);
-      win[e] = mm < m ? Ybp[(src * 2 + c) * m + mm] : 0.f;
-    }
-    for (int e = lane; e < wc * 2; e += 32) {
-      const int cell = e >> 1;
-      const int ds = cell / w, dt = cell - (cell / w) * w;
-      const size_t src = (size_t)(ij.x + ds) * I.gs_cols + (ij.y + dt);
-      dwin[e] = dp[src * 2 + (e & 1)];
-    }
-    for (int e = lane; e < wc; e += 32) tap[e] = (double)taper[e];
-    __syncwarp();
-    warm_node<MP>(win, dwin, tap, w, m, I.alpha, tol, max_sweeps,
-                  static_cast<float *>(I.X) + (size_t)pid * 2 * m,
-                  mean ? mean + 2 * (I.node_off + pid) : nullptr,
-                  spread ? spread + 2 * (I.node_off + pid) : nullptr, scr,
-                  I.basis + (size_t)pid * MP * MP, counters);
-    __syncwarp();
-  }
-}
-
-template <int MP, typename S, typename T, int TI, int TJ>
-cudaError_t launch_tile_shape(letkf_ctx *h, int cls, void *mean, void *spread, T tol, T kthr) {
-  size_t need = 0;
-  for (const LkInst &I : h->inst)
-    if (I.mp == MP) {
-      const size_t b = tile_layout<MP, S, T, TI, TJ>(I.w).total;
-      need = b > need ? b : need;
-    }
-  analysis_tile_kernel<MP, S, T, TI, TJ><<<h->n_tiles[cls], TI * TJ * 32, need, h->stream>>>(
-      h->d_inst, h->tiles[cls], (S *)mean, (S *)spread, tol, h->max_sweeps, kthr, h->counters,
-      h->worklist + (size_t)cls * h->n_pts_total);
-  return cudaGetLastError();
-}
-
-template <int MP, typename S, typename T>
-cudaError_t launch_tile(letkf_ctx *h, int cls, void *mean, void *spread, T tol, T kthr) {
-  switch (h->tile_shape[cls]) {
-#define LK_CASE(id, ti, tj) \
-  case id:                  \
-    return launch_tile_shape<MP, S, T, ti, tj>(h, cls, mean, spread, tol, kthr);
-    LK_FOR_SHAPES(LK_CASE)
-#undef LK_CASE
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <int MP>
-cudaError_t launch_list(letkf_ctx *h, int cls, void *mean, void *spread) {
-  int wmax = 1;
-  for (const LkInst &I : h->inst)
-    if (I.mp == MP) wmax = I.w > wmax ? I.w : wmax;
-  const size_t bytes = (size_t)LIST_WARPS * list_warp_bytes<MP>(wmax);
-  long long n = 0;
-  for (const LkInst &I : h->inst)
-    if (I.mp == MP) n += I.n_pts;
-  const long long want = (n + LIST_WARPS - 1) / LIST_WARPS;
-  const long long cap = (long long)LIST_CTAS_PER_SM * lk_sm_count(h->device);
-  const int blocks = (int)(want < cap ? want : cap);
-  analysis_list_kernel<MP><<<blocks, LIST_WARPS * 32, bytes, h->stream>>>(
-      h->d_inst, h->worklist + (size_t)cls * h->n_pts_total, h->counters + 4 + cls, (float *)mean,
-      (float *)spread, h->tol64, h->max_sweeps, h->counters, wmax);
-  return cudaGetLastError();
-}
-
-// One width class: FP64 handles run the tile kernel; FP32 handles the
-// two-columns-per-lane kernel (letkf_pair.cu), then, for MP <= 32, the FP64
-// re-analysis of the nodes it queued.
+// One width class: FP64 handles run one CTA per node (letkf_node64.cu); FP32
+// handles the two-columns-per-lane kernel (letkf_pair.cu), then, for MP <= 32,
+// the FP64 analysis of the nodes it queued.
 template <int MP>
 cudaError_t launch_class(letkf_ctx *h, int cls, void *mean, void *spread) {
   if (h->n_tiles[cls] == 0) return cudaSuccess;
@@ -404,33 +213,6 @@ cudaError_t launch_class(letkf_ctx *h, int cls, void *mean, void *spread) {
   cudaError_t e = lk_launch_pair(h, cls, mean, spread);
   if (e != cudaSuccess || h->fp64_kappa <= 0 || MP > 32) return e;
   return lk_launch_list64(h, cls, mean, spread);
-}
-
-template <int MP, typename S, typename T, int TI, int TJ>
-cudaError_t set_smem(int w) {
-  return cudaFuncSetAttribute(analysis_tile_kernel<MP, S, T, TI, TJ>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tile_layout<MP, S, T, TI, TJ>(w).total);
-}
-
-template <int MP>
-cudaError_t setup_class(letkf_ctx *h) {
-  int wmax = 0;
-  for (const LkInst &I : h->inst)
-    if (I.mp == MP) wmax = I.w > wmax ? I.w : wmax;
-  if (wmax == 0) return cudaSuccess;
-  cudaError_t e = cudaSuccess;
-  if (h->precision == 1) {
-#define LK_SET(id, ti, tj) \
-  if (e == cudaSuccess) e = set_smem<MP, double, double, ti, tj>(wmax);
-    LK_FOR_SHAPES(LK_SET)
-#undef LK_SET
-    return e;
-  }
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(analysis_list_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(LIST_WARPS * list_warp_bytes<MP>(wmax)));
-  return e;
 }
 
 }  // namespace
@@ -454,12 +236,7 @@ void lk_tile_shape(int s, int *ti, int *tj) {
 int lk_width_class(int m) { return m <= 16 ? 0 : (m <= 32 ? 1 : 2); }
 
 // Raises the dynamic shared-memory limit of the analysis kernels this handle uses.
-cudaError_t lk_setup_analysis(letkf_ctx *h) {
-  cudaError_t e = setup_class<16>(h);
-  if (e == cudaSuccess) e = setup_class<32>(h);
-  if (e == cudaSuccess) e = lk_setup_pair(h);
-  return e;
-}
+cudaError_t lk_setup_analysis(letkf_ctx *h) { return lk_setup_pair(h); }
 
 cudaError_t lk_launch_analysis_class(letkf_ctx *h, int cls, void *mean, void *spread) {
   cudaError_t e = cudaMemsetAsync(h->counters + 1, 0, 7 * sizeof(int), h->stream);

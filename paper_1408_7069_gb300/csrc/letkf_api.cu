@@ -255,8 +255,6 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   h->cfg = h->cfgs[0];
   h->stream = (cudaStream_t)stream;
   h->precision = cfgs[0].precision;
-  if (h->precision == 1)
-    for (int &t : h->tile_shape) t = LK_SHAPE_FP64_DEFAULT;
   h->rsz = h->precision ? sizeof(double) : sizeof(float);
   h->max_sweeps = cfgs[0].max_sweeps > 0 ? cfgs[0].max_sweeps : 20;
   h->fp64_kappa = cfgs[0].fp64_kappa;
@@ -757,6 +755,13 @@ letkf_status letkf_autotune(letkf_t h, const void *y_dev, int32_t reps, int32_t 
   if (!y_dev || reps < 1) return fail(h, LETKF_ERR_ARG, "y_dev and reps >= 1 are required");
   DeviceGuard dg(h->device);
   LK_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->precision == 1) {                 // one CTA per node: no tile shape to choose
+    for (int cls = 0; cls < 3; ++cls) {
+      if (shapes_out) shapes_out[cls] = h->tile_shape[cls];
+      if (us_out) us_out[cls] = 0.f;
+    }
+    return LETKF_OK;
+  }
   const int ns = lk_num_tile_shapes();
   // every timed analysis starts from the same ensemble and eigenbases
   size_t n_basis = 0;

@@ -28,9 +28,6 @@ constexpr int LK_TILE_MAX = 8;
 // them. Each side divides LK_TILE_MAX, so the padded grid covers every halo.
 #define LK_FOR_SHAPES(X) X(0, 2, 4) X(1, 4, 4) X(2, 2, 2) X(3, 1, 8) X(4, 1, 2) X(5, 1, 1)
 constexpr int LK_NUM_SHAPES = 6;
-// Default shape of FP64 handles: one node per CTA, which spreads the nodes
-// over the most SMs (their FP64 rate, not the halo reuse, bounds the analysis).
-constexpr int LK_SHAPE_FP64_DEFAULT = 5;
 // CTAs of the residual reduction per instance (fixed, so the sum order is fixed).
 constexpr int LK_RES_BLOCKS = 128;
 // Threads per CTA of the warp-per-item kernels (observation, forecast, reverse
@@ -166,7 +163,7 @@ cudaError_t lk_launch_list64(letkf_ctx *h, int cls, void *mean, void *spread);
 
 // Whether width class cls of the handle can take tile shape `shape`: FP32
 // handles need whole warps of nodes and, in class 2 (one node per warp), at
-// most 8 nodes per tile.
+// most 8 nodes per tile. (FP64 handles take any shape, which they ignore.)
 bool lk_shape_ok(const letkf_ctx *h, int cls, int shape);
 int lk_num_tile_shapes();
 void lk_tile_shape(int s, int *ti, int *tj);

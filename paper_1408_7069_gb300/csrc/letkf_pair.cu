@@ -570,7 +570,7 @@ cudaError_t lk_launch_pair(letkf_ctx *h, int cls, void *mean, void *spread) {
 bool lk_shape_ok(const letkf_ctx *h, int cls, int shape) {
   int ti, tj;
   lk_tile_shape(shape, &ti, &tj);
-  if (h->precision == 1) return true;     // FP64 tile kernel: one warp per node
+  if (h->precision == 1) return true;     // FP64 handles analyse one node per CTA
   switch (cls) {
     case 0: return (ti * tj) % PairCfg<16>::NPW == 0;
     case 1: return (ti * tj) % PairCfg<32>::NPW == 0;
