@@ -6,6 +6,7 @@ storage type. Tolerances (norm-wise over all nodes of a frame): analysis mean
 handles; plus max-abs checks scaled by the RMS of the reference.
 """
 import functools
+from dataclasses import replace
 
 import numpy as np
 import pytest
@@ -82,13 +83,17 @@ def test_analysis_teacher_forced(w, k):
     f.close()
 
 
-def test_fp64_fallback_matches_oracle_and_counts_points():
+FALLBACK = [W.TEL_16M, replace(W.TOY_8X8, name="toy-fp32-m12", precision=0, m=12, seeds=(17, 18, 19))]
+
+
+@pytest.mark.parametrize("w", FALLBACK, ids=[w.name for w in FALLBACK])
+def test_fp64_fallback_matches_oracle_and_counts_points(w):
     """Prior-draw background (kappa ~ 1e4): with every node routed to the FP64
     path (threshold just above 1) the FP32 tolerances hold and the nodes are
     counted; the FP32-only path is further off (its mean solve A^-1 C d
     carries the FP32 Gram's rounding times kappa), which is what the
-    kappa_hat rule is for."""
-    w = W.TEL_16M
+    kappa_hat rule is for. Both width classes of the FP64 path: 32 columns
+    (m = 24) and 16 (m = 12)."""
     inp, geom = inputs(w, 8)
     Xb_r = inp.X0.astype(np.float32)
     y_r = inp.slopes[0].astype(np.float32)
