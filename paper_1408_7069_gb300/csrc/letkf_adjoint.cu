@@ -400,16 +400,27 @@ __global__ void __launch_bounds__(LK_WARP_CTA)
       }
     }
     const int nc = wc - c0 < 32 ? wc - c0 : 32;
-#pragma unroll 4
-    for (int u = 0; u < nc; ++u) {
-      const long long cu = __shfl_sync(FULL, cell, u);
-      if (cu < 0) continue;
-      if (mem) {
-        y0 += ybw[(cu * 2 + 0) * m + lane];
-        y1 += ybw[(cu * 2 + 1) * m + lane];
+    // eight candidates at a time: their loads first (all in flight together),
+    // then the sums in candidate order
+    for (int u0 = 0; u0 < nc; u0 += 8) {
+      double a0[8], a1[8], e0[8], e1[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const long long cu = __shfl_sync(FULL, cell, (u0 + u) & 31);
+        const bool ok = u0 + u < nc && cu >= 0;
+        a0[u] = ok && mem ? ybw[(cu * 2 + 0) * m + lane] : 0.0;
+        a1[u] = ok && mem ? ybw[(cu * 2 + 1) * m + lane] : 0.0;
+        e0[u] = ok ? dbw[cu * 2 + 0] : 0.0;
+        e1[u] = ok ? dbw[cu * 2 + 1] : 0.0;
       }
-      d0 += dbw[cu * 2 + 0];
-      d1 += dbw[cu * 2 + 1];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (u0 + u >= nc) break;
+        y0 += a0[u];
+        y1 += a1[u];
+        d0 += e0[u];
+        d1 += e1[u];
+      }
     }
   }
   const size_t g = (size_t)(st.x + I.h) * I.gs_cols + (st.y + I.h);
