@@ -246,9 +246,10 @@ cudaError_t lk_launch_analysis_class(letkf_ctx *h, int cls, void *mean, void *sp
   return h->n_tiles[2] ? lk_launch_pair(h, 2, mean, spread) : cudaSuccess;
 }
 
+// Every caller launches the observation kernel just before; it zeroes the
+// counters this analysis counts into (no memset node breaks the launch chain).
 cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread) {
-  cudaError_t e = cudaMemsetAsync(h->counters + 1, 0, 7 * sizeof(int), h->stream);
-  if (e == cudaSuccess) e = launch_class<16>(h, 0, mean, spread);
+  cudaError_t e = launch_class<16>(h, 0, mean, spread);
   if (e == cudaSuccess) e = launch_class<32>(h, 1, mean, spread);
   if (e == cudaSuccess && h->n_tiles[2]) e = lk_launch_pair(h, 2, mean, spread);
   return e;

@@ -181,6 +181,37 @@ __device__ __forceinline__ T lk_warp_sum(T v) {
   return v;
 }
 
+// Programmatic dependent launch of the per-frame kernels: each is launched
+// with lk_launch_pdl, so that it can be scheduled while its predecessor on the
+// stream drains; its first statement is lk_pdl_wait(), which returns once the
+// predecessor grid has completed and its writes are visible (a no-op for a
+// kernel launched without the attribute). The residual and forecast kernels
+// then call lk_pdl_trigger(), letting the next kernel launch at once. The
+// observation and analysis kernels do not: an analysis launched early has its
+// CTAs placed on SMs that are still busy, several to an SM, which doubles the
+// time of a latency-bound analysis that does not fill the GPU (measured on the
+// 16 m system); their dependents launch as their CTAs exit.
+__device__ __forceinline__ void lk_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void lk_pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t lk_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // SplitMix64 output after the state advanced counter + 1 steps from seed
 // (Steele, Lea & Flood 2014).
 __device__ __forceinline__ unsigned long long lk_splitmix64(unsigned long long seed,

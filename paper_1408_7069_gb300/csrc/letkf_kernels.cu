@@ -18,6 +18,10 @@ __global__ void __launch_bounds__(LK_WARP_CTA) obs_kernel(const LkInst *__restri
                                                   long long p_total, const S *__restrict__ y,
                                                   const long long *__restrict__ run_idx,
                                                   int *__restrict__ counters) {
+  lk_pdl_wait();   // no early trigger: an analysis launched early would have its CTAs
+                   // packed onto the SMs this kernel still occupies
+  // the analysis that follows counts into counters[1..7] (queue lengths, sweeps)
+  if (blockIdx.x == 0 && threadIdx.x < 7) counters[1 + threadIdx.x] = 0;
   const long long wi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wi >= n_items) return;
@@ -106,6 +110,8 @@ __global__ void __launch_bounds__(LK_WARP_CTA) forecast_kernel(const LkInst *__r
                                                        long long n_items, const S *__restrict__ noise,
                                                        long long *__restrict__ frame,
                                                        int *__restrict__ ticket) {
+  lk_pdl_wait();
+  lk_pdl_trigger();
   const long long wi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wi < n_items) forecast_node<S>(insts, items[wi], lane, noise, frame);
@@ -136,6 +142,8 @@ __global__ void __launch_bounds__(64) residual_kernel(const LkInst *__restrict__
                                                        int *__restrict__ tickets, int n_inst,
                                                        double *__restrict__ resvar,
                                                        double *__restrict__ piston) {
+  lk_pdl_wait();
+  lk_pdl_trigger();
   const LkInst &I = insts[blockIdx.y];
   const long long k = run_idx ? *run_idx : 0;
   const S *tr = truth + k * n_pts_total + I.node_off;
@@ -232,27 +240,22 @@ cudaError_t lk_launch_obs(letkf_ctx *h, const void *y, const long long *run_idx)
   if (h->sap_total == 0) return cudaSuccess;
   const int blocks = warp_blocks(h->sap_total);
   if (h->precision == 1)
-    obs_kernel<double><<<blocks, LK_WARP_CTA, 0, h->stream>>>(h->d_inst, h->obs_items, h->sap_total,
-                                                      h->p_total, (const double *)y, run_idx,
-                                                      h->counters);
-  else
-    obs_kernel<float><<<blocks, LK_WARP_CTA, 0, h->stream>>>(h->d_inst, h->obs_items, h->sap_total,
-                                                     h->p_total, (const float *)y, run_idx,
-                                                     h->counters);
-  return cudaGetLastError();
+    return lk_launch_pdl(obs_kernel<double>, blocks, LK_WARP_CTA, 0, h->stream, h->d_inst,
+                         h->obs_items, h->sap_total, h->p_total, (const double *)y, run_idx,
+                         h->counters);
+  return lk_launch_pdl(obs_kernel<float>, blocks, LK_WARP_CTA, 0, h->stream, h->d_inst,
+                       h->obs_items, h->sap_total, h->p_total, (const float *)y, run_idx,
+                       h->counters);
 }
 
 cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise) {
   const int blocks = warp_blocks(h->n_pts_total);
   int *ticket = h->tickets + h->n_inst;
   if (h->precision == 1)
-    forecast_kernel<double><<<blocks, LK_WARP_CTA, 0, h->stream>>>(h->d_inst, h->node_items,
-                                                           h->n_pts_total, (const double *)noise,
-                                                           h->frame, ticket);
-  else
-    forecast_kernel<float><<<blocks, LK_WARP_CTA, 0, h->stream>>>(h->d_inst, h->node_items, h->n_pts_total,
-                                                          (const float *)noise, h->frame, ticket);
-  return cudaGetLastError();
+    return lk_launch_pdl(forecast_kernel<double>, blocks, LK_WARP_CTA, 0, h->stream, h->d_inst,
+                         h->node_items, h->n_pts_total, (const double *)noise, h->frame, ticket);
+  return lk_launch_pdl(forecast_kernel<float>, blocks, LK_WARP_CTA, 0, h->stream, h->d_inst,
+                       h->node_items, h->n_pts_total, (const float *)noise, h->frame, ticket);
 }
 
 cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
@@ -264,14 +267,12 @@ cudaError_t lk_launch_residual_on(letkf_ctx *h, cudaStream_t stream, const void 
                                   double *resvar, const long long *run_idx, double *piston) {
   const dim3 grid(LK_RES_BLOCKS, h->n_inst);
   if (h->precision == 1)
-    residual_kernel<double><<<grid, 64, 0, stream>>>(h->d_inst, h->n_pts_total,
-                                                         (const double *)truth, run_idx, h->partial,
-                                                         h->tickets, h->n_inst, resvar, piston);
-  else
-    residual_kernel<float><<<grid, 64, 0, stream>>>(h->d_inst, h->n_pts_total,
-                                                        (const float *)truth, run_idx, h->partial,
-                                                        h->tickets, h->n_inst, resvar, piston);
-  return cudaGetLastError();
+    return lk_launch_pdl(residual_kernel<double>, grid, 64, 0, stream, h->d_inst, h->n_pts_total,
+                         (const double *)truth, run_idx, h->partial, h->tickets, h->n_inst,
+                         resvar, piston);
+  return lk_launch_pdl(residual_kernel<float>, grid, 64, 0, stream, h->d_inst, h->n_pts_total,
+                       (const float *)truth, run_idx, h->partial, h->tickets, h->n_inst, resvar,
+                       piston);
 }
 
 cudaError_t lk_launch_basis_reset(letkf_ctx *h) {

@@ -341,6 +341,7 @@ __global__ void __launch_bounds__(N64_THREADS)
                   S *__restrict__ mean, S *__restrict__ spread, double tol, int max_sweeps,
                   int *__restrict__ counters) {
   extern __shared__ __align__(16) double n64_smem[];
+  lk_pdl_wait();   // no early trigger (long kernel): dependents launch as its CTAs exit
   const int2 it = items[blockIdx.x];
   const LkInst &I = insts[it.x];
   if (I.mp != MP) return;
@@ -358,6 +359,7 @@ __global__ void __launch_bounds__(N64_THREADS)
                        float *__restrict__ spread, double tol, int max_sweeps,
                        int *__restrict__ counters) {
   extern __shared__ __align__(16) double n64_smem[];
+  lk_pdl_wait();   // no early trigger (long kernel): dependents launch as its CTAs exit
   const int qn = *queue_len;
   for (int idx = blockIdx.x; idx < qn; idx += gridDim.x) {
     const int2 it = worklist[idx];
@@ -386,10 +388,9 @@ int n64_sm_count(int device) {
 template <int MP>
 cudaError_t launch_node64(letkf_ctx *h, void *mean, void *spread) {
   const size_t smem = n64_smem_doubles<MP>() * sizeof(double);
-  node64_kernel<MP, double><<<(unsigned)h->n_pts_total, N64_THREADS, smem, h->stream>>>(
-      h->d_inst, h->node_items, (double *)mean, (double *)spread, h->tol64, h->max_sweeps,
-      h->counters);
-  return cudaGetLastError();
+  return lk_launch_pdl(node64_kernel<MP, double>, (unsigned)h->n_pts_total, N64_THREADS, smem,
+                       h->stream, h->d_inst, h->node_items, (double *)mean, (double *)spread,
+                       h->tol64, h->max_sweeps, h->counters);
 }
 
 template <int MP>
@@ -401,10 +402,9 @@ cudaError_t launch_list64(letkf_ctx *h, int cls, void *mean, void *spread) {
   const long long cap = 4LL * n64_sm_count(h->device);
   const unsigned blocks = (unsigned)(n < cap ? n : cap);
   const size_t smem = n64_smem_doubles<MP>() * sizeof(double);
-  node64_list_kernel<MP><<<blocks, N64_THREADS, smem, h->stream>>>(
-      h->d_inst, h->worklist + (size_t)cls * h->n_pts_total, h->counters + 4 + cls,
-      (float *)mean, (float *)spread, h->tol64, h->max_sweeps, h->counters);
-  return cudaGetLastError();
+  return lk_launch_pdl(node64_list_kernel<MP>, blocks, N64_THREADS, smem, h->stream, h->d_inst,
+                       h->worklist + (size_t)cls * h->n_pts_total, h->counters + 4 + cls,
+                       (float *)mean, (float *)spread, h->tol64, h->max_sweeps, h->counters);
 }
 
 }  // namespace

@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
                          float *__restrict__ mean, float *__restrict__ spread, float tol,
                          float stop, int max_sweeps, float kappa_thr, int *__restrict__ counters,
                          int *__restrict__ queue, int2 *__restrict__ worklist, int keep_basis) {
+  lk_pdl_wait();   // no early trigger: the next kernel launches as this one's CTAs exit
   using C = PairCfg<MP>;
   constexpr int K2 = C::K2, LPN = C::LPN, GL = C::GL;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -504,10 +505,10 @@ cudaError_t launch_shape(letkf_ctx *h, const LkTile *tiles, int n_tiles, float *
       const size_t b = pair_layout<MP, TI, TJ>(I.w).total;
       need = b > need ? b : need;
     }
-  analysis_pair_kernel<MP, TI, TJ><<<n_tiles, TI * TJ * 32 / PairCfg<MP>::NPW, need, h->stream>>>(
-      h->d_inst, tiles, mean, spread, (float)h->tol32, (float)h->stop32, h->max_sweeps, kthr,
-      h->counters, queue, worklist, h->keep_basis);
-  return cudaGetLastError();
+  return lk_launch_pdl(analysis_pair_kernel<MP, TI, TJ>, n_tiles,
+                       TI * TJ * 32 / PairCfg<MP>::NPW, need, h->stream, h->d_inst, tiles, mean,
+                       spread, (float)h->tol32, (float)h->stop32, h->max_sweeps, kthr, h->counters,
+                       queue, worklist, h->keep_basis);
   }
 }
 
