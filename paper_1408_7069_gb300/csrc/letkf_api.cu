@@ -450,21 +450,18 @@ letkf_status enqueue_frame(letkf_ctx *h, const void *y_seq, const void *truth_se
 letkf_status enqueue_step(letkf_ctx *h, bool with_truth) {
   unsigned char *yd = h->step_dev + h->step_off[0], *td = h->step_dev + h->step_off[1];
   unsigned char *md = h->step_dev + h->step_off[2], *rd = h->step_dev + h->step_off[3];
-  unsigned char *yp = h->step_pin + h->step_off[0], *tp = h->step_pin + h->step_off[1];
-  unsigned char *mp = h->step_pin + h->step_off[2], *rp = h->step_pin + h->step_off[3];
-  if (with_truth)
-    LK_CUDA(h, cudaMemcpyAsync(td, tp, h->n_pts_total * h->rsz, cudaMemcpyHostToDevice,
-                               h->stream));
-  LK_CUDA(h, cudaMemcpyAsync(yd, yp, h->p_total * h->rsz, cudaMemcpyHostToDevice, h->stream));
+  unsigned char *yp = h->step_pin + h->step_off[0], *mp = h->step_pin + h->step_off[2];
+  // y and truth are adjacent in the staging buffers: one upload covers both
+  const size_t up = with_truth ? h->step_off[1] + h->n_pts_total * h->rsz : h->p_total * h->rsz;
+  LK_CUDA(h, cudaMemcpyAsync(yd, yp, up, cudaMemcpyHostToDevice, h->stream));
   letkf_status st = enqueue_head(h, yd, with_truth ? td : nullptr,
                                  with_truth ? reinterpret_cast<double *>(rd) : nullptr, nullptr);
   if (st != LETKF_OK) return st;
   LK_CUDA(h, lk_launch_analysis(h, md, nullptr));
-  LK_CUDA(h, cudaMemcpyAsync(mp, md, 2 * h->n_pts_total * h->rsz, cudaMemcpyDeviceToHost,
-                             h->stream));
-  if (with_truth)
-    LK_CUDA(h, cudaMemcpyAsync(rp, rd, h->n_inst * sizeof(double), cudaMemcpyDeviceToHost,
-                               h->stream));
+  // mean and resvar are adjacent too: one download
+  const size_t down = with_truth ? h->step_off[3] + h->n_inst * sizeof(double) - h->step_off[2]
+                                 : 2 * h->n_pts_total * h->rsz;
+  LK_CUDA(h, cudaMemcpyAsync(mp, md, down, cudaMemcpyDeviceToHost, h->stream));
   if (h->ev_out)
     LK_CUDA(h, cudaEventRecordWithFlags(h->ev_out, h->stream, cudaEventRecordExternal));
   LK_CUDA(h, lk_launch_forecast(h, nullptr));
