@@ -207,10 +207,18 @@ __device__ void node64(const LkInst &I, int pid, S *__restrict__ mean_out,
         const double scale = sqrt(app * aqq);
         double cs = 1.0, sn = 0.0, tr = 0.0;
         if (fabs(dot) > tol * scale) {
-          const double zeta = (aqq - app) / (2.0 * dot);
-          const double az = fabs(zeta);
-          tr = az > 1e15 ? 0.5 / zeta : copysign(1.0, zeta) / (az + sqrt(1.0 + zeta * zeta));
-          cs = rsqrt(1.0 + tr * tr);
+          // the tangent t of the rotation angle (|theta| <= pi/4) in FP32, from
+          // x = aqq - app and y = 2 dot formed in FP64: cos 2theta = |x|/h,
+          // c^2 = (1 + cos 2theta)/2, t = sin 2theta / (2 c^2), h = sqrt(x^2 + y^2).
+          // Then c = (1 + t^2)^-1/2 and s = c t in FP64, so the rotation is
+          // orthogonal to FP64 rounding; an FP32-accurate angle leaves the pair's
+          // cosine at ~1e-7 of its value, which the next sweep removes.
+          const float x = (float)(aqq - app), y = (float)(2.0 * dot);
+          const float rh = rsqrtf(fmaxf(fmaf(x, x, y * y), 1e-37f));
+          const float c2 = fmaf(0.5f * fabsf(x), rh, 0.5f);
+          const float t = (x >= 0.f ? y : -y) * (0.5f * rh) / c2;
+          tr = (double)t;
+          cs = rsqrt(fma(tr, tr, 1.0));
           sn = cs * tr;
           flags |= fabs(dot) > stop * scale ? 3 : 1;
         }
