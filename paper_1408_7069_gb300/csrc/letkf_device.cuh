@@ -105,9 +105,20 @@ __device__ __forceinline__ int jacobi_step(T (&b)[MP], T (&v)[MP], T &nrm, int t
   int rot = 0;
   const T scale = sqrt(app * aqq);
   if (fabs(dot) > tol * scale) {
-    const T zeta = (aqq - app) / (T(2) * dot);
-    const T az = fabs(zeta);
-    tr = az > T(1e15) ? T(0.5) / zeta : copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
+    if constexpr (sizeof(T) == 8) {
+      // FP64: the tangent in FP32 from x = aqq - app and y = 2 dot formed in
+      // FP64 (cos 2theta = |x|/h, c^2 = (1 + cos 2theta)/2, t = sin 2theta / (2 c^2)),
+      // then c = (1 + t^2)^-1/2 and s = c t in FP64: an orthogonal rotation whose
+      // FP32-accurate angle leaves the pair's cosine at ~1e-7 of its value
+      const float x = (float)(aqq - app), y = (float)(T(2) * dot);
+      const float rh = rsqrtf(fmaxf(fmaf(x, x, y * y), 1e-37f));
+      const float c2 = fmaf(0.5f * fabsf(x), rh, 0.5f);
+      tr = (T)((x >= 0.f ? y : -y) * (0.5f * rh) / c2);
+    } else {
+      const T zeta = (aqq - app) / (T(2) * dot);
+      const T az = fabs(zeta);
+      tr = az > T(1e15) ? T(0.5) / zeta : copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
+    }
     cs = lk_rsqrt(T(1) + tr * tr);
     sn = cs * tr;
     rot = fabs(dot) > stop * scale ? 3 : 1;
