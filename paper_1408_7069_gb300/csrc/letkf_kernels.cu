@@ -237,7 +237,8 @@ int warp_blocks(long long warps) {
 }  // namespace
 
 cudaError_t lk_launch_obs(letkf_ctx *h, const void *y, const long long *run_idx) {
-  if (h->sap_total == 0) return cudaSuccess;
+  // no subaperture, no kernel: the analysis counters are zeroed here instead
+  if (h->sap_total == 0) return cudaMemsetAsync(h->counters + 1, 0, 7 * sizeof(int), h->stream);
   const int blocks = warp_blocks(h->sap_total);
   if (h->precision == 1)
     return lk_launch_pdl(obs_kernel<double>, blocks, LK_WARP_CTA, 0, h->stream, h->d_inst,
