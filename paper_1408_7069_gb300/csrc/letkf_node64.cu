@@ -24,6 +24,8 @@
 //          Xa_r = xbar_r + X'_r wbar + X'_r W for the node's two rows
 #include <math.h>
 
+#include <atomic>
+
 #include "letkf_device.cuh"
 
 namespace {
@@ -380,17 +382,18 @@ __global__ void __launch_bounds__(N64_THREADS)
   }
 }
 
-// SM count of the handle's device (read once per device).
+// SM count of the handle's device (read once per device; handles on several
+// host threads may race to fill the cache, with the same value).
 int n64_sm_count(int device) {
-  static int cache[64] = {0};
+  static std::atomic<int> cache[64];
   const int d = device >= 0 && device < 64 ? device : 0;
-  if (cache[d] == 0) {
-    int n = 0;
+  int n = cache[d].load(std::memory_order_relaxed);
+  if (n == 0) {
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0)
       n = 1;
-    cache[d] = n;
+    cache[d].store(n, std::memory_order_relaxed);
   }
-  return cache[d];
+  return n;
 }
 
 template <int MP>
