@@ -335,5 +335,18 @@ def test_step_from_host_buffers_equals_run():
     assert np.array_equal(b.get_state().cpu().numpy(), Xa)
     with pytest.raises(ValueError):
         b.step(y[0].astype(np.float64))
+    # without truth (its own graph, no residual): the same analysis as letkf_analyze
+    c = Letkf.from_workload(w, bank=inp.bank)
+    c.set_state(torch.from_numpy(Xa).cuda())
+    c.set_frame(frames)
+    mc, rc = c.step(np.ascontiguousarray(y[0]))
+    assert rc is None
+    d = Letkf.from_workload(w, bank=inp.bank)
+    d.set_state(torch.from_numpy(Xa).cuda())
+    md, _ = d.analyze(torch.from_numpy(y[0]).cuda())
+    d.sync()
+    assert np.array_equal(mc, md.cpu().numpy())
     a.close()
     b.close()
+    c.close()
+    d.close()
