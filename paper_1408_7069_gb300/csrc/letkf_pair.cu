@@ -23,13 +23,17 @@
 // (an exact 90-degree rotation, the sign being irrelevant), which keeps the
 // register roles of every lane the same. A rotation is applied as
 // P' = c P - s Q, Q' = s P + c Q, exact for c = 1, s = 0 (no rotation) and for
-// the swap. A node whose sweep made no rotation is converged and freezes (its
-// lanes shuffle from themselves), so its result does not depend on the nodes
-// that share its warp.
+// the swap. A node is converged after a sweep whose rotations all had cosines
+// at most the stop cosine (letkf_set_jacobi; with stop <= the rotation
+// threshold, a sweep without rotations) and then freezes (its lanes shuffle
+// from themselves), so its result does not depend on the nodes that share its
+// warp.
 //
 // For MP <= 32, kappa_hat = 1 + rho tr(G)/(m-1) bounds the condition number
-// before the eigensolve; nodes above the threshold are queued for the FP64
-// list kernel. Wider problems have no FP64 fallback.
+// before the eigensolve; nodes above the threshold still take this FP32 sweep,
+// store their eigenbasis (the start of their FP64 sweep) and leave X alone:
+// they are queued for the FP64 list kernel of letkf_node64.cu, which writes
+// them. Wider problems have no FP64 fallback.
 #include <math.h>
 #include <stdint.h>
 
