@@ -189,7 +189,11 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
       b[i] = s;
     }
     __syncwarp();
-    jacobi<MP, T, false>(b, v, tol, a.max_sweeps, a.counters);
+    // U0 is this frame's converged basis, so the first sweep's rotations are at
+    // rounding level: stop after the first sweep whose cosines all stay below
+    // 1e-3 (one sweep, leaving pairs within about 1e-6) instead of running a
+    // second sweep only to find no rotation
+    jacobi<MP, T, false>(b, v, tol, a.max_sweeps, a.counters, T(1e-3));
   } else {
     if (U0) {
       warm_basis<MP, T>(b, v, U0 + (size_t)pid * MP * MP, Ms, Vs);
