@@ -94,6 +94,19 @@ struct AdjArgs {
   int *counters;
 };
 
+// hi + lo += a * b with the product's and the sum's rounding errors kept in lo
+// (FMA two-product and Knuth's two-sum): a compensated FP32 accumulation. The
+// _rn intrinsics keep the compiler from contracting the steps into FMAs.
+__device__ __forceinline__ void df_add_prod(float &hi, float &lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = fmaf(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(se, pe));
+}
+
 // Adjoint of one node's analysis. T = float: FP32 handle, warm start from the
 // frame's stored eigenbasis U0 and B-only Jacobi, nodes above kappa_thr queued.
 // T = double: accumulated eigenvectors, started from the identity (FP64
@@ -342,11 +355,14 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
   const double alpha_bar = double(lk_warp_sum(dg));   // d/d((m-1)/rho) = tr(A_bar)
 
   // ---- window slopes: y_bar_j = 2 c_j A_bar y_j + c_j d_j b_bar, d_bar_j, c_bar_j ----
-  // sum_j c_bar_j c_j and sum_j c_bar_j dc_j/dL, accumulated in FP64 (their
-  // terms cancel strongly over the window); dc_j/dsigma2 = -c_j / sigma2 is
-  // applied once per node
+  // sum_j c_bar_j c_j and sum_j c_bar_j dc_j/dL, whose terms cancel strongly
+  // over the window: in FP64 for FP64 handles; for FP32 handles as compensated
+  // FP32 sums (the products' and the additions' rounding errors carried in a
+  // second float, about FP64 accuracy without the FP64 pipe); dc_j/dsigma2 =
+  // -c_j / sigma2 is applied once per node
   const T bbl = col ? V(S_BB)[lane] : T(0);
   double gs2 = 0, gL = 0;
+  float gs2h = 0.f, gs2l = 0.f, gLh = 0.f, gLl = 0.f;
   double *yb_out = a.ybw + (size_t)pid * wc * 2 * m;
   double *db_out = a.dbw + (size_t)pid * wc * 2;
   for (int cell = 0; cell < wc; ++cell) {
@@ -363,10 +379,20 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
       const T yay = lk_warp_sum(yl * ay);
       if (mem) yb_out[((size_t)cell * 2 + c) * m + lane] = double(T(2) * cj * ay + cj * dj * bbl);
       if (lane == 0) db_out[cell * 2 + c] = double(cj * yb);
-      const double cbar = double(fma(dj, yb, yay));
-      gs2 = fma(cbar, double(cj), gs2);
-      gL = fma(cbar, dtap[cell], gL);
+      if constexpr (std::is_same<T, float>::value) {
+        const float cb = fmaf(dj, yb, yay);
+        df_add_prod(gs2h, gs2l, cb, cj);
+        df_add_prod(gLh, gLl, cb, (float)dtap[cell]);
+      } else {
+        const double cbar = double(fma(dj, yb, yay));
+        gs2 = fma(cbar, double(cj), gs2);
+        gL = fma(cbar, dtap[cell], gL);
+      }
     }
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    gs2 = (double)gs2h + (double)gs2l;
+    gL = (double)gLh + (double)gLl;
   }
   if (lane == 0) {
     a.theta[(size_t)pid * 3 + 0] = alpha_bar * (-(m - 1) / (a.rho * a.rho));
