@@ -23,7 +23,7 @@ def cache_path() -> str:
 
 
 # Bumped whenever the analysis kernels change, so that cached choices are retimed.
-KERNEL_REVISION = 3
+KERNEL_REVISION = 4
 
 
 def signature(gpu_name: str, shapes) -> str:
