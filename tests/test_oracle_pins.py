@@ -250,17 +250,6 @@ def test_splitmix64_published_vector():
     assert oracle.splitmix64(int(g["seed"]), 0) == int(g["first"], 16)
 
 
-def test_bank_noise_picks_wrapped_screen_values():
-    bank = np.arange(3 * 8 * 8, dtype=np.float32).reshape(3, 8, 8)
-    pts = np.array([[0, 0], [7, 7], [3, 5]])
-    v = oracle.bank_noise(bank, pts, 4, seed=99, frame=5, scale=2.0)
-    for i in range(4):
-        h = oracle.splitmix64(99, (5 << 16) | i)
-        b, ox, oy = h % 3, (h >> 16) % 8, (h >> 40) % 8
-        for r, (pi, pj) in enumerate(pts):
-            assert v[r, i] == 2.0 * bank[b, (pi + ox) % 8, (pj + oy) % 8]
-
-
 def test_residual_variance_removes_piston():
     X = np.zeros((5, 2, 3))
     X[:, 0, :] = np.arange(5)[:, None]
