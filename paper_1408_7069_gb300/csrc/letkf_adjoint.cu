@@ -19,7 +19,9 @@
 // The eigenbasis comes from the forward analysis of the same frame: FP32 nodes
 // refine the stored basis with a B-only Jacobi (one sweep at most in practice);
 // nodes whose kappa_hat bound sends them to FP64 in the forward analysis are
-// queued and redone in FP64 from the identity with accumulated eigenvectors.
+// queued and redone in FP64 with accumulated eigenvectors, starting from the
+// FP32 basis U0 that the forward pair kernel stored for the node (FP64 handles
+// start from the identity).
 //
 // Every node writes the adjoints of its window's slopes to its own slots; a
 // subaperture kernel sums them over the nodes whose window holds the slope (in
