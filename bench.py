@@ -47,6 +47,10 @@ def parse_args(argv=None):
                     help="skip the 8x8 FP64 and 16 m FP32 measurements")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the reverse-mode (letkf_grad) measurement")
+    ap.add_argument("--phase-split", action="store_true",
+                    help="print where the FP32 analysis kernel spends its cycles (builds and "
+                         "loads the phase-clock variant of the library) instead of the bench line")
+    ap.add_argument("--phase-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -352,6 +356,54 @@ def adjoint_arm(torch, L, reps: int = 3):
             "fd_launch": "6 x letkf_run of 200 frames (one graph replay per frame)"}
 
 
+# --------------------------------------------------------------------------- phase split
+def phase_worker(args):
+    """Runs with LETKF_LIBRARY pointing at the phase-clock build: the ELT loop
+    as in the main measurement, then the analysis kernel's cycles per phase
+    over `steps` analyses."""
+    import numpy as np
+    import torch
+    from paper_1408_7069_gb300 import synth
+    from paper_1408_7069_gb300 import letkf as L
+    torch.cuda.set_device(0)
+    w = workload()
+    K, Wm = args.steps, args.warmup
+    inp = synth.make_loop_inputs(w, frames=Wm + K + 1)
+    f = L.Letkf.from_workload(w, bank=inp.bank)
+    h, s = f.h, f.stream
+    y = torch.from_numpy(inp.slopes.astype(np.float32)).cuda()
+    f.set_state(torch.from_numpy(inp.X0.astype(np.float32)).cuda())
+    with torch.cuda.stream(s):
+        for k in range(Wm):
+            L.letkf_analyze(h, y[k], None, None)
+            L.letkf_forecast(h)
+    L.letkf_sync(h)
+    if L.letkf_phase_clocks() is None:
+        raise RuntimeError("the loaded library has no phase clocks")
+    with torch.cuda.stream(s):
+        for i in range(K):
+            L.letkf_analyze(h, y[Wm + i], None, None)
+            L.letkf_forecast(h)
+    L.letkf_sync(h)
+    c = L.letkf_phase_clocks()
+    f.close()
+    names = ["halo_staging", "gram_and_kappa", "jacobi_sweeps", "transform_and_apply"]
+    tot = sum(c[:4])
+    print(json.dumps({"workload": w.name, "analyses": K, "warps_per_analysis": c[4] / K,
+                      "cycles_per_warp": {n: c[i] / c[4] for i, n in enumerate(names)},
+                      "share": {n: c[i] / tot for i, n in enumerate(names)}}))
+    return 0
+
+
+def phase_split(args):
+    from paper_1408_7069_gb300.build import build_library
+    lib = build_library(phase_clocks=True)
+    env = dict(os.environ, LETKF_LIBRARY=lib)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--phase-worker", "--steps",
+                        str(args.steps), "--warmup", str(args.warmup)], env=env, timeout=900)
+    return r.returncode
+
+
 # --------------------------------------------------------------------------- CPU oracle
 def cpu_worker(seconds: float):
     """Runs in a single-threaded subprocess: the FP64 oracle on full frames of
@@ -460,6 +512,8 @@ def gpu_arm(args):
     w = workload(rank)
     K, Wm = args.steps, args.warmup
     frames = Wm + K + 1
+    # FP32 / FP64 arithmetic peaks of this GPU at the clocks it holds now
+    peaks = L.letkf_fma_peaks()
     inp = synth.make_loop_inputs(w, frames=frames)
     f = L.Letkf.from_workload(w, bank=inp.bank)
     h, s = f.h, f.stream
@@ -554,6 +608,8 @@ def gpu_arm(args):
 
     ws = f.points()[1]
     flops = opcount.frame_analysis_ops(w.m, ws)
+    peak_key = max(("fp32_tflops", "fp32x2_tflops"), key=lambda k: peaks[k])
+    fp32_peak = peaks[peak_key]
     ana_mean_s = statistics.mean(ana_ms) / 1e3
     achieved = flops / ana_mean_s / 1e12
     fallback = 1 if f.precision == 0 else 0
@@ -576,8 +632,14 @@ def gpu_arm(args):
         "e2e": {"value": e2e_fps, "unit": UNIT,
                 "h2d_bytes_per_step": -(-4 * f.p // 256) * 256 + 4 * f.n_pts,
                 "d2h_bytes_per_step": -(-4 * 2 * f.n_pts // 256) * 256 + 8},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "peak_source": "measured: letkf_fma_peaks (FP32 FMA chains over the whole "
+                                    f"GPU at {peaks[peak_key.replace('tflops', 'mhz')]:.0f} MHz, "
+                                    f"{'packed two-wide' if peak_key == 'fp32x2_tflops' else 'scalar'}"
+                                    " FMAs, the faster form); nominal "
+                                    f"{FP32_PEAK_TFLOPS:.1f} at 2070 MHz",
+                     "fma_peaks": peaks,
                      "traffic": profile_traffic(),
                      "kernel": "letkf_analyze (observation + analysis_pair_kernel + FP64 list kernels)",
                      "flops_per_launch": flops,
@@ -610,6 +672,10 @@ def main(argv=None):
     if args.cpu_worker:
         cpu_worker(args.cpu_seconds)
         return 0
+    if args.phase_worker:
+        return phase_worker(args)
+    if args.phase_split:
+        return phase_split(args)
     if args.impl == "reference":
         return reference_arm(args)
     return gpu_arm(args)

@@ -279,13 +279,49 @@ letkf_status letkf_stats(letkf_t h, int32_t *fp64_points, int32_t *max_sweeps,
  * y_dev: device float [p]. mean_dev, spread_dev: device float [n_pts][2] or NULL.
  * stream: cudaStream_t for all of the work (NULL = legacy default stream).
  * errbuf: caller buffer of errlen bytes for a message on failure, or NULL.
- * The first call on a device looks up the array's device address; make it
- * before any stream capture. Every call shares the array and overwrites its
- * contents (the grids are cleared at the start of each call); calls whose GPU
- * work overlaps (other streams, other host threads) race. */
+ * cfg->fp64_kappa > 0: nodes whose kappa_hat (see letkf_analyze) exceeds it
+ *   are counted (this path has no FP64 fallback: their mean may miss the FP32
+ *   tolerance); letkf_noalloc_status reports the count.
+ * The first call on a device looks up the array's device address. The call
+ * copies its tables from host memory that the next call reuses, so it cannot
+ * be captured into a CUDA graph: on a capturing stream it returns
+ * LETKF_ERR_ARG and launches nothing. Every call shares the array and
+ * overwrites its contents (the grids and the status counters are cleared at
+ * the start of each call); calls whose GPU work overlaps (other streams, other
+ * host threads) race. Faults found on the device are not returned by this
+ * call: read them with letkf_noalloc_status. */
 letkf_status letkf_analyze_noalloc(const letkf_config *cfg, void *X_dev, const void *y_dev,
                                    void *mean_dev, void *spread_dev, void *stream, char *errbuf,
                                    size_t errlen);
+
+/* Status of the last letkf_analyze_noalloc call on the current device, for the
+ * same callers (it allocates nothing either). Synchronises `stream` (the
+ * stream of that call), then reads the status word from the static array:
+ * LETKF_ERR_NONFINITE if a node met NaN or Inf, else LETKF_ERR_NOCONVERGE if a
+ * node reached the sweep limit, else LETKF_OK; LETKF_ERR_CUDA if a CUDA call
+ * failed. kappa_nodes (host, may be NULL): the number of nodes whose kappa_hat
+ * exceeded cfg->fp64_kappa in that call. The paper has no counterpart. */
+letkf_status letkf_noalloc_status(void *stream, int32_t *kappa_nodes);
+
+/* Measured arithmetic peaks of the current device, the denominators of the
+ * analysis roofline (the analysis is bound by FP32 arithmetic, its fallback by
+ * FP64). Independent FMA chains in every thread of a grid of 4 CTAs of 256
+ * threads per SM, timed with CUDA events after a warm-up launch; the SM clock
+ * is read from clock64 and the global timer of every CTA. out: host double[7]:
+ * FP32 TFLOP/s with scalar FMAs and the SM MHz during that kernel, FP32 TFLOP/s
+ * with packed two-wide FMAs and its MHz, FP64 TFLOP/s and its MHz, the SM
+ * count (an FMA counts as two flops). Takes about 0.1 s; allocates and frees
+ * device memory; synchronises. It changes no clock or other device setting.
+ * The paper has no counterpart. */
+letkf_status letkf_fma_peaks(double *out);
+
+/* Where the FP32 analysis kernel spends its time, in a library built with
+ * phase clocks (build option LK_PHASE_CLOCKS; LETKF_ERR_STATE otherwise):
+ * SM cycles summed over its warps since the last call, out: host uint64_t[5]
+ * = halo staging, Gram and kappa_hat, Jacobi sweeps, eigenpairs + transform +
+ * apply (Section 4.2's steps), and the number of warps. Synchronises the
+ * device and resets the counts. The paper has no counterpart. */
+letkf_status letkf_phase_clocks(uint64_t *out);
 
 /* Text of the last error on this handle (or of the last failed create when h is NULL). */
 const char *letkf_last_error(letkf_t h);

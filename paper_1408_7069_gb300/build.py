@@ -18,8 +18,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libletkf.so")
+PHASE_LIB = os.path.join(PKG, "libletkf_phase.so")
 SOURCES = ["letkf_api.cu", "letkf_kernels.cu", "letkf_analysis.cu", "letkf_adjoint.cu", "letkf_pair.cu",
-           "letkf_node64.cu"]
+           "letkf_node64.cu", "letkf_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,15 +31,22 @@ def nvcc() -> str:
     return cand
 
 
-def build_library(verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build_library(verbose: bool = False, ptxas_info: bool = False,
+                  phase_clocks: bool = False) -> str:
+    """Compile the library; ``phase_clocks`` builds the instrumented variant
+    (per-phase cycle counts of the FP32 analysis kernel) as libletkf_phase.so."""
+    bdir = os.path.join(BUILD, "phase") if phase_clocks else BUILD
+    out = PHASE_LIB if phase_clocks else LIB
+    os.makedirs(bdir, exist_ok=True)
     flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE,
              "--expt-relaxed-constexpr"]
     if ptxas_info:
         flags += ["-Xptxas", "-v"]
+    if phase_clocks:
+        flags += ["-DLK_PHASE_CLOCKS"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(bdir, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc(), *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -51,14 +59,15 @@ def build_library(verbose: bool = False, ptxas_info: bool = False) -> str:
         for obj, log in results:
             if log.strip():
                 print(log, file=sys.stderr)
-    tmp = LIB + ".tmp"
+    tmp = out + ".tmp"
     cmd = [nvcc(), "-shared", *ARCH, "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":
-    print(build_library(verbose=True, ptxas_info="-v" in sys.argv))
+    print(build_library(verbose=True, ptxas_info="-v" in sys.argv,
+                        phase_clocks="--phase-clocks" in sys.argv))

@@ -161,10 +161,16 @@ __device__ __forceinline__ void analyze_node_accum(const S *__restrict__ win,
                                                    S *__restrict__ xrow, S *__restrict__ mean_out,
                                                    S *__restrict__ spread_out,
                                                    T *__restrict__ scr, int *__restrict__ counters,
-                                                   float *__restrict__ U) {
+                                                   float *__restrict__ U, T kappa_thr = T(0)) {
   const int lane = threadIdx.x & 31;
   T b[MP], diag, cd;
   gram<MP, S, T>(win, dwin, stride, tap, w, m, alpha, b, diag, cd);
+  if (kappa_thr > T(0)) {
+    // kappa_hat = 1 + tr(G) / alpha bounds the condition number of A: above the
+    // threshold the FP32 mean solve may miss the stated accuracy; count the node
+    const T trg = lk_warp_sum(lane < MP ? diag : T(0));
+    if (lane == 0 && T(1) + trg / alpha > kappa_thr) atomicAdd(&counters[1], 1);
+  }
   T v[MP];
 #pragma unroll
   for (int k = 0; k < MP; ++k) v[k] = (k == lane) ? T(1) : T(0);
@@ -324,7 +330,7 @@ template <int MP>
 __global__ void __launch_bounds__(NA_TI *NA_TJ * 32)
     analysis_noalloc_kernel(const LkInst *__restrict__ insts, const LkTile *__restrict__ tiles,
                             float *__restrict__ mean, float *__restrict__ spread, float tol,
-                            int max_sweeps, int *__restrict__ counters) {
+                            int max_sweeps, float kappa_thr, int *__restrict__ counters) {
   extern __shared__ __align__(16) unsigned char smem[];
   const LkTile tl = tiles[blockIdx.x];
   const LkInst &I = insts[tl.inst];
@@ -351,7 +357,7 @@ __global__ void __launch_bounds__(NA_TI *NA_TJ * 32)
                                        mean ? mean + 2 * pid : nullptr,
                                        spread ? spread + 2 * pid : nullptr,
                                        scr + (size_t)warp * scratch_elems<MP, float>(), counters,
-                                       nullptr);
+                                       nullptr, kappa_thr);
 }
 
 // Device address of the scratch on the current device; looked up once per device.
@@ -392,6 +398,16 @@ extern "C" letkf_status letkf_analyze_noalloc(const letkf_config *cfg, void *X_d
   if (c.precision != 0 || (c.taper != 0 && c.taper != 1) || !(c.rho > 0) || !(c.sigma2 > 0) ||
       !isfinite(c.rho) || !isfinite(c.sigma2)) {
     na_error(errbuf, errlen, "precision must be 0, taper 0 or 1, rho and sigma2 finite and > 0");
+    return LETKF_ERR_ARG;
+  }
+  // The tables below are copied from host memory that the next call reuses: a
+  // graph captured from this call would keep those host pointers, so capture
+  // is refused (the status query cannot be captured either: it synchronises).
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess ||
+      cap != cudaStreamCaptureStatusNone) {
+    (void)cudaGetLastError();
+    na_error(errbuf, errlen, "letkf_analyze_noalloc cannot be captured into a CUDA graph");
     return LETKF_ERR_ARG;
   }
   int dev = 0;
@@ -506,19 +522,39 @@ extern "C" letkf_status letkf_analyze_noalloc(const letkf_config *cfg, void *X_d
   tmp.counters = reinterpret_cast<int *>(base + NA_OFF_COUNTERS);
   if (e == cudaSuccess) e = lk_launch_obs(&tmp, y_dev, nullptr);
   const int sweeps = c.max_sweeps > 0 ? c.max_sweeps : 20;
+  const float kthr = c.fp64_kappa > 0 ? (float)c.fp64_kappa : 0.f;
   if (e == cudaSuccess) {
     const LkTile *tiles = reinterpret_cast<const LkTile *>(base + NA_OFF_TILES);
     if (mp == 16)
       analysis_noalloc_kernel<16><<<n_tiles, NA_TI * NA_TJ * 32, smem, st>>>(
-          tmp.d_inst, tiles, (float *)mean_dev, (float *)spread_dev, 4e-6f, sweeps, tmp.counters);
+          tmp.d_inst, tiles, (float *)mean_dev, (float *)spread_dev, 4e-6f, sweeps, kthr, tmp.counters);
     else
       analysis_noalloc_kernel<32><<<n_tiles, NA_TI * NA_TJ * 32, smem, st>>>(
-          tmp.d_inst, tiles, (float *)mean_dev, (float *)spread_dev, 4e-6f, sweeps, tmp.counters);
+          tmp.d_inst, tiles, (float *)mean_dev, (float *)spread_dev, 4e-6f, sweeps, kthr, tmp.counters);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {
     na_error(errbuf, errlen, cudaGetErrorString(e));
     return LETKF_ERR_CUDA;
   }
+  return LETKF_OK;
+}
+
+extern "C" letkf_status letkf_noalloc_status(void *stream, int32_t *kappa_nodes) {
+  if (kappa_nodes) *kappa_nodes = 0;
+  int dev = 0;
+  unsigned char *base = nullptr;
+  cudaError_t e = cudaGetDevice(&dev);
+  int c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (e == cudaSuccess) e = na_scratch_address(dev, &base);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaMemcpy(c, base + NA_OFF_COUNTERS, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return LETKF_ERR_CUDA;
+  if (kappa_nodes) *kappa_nodes = c[1];
+  if (c[0] & LK_BIT_NONFINITE) return LETKF_ERR_NONFINITE;
+  if (c[0] & LK_BIT_NOCONVERGE) return LETKF_ERR_NOCONVERGE;
   return LETKF_OK;
 }

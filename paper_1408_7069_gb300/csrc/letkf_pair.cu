@@ -39,6 +39,17 @@
 
 #include "letkf_device.cuh"
 
+// Phase clocks (a library built with -DLK_PHASE_CLOCKS only): lane 0 of every
+// warp adds the SM cycles it spent in each phase of the kernel, summed over
+// warps: [0] halo staging, [1] Gram and kappa_hat, [2] Jacobi sweeps,
+// [3] eigenpairs, transform and apply, [4] number of warps.
+#ifdef LK_PHASE_CLOCKS
+__device__ unsigned long long g_lk_phase_clocks[5];
+#define LK_PHASE_STAMP(t) const long long t = clock64()
+#else
+#define LK_PHASE_STAMP(t)
+#endif
+
 namespace {
 
 template <int MP>
@@ -230,6 +241,7 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
                          float stop, int max_sweeps, float kappa_thr, int *__restrict__ counters,
                          int *__restrict__ queue, int2 *__restrict__ worklist, int keep_basis) {
   lk_pdl_wait();   // no early trigger: the next kernel launches as this one's CTAs exit
+  LK_PHASE_STAMP(ph0);
   using C = PairCfg<MP>;
   constexpr int K2 = C::K2, LPN = C::LPN, GL = C::GL;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -243,6 +255,7 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
   float *tap = reinterpret_cast<float *>(smem + Ly.tap);
   stage_pair_tile<MP, TI, TJ>(I, tl.i0, tl.j0, halo, dh, tap);
   __syncthreads();
+  LK_PHASE_STAMP(ph1);
 
   const int lane = threadIdx.x & 31;
   const int grp = lane / GL, li = lane - grp * GL;    // node of the warp, lane within the node
@@ -329,6 +342,7 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
   }
 
   // ---- Jacobi sweeps ----
+  LK_PHASE_STAMP(ph2);
   const float tol2 = tol * tol, stop2 = stop * stop;
   const int base = grp * GL;
   const int up = live ? base + (li + 1) % LPN : lane;
@@ -369,6 +383,7 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
   }
 
   // ---- eigenpairs: lambda = |b|, v = b / lambda ----
+  LK_PHASE_STAMP(ph3);
   const float lP = sqrtf(dotk<K2>(P, P)), lQ = sqrtf(dotk<K2>(Q, Q));
   {
     const float iP = 1.f / lP, iQ = 1.f / lQ;
@@ -486,6 +501,17 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
     if (!isfinite(mu0) || !isfinite(mu1) || !isfinite(sp0) || !isfinite(sp1))
       atomicOr(&counters[0], LK_BIT_NONFINITE);
   }
+#ifdef LK_PHASE_CLOCKS
+  __syncwarp();
+  LK_PHASE_STAMP(ph4);
+  if (lane == 0) {
+    atomicAdd(&g_lk_phase_clocks[0], (unsigned long long)(ph1 - ph0));
+    atomicAdd(&g_lk_phase_clocks[1], (unsigned long long)(ph2 - ph1));
+    atomicAdd(&g_lk_phase_clocks[2], (unsigned long long)(ph3 - ph2));
+    atomicAdd(&g_lk_phase_clocks[3], (unsigned long long)(ph4 - ph3));
+    atomicAdd(&g_lk_phase_clocks[4], 1ull);
+  }
+#endif
 }
 
 // A tile fills whole warps (its node count is a multiple of the nodes per
@@ -590,4 +616,21 @@ cudaError_t lk_setup_pair(letkf_ctx *h) {
   if (e == cudaSuccess) e = setup_mp<48>(h);
   if (e == cudaSuccess) e = setup_mp<64>(h);
   return e;
+}
+
+extern "C" letkf_status letkf_phase_clocks(uint64_t *out) {
+#ifdef LK_PHASE_CLOCKS
+  if (!out) return LETKF_ERR_ARG;
+  unsigned long long v[5] = {0, 0, 0, 0, 0};
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(v, g_lk_phase_clocks, sizeof(v));
+  const unsigned long long z[5] = {0, 0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_lk_phase_clocks, z, sizeof(z));
+  if (e != cudaSuccess) return LETKF_ERR_CUDA;
+  for (int i = 0; i < 5; ++i) out[i] = v[i];
+  return LETKF_OK;
+#else
+  (void)out;
+  return LETKF_ERR_STATE;
+#endif
 }

@@ -15,7 +15,9 @@ from ctypes import POINTER, byref, c_char_p, c_double, c_int32, c_uint64, c_void
 import numpy as np
 
 PKG_DIR = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG_DIR, "libletkf.so")
+# LETKF_LIBRARY selects another build of the same library (e.g. the one with
+# phase clocks); by default the in-tree libletkf.so.
+LIB_PATH = os.environ.get("LETKF_LIBRARY") or os.path.join(PKG_DIR, "libletkf.so")
 HEADER = os.path.join(os.path.dirname(PKG_DIR), "include", "letkf.h")
 
 LETKF_OK = 0
@@ -53,6 +55,9 @@ _SIGS = {
     "letkf_stats": [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)],
     "letkf_analyze_noalloc": [POINTER(letkf_config), c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_char_p, ctypes.c_size_t],
+    "letkf_noalloc_status": [c_void_p, POINTER(c_int32)],
+    "letkf_fma_peaks": [c_void_p],
+    "letkf_phase_clocks": [c_void_p],
     "letkf_create_batch": [POINTER(letkf_config), c_int32, c_void_p, POINTER(c_void_p)],
     "letkf_query_instance": [c_void_p, c_int32, POINTER(c_int32), POINTER(c_int32),
                              POINTER(c_int32), POINTER(c_int32)],
@@ -249,6 +254,36 @@ def letkf_analyze_noalloc(cfg: letkf_config, X, y, mean=None, spread=None, strea
                                      c_void_p(stream_ptr), buf, 256)
     if st != LETKF_OK:
         raise LetkfError(st, buf.value.decode())
+
+
+def letkf_noalloc_status(stream_ptr: int = 0) -> tuple:
+    """(status, kappa_nodes) of the last allocation-free analysis on the
+    current device; synchronises the stream. Returns the status code rather
+    than raising, so that a caller can tell the faults apart."""
+    n = c_int32(0)
+    st = lib().letkf_noalloc_status(c_void_p(stream_ptr), byref(n))
+    return int(st), int(n.value)
+
+
+def letkf_fma_peaks() -> dict:
+    """Measured FP32 (scalar and packed FMA) and FP64 peaks of the current
+    device in TFLOP/s, each with the SM clock (MHz) it ran at."""
+    out = (c_double * 7)()
+    _check(lib().letkf_fma_peaks(out), None)
+    return {"fp32_tflops": out[0], "fp32_mhz": out[1], "fp32x2_tflops": out[2],
+            "fp32x2_mhz": out[3], "fp64_tflops": out[4], "fp64_mhz": out[5], "sms": int(out[6])}
+
+
+def letkf_phase_clocks():
+    """Cycles of the FP32 analysis kernel's phases (staging, Gram, Jacobi,
+    apply) and its warp count since the last call, or None when the library
+    was built without phase clocks."""
+    out = (ctypes.c_uint64 * 5)()
+    st = lib().letkf_phase_clocks(out)
+    if st == 6:
+        return None
+    _check(st, None)
+    return list(out)
 
 
 def letkf_last_error(h=None) -> str:

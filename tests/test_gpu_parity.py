@@ -309,6 +309,23 @@ def test_nonfinite_slopes_are_reported_and_handle_survives():
     f.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp32", "fp64"])
+def test_sweep_limit_is_reported_and_handle_survives(precision):
+    # one Jacobi sweep cannot converge a node problem of the prior draw:
+    # LETKF_ERR_NOCONVERGE surfaces at letkf_sync, and the status word is cleared
+    w = W.TEL_16M
+    inp, geom = inputs(w, 8)
+    dt = np.float32 if precision == 0 else np.float64
+    f = Letkf.from_workload(w, bank=inp.bank, precision=precision, max_sweeps=1)
+    f.set_state(torch.from_numpy(inp.X0.astype(dt)).cuda())
+    f.analyze(torch.from_numpy(inp.slopes[1].astype(dt)).cuda())
+    with pytest.raises(LetkfError) as e:
+        f.sync()
+    assert e.value.status == 3
+    f.sync()                                  # cleared by the first sync
+    f.close()
+
+
 def test_step_from_host_buffers_equals_run():
     """letkf_step (host buffers, one graph per frame) runs the same frames as
     letkf_run: same residuals, same final ensemble, and the returned analysis
