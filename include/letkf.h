@@ -234,7 +234,7 @@ letkf_status letkf_grad(letkf_t h, int32_t frames, const void *y_seq_dev, const 
  * mix of instances. letkf_tile_shape describes compiled shape number `shape`
  * (0 .. count-1; LETKF_ERR_ARG beyond). Instances are grouped in width classes
  * by ensemble size: 0 for m <= 16, 1 for m <= 32, 2 for m <= 64 (one node per
- * warp, tiles of at most 8 nodes, no FP64 fallback). On FP32 handles a tile
+ * warp, tiles of at most 8 nodes). On FP32 handles a tile
  * holds whole warps of nodes (a multiple of 4 nodes in class 0, of 2 in class
  * 1); a shape a class cannot take gives LETKF_ERR_ARG. New handles start at
  * shape 0 (2 x 4). letkf_set_tile_shape

@@ -210,14 +210,14 @@ __device__ __forceinline__ void stage_tile(const LkInst &I, int i0, int j0, S *h
 }
 
 // One width class: FP64 handles run one CTA per node (letkf_node64.cu); FP32
-// handles the two-columns-per-lane kernel (letkf_pair.cu), then, for MP <= 32,
-// the FP64 analysis of the nodes it queued.
+// handles the two-columns-per-lane kernel (letkf_pair.cu), then the FP64
+// analysis of the nodes it queued.
 template <int MP>
 cudaError_t launch_class(letkf_ctx *h, int cls, void *mean, void *spread) {
   if (h->n_tiles[cls] == 0) return cudaSuccess;
   if (h->precision == 1) return lk_launch_node64(h, cls, mean, spread);
   cudaError_t e = lk_launch_pair(h, cls, mean, spread);
-  if (e != cudaSuccess || h->fp64_kappa <= 0 || MP > 32) return e;
+  if (e != cudaSuccess || h->fp64_kappa <= 0) return e;
   return lk_launch_list64(h, cls, mean, spread);
 }
 
@@ -242,14 +242,20 @@ void lk_tile_shape(int s, int *ti, int *tj) {
 int lk_width_class(int m) { return m <= 16 ? 0 : (m <= 32 ? 1 : 2); }
 
 // Raises the dynamic shared-memory limit of the analysis kernels this handle uses.
-cudaError_t lk_setup_analysis(letkf_ctx *h) { return lk_setup_pair(h); }
+cudaError_t lk_setup_analysis(letkf_ctx *h) {
+  cudaError_t e = lk_setup_pair(h);
+  bool wide = false;
+  for (const LkInst &I : h->inst) wide = wide || I.mp > 32;
+  if (e == cudaSuccess && wide && h->precision == 0) e = lk_setup_node64w();
+  return e;
+}
 
 cudaError_t lk_launch_analysis_class(letkf_ctx *h, int cls, void *mean, void *spread) {
   cudaError_t e = cudaMemsetAsync(h->counters + 1, 0, 7 * sizeof(int), h->stream);
   if (e != cudaSuccess) return e;
   if (cls == 0) return launch_class<16>(h, 0, mean, spread);
   if (cls == 1) return launch_class<32>(h, 1, mean, spread);
-  return h->n_tiles[2] ? lk_launch_pair(h, 2, mean, spread) : cudaSuccess;
+  return launch_class<64>(h, 2, mean, spread);
 }
 
 // Every caller launches the observation kernel just before; it zeroes the
@@ -257,7 +263,7 @@ cudaError_t lk_launch_analysis_class(letkf_ctx *h, int cls, void *mean, void *sp
 cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread) {
   cudaError_t e = launch_class<16>(h, 0, mean, spread);
   if (e == cudaSuccess) e = launch_class<32>(h, 1, mean, spread);
-  if (e == cudaSuccess && h->n_tiles[2]) e = lk_launch_pair(h, 2, mean, spread);
+  if (e == cudaSuccess) e = launch_class<64>(h, 2, mean, spread);
   return e;
 }
 

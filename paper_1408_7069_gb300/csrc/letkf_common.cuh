@@ -160,6 +160,8 @@ cudaError_t lk_setup_pair(letkf_ctx *h);
 // the pair kernel queued in class cls of an FP32 handle.
 cudaError_t lk_launch_node64(letkf_ctx *h, int cls, void *mean, void *spread);
 cudaError_t lk_launch_list64(letkf_ctx *h, int cls, void *mean, void *spread);
+// Shared-memory limit of the wide class's FP64 list kernel (MP = 48 / 64 queue).
+cudaError_t lk_setup_node64w();
 
 // Whether width class cls of the handle can take tile shape `shape`: FP32
 // handles need whole warps of nodes and, in class 2 (one node per warp), at

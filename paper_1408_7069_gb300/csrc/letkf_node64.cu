@@ -382,6 +382,325 @@ __global__ void __launch_bounds__(N64_THREADS)
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 fallback of the wide class (m = 33..64): the nodes the pair kernel
+// queued for MP = 48 and MP = 64, both padded to 64 columns here (identity on
+// the padding). One CTA of eight warps per node: thread t holds column
+// c = t % 64 of a row block rb = t / 64 of 16 rows (two warps per block).
+// The partner column c ^ t of a Jacobi step lies in the other warp of the
+// block for t >= 32, so columns are exchanged through shared memory, not by
+// shuffles. The eigensolve is one-sided Jacobi on B = A V0 alone, V0 the
+// node's stored FP32 eigenbasis made orthonormal by one Newton-Schulz step:
+// for A > 0 the converged columns are lambda_c q_c, so q_c = b_c / |b_c|
+// needs no accumulated V (the lost relative accuracy of the small eigenpairs,
+// about eps64 kappa_hat, stays far below the FP32 outputs).
+// ---------------------------------------------------------------------------
+constexpr int N64W_MP = 64;
+constexpr int N64W_THREADS = 256;
+constexpr int N64W_NB = N64W_THREADS / N64W_MP;   // 4 row blocks
+constexpr int N64W_RB = N64W_MP / N64W_NB;        // 16 rows per thread
+constexpr int N64W_LD = N64W_MP + 1;
+
+// Shared memory in doubles: three [64][65] matrices (A, V and G during the
+// Newton-Schulz step; B exchange and output terms later), column sums [2][4][64],
+// 12 vectors of 64.
+__host__ __device__ constexpr size_t n64w_smem_doubles() {
+  return 3 * (size_t)N64W_MP * N64W_LD + 2 * (size_t)N64W_NB * N64W_MP + 12 * (size_t)N64W_MP;
+}
+
+// Sum over the row blocks of column c (every thread of the column gets it).
+__device__ __forceinline__ double colsum_w(double x, double *red, int &buf) {
+  const int c = threadIdx.x % N64W_MP, rb = threadIdx.x / N64W_MP;
+  double *r = red + (size_t)buf * N64W_NB * N64W_MP;
+  r[rb * N64W_MP + c] = x;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < N64W_NB; ++q) s += r[q * N64W_MP + c];
+  buf ^= 1;
+  return s;
+}
+
+__device__ void node64w(const LkInst &I, int pid, float *__restrict__ mean_out,
+                        float *__restrict__ spread_out, double tol, double stop, int max_sweeps,
+                        int *__restrict__ counters, double *smem) {
+  constexpr int MP = N64W_MP, NB = N64W_NB, RB = N64W_RB, LD = N64W_LD;
+  const int tid = threadIdx.x, c = tid % MP, rb = tid / MP, r0 = rb * RB;
+  const int m = I.m, w = I.w, ms = I.mp;        // ms: width of the stored basis (48 or 64)
+  double *M0 = smem, *M1 = M0 + MP * LD, *M2 = M1 + MP * LD;
+  double *red = M2 + MP * LD, *vec = red + 2 * NB * MP;
+  int buf = 0;
+
+  // ---- Gram (FP64): rows r0 .. r0+RB-1 of column c of A, and (C d)_c ----
+  const int2 ij = I.pts[pid];
+  const float *Ybp = static_cast<const float *>(I.Ybp);
+  const float *dp = static_cast<const float *>(I.dp);
+  const float *taper = static_cast<const float *>(I.taper);
+  double b[RB];
+#pragma unroll
+  for (int i = 0; i < RB; ++i) b[i] = 0.0;
+  double cd = 0.0;
+  for (int ds = 0; ds < w; ++ds) {
+    for (int dt = 0; dt < w; ++dt) {
+      const size_t src = (size_t)(ij.x + ds) * I.gs_cols + (ij.y + dt);
+      const double tw = (double)taper[ds * w + dt];
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        const float *yv = Ybp + (src * 2 + cc) * m;
+        const double cy = tw * (c < m ? (double)yv[c] : 0.0);
+        cd = fma(cy, (double)dp[src * 2 + cc], cd);
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+          const int r = r0 + i;
+          b[i] = fma(cy, r < m ? (double)yv[r] : 0.0, b[i]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < RB; ++i)
+    if (r0 + i == c) b[i] += c < m ? I.alpha : 1.0;
+
+  // ---- V0: stored FP32 basis (ms x ms, row-major), identity beyond ms ----
+  const float *U = I.basis + (size_t)pid * ms * ms;
+#pragma unroll
+  for (int i = 0; i < RB; ++i) {
+    const int r = r0 + i;
+    M0[r * LD + c] = b[i];                                       // A
+    M1[r * LD + c] = (r < ms && c < ms) ? (double)U[r * ms + c] : (r == c ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  // Newton-Schulz: V <- V (3I - V^T V) / 2; G = V^T V in M2
+#pragma unroll 4
+  for (int i = 0; i < RB; ++i) {
+    const int j = r0 + i;
+    double g = 0.0;
+    for (int k = 0; k < MP; ++k) g = fma(M1[k * LD + j], M1[k * LD + c], g);
+    M2[j * LD + c] = g;
+  }
+  __syncthreads();
+  double v[RB];
+#pragma unroll 4
+  for (int i = 0; i < RB; ++i) {
+    const int r = r0 + i;
+    double t = 0.0;
+    for (int j = 0; j < MP; ++j) t = fma(M1[r * LD + j], M2[j * LD + c], t);
+    v[i] = fma(-0.5, t, 1.5 * M1[r * LD + c]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < RB; ++i) M1[(r0 + i) * LD + c] = v[i];
+  __syncthreads();
+#pragma unroll 4
+  for (int i = 0; i < RB; ++i) {                                // B = A V
+    const int r = r0 + i;
+    double t = 0.0;
+    for (int k = 0; k < MP; ++k) t = fma(M0[r * LD + k], M1[k * LD + c], t);
+    b[i] = t;
+  }
+  __syncthreads();                     // M0 / M1 are reused as the exchange buffer
+
+  // ---- B-only sweeps, pairs (c, c ^ t) for t = 1 .. 63 ----
+  // Per step: B to shared memory, partner rows read back, partial dots summed
+  // over the row blocks by the 64 threads of block 0 (thread = column), which
+  // compute the rotation and the new tracked norm; every thread then applies
+  // the rotation to its rows. Three barriers per step.
+  if (stop < tol) stop = tol;
+  double *Bx = M0;
+  double *rot = vec;                   // [2][64]: c, signed s
+  double *nrm_s = vec + 2 * MP;        // [64] tracked squared norms
+  const bool lead = tid < MP;          // block 0: thread = column
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps; ++sweep) {
+    double part = 0.0;
+#pragma unroll
+    for (int i = 0; i < RB; ++i) part = fma(b[i], b[i], part);
+    const double nb = colsum_w(part, red, buf);
+    if (lead) nrm_s[c] = nb;
+    __syncthreads();
+    int flags = 0;
+    for (int t = 1; t < MP; ++t) {
+#pragma unroll
+      for (int i = 0; i < RB; ++i) Bx[(r0 + i) * LD + c] = b[i];
+      __syncthreads();
+      double pb[RB], pd = 0.0;
+      const int pc = c ^ t;
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        pb[i] = Bx[(r0 + i) * LD + pc];
+        pd = fma(b[i], pb[i], pd);
+      }
+      red[rb * MP + c] = pd;
+      __syncthreads();
+      double nnew = 0.0;
+      if (lead) {
+        double dot = 0.0;
+        for (int q = 0; q < NB; ++q) dot += red[q * MP + c];
+        const double mine = nrm_s[c], other = nrm_s[pc];
+        const bool isp = c < pc;
+        const double app = isp ? mine : other, aqq = isp ? other : mine;
+        double cs = 1.0, sn = 0.0, tr = 0.0;
+        if (fabs(dot) > tol * sqrt(app * aqq)) {
+          // the tangent in FP32 from x = aqq - app and y = 2 dot formed in FP64,
+          // then c = (1 + t^2)^-1/2 and s = c t in FP64 (orthogonal to FP64 rounding)
+          const float x = (float)(aqq - app), y = (float)(2.0 * dot);
+          const float rh = rsqrtf(fmaxf(fmaf(x, x, y * y), 1e-37f));
+          const float c2 = fmaf(0.5f * fabsf(x), rh, 0.5f);
+          const float tt = (x >= 0.f ? y : -y) * (0.5f * rh) / c2;
+          tr = (double)tt;
+          cs = rsqrt(fma(tr, tr, 1.0));
+          sn = cs * tr;
+          flags |= fabs(dot) > stop * sqrt(app * aqq) ? 3 : 1;
+        }
+        nnew = isp ? (app - tr * dot) : (aqq + tr * dot);
+        rot[c] = cs;
+        rot[MP + c] = isp ? -sn : sn;  // p' = c p - s q ; q' = s p + c q
+      }
+      __syncthreads();
+      const double cs = rot[c], sg = rot[MP + c];
+#pragma unroll
+      for (int i = 0; i < RB; ++i) b[i] = fma(sg, pb[i], cs * b[i]);
+      if (lead) nrm_s[c] = nnew;       // read again only after the next step's first barrier
+    }
+    if (!__syncthreads_or(flags & 2)) {
+      converged = true;
+      break;
+    }
+  }
+  if (tid == 0) {
+    atomicMax(&counters[2], converged ? sweep + 1 : sweep);
+    atomicAdd(&counters[3], converged ? sweep + 1 : sweep);
+    if (!converged) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
+  }
+
+  // ---- eigenpairs, transform and apply ----
+  double part = 0.0;
+#pragma unroll
+  for (int i = 0; i < RB; ++i) part = fma(b[i], b[i], part);
+  const double nb = colsum_w(part, red, buf);
+  const double lam = nb > 0.0 ? sqrt(nb) : 1.0;
+  const double il = 1.0 / lam;
+#pragma unroll
+  for (int i = 0; i < RB; ++i) b[i] *= il;                     // q = b / lambda
+  float *xrow = static_cast<float *>(I.X) + (size_t)pid * 2 * m;
+  double *cdv = vec + 3 * MP, *xs0 = cdv + MP, *xs1 = xs0 + MP;
+  double *gz0 = xs1 + MP, *gz1 = gz0 + MP, *gs0 = gz1 + MP, *gs1 = gs0 + MP;
+  if (rb == 0) {
+    cdv[c] = cd;
+    xs0[c] = c < m ? (double)xrow[c] : 0.0;
+    xs1[c] = c < m ? (double)xrow[m + c] : 0.0;
+  }
+  __syncthreads();
+  double xb0 = 0.0, xb1 = 0.0;
+  for (int j = 0; j < MP; ++j) {
+    xb0 += xs0[j];
+    xb1 += xs1[j];
+  }
+  const double inv_m = 1.0 / m;
+  xb0 *= inv_m;
+  xb1 *= inv_m;
+  double pu = 0.0, p0 = 0.0, p1 = 0.0;
+#pragma unroll
+  for (int i = 0; i < RB; ++i) {
+    const int r = r0 + i;
+    pu = fma(b[i], cdv[r], pu);                               // (Q^T C d)_c
+    p0 = fma(b[i], r < m ? xs0[r] - xb0 : 0.0, p0);           // (X'_0 Q)_c
+    p1 = fma(b[i], r < m ? xs1[r] - xb1 : 0.0, p1);
+  }
+  const double u = colsum_w(pu, red, buf);
+  const double g0 = colsum_w(p0, red, buf);
+  const double g1 = colsum_w(p1, red, buf);
+  // every eigenvector gets its root (a warm start leaves the padding's unit
+  // eigenvectors in arbitrary columns; their g0, g1 are zero)
+  const double z = u / lam, sroot = sqrt((m - 1) / lam);
+  if (rb == 0) {
+    gz0[c] = g0 * z;
+    gz1[c] = g1 * z;
+    gs0[c] = g0 * sroot;
+    gs1[c] = g1 * sroot;
+  }
+  __syncthreads();
+  // (X'_r W)_j = sum_c Q[j][c] g_r,c sroot_c: the terms, then a row sum per member
+#pragma unroll
+  for (int i = 0; i < RB; ++i) {
+    const int r = r0 + i;
+    M1[r * LD + c] = b[i] * gs0[c];
+    M2[r * LD + c] = b[i] * gs1[c];
+  }
+  __syncthreads();
+  double xa0 = 0.0, xa1 = 0.0;
+  const bool mem = tid < m;
+  if (tid < MP) {
+    const int j = tid;
+    double q0 = 0.0, q1 = 0.0, P0 = 0.0, P1 = 0.0;
+    for (int k = 0; k < MP; ++k) {
+      q0 += M1[j * LD + k];
+      q1 += M2[j * LD + k];
+      P0 += gz0[k];                                           // X'_r wbar
+      P1 += gz1[k];
+    }
+    xa0 = xb0 + P0 + q0;
+    xa1 = xb1 + P1 + q1;
+    if (mem) {
+      xrow[j] = (float)xa0;
+      xrow[m + j] = (float)xa1;
+    }
+  }
+  // mean and spread over the members (threads 0 .. 63: two warps)
+  double *sm4 = vec + 10 * MP;         // [4] warp partial sums
+  const int wp = tid >> 5, ln = tid & 31;
+  double s0 = lk_warp_sum(mem ? xa0 : 0.0), s1 = lk_warp_sum(mem ? xa1 : 0.0);
+  if (ln == 0 && wp < 2) {
+    sm4[2 * wp] = s0;
+    sm4[2 * wp + 1] = s1;
+  }
+  __syncthreads();
+  const double mu0 = (sm4[0] + sm4[2]) * inv_m, mu1 = (sm4[1] + sm4[3]) * inv_m;
+  __syncthreads();
+  const double e0 = mem ? xa0 - mu0 : 0.0, e1 = mem ? xa1 - mu1 : 0.0;
+  s0 = lk_warp_sum(e0 * e0);
+  s1 = lk_warp_sum(e1 * e1);
+  if (ln == 0 && wp < 2) {
+    sm4[2 * wp] = s0;
+    sm4[2 * wp + 1] = s1;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double sp0 = sqrt((sm4[0] + sm4[2]) / (m - 1)), sp1 = sqrt((sm4[1] + sm4[3]) / (m - 1));
+    if (mean_out) {
+      mean_out[0] = (float)mu0;
+      mean_out[1] = (float)mu1;
+    }
+    if (spread_out) {
+      spread_out[0] = (float)sp0;
+      spread_out[1] = (float)sp1;
+    }
+    if (!isfinite(mu0) || !isfinite(mu1) || !isfinite(sp0) || !isfinite(sp1))
+      atomicOr(&counters[0], LK_BIT_NONFINITE);
+  }
+}
+
+// The wide class's queue (MP = 48 and 64 nodes of FP32 handles): a fixed grid
+// of CTAs walking it.
+__global__ void __launch_bounds__(N64W_THREADS)
+    node64w_list_kernel(const LkInst *__restrict__ insts, const int2 *__restrict__ worklist,
+                        const int *__restrict__ queue_len, float *__restrict__ mean,
+                        float *__restrict__ spread, double tol, int max_sweeps,
+                        int *__restrict__ counters) {
+  extern __shared__ __align__(16) double n64_smem[];
+  lk_pdl_wait();   // no early trigger (long kernel): dependents launch as its CTAs exit
+  const int qn = *queue_len;
+  for (int idx = blockIdx.x; idx < qn; idx += gridDim.x) {
+    const int2 it = worklist[idx];
+    const LkInst &I = insts[it.x];
+    const long long row = I.node_off + it.y;
+    node64w(I, it.y, mean ? mean + 2 * row : nullptr, spread ? spread + 2 * row : nullptr, tol,
+            LK_WARM_STOP64, max_sweeps, counters, n64_smem);
+    __syncthreads();                       // shared memory is reused by the next node
+  }
+}
+
 // SM count of the handle's device (read once per device; handles on several
 // host threads may race to fill the cache, with the same value).
 int n64_sm_count(int device) {
@@ -418,13 +737,32 @@ cudaError_t launch_list64(letkf_ctx *h, int cls, void *mean, void *spread) {
                        (float *)mean, (float *)spread, h->tol64, h->max_sweeps, h->counters);
 }
 
+cudaError_t launch_list64w(letkf_ctx *h, void *mean, void *spread) {
+  long long n = 0;
+  for (const LkInst &I : h->inst)
+    if (I.mp > 32) n += I.n_pts;
+  if (n == 0) return cudaSuccess;
+  const long long cap = 2LL * n64_sm_count(h->device);
+  const unsigned blocks = (unsigned)(n < cap ? n : cap);
+  return lk_launch_pdl(node64w_list_kernel, blocks, N64W_THREADS,
+                       n64w_smem_doubles() * sizeof(double), h->stream, h->d_inst,
+                       h->worklist + (size_t)2 * h->n_pts_total, h->counters + 6, (float *)mean,
+                       (float *)spread, h->tol64, h->max_sweeps, h->counters);
+}
+
 }  // namespace
+
+cudaError_t lk_setup_node64w() {
+  return cudaFuncSetAttribute(node64w_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(n64w_smem_doubles() * sizeof(double)));
+}
 
 cudaError_t lk_launch_node64(letkf_ctx *h, int cls, void *mean, void *spread) {
   return cls == 0 ? launch_node64<16>(h, mean, spread) : launch_node64<32>(h, mean, spread);
 }
 
 cudaError_t lk_launch_list64(letkf_ctx *h, int cls, void *mean, void *spread) {
+  if (cls == 2) return launch_list64w(h, mean, spread);
   return cls == 0 ? launch_list64<16>(h, cls, mean, spread)
                   : launch_list64<32>(h, cls, mean, spread);
 }

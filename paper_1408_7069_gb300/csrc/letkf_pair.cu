@@ -29,11 +29,12 @@
 // from themselves), so its result does not depend on the nodes that share its
 // warp.
 //
-// For MP <= 32, kappa_hat = 1 + rho tr(G)/(m-1) bounds the condition number
-// before the eigensolve; nodes above the threshold still take this FP32 sweep,
-// store their eigenbasis (the start of their FP64 sweep) and leave X alone:
-// they are queued for the FP64 list kernel of letkf_node64.cu, which writes
-// them. Wider problems have no FP64 fallback.
+// kappa_hat = 1 + rho tr(G)/(m-1) bounds the condition number before the
+// eigensolve; nodes above the threshold still take this FP32 sweep, store
+// their eigenbasis (the start of their FP64 sweep) and leave X alone: they are
+// queued, per width class, for the FP64 list kernels of letkf_node64.cu
+// (MP = 16 and 32: node64_list_kernel; MP = 48 and 64 share one queue:
+// node64w_list_kernel), which write them.
 #include <math.h>
 #include <stdint.h>
 
@@ -546,7 +547,7 @@ template <int MP>
 cudaError_t launch_mp(letkf_ctx *h, int cls, const LkTile *tiles, int n_tiles, float *mean,
                       float *spread) {
   const float kthr = h->fp64_kappa > 0 ? (float)h->fp64_kappa : 0.f;
-  int *queue = (MP <= 32 && kthr > 0.f) ? h->counters + 4 + cls : nullptr;
+  int *queue = kthr > 0.f ? h->counters + 4 + cls : nullptr;
   int2 *wl = h->worklist + (size_t)cls * h->n_pts_total;
   switch (h->tile_shape[cls]) {
 #define LK_CASE(id, ti, tj) \

@@ -132,9 +132,8 @@ WIDE = [replace(W.ELT_80X80, name="w48", nsub=16, m=48, window=7, seeds=(141, 14
 
 @pytest.mark.parametrize("w", WIDE, ids=[w.name for w in WIDE])
 def test_wide_ensemble_matches_oracle(w):
-    """33..64 members (one node per warp, padded to 48 or 64 columns, FP32 only) on steady-state loop
-    backgrounds (the prior-draw transient needs the FP64 path, which this width
-    class does not have)."""
+    """33..64 members (one node per warp, padded to 48 or 64 columns) on a
+    steady-state loop background."""
     inp = synth.make_loop_inputs(w, frames=10)
     geom = oracle.build_geometry(inp.subap_mask, w.window, w.taper, w.loc_len)
     X = inp.X0.copy()
@@ -207,3 +206,102 @@ def test_wide_tile_shapes_leave_results_unchanged():
         if ref is None:
             ref = X
         assert np.array_equal(X, ref), shape
+
+
+@pytest.mark.parametrize("w", WIDE, ids=[w.name for w in WIDE])
+def test_wide_ensemble_fp64_fallback_from_the_prior_draw(w):
+    """The prior draw and the frames after it: ill-conditioned node problems
+    (kappa_hat above the threshold) of the wide class are redone in FP64 and
+    every frame matches the oracle, teacher-forced (the same FP32 background
+    into both)."""
+    inp = synth.make_loop_inputs(w, frames=5)
+    geom = oracle.build_geometry(inp.subap_mask, w.window, w.taper, w.loc_len)
+    f = L.Letkf.from_workload(w, bank=inp.bank)
+    f.set_state(torch.from_numpy(inp.X0.astype(np.float32)).cuda())
+    fp64 = []
+    for k in range(4):
+        Xb = f.get_state().cpu().numpy().astype(np.float64)
+        y = inp.slopes[k].astype(np.float32)
+        rXa, rmean, rspread = oracle.analysis_batched(geom, Xb, y.astype(np.float64), w.sigma2,
+                                                      w.rho)
+        mean, spread = f.analyze(torch.from_numpy(y).cuda())
+        f.sync()
+        fp64.append(f.stats()[0])
+        Xa = f.get_state().cpu().numpy().astype(np.float64)
+        assert rel(mean.cpu().numpy(), rmean) <= 1e-4, (k, rel(mean.cpu().numpy(), rmean))
+        assert rel(spread.cpu().numpy(), rspread) <= 1e-3, k
+        assert rel(Xa - Xa.mean(-1, keepdims=True), rXa - rXa.mean(-1, keepdims=True)) <= 1e-3, k
+        f.forecast()
+    assert fp64[0] > geom.n_pts // 2          # the prior draw sends most nodes to FP64
+    f.close()
+
+
+def _mix_inputs(ws, frames):
+    import multiprocessing as mp
+    import os
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.starmap(synth.make_loop_inputs, [(w, frames) for w in ws])
+
+
+def test_config5_mix_teacher_forced_at_sampled_nodes():
+    """The bench's 48-instance mix (nsub 16..96, m in {16, 24, 32, 48}) in one
+    handle from the prior draw: at frames 0..3 the analysis of 48 sampled nodes
+    of every instance matches the oracle's analysis of those nodes from the
+    same FP32 background (norm-wise over the sample, 1e-4 mean, 1e-3 spread)."""
+    ws = W.batched_instances(48, seed=50, frames=5)
+    assert any(w.m == 48 for w in ws)
+    ins = _mix_inputs(ws, 5)
+    geoms = [oracle.build_geometry(i.subap_mask, w.window, w.taper, w.loc_len)
+             for w, i in zip(ws, ins)]
+    f = L.Letkf.batch(ws, [i.bank for i in ins])
+    X0 = np.concatenate([i.X0.astype(np.float32).ravel() for i in ins])
+    f.set_state(torch.from_numpy(X0).cuda())
+    for k in range(4):
+        Xs = [x.cpu().numpy().astype(np.float64) for x in f.split_state(f.get_state())]
+        y = np.concatenate([i.slopes[k].astype(np.float32) for i in ins])
+        mean, spread = f.analyze(torch.from_numpy(y).cuda())
+        f.sync()
+        nfp64 = f.stats()[0]
+        if k == 0:
+            assert nfp64 > 0
+        mean, spread = mean.cpu().numpy(), spread.cpu().numpy()
+        row = 0
+        for w, inp, Xb, geom in zip(ws, ins, Xs, geoms):
+            n = geom.n_pts
+            sample = np.linspace(0, n - 1, 48).astype(int)
+            _, rmean, rspread = oracle.analysis_batched(
+                geom, Xb, inp.slopes[k].astype(np.float32).astype(np.float64), w.sigma2, w.rho,
+                nodes=sample)
+            gm, gs = mean[row:row + n][sample], spread[row:row + n][sample]
+            assert rel(gm, rmean[sample]) <= 1e-4, (k, w.name, rel(gm, rmean[sample]))
+            assert rel(gs, rspread[sample]) <= 1e-3, (k, w.name)
+            row += n
+        f.forecast()
+    f.close()
+
+
+def test_config5_reduced_mix_closed_loop():
+    """The mix's wide (m = 48) instances plus three others, grids capped at
+    24 x 24 so that the oracle runs every node: 10 closed-loop frames from the
+    prior draw, the criterion of every instance within 1e-3 of the oracle's."""
+    full = W.batched_instances(48, seed=50, frames=10)
+    wide = [w for w in full if w.m == 48][:4]
+    other = [w for w in full if w.m != 48][:3]
+    ws = [replace(w, nsub=min(w.nsub, 24)) for w in wide + other]
+    ins = _mix_inputs(ws, 10)
+    f = L.Letkf.batch(ws, [i.bank for i in ins])
+    X0 = np.concatenate([i.X0.astype(np.float32).ravel() for i in ins])
+    y = torch.from_numpy(np.concatenate([i.slopes.astype(np.float32) for i in ins], 1)).cuda()
+    t = torch.from_numpy(np.concatenate([i.truth.astype(np.float32) for i in ins], 1)).cuda()
+    f.set_state(torch.from_numpy(X0).cuda())
+    rv = f.run(10, y, t, use_graph=True).cpu().numpy()
+    f.sync()
+    f.close()
+    for k, (w, inp) in enumerate(zip(ws, ins)):
+        geom = oracle.build_geometry(inp.subap_mask, w.window, w.taper, w.loc_len)
+        rv_ref, _, _ = oracle.closed_loop(
+            geom, inp.truth.astype(np.float32).astype(np.float64),
+            inp.slopes.astype(np.float32).astype(np.float64), inp.bank, w.m, w.sigma2, w.rho,
+            w.a_ar1, w.noise_std, w.seeds[2], 10,
+            X0=inp.X0.astype(np.float32).astype(np.float64), batched=True)
+        assert np.max(np.abs(rv[:, k] - rv_ref) / rv_ref) <= 1e-3, (w.name, rv[:, k], rv_ref)
