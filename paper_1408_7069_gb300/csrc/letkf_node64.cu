@@ -471,7 +471,7 @@ __device__ void node64w(const LkInst &I, int pid, float *__restrict__ mean_out,
   }
   __syncthreads();
   // Newton-Schulz: V <- V (3I - V^T V) / 2; G = V^T V in M2
-#pragma unroll 4
+#pragma unroll
   for (int i = 0; i < RB; ++i) {
     const int j = r0 + i;
     double g = 0.0;
@@ -480,7 +480,7 @@ __device__ void node64w(const LkInst &I, int pid, float *__restrict__ mean_out,
   }
   __syncthreads();
   double v[RB];
-#pragma unroll 4
+#pragma unroll
   for (int i = 0; i < RB; ++i) {
     const int r = r0 + i;
     double t = 0.0;
@@ -491,7 +491,7 @@ __device__ void node64w(const LkInst &I, int pid, float *__restrict__ mean_out,
 #pragma unroll
   for (int i = 0; i < RB; ++i) M1[(r0 + i) * LD + c] = v[i];
   __syncthreads();
-#pragma unroll 4
+#pragma unroll
   for (int i = 0; i < RB; ++i) {                                // B = A V
     const int r = r0 + i;
     double t = 0.0;
@@ -742,7 +742,7 @@ cudaError_t launch_list64w(letkf_ctx *h, void *mean, void *spread) {
   for (const LkInst &I : h->inst)
     if (I.mp > 32) n += I.n_pts;
   if (n == 0) return cudaSuccess;
-  const long long cap = 2LL * n64_sm_count(h->device);
+  const long long cap = n64_sm_count(h->device);        // one CTA per SM (216 registers)
   const unsigned blocks = (unsigned)(n < cap ? n : cap);
   return lk_launch_pdl(node64w_list_kernel, blocks, N64W_THREADS,
                        n64w_smem_doubles() * sizeof(double), h->stream, h->d_inst,
