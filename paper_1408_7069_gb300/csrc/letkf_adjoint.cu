@@ -21,7 +21,7 @@
 // nodes whose kappa_hat bound sends them to FP64 in the forward analysis are
 // queued and redone in FP64 with accumulated eigenvectors, starting from the
 // FP32 basis U0 that the forward pair kernel stored for the node (FP64 handles
-// start from the identity).
+// start from the FP32-rounded FP64 basis their forward node kernel stored).
 //
 // Every node writes the adjoints of its window's slopes to its own slots; a
 // subaperture kernel sums them over the nodes whose window holds the slope (in
@@ -111,9 +111,10 @@ __device__ __forceinline__ void df_add_prod(float &hi, float &lo, float a, float
 
 // Adjoint of one node's analysis. T = float: FP32 handle, warm start from the
 // frame's stored eigenbasis U0 and B-only Jacobi, nodes above kappa_thr queued.
-// T = double: accumulated eigenvectors, started from the identity (FP64
-// handles) or, with `list` (the FP64 queue of an FP32 handle), from the FP32
-// basis U0 the forward pair kernel stored for the queued node.
+// T = double: accumulated eigenvectors, started from the FP32-rounded basis U0
+// that the frame's forward analysis stored: the FP64 node kernel's for FP64
+// handles, or, with `list` (the FP64 queue of an FP32 handle), the forward pair
+// kernel's for the queued node.
 template <int MP, typename S, typename T>
 __global__ void __launch_bounds__(ADJ_WARPS * 32)
     adjoint_node_kernel(const LkInst *__restrict__ insts, const int2 *__restrict__ list,
@@ -597,9 +598,10 @@ cudaError_t launch_nodes(letkf_ctx *h, LkAdjWork *W, const float *U0, const AdjA
   const LkInst &I = h->inst[0];
   const int blocks = (I.n_pts + ADJ_WARPS - 1) / ADJ_WARPS;
   if (h->precision == 1) {
+    // FP64 handles: refined from the eigenbasis the forward node64 kernel stored
     adjoint_node_kernel<MP, double, double>
         <<<blocks, ADJ_WARPS * 32, node_smem<MP, double, double>(I), h->stream>>>(
-            h->d_inst, nullptr, nullptr, nullptr, 0.f, nullptr, nullptr, h->tol64, a);
+            h->d_inst, nullptr, nullptr, U0, 0.f, nullptr, nullptr, h->tol64, a);
     return cudaGetLastError();
   }
   const float kthr = h->fp64_kappa > 0 ? (float)h->fp64_kappa : 0.f;

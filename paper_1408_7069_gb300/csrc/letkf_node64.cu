@@ -83,7 +83,7 @@ __device__ __forceinline__ double colsum(double x, double *red, int &buf) {
 template <int MP, typename S, bool WARM>
 __device__ void node64(const LkInst &I, int pid, S *__restrict__ mean_out,
                        S *__restrict__ spread_out, double tol, double stop, int max_sweeps,
-                       int *__restrict__ counters, double *smem) {
+                       int *__restrict__ counters, double *smem, bool keep_basis = false) {
   constexpr int NB = N64<MP>::NB, RB = N64<MP>::RB, LD = N64<MP>::LD;
   const int tid = threadIdx.x, c = tid % MP, rb = tid / MP, r0 = rb * RB;
   const int m = I.m, w = I.w;
@@ -250,6 +250,16 @@ __device__ void node64(const LkInst &I, int pid, S *__restrict__ mean_out,
     atomicAdd(&counters[3], converged ? sweep + 1 : sweep);
     if (!converged) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
   }
+  if (keep_basis) {
+    // the eigenvectors (rounded to FP32) for the reverse mode, which refines
+    // them in FP64 instead of sweeping from the identity again
+    float *U = I.basis + (size_t)pid * MP * MP;
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+      const int r = r0 + i;
+      U[r * MP + c] = isfinite(v[i]) ? (float)v[i] : (r == c ? 1.f : 0.f);
+    }
+  }
   __syncthreads();                           // rot (in vec) is reused below
 
   // ---- weights and update: lambda_c = |B e_c|, column c of V is v ----
@@ -349,7 +359,7 @@ template <int MP, typename S>
 __global__ void __launch_bounds__(N64_THREADS)
     node64_kernel(const LkInst *__restrict__ insts, const int2 *__restrict__ items,
                   S *__restrict__ mean, S *__restrict__ spread, double tol, int max_sweeps,
-                  int *__restrict__ counters) {
+                  int *__restrict__ counters, int keep_basis) {
   extern __shared__ __align__(16) double n64_smem[];
   lk_pdl_wait();   // no early trigger (long kernel): dependents launch as its CTAs exit
   const int2 it = items[blockIdx.x];
@@ -357,7 +367,7 @@ __global__ void __launch_bounds__(N64_THREADS)
   if (I.mp != MP) return;
   const long long row = I.node_off + it.y;
   node64<MP, S, false>(I, it.y, mean ? mean + 2 * row : nullptr, spread ? spread + 2 * row : nullptr,
-                       tol, 0.0, max_sweeps, counters, n64_smem);
+                       tol, 0.0, max_sweeps, counters, n64_smem, keep_basis != 0);
 }
 
 // FP32 handles: the nodes the pair kernel queued, a fixed grid of CTAs walking
@@ -720,7 +730,7 @@ cudaError_t launch_node64(letkf_ctx *h, void *mean, void *spread) {
   const size_t smem = n64_smem_doubles<MP>() * sizeof(double);
   return lk_launch_pdl(node64_kernel<MP, double>, (unsigned)h->n_pts_total, N64_THREADS, smem,
                        h->stream, h->d_inst, h->node_items, (double *)mean, (double *)spread,
-                       h->tol64, h->max_sweeps, h->counters);
+                       h->tol64, h->max_sweeps, h->counters, h->keep_basis);
 }
 
 template <int MP>
