@@ -216,6 +216,22 @@ def batched_arm(torch, L, K, Wm):
     f.sync()
     ms = e0.elapsed_time(e1)
     fp64_last, sweeps, total = f.stats()
+    # the same frames as one launch (letkf_run_graph) with in-graph stamps
+    stamps = torch.zeros(K + 1, dtype=torch.int64, device="cuda")
+    for rep in range(2):                     # the first call instantiates the graph
+        f.set_state(X0)
+        f.set_frame(0)
+        f.run(Wm, y, use_graph=True)
+        torch.cuda.synchronize()
+        e0.record(f.stream)
+        L.letkf_run_graph(f.h, K, yt, None, None, stamps)
+        e1.record(f.stream)
+        torch.cuda.synchronize()
+    f.sync()
+    st_us = np.diff(stamps.cpu().numpy().astype(np.float64)) / 1e3
+    one_launch = {"frames_per_s": K / (e0.elapsed_time(e1) / 1e3),
+                  "p50_us": percentile(list(st_us), 50), "p99_us": percentile(list(st_us), 99),
+                  "launch": "letkf_run_graph: all frames of all 48 instances in one CUDA graph"}
     nodes = f.n_pts
     out = {"instances": len(ws), "nodes": nodes,
            "members": {str(k): sum(1 for w in ws if w.m == k) for k in (16, 24, 32, 48)},
@@ -224,6 +240,7 @@ def batched_arm(torch, L, K, Wm):
            "tile_shapes": rec.get("tiles"), "autotune_us": rec.get("us"),
            "autotune_cached": rec.get("cached"), "jacobi_sweeps_mean": total / max(1, nodes),
            "fp64_nodes_last_frame": fp64_last, "prior_draw_frames": transient,
+           "one_launch": one_launch,
            "parity": "48 sampled nodes of every instance against the oracle at frames 0-3 from "
                      "the prior draw, and a reduced mix (its m = 48 instances) over 10 closed-loop "
                      "frames (GPU tests)",
@@ -609,6 +626,28 @@ def gpu_arm(args):
     L.letkf_sync(h)
     graph_fps = K / (g0.elapsed_time(g1) / 1e3)
 
+    # every frame in ONE CUDA-graph launch (letkf_run_graph), per-frame times
+    # from global-timer stamps written inside the launch (state in L2, no flush)
+    Kp = min(K, 1000)
+    stamps = torch.zeros(Kp + 1, dtype=torch.int64, device="cuda")
+    persistent = None
+    for rep in range(2):                     # the first call instantiates the graph
+        f.set_state(X0)
+        f.set_frame(0)
+        L.letkf_run(h, Wm, y, truth, resvar, True)
+        torch.cuda.synchronize()
+        g0.record(s)
+        L.letkf_run_graph(h, Kp, y[Wm:], truth[Wm:], resvar[Wm:], stamps)
+        g1.record(s)
+        torch.cuda.synchronize()
+        L.letkf_sync(h)
+    st_us = np.diff(stamps.cpu().numpy().astype(np.float64)) / 1e3
+    persistent = {"frames": Kp, "frames_per_s": Kp / (g0.elapsed_time(g1) / 1e3),
+                  "p50_us": percentile(list(st_us), 50), "p99_us": percentile(list(st_us), 99),
+                  "max_us": float(st_us.max()),
+                  "launch": "letkf_run_graph: all frames captured in one CUDA graph, one launch; "
+                            "per-frame times from %globaltimer stamps inside it"}
+
     # end to end through the public API with host buffers: one letkf_step per
     # frame (inputs copied in from host memory, analysis mean and residual
     # copied out, synchronised), as a real-time controller calls it
@@ -652,6 +691,7 @@ def gpu_arm(args):
         "p50_us": 1e3 * percentile(frame_ms, 50), "p99_us": 1e3 * percentile(frame_ms, 99),
         "max_us": 1e3 * max(frame_ms),
         "graph_frames_per_s": graph_fps,
+        "persistent": persistent,
         # letkf_step's staging places y, truth, mean and the residual at 256-byte
         # aligned offsets and moves each pair with one copy (gap included)
         "e2e": {"value": e2e_fps, "unit": UNIT,

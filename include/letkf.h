@@ -160,6 +160,18 @@ letkf_status letkf_residual(letkf_t h, const void *truth_dev, double *resvar_dev
 letkf_status letkf_run(letkf_t h, int32_t frames, const void *y_seq_dev, const void *truth_seq_dev,
                        double *resvar_dev, int32_t use_graph);
 
+/* The closed loop of letkf_run over `frames` frames (1..65536) as ONE launch:
+ * every frame of every instance (residual, observation, analysis, forecast)
+ * is captured into one CUDA graph, instantiated once per (frames, pointers)
+ * and launched once, so the host takes no part between frames. Same results
+ * as letkf_run, bit for bit. stamps_dev: device uint64_t[frames + 1] or NULL;
+ * element 0 receives the global timer (ns) at the start of the launch and
+ * element k + 1 once frame k has completed, so per-frame times are taken
+ * inside the launch. Requires a non-default stream and a noise bank for every
+ * instance. */
+letkf_status letkf_run_graph(letkf_t h, int32_t frames, const void *y_seq_dev,
+                             const void *truth_seq_dev, double *resvar_dev, uint64_t *stamps_dev);
+
 /* Change instance i's inflation rho, slope noise variance sigma2 and taper
  * half-support loc_len (<= 0: window / 4) in place (Section 4.2: A = (m-1)/rho I
  * + Yb^T R^-1 Yb with R^-1 = diag(tau_j / sigma2)); the next analysis uses them.

@@ -65,6 +65,8 @@ letkf_status upload(letkf_ctx *h, void *dst, const void *src, size_t bytes) {
 void drop_graphs(letkf_ctx *h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
+  if (h->mgraph) cudaGraphExecDestroy(h->mgraph);
+  h->mgraph = nullptr;
   for (cudaGraphExec_t &g : h->step_graph) {
     if (g) cudaGraphExecDestroy(g);
     g = nullptr;
@@ -615,6 +617,58 @@ letkf_status letkf_run(letkf_t h, int32_t frames, const void *y_seq_dev, const v
       if (st != LETKF_OK) return st;
     }
   }
+  h->frame_host += frames;
+  return LETKF_OK;
+}
+
+letkf_status letkf_run_graph(letkf_t h, int32_t frames, const void *y_seq_dev,
+                             const void *truth_seq_dev, double *resvar_dev,
+                             uint64_t *stamps_dev) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (frames < 1 || frames > (1 << 16)) return fail(h, LETKF_ERR_ARG, "frames must be 1..65536");
+  if (!y_seq_dev) return fail(h, LETKF_ERR_ARG, "y_seq_dev is NULL");
+  if (!all_have_banks(h))
+    return fail(h, LETKF_ERR_STATE, "letkf_run_graph needs a noise bank for every instance");
+  if (h->stream == nullptr)
+    return fail(h, LETKF_ERR_STATE, "graph capture needs a non-default stream");
+  DeviceGuard dg(h->device);
+  unsigned long long *stamps = reinterpret_cast<unsigned long long *>(stamps_dev);
+  if (!h->mgraph || h->mgraph_frames != frames || h->mgraph_y != y_seq_dev ||
+      h->mgraph_truth != truth_seq_dev || h->mgraph_resvar != resvar_dev ||
+      h->mgraph_stamps != stamps) {
+    if (h->mgraph) {
+      cudaGraphExecDestroy(h->mgraph);
+      h->mgraph = nullptr;
+    }
+    LK_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    letkf_status st = LETKF_OK;
+    cudaError_t ce = stamps ? lk_launch_stamp(h, stamps) : cudaSuccess;
+    if (ce != cudaSuccess) st = cuda_fail(h, ce, "stamp launch");
+    for (int k = 0; k < frames && st == LETKF_OK; ++k) {
+      st = enqueue_frame(h, y_seq_dev, truth_seq_dev, resvar_dev);
+      if (st == LETKF_OK && stamps) {
+        ce = lk_launch_stamp(h, stamps + k + 1);
+        if (ce != cudaSuccess) st = cuda_fail(h, ce, "stamp launch");
+      }
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (st != LETKF_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->mgraph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    h->mgraph_frames = frames;
+    h->mgraph_y = y_seq_dev;
+    h->mgraph_truth = truth_seq_dev;
+    h->mgraph_resvar = resvar_dev;
+    h->mgraph_stamps = stamps;
+  }
+  LK_CUDA(h, cudaMemsetAsync(h->frame + 1, 0, sizeof(long long), h->stream));
+  LK_CUDA(h, cudaGraphLaunch(h->mgraph, h->stream));
   h->frame_host += frames;
   return LETKF_OK;
 }

@@ -118,6 +118,12 @@ struct letkf_ctx {
   cudaGraphExec_t graph = nullptr;
   const void *graph_y = nullptr, *graph_truth = nullptr;
   const double *graph_resvar = nullptr;
+  // graph of a whole run of frames (letkf_run_graph)
+  cudaGraphExec_t mgraph = nullptr;
+  int mgraph_frames = 0;
+  const void *mgraph_y = nullptr, *mgraph_truth = nullptr;
+  const double *mgraph_resvar = nullptr;
+  const unsigned long long *mgraph_stamps = nullptr;
 
   LkAdjWork *adj = nullptr;         // letkf_grad buffers and graph, built on first use
 
@@ -151,6 +157,8 @@ cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
 cudaError_t lk_launch_residual_on(letkf_ctx *h, cudaStream_t stream, const void *truth,
                                   double *resvar, const long long *run_idx, double *piston);
 cudaError_t lk_launch_basis_reset(letkf_ctx *h);   // warm-start eigenbases -> identity
+// Writes the global timer (ns) into *dst once the preceding work has completed.
+cudaError_t lk_launch_stamp(letkf_ctx *h, unsigned long long *dst);
 cudaError_t lk_setup_analysis(letkf_ctx *h);
 // FP32 analysis of width class cls, two columns per lane (letkf_pair.cu).
 cudaError_t lk_launch_pair(letkf_ctx *h, int cls, void *mean, void *spread);

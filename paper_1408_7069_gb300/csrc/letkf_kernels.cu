@@ -281,3 +281,15 @@ cudaError_t lk_launch_basis_reset(letkf_ctx *h) {
   return cudaGetLastError();
 }
 
+// Frame stamp of a multi-frame graph: the global timer (ns) once the frame's
+// last kernel has completed (a plain launch waits for the whole forecast grid).
+__global__ void stamp_kernel(unsigned long long *__restrict__ dst) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  *dst = t;
+}
+
+cudaError_t lk_launch_stamp(letkf_ctx *h, unsigned long long *dst) {
+  stamp_kernel<<<1, 1, 0, h->stream>>>(dst);
+  return cudaGetLastError();
+}

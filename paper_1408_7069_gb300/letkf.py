@@ -51,6 +51,7 @@ _SIGS = {
     "letkf_analyze": [c_void_p, c_void_p, c_void_p, c_void_p],
     "letkf_residual": [c_void_p, c_void_p, c_void_p],
     "letkf_run": [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32],
+    "letkf_run_graph": [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p],
     "letkf_sync": [c_void_p],
     "letkf_stats": [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)],
     "letkf_analyze_noalloc": [POINTER(letkf_config), c_void_p, c_void_p, c_void_p, c_void_p,
@@ -205,6 +206,11 @@ def letkf_residual(h, truth, resvar) -> None:
 def letkf_run(h, frames: int, y_seq, truth_seq=None, resvar=None, use_graph: bool = True) -> None:
     _check(lib().letkf_run(h, int(frames), _ptr(y_seq), _ptr(truth_seq), _ptr(resvar),
                            1 if use_graph else 0), h)
+
+
+def letkf_run_graph(h, frames: int, y_seq, truth_seq=None, resvar=None, stamps=None) -> None:
+    _check(lib().letkf_run_graph(h, int(frames), _ptr(y_seq), _ptr(truth_seq), _ptr(resvar),
+                                 _ptr(stamps)), h)
 
 
 def letkf_set_params(h, i: int, rho: float, sigma2: float, loc_len: float) -> None:
@@ -455,6 +461,30 @@ class Letkf:
         letkf_run(self.h, frames, y_seq, truth_seq, resvar, use_graph)
         self._leave()
         return resvar
+
+    def run_graph(self, frames: int, y_seq, truth_seq=None, resvar=None, stamps: bool = False):
+        """All `frames` frames as one CUDA-graph launch (letkf_run_graph).
+        Returns (resvar or None, per-frame durations in microseconds from the
+        in-graph timer stamps, or None)."""
+        self._t(y_seq, (y_seq.shape[0], self.p))
+        if y_seq.shape[0] < frames:
+            raise ValueError("y_seq shorter than frames")
+        if truth_seq is not None:
+            self._t(truth_seq, (truth_seq.shape[0], self.n_pts))
+            if truth_seq.shape[0] < frames:
+                raise ValueError("truth_seq shorter than frames")
+            if resvar is None:
+                shape = (frames,) if self.n_inst == 1 else (frames, self.n_inst)
+                resvar = self._torch.zeros(*shape, dtype=self._torch.float64, device="cuda")
+        st = self._torch.zeros(frames + 1, dtype=self._torch.int64, device="cuda") if stamps else None
+        self._enter()
+        letkf_run_graph(self.h, frames, y_seq, truth_seq, resvar, st)
+        self._leave()
+        us = None
+        if stamps:
+            t = st.cpu().numpy().astype(np.float64)
+            us = np.diff(t) / 1e3
+        return resvar, us
 
     def set_params(self, rho: float, sigma2: float, loc_len: float, instance: int = 0):
         letkf_set_params(self.h, instance, rho, sigma2, loc_len)

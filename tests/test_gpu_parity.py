@@ -326,6 +326,37 @@ def test_sweep_limit_is_reported_and_handle_survives(precision):
     f.close()
 
 
+@pytest.mark.parametrize("w", [W.TEL_16M, W.TOY_8X8], ids=["16m", "8x8-fp64"])
+def test_run_graph_equals_run_bitwise(w):
+    """letkf_run_graph (every frame in one CUDA-graph launch, timer stamps
+    inside it) leaves the state and the criterion of letkf_run, bit for bit."""
+    frames = 12
+    inp, geom = inputs(w, frames)
+    rt = dtype_of(w)
+    X0 = torch.from_numpy(inp.X0.astype(rt)).cuda()
+    y = torch.from_numpy(inp.slopes.astype(rt)).cuda()
+    t = torch.from_numpy(inp.truth.astype(rt)).cuda()
+    f = Letkf.from_workload(w, bank=inp.bank)
+    f.set_state(X0)
+    rv_a = f.run(frames, y, t, use_graph=True)
+    f.sync()
+    Xa = f.get_state().cpu().numpy()
+    f.set_state(X0)
+    f.set_frame(0)
+    rv_b, us = f.run_graph(frames, y, t, stamps=True)
+    f.sync()
+    assert np.array_equal(f.get_state().cpu().numpy(), Xa)
+    assert np.array_equal(rv_a.cpu().numpy(), rv_b.cpu().numpy())
+    assert us.shape == (frames,) and np.all(us > 0) and np.all(us < 1e6)
+    # a second launch of the same graph continues the loop like letkf_run
+    f.set_state(X0)
+    f.set_frame(0)
+    f.run_graph(frames, y, t)
+    f.sync()
+    assert np.array_equal(f.get_state().cpu().numpy(), Xa)
+    f.close()
+
+
 def test_step_from_host_buffers_equals_run():
     """letkf_step (host buffers, one graph per frame) runs the same frames as
     letkf_run: same residuals, same final ensemble, and the returned analysis
