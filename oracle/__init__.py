@@ -4,3 +4,4 @@ Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and reference
 legs import this package. It shares no code with the CUDA library.
 """
 from .letkf_oracle import *  # noqa: F401,F403
+from . import letkf_domains  # noqa: F401,E402
