@@ -81,6 +81,11 @@ typedef struct {
   const float *noise_bank;     /* host [bank_B][bank_G][bank_G] screens, or NULL; copied */
   int32_t bank_B, bank_G;      /* bank shape (ignored when noise_bank is NULL) */
   int32_t max_sweeps;          /* Jacobi sweep limit per node; <= 0 -> 20 */
+  int32_t partition;           /* 0: every node is its own local domain (the per-node analysis);
+                                  P in 1..64: multi-actuator local domains of a P x P partition
+                                  of the node grid (Section 4.1), single instance, FP32, m 2..128 */
+  int32_t piston;              /* with partition > 0: nonzero = remove the differential pistons
+                                  between domains by least squares (Section 4.4) */
 } letkf_config;
 
 /* Validate the configuration, build the node list, the per-node observation
@@ -110,6 +115,23 @@ letkf_status letkf_query(letkf_t h, int32_t *n_pts, int32_t *p, int32_t *m);
 /* Sizes of instance i and the number of instances. Host pointers, any may be NULL. */
 letkf_status letkf_query_instance(letkf_t h, int32_t i, int32_t *n_pts, int32_t *p, int32_t *m,
                                   int32_t *n_inst);
+
+/* Local domains of a handle created with partition = P > 0 (Section 4.1): the
+ * node grid's side of N = nsub + 1 nodes is cut into blocks [floor(b N / P),
+ * floor((b + 1) N / P)), b = 0 .. P-1, and the valid nodes of each of the P x P
+ * blocks form a domain (empty blocks are dropped; domains are numbered
+ * row-major over the blocks). Every domain is analysed as one local problem
+ * (Section 4.2) with n_d = 2 x its nodes state rows, observing the union of
+ * its nodes' windows with tau = Gaspari-Cohn of the distance from the
+ * subaperture centre to the domain's node box (tau = 1 inside it), and with
+ * piston != 0 the analysis mean increments are made continuous across domain
+ * borders by one least-squares constant per domain and state row (Section 4.4;
+ * the constants of each connected group of domains have zero node-weighted
+ * mean). letkf_stats then counts in fp64_points the domains whose kappa_hat
+ * exceeds fp64_kappa (there is no FP64 path for domains).
+ * n_dom: number of domains (0 for a per-node handle); node_dom_host: host
+ * int32 [n_pts], the domain of every node, or NULL. Either may be NULL. */
+letkf_status letkf_query_domains(letkf_t h, int32_t *n_dom, int32_t *node_dom_host);
 
 /* Host copies of the node coordinates [n_pts][2] (i, j) and of the number of
  * valid window slopes per node [n_pts] (p_l, Section 4.2's p_d). Either may be NULL. */

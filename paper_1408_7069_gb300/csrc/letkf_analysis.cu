@@ -261,6 +261,7 @@ cudaError_t lk_launch_analysis_class(letkf_ctx *h, int cls, void *mean, void *sp
 // Every caller launches the observation kernel just before; it zeroes the
 // counters this analysis counts into (no memset node breaks the launch chain).
 cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread) {
+  if (h->dom) return lk_launch_domains(h, mean, spread);
   cudaError_t e = launch_class<16>(h, 0, mean, spread);
   if (e == cudaSuccess) e = launch_class<32>(h, 1, mean, spread);
   if (e == cudaSuccess) e = launch_class<64>(h, 2, mean, spread);
@@ -399,6 +400,10 @@ extern "C" letkf_status letkf_analyze_noalloc(const letkf_config *cfg, void *X_d
       c.window > NA_MAX_W) {
     na_error(errbuf, errlen,
              "size beyond the allocation-free maximum: nsub 1..128, m 2..32, window 1..15");
+    return LETKF_ERR_ARG;
+  }
+  if (c.partition != 0) {
+    na_error(errbuf, errlen, "the allocation-free analysis is per node (partition must be 0)");
     return LETKF_ERR_ARG;
   }
   if (c.precision != 0 || (c.taper != 0 && c.taper != 1) || !(c.rho > 0) || !(c.sigma2 > 0) ||

@@ -31,20 +31,7 @@ letkf_status cuda_fail(letkf_ctx *h, cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);  \
   } while (0)
 
-// Gaspari & Cohn (1999) compactly supported 5th-order piecewise rational
-// function of z = r / c (their Eq. 4.10): 1 at z = 0, 0 for z >= 2.
-double gaspari_cohn(double z) {
-  z = fabs(z);
-  if (z <= 1.0) {
-    const double z2 = z * z, z3 = z2 * z;
-    return ((-0.25 * z + 0.5) * z + 0.625) * z3 - (5.0 / 3.0) * z2 + 1.0;
-  }
-  if (z < 2.0) {
-    const double z2 = z * z;
-    return (((z / 12.0 - 0.5) * z + 0.625) * z + 5.0 / 3.0) * z2 - 5.0 * z + 4.0 - (2.0 / 3.0) / z;
-  }
-  return 0.0;
-}
+double gaspari_cohn(double z) { return lk_gaspari_cohn(z); }
 
 template <typename T>
 letkf_status dalloc(letkf_ctx *h, T **dst, size_t bytes) {
@@ -76,6 +63,7 @@ void drop_graphs(letkf_ctx *h) {
 
 void release(letkf_ctx *h) {
   drop_graphs(h);
+  lk_domains_release(h);
   for (cudaEvent_t ev : {h->ev_fork, h->ev_join, h->ev_out})
     if (ev) cudaEventDestroy(ev);
   if (h->side) cudaStreamDestroy(h->side);
@@ -105,7 +93,14 @@ struct DeviceGuard {
 letkf_status check_config(const letkf_config &c) {
   if (c.nsub < 1 || c.nsub > 1024) return fail(nullptr, LETKF_ERR_ARG, "nsub must be in 1..1024");
   if (!c.subap_mask) return fail(nullptr, LETKF_ERR_ARG, "subap_mask is NULL");
-  if (c.m < 2 || c.m > 64) return fail(nullptr, LETKF_ERR_ARG, "m must be in 2..64");
+  if (c.partition < 0 || c.partition > 64)
+    return fail(nullptr, LETKF_ERR_ARG, "partition must be in 0..64");
+  if (c.partition > 0 && (c.m < 2 || c.m > 128))
+    return fail(nullptr, LETKF_ERR_ARG, "m must be in 2..128 with local domains");
+  if (c.partition > 0 && c.precision != 0)
+    return fail(nullptr, LETKF_ERR_ARG, "local domains are analysed in FP32 (precision 0)");
+  if (c.partition == 0 && (c.m < 2 || c.m > 64))
+    return fail(nullptr, LETKF_ERR_ARG, "m must be in 2..64");
   if (c.precision == 1 && c.m > 32)
     return fail(nullptr, LETKF_ERR_ARG, "m must be in 2..32 with precision 1");
   if (c.window < 1 || c.window > 31) return fail(nullptr, LETKF_ERR_ARG, "window must be in 1..31");
@@ -246,6 +241,8 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
     if (st != LETKF_OK) return st;
     if (cfgs[k].precision != cfgs[0].precision)
       return fail(nullptr, LETKF_ERR_ARG, "all instances of a batch share one precision");
+    if (cfgs[k].partition > 0 && n > 1)
+      return fail(nullptr, LETKF_ERR_ARG, "local domains take a single-instance handle");
   }
   letkf_ctx *h = new (std::nothrow) letkf_ctx();
   if (!h) return fail(nullptr, LETKF_ERR_NOMEM, "host allocation failed");
@@ -284,7 +281,8 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
     I.m = c.m;
     I.w = c.window;
     I.h = c.window / 2;
-    I.mp = c.m <= 16 ? 16 : (c.m <= 32 ? 32 : (c.m <= 48 ? 48 : 64));
+    // (domain handles use no per-node kernel and keep the smallest basis store)
+    I.mp = c.partition > 0 ? 16 : c.m <= 16 ? 16 : (c.m <= 32 ? 32 : (c.m <= 48 ? 48 : 64));
     I.n_pts = (int)geo[k].pts.size();
     I.n_sap = (int)geo[k].saps.size();
     I.p = 2 * I.n_sap;
@@ -406,7 +404,16 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   if (e == cudaSuccess) e = cudaMemset(h->frame, 0, 2 * sizeof(long long));
   if (e == cudaSuccess) e = cudaMemset(h->tickets, 0, (size_t)(n + 1) * sizeof(int));
   if (e != cudaSuccess) LK_TRY(cuda_fail(h, e, "cudaMemset"));
-  for (int cls = 0; cls < 3; ++cls) LK_TRY(build_tiles(h, cls, pids));
+  if (cfgs[0].partition > 0) {
+    h->dom_pid = geo[0].pid;
+    h->dom_pts = geo[0].pts;
+    h->dom_saps = geo[0].saps;
+    letkf_status ds = lk_domains_build(h, cfgs[0], h->dom_pid, h->dom_pts, h->dom_saps, h->err);
+    if (ds != LETKF_OK && h->err.empty()) h->err = "local-domain set-up failed";
+    LK_TRY(ds);
+  } else {
+    for (int cls = 0; cls < 3; ++cls) LK_TRY(build_tiles(h, cls, pids));
+  }
   e = lk_setup_analysis(h);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) LK_TRY(cuda_fail(h, e, "device set-up"));
@@ -673,6 +680,16 @@ letkf_status letkf_run_graph(letkf_t h, int32_t frames, const void *y_seq_dev,
   return LETKF_OK;
 }
 
+letkf_status letkf_query_domains(letkf_t h, int32_t *n_dom, int32_t *node_dom_host) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (n_dom) *n_dom = lk_domain_count(h);
+  if (node_dom_host && h->dom) {
+    DeviceGuard dg(h->device);
+    if (!lk_domain_of_nodes(h, node_dom_host)) return fail(h, LETKF_ERR_CUDA, "cudaMemcpy");
+  }
+  return LETKF_OK;
+}
+
 letkf_status letkf_set_params(letkf_t h, int32_t i, double rho, double sigma2, double loc_len) {
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
   if (i < 0 || i >= h->n_inst) return fail(h, LETKF_ERR_ARG, "no such instance");
@@ -691,6 +708,8 @@ letkf_status letkf_set_params(letkf_t h, int32_t i, double rho, double sigma2, d
   taper_table(c, tap);
   letkf_status st = upload_taper(h, I, tap);
   if (st == LETKF_OK) st = upload(h, h->d_inst + i, &I, sizeof(LkInst));
+  if (st == LETKF_OK && h->dom)
+    st = lk_domains_set_params(h, c, h->dom_pid, h->dom_pts, h->dom_saps, h->err);
   drop_graphs(h);          // the reverse mode's graph holds rho and sigma2 as kernel arguments
   return st;
 }
@@ -806,7 +825,7 @@ letkf_status letkf_autotune(letkf_t h, const void *y_dev, int32_t reps, int32_t 
   if (!y_dev || reps < 1) return fail(h, LETKF_ERR_ARG, "y_dev and reps >= 1 are required");
   DeviceGuard dg(h->device);
   LK_CUDA(h, cudaStreamSynchronize(h->stream));
-  if (h->precision == 1) {                 // one CTA per node: no tile shape to choose
+  if (h->precision == 1 || h->dom) {      // one CTA per node or domain: no tile shape
     for (int cls = 0; cls < 3; ++cls) {
       if (shapes_out) shapes_out[cls] = h->tile_shape[cls];
       if (us_out) us_out[cls] = 0.f;
@@ -914,3 +933,18 @@ letkf_status letkf_stats(letkf_t h, int32_t *fp64_points, int32_t *max_sweeps,
 const char *letkf_last_error(letkf_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 }  // extern "C"
+
+// Gaspari & Cohn (1999) compactly supported 5th-order piecewise rational
+// function of z = r / c (their Eq. 4.10): 1 at z = 0, 0 for z >= 2.
+double lk_gaspari_cohn(double z) {
+  z = fabs(z);
+  if (z <= 1.0) {
+    const double z2 = z * z, z3 = z2 * z;
+    return ((-0.25 * z + 0.5) * z + 0.625) * z3 - (5.0 / 3.0) * z2 + 1.0;
+  }
+  if (z < 2.0) {
+    const double z2 = z * z;
+    return (((z / 12.0 - 0.5) * z + 0.625) * z + 5.0 / 3.0) * z2 - 5.0 * z + 4.0 - (2.0 / 3.0) / z;
+  }
+  return 0.0;
+}

@@ -71,6 +71,7 @@ struct LkTile {             // one analysis CTA: instance, tile origin (node coo
 };
 
 struct LkAdjWork;           // reverse-mode workspace (letkf_adjoint.cu)
+struct LkDom;               // local-domain tables (letkf_domains.cu)
 
 struct letkf_ctx {
   letkf_config cfg;         // first instance's config (host pointers cleared)
@@ -126,6 +127,11 @@ struct letkf_ctx {
   const unsigned long long *mgraph_stamps = nullptr;
 
   LkAdjWork *adj = nullptr;         // letkf_grad buffers and graph, built on first use
+  // multi-actuator local domains (cfg.partition > 0): tables, and the host
+  // geometry they are rebuilt from when sigma2 or the taper changes
+  LkDom *dom = nullptr;
+  std::vector<int> dom_pid;
+  std::vector<int2> dom_pts, dom_saps;
 
   // letkf_step: pinned staging and device copies of one frame's inputs and
   // outputs (y, truth, mean, resvar), and its graphs without / with truth
@@ -179,6 +185,20 @@ int lk_num_tile_shapes();
 void lk_tile_shape(int s, int *ti, int *tj);
 int lk_width_class(int m);          // 0: m <= 16, 1: m <= 32, 2: m <= 64
 void lk_adjoint_release(letkf_ctx *h);  // frees the letkf_grad workspace (and its graph)
+// Gaspari & Cohn (1999) 5th-order piecewise rational function of z = r / c.
+double lk_gaspari_cohn(double z);
+// Local domains (letkf_domains.cu): build / rebuild the tables of a
+// single-instance handle with cfg.partition > 0, free them, analyse.
+letkf_status lk_domains_build(letkf_ctx *h, const letkf_config &c, const std::vector<int> &pid,
+                              const std::vector<int2> &pts, const std::vector<int2> &saps,
+                              std::string &err);
+letkf_status lk_domains_set_params(letkf_ctx *h, const letkf_config &c,
+                                   const std::vector<int> &pid, const std::vector<int2> &pts,
+                                   const std::vector<int2> &saps, std::string &err);
+void lk_domains_release(letkf_ctx *h);
+int lk_domain_count(const letkf_ctx *h);
+int lk_domain_of_nodes(const letkf_ctx *h, int *node_dom_host);
+cudaError_t lk_launch_domains(letkf_ctx *h, void *mean, void *spread);
 
 // ---------------------------------------------------------------------------
 // Device helpers

@@ -37,7 +37,8 @@ class letkf_config(ctypes.Structure):
                 ("taper", c_int32), ("loc_len", c_double), ("rho", c_double), ("sigma2", c_double),
                 ("a_ar1", c_double), ("noise_std", c_double), ("precision", c_int32),
                 ("fp64_kappa", c_double), ("seed", c_uint64), ("noise_bank", c_void_p),
-                ("bank_B", c_int32), ("bank_G", c_int32), ("max_sweeps", c_int32)]
+                ("bank_B", c_int32), ("bank_G", c_int32), ("max_sweeps", c_int32),
+                ("partition", c_int32), ("piston", c_int32)]
 
 
 _SIGS = {
@@ -45,6 +46,7 @@ _SIGS = {
     "letkf_destroy": [c_void_p],
     "letkf_query": [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)],
     "letkf_query_points": [c_void_p, c_void_p, c_void_p],
+    "letkf_query_domains": [c_void_p, POINTER(c_int32), c_void_p],
     "letkf_get_state": [c_void_p, c_void_p],
     "letkf_set_state": [c_void_p, c_void_p],
     "letkf_forecast": [c_void_p, c_void_p],
@@ -303,7 +305,8 @@ def letkf_last_error(h=None) -> str:
 def make_config(subap_mask, m: int, window: int, taper: int = 1, loc_len: float = 0.0,
                 rho: float = 1.0, sigma2: float = 0.01, a_ar1: float = 1.0,
                 noise_std: float = 0.0, precision: int = 0, fp64_kappa: float = 300.0,
-                seed: int = 0, bank=None, max_sweeps: int = 0):
+                seed: int = 0, bank=None, max_sweeps: int = 0, partition: int = 0,
+                piston: int = 0):
     """A letkf_config plus the numpy arrays its pointers refer to (keep both alive)."""
     mask = np.ascontiguousarray(subap_mask, dtype=np.uint8)
     bank = None if bank is None else np.ascontiguousarray(bank, dtype=np.float32)
@@ -317,6 +320,7 @@ def make_config(subap_mask, m: int, window: int, taper: int = 1, loc_len: float 
         cfg.noise_bank = bank.ctypes.data
         cfg.bank_B, cfg.bank_G = bank.shape[0], bank.shape[1]
     cfg.max_sweeps = max_sweeps
+    cfg.partition, cfg.piston = partition, piston
     return cfg, (mask, bank)
 
 
@@ -324,7 +328,8 @@ def workload_config(w, bank=None, **kw):
     from .synth import pupil_subap_mask
     args = dict(m=w.m, window=w.window, taper=w.taper, loc_len=w.loc_len, rho=w.rho,
                 sigma2=w.sigma2, a_ar1=w.a_ar1, noise_std=w.noise_std, precision=w.precision,
-                seed=w.seeds[2], bank=bank)
+                seed=w.seeds[2], bank=bank, partition=getattr(w, "partition", 0),
+                piston=getattr(w, "piston", 0))
     args.update(kw)
     return make_config(pupil_subap_mask(w.nsub, w.obscuration, w.square), **args)
 
@@ -405,6 +410,17 @@ class Letkf:
     # -- API -----------------------------------------------------------------
     def points(self):
         return letkf_query_points(self.h, self.n_pts)
+
+    def domains(self):
+        """(number of local domains, domain of every node) of a handle with a
+        partition; (0, None) for the per-node analysis."""
+        n = c_int32(0)
+        _check(lib().letkf_query_domains(self.h, byref(n), None), self.h)
+        if n.value == 0:
+            return 0, None
+        nd = np.empty(self.n_pts, np.int32)
+        _check(lib().letkf_query_domains(self.h, None, nd.ctypes.data), self.h)
+        return n.value, nd
 
     def new(self, *shape):
         return self._torch.zeros(*shape, dtype=self.dtype, device="cuda")

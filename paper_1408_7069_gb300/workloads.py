@@ -35,6 +35,8 @@ class Workload:
     seeds: tuple              # (truth, slope noise, forecast-noise bank)
     shift: float = 0.003      # frozen-flow displacement per frame, in pitches
     bank_count: int = 16
+    partition: int = 0        # 0: per-node analysis; P: local domains of a P x P node partition
+    piston: int = 0           # with a partition: differential-piston least squares
 
     @property
     def sigma2(self) -> float:
@@ -87,7 +89,21 @@ TINY_4X4 = Workload("tiny-4x4-m8-w3", nsub=4, pitch=0.5, obscuration=0.0, square
                     window=3, taper=1, loc_len=1.0, rho=1.05, sigma=0.1, q_model=0.003,
                     r0=0.15, L0=25.0, frames=20, truth="ar1", precision=1, seeds=(1, 2, 3))
 
-ALL = {w.name: w for w in (TOY_8X8, TEL_16M, ELT_80X80, ADJ_16M, TINY_4X4)}
+# Multi-actuator local domains (Section 4) at the paper's own sizes (Section 5.3,
+# Tables 1-2): m = 101, 5 x 5 windows, so that 4 x 4-node domains observe at most
+# 8 x 8 subapertures (n_max = 32, p_max = 128), differential pistons removed.
+# 16 m telescope without central obscuration (Section 5), 9 x 9 partition.
+DOM_16M = Workload("dom-16m-32x32-m101-p9", nsub=32, pitch=0.5, obscuration=0.0, square=False,
+                   m=101, window=5, taper=1, loc_len=0.0, rho=1.02, sigma=0.1, q_model=0.006,
+                   r0=0.15, L0=25.0, frames=1000, truth="frozen", precision=0,
+                   seeds=(81, 82, 83), shift=0.003, partition=9, piston=1)
+# 40 m telescope, 80 x 80 sensor, 21 x 21 partition (373 domains, Section 5.3).
+DOM_40M = Workload("dom-40m-80x80-m101-p21", nsub=80, pitch=0.5, obscuration=0.0, square=False,
+                   m=101, window=5, taper=1, loc_len=0.0, rho=1.02, sigma=0.1, q_model=0.005,
+                   r0=0.15, L0=25.0, frames=1000, truth="frozen", precision=0,
+                   seeds=(91, 92, 93), shift=0.003, partition=21, piston=1)
+
+ALL = {w.name: w for w in (TOY_8X8, TEL_16M, ELT_80X80, ADJ_16M, TINY_4X4, DOM_16M, DOM_40M)}
 
 
 def batched_instances(count: int = 48, seed: int = 50, frames: int = 500) -> list:
