@@ -33,13 +33,29 @@ def test_library_exports_every_declared_symbol(built):
         assert hasattr(built, name), name
 
 
-def test_config_struct_layout_matches_c():
-    # natural alignment of the C struct in include/letkf.h
-    offs = {n: getattr(L.letkf_config, n).offset for n, _ in L.letkf_config._fields_}
-    assert offs["nsub"] == 0 and offs["subap_mask"] == 8 and offs["m"] == 16
-    assert offs["loc_len"] == 32 and offs["precision"] == 72 and offs["fp64_kappa"] == 80
-    assert offs["seed"] == 88 and offs["noise_bank"] == 96 and offs["bank_B"] == 104
-    assert ctypes.sizeof(L.letkf_config) == 120
+def test_config_struct_layout_matches_c(tmp_path):
+    """The ctypes mirror of letkf_config has the C compiler's layout: every
+    field's offset and the size, printed by a C program built against
+    include/letkf.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [n for n, _ in L.letkf_config._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"letkf.h\"\nint main(void) {\n"
+                   + "".join(f'  printf("{n} %zu\\n", offsetof(letkf_config, {n}));\n'
+                             for n in fields)
+                   + '  printf("size %zu\\n", sizeof(letkf_config));\n  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(L.HEADER))
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.splitlines())
+    for n in fields:
+        assert getattr(L.letkf_config, n).offset == int(out[n]), n
+    assert ctypes.sizeof(L.letkf_config) == int(out["size"])
 
 
 def _cfg(mask, **kw):
