@@ -130,8 +130,10 @@ letkf_status letkf_query_instance(letkf_t h, int32_t i, int32_t *n_pts, int32_t 
  * mean). letkf_stats then counts in fp64_points the domains whose kappa_hat
  * exceeds fp64_kappa (there is no FP64 path for domains).
  * n_dom: number of domains (0 for a per-node handle); node_dom_host: host
- * int32 [n_pts], the domain of every node, or NULL. Either may be NULL. */
-letkf_status letkf_query_domains(letkf_t h, int32_t *n_dom, int32_t *node_dom_host);
+ * int32 [n_pts], the domain of every node; obs_count_host: host int32
+ * [n_dom], the number of slopes each domain observes (p_d). Any may be NULL. */
+letkf_status letkf_query_domains(letkf_t h, int32_t *n_dom, int32_t *node_dom_host,
+                                 int32_t *obs_count_host);
 
 /* Host copies of the node coordinates [n_pts][2] (i, j) and of the number of
  * valid window slopes per node [n_pts] (p_l, Section 4.2's p_d). Either may be NULL. */

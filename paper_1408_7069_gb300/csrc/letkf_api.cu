@@ -680,12 +680,16 @@ letkf_status letkf_run_graph(letkf_t h, int32_t frames, const void *y_seq_dev,
   return LETKF_OK;
 }
 
-letkf_status letkf_query_domains(letkf_t h, int32_t *n_dom, int32_t *node_dom_host) {
+letkf_status letkf_query_domains(letkf_t h, int32_t *n_dom, int32_t *node_dom_host,
+                                 int32_t *obs_count_host) {
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
   if (n_dom) *n_dom = lk_domain_count(h);
-  if (node_dom_host && h->dom) {
+  if (h->dom && (node_dom_host || obs_count_host)) {
     DeviceGuard dg(h->device);
-    if (!lk_domain_of_nodes(h, node_dom_host)) return fail(h, LETKF_ERR_CUDA, "cudaMemcpy");
+    if (node_dom_host && !lk_domain_of_nodes(h, node_dom_host))
+      return fail(h, LETKF_ERR_CUDA, "cudaMemcpy");
+    if (obs_count_host && !lk_domain_obs_counts(h, obs_count_host))
+      return fail(h, LETKF_ERR_CUDA, "cudaMemcpy");
   }
   return LETKF_OK;
 }

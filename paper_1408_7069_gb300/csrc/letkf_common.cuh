@@ -198,6 +198,7 @@ letkf_status lk_domains_set_params(letkf_ctx *h, const letkf_config &c,
 void lk_domains_release(letkf_ctx *h);
 int lk_domain_count(const letkf_ctx *h);
 int lk_domain_of_nodes(const letkf_ctx *h, int *node_dom_host);
+int lk_domain_obs_counts(const letkf_ctx *h, int *obs_host);
 cudaError_t lk_launch_domains(letkf_ctx *h, void *mean, void *spread);
 
 // ---------------------------------------------------------------------------

@@ -650,6 +650,16 @@ int lk_domain_of_nodes(const letkf_ctx *h, int *node_dom_host) {
                     cudaMemcpyDeviceToHost) == cudaSuccess;
 }
 
+int lk_domain_obs_counts(const letkf_ctx *h, int *obs_host) {
+  if (!h->dom) return 0;
+  std::vector<int> off(h->dom->n_dom + 1);
+  if (cudaMemcpy(off.data(), h->dom->obs_off, off.size() * sizeof(int), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return 0;
+  for (int d = 0; d < h->dom->n_dom; ++d) obs_host[d] = off[d + 1] - off[d];
+  return 1;
+}
+
 // Analysis of every domain, then (with the piston correction) the piston
 // constants and their application.
 cudaError_t lk_launch_domains(letkf_ctx *h, void *mean, void *spread) {

@@ -46,7 +46,7 @@ _SIGS = {
     "letkf_destroy": [c_void_p],
     "letkf_query": [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)],
     "letkf_query_points": [c_void_p, c_void_p, c_void_p],
-    "letkf_query_domains": [c_void_p, POINTER(c_int32), c_void_p],
+    "letkf_query_domains": [c_void_p, POINTER(c_int32), c_void_p, c_void_p],
     "letkf_get_state": [c_void_p, c_void_p],
     "letkf_set_state": [c_void_p, c_void_p],
     "letkf_forecast": [c_void_p, c_void_p],
@@ -415,12 +415,19 @@ class Letkf:
         """(number of local domains, domain of every node) of a handle with a
         partition; (0, None) for the per-node analysis."""
         n = c_int32(0)
-        _check(lib().letkf_query_domains(self.h, byref(n), None), self.h)
+        _check(lib().letkf_query_domains(self.h, byref(n), None, None), self.h)
         if n.value == 0:
             return 0, None
         nd = np.empty(self.n_pts, np.int32)
-        _check(lib().letkf_query_domains(self.h, None, nd.ctypes.data), self.h)
+        _check(lib().letkf_query_domains(self.h, None, nd.ctypes.data, None), self.h)
         return n.value, nd
+
+    def domain_sizes(self):
+        """(n_d, p_d) of every local domain: state rows and observed slopes."""
+        n, nd = self.domains()
+        pd = np.empty(n, np.int32)
+        _check(lib().letkf_query_domains(self.h, None, None, pd.ctypes.data), self.h)
+        return 2 * np.bincount(nd, minlength=n), pd
 
     def new(self, *shape):
         return self._torch.zeros(*shape, dtype=self.dtype, device="cuda")
