@@ -318,8 +318,10 @@ def domains_arm(torch, L, K: int = 200, Wm: int = 20):
     JSON line (the paper's own CPU figures are quoted as context)."""
     import numpy as np
     from paper_1408_7069_gb300 import opcount, synth, workloads as W
+    from dataclasses import replace
     out = {}
-    for w in (W.DOM_16M, W.DOM_40M):
+    glob = replace(W.DOM_16M, name="global-16m-32x32-m101", partition=1, piston=0, taper=0)
+    for w in (W.DOM_16M, W.DOM_40M, glob):
         inp = synth.make_loop_inputs(w, frames=Wm + K + 1)
         f = L.Letkf.from_workload(w, bank=inp.bank)
         h, s = f.h, f.stream

@@ -21,6 +21,9 @@
 //           shared memory after every round. Converged columns are lambda q.
 //   apply   G = X' Q, z = Lambda^-1 Q^T c, Xa_r = xbar_r + sum_c G_rc (z_c +
 //           sqrt((m-1)/lambda_c) Q_jc) for every row r of the domain
+// A partition of 1 (one domain over the whole grid, the global ETKF of
+// Section 3.1.1 when the window covers the pupil) runs as the multi-kernel
+// pipeline below instead, for any number of slopes and nodes.
 // Then the piston kernels: per domain and state row the constant that
 // minimises the squared jumps of the mean increment across border edges
 // (4-neighbour nodes in different domains), c = K b with b the per-domain
@@ -48,6 +51,11 @@ struct LkDom {
   float *delta = nullptr;                         // [n_pts][2] mean increments
   float *cpist = nullptr;                         // [D][2] piston constants
   std::vector<double> tau;                        // host: tau of each observed slope
+  // one domain covering the grid (partition 1): the global ETKF pipeline
+  int global = 0, kchunks = 0;
+  double *gpart = nullptr;                        // [kchunks][MPD][MPD] Gram partial sums
+  double *cpart = nullptr;                        // [kchunks][MPD]
+  float *T = nullptr;                             // [m][m] transform wbar 1^T + W
 };
 
 namespace {
@@ -70,8 +78,9 @@ struct DomArgs {
   int max_sweeps, max_obs, max_rows;
 };
 
-// Shared-memory layout (floats): S / Q region, s, c, z, sroot, lambda, the
-// column exchange [2][G][MPD] and its norms [2][G], X' and G = X'Q [rows][MPD],
+// Shared-memory layout (floats): S / Q region, s, c, z, sroot, the column
+// exchange [2][G][MPD] and its norms [2][G] (G = X'Q reuses the exchange after
+// the sweeps when it fits, so that two CTAs share an SM), X' [rows][MPD],
 // xbar [rows], 4 reduction slots.
 struct DomLayout {
   int ld, sq, sv, cv, zv, sr, xb, xn, xd, gm, xm, red, total;
@@ -88,10 +97,15 @@ __host__ __device__ inline DomLayout dom_layout(int mpd, int max_obs, int max_ro
   L.xb = L.sr + mpd;
   L.xn = L.xb + 2 * (mpd / 2) * mpd;
   L.xd = L.xn + 2 * (mpd / 2);
-  L.gm = L.xd + max_rows * mpd;
-  L.xm = L.gm + max_rows * mpd;
+  L.xm = L.xd + max_rows * mpd;
   L.red = L.xm + max_rows;
   L.total = L.red + 4;
+  if (max_rows <= mpd) {
+    L.gm = L.xb;                       // [rows][MPD] <= [2][MPD/2][MPD]
+  } else {
+    L.gm = L.total;
+    L.total += max_rows * mpd;
+  }
   return L;
 }
 
@@ -383,6 +397,300 @@ __global__ void __launch_bounds__(LK_WARP_CTA)
   }
 }
 
+// ---------------------------------------------------------------------------
+// One domain covering the grid (partition 1): the global ETKF (Section 3.1.1)
+// for any number of slopes and nodes, as three kernels:
+//   gram    FP64 partial sums of A = S^T S and c = S^T s over chunks of slopes,
+//           one CTA per (upper-triangle 32 x 32 tile of A, chunk), S and s as in
+//           the domain kernel (sqrt(tau / sigma2) times the grid's values)
+//   solve   one CTA: A = (m-1)/rho I + the partials (FP64), its FP32 rounding
+//           diagonalised by the domain kernel's Jacobi (A = Q Lambda Q^T), then
+//           wbar = A^-1 c by mixed-precision iterative refinement (residual
+//           c - A wbar in FP64, correction Q Lambda^-1 Q^T r in FP32: the error
+//           contracts by about kappa eps32 per step, so a few steps reach the
+//           FP64 solution although kappa_hat reaches 1e4-1e5 for the whole
+//           pupil), and T = wbar 1^T + Q ((m-1) Lambda^-1)^(1/2) Q^T
+//   apply   a CTA per 16 state rows: Xa_r = xbar_r + X'_r T, mean, spread
+// ---------------------------------------------------------------------------
+constexpr int GL_TILE = 32, GL_KC = 64, GL_REFINE = 4;
+
+__global__ void __launch_bounds__(256)
+    global_gram_kernel(const LkInst *__restrict__ insts, const int *__restrict__ obs_slot,
+                       const float *__restrict__ obs_w, int np, int mpt,
+                       double *__restrict__ gpart, double *__restrict__ cpart) {
+  __shared__ double si[GL_KC][GL_TILE + 1], sj[GL_KC][GL_TILE + 1], sv[GL_KC];
+  lk_pdl_wait();
+  const LkInst &I = insts[0];
+  const int m = I.m;
+  const float *Ybp = static_cast<const float *>(I.Ybp);
+  const float *dp = static_cast<const float *>(I.dp);
+  // upper-triangle tile (ti <= tj) from blockIdx.x
+  const int nt = mpt / GL_TILE;
+  int ti = 0, tj = blockIdx.x;
+  while (tj >= nt - ti) {
+    tj -= nt - ti;
+    ++ti;
+  }
+  tj += ti;
+  const int kc = blockIdx.y, k0 = kc * GL_KC;
+  const int kn = np - k0 < GL_KC ? np - k0 : GL_KC;
+  for (int e = threadIdx.x; e < GL_KC * GL_TILE; e += blockDim.x) {
+    const int k = e / GL_TILE, i = e - k * GL_TILE;
+    double a = 0.0, b = 0.0;
+    if (k < kn) {
+      const int slot = obs_slot[k0 + k];
+      const double sw = sqrt((double)obs_w[k0 + k]);
+      const int ri = ti * GL_TILE + i, rj = tj * GL_TILE + i;
+      if (ri < m) a = sw * (double)Ybp[(size_t)slot * m + ri];
+      if (rj < m) b = sw * (double)Ybp[(size_t)slot * m + rj];
+    }
+    si[k][i] = a;
+    sj[k][i] = b;
+  }
+  for (int k = threadIdx.x; k < GL_KC; k += blockDim.x)
+    sv[k] = k < kn ? sqrt((double)obs_w[k0 + k]) * (double)dp[obs_slot[k0 + k]] : 0.0;
+  __syncthreads();
+  const int a0 = (threadIdx.x / 16) * 2, b0 = (threadIdx.x % 16) * 2;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int k = 0; k < GL_KC; ++k) {
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+      for (int y = 0; y < 2; ++y) acc[x][y] = fma(si[k][a0 + x], sj[k][b0 + y], acc[x][y]);
+  }
+  double *out = gpart + (size_t)kc * mpt * mpt;
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int y = 0; y < 2; ++y)
+      out[(size_t)(ti * GL_TILE + a0 + x) * mpt + tj * GL_TILE + b0 + y] = acc[x][y];
+  if (ti == tj && threadIdx.x < GL_TILE) {
+    double c = 0.0;
+    for (int k = 0; k < GL_KC; ++k) c = fma(si[k][threadIdx.x], sv[k], c);
+    cpart[(size_t)kc * mpt + ti * GL_TILE + threadIdx.x] = c;
+  }
+}
+
+// Shared memory of the solve kernel: A (FP64, [MPD][MPD+1]), c, wbar, r (FP64),
+// then one float region used first as the Jacobi's column exchange and then
+// for Q ([MPD][MPD+1]), and lambda, t, sroot.
+template <int RPL>
+__host__ __device__ constexpr size_t gsolve_qfloats() {
+  constexpr size_t MPD = 8 * RPL, q = MPD * (MPD + 1), x = 2 * (MPD / 2) * MPD + 2 * (MPD / 2);
+  return q > x ? q : x;
+}
+template <int RPL>
+size_t global_solve_smem() {
+  constexpr int MPD = 8 * RPL;
+  return sizeof(double) * ((size_t)MPD * (MPD + 1) + 3 * MPD) +
+         sizeof(float) * (gsolve_qfloats<RPL>() + 3 * MPD);
+}
+
+template <int RPL>
+__global__ void __launch_bounds__(32 * RPL)
+    global_solve_kernel(const LkInst *__restrict__ insts, const double *__restrict__ gpart,
+                        const double *__restrict__ cpart, int kchunks, int mpt,
+                        float *__restrict__ T, float tol, float stop, int max_sweeps,
+                        int *__restrict__ counters) {
+  constexpr int MPD = 8 * RPL, G = MPD / 2, NT = 4 * MPD, LD = MPD + 1;
+  extern __shared__ __align__(16) double gsm[];
+  lk_pdl_wait();
+  const LkInst &I = insts[0];
+  const int m = I.m, tid = threadIdx.x;
+  double *A = gsm;                              // [MPD][LD] FP64
+  double *c64 = A + MPD * LD, *w64 = c64 + MPD, *r64 = w64 + MPD;
+  float *Qs = reinterpret_cast<float *>(r64 + MPD);   // [MPD][LD], after the sweeps
+  float *xb = Qs, *xn = xb + 2 * G * MPD;             // exchange, during the sweeps
+  float *lam = Qs + gsolve_qfloats<RPL>(), *tv = lam + MPD, *sr = tv + MPD;
+  const double alpha = I.alpha;
+  // ---- A and c from the partial sums: element (i, j) of the upper triangle
+  // was summed in tile (min / 32, max / 32) at (min, max) ----
+  for (int e = tid; e < MPD * MPD; e += NT) {
+    const int i = e / MPD, j = e - i * MPD;
+    const int a = i <= j ? i : j, b = i <= j ? j : i;
+    double s = 0.0;
+    for (int k = 0; k < kchunks; ++k) s += gpart[((size_t)k * mpt + a) * mpt + b];
+    if (i == j) s += i < m ? alpha : 1.0;
+    A[i * LD + j] = s;
+  }
+  if (tid < MPD) {
+    double s = 0.0;
+    for (int k = 0; k < kchunks; ++k) s += cpart[(size_t)k * mpt + tid];
+    c64[tid] = s;
+    w64[tid] = 0.0;
+  }
+  __syncthreads();
+  // ---- FP32 Jacobi on the rounded A (the domain kernel's layout and rounds) ----
+  const int g = tid >> 3, l = tid & 7;
+  float P[RPL], Q[RPL];
+#pragma unroll
+  for (int i = 0; i < RPL; ++i) {
+    P[i] = (float)A[(l + 8 * i) * LD + 2 * g];
+    Q[i] = (float)A[(l + 8 * i) * LD + 2 * g + 1];
+  }
+  const float tol2 = tol * tol, stop2 = stop * stop;
+  int buf = 0, sweeps = 0;
+  bool conv = false;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    float pp = 0.f, qq = 0.f;
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) {
+      pp = fmaf(P[i], P[i], pp);
+      qq = fmaf(Q[i], Q[i], qq);
+    }
+    float nP = group8_sum(pp), nQ = group8_sum(qq);
+    int flags = 0;
+    for (int r = 0; r < G; ++r) {
+      flags |= dom_round<RPL>(P, Q, nP, nQ, tol2, stop2, false);
+      dom_xfer<RPL>(Q, nQ, xb, xn, buf, g, l, g + 1 < G ? g + 1 : 0);
+      flags |= dom_round<RPL>(P, Q, nP, nQ, tol2, stop2, g == G - 1);
+      dom_xfer<RPL>(P, nP, xb, xn, buf, g, l, g > 0 ? g - 1 : G - 1);
+    }
+    sweeps = sweep + 1;
+    if (!__syncthreads_or(flags & 2)) {
+      conv = true;
+      break;
+    }
+  }
+  if (tid == 0) {
+    atomicMax(&counters[2], sweeps);
+    atomicAdd(&counters[3], sweeps);
+    if (!conv) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
+  }
+  float pp = 0.f, qq = 0.f;
+#pragma unroll
+  for (int i = 0; i < RPL; ++i) {
+    pp = fmaf(P[i], P[i], pp);
+    qq = fmaf(Q[i], Q[i], qq);
+  }
+  const float lP = sqrtf(group8_sum(pp)), lQ = sqrtf(group8_sum(qq));
+  __syncthreads();                              // the exchange region becomes Q
+#pragma unroll
+  for (int i = 0; i < RPL; ++i) {
+    Qs[(l + 8 * i) * LD + 2 * g] = P[i] / lP;
+    Qs[(l + 8 * i) * LD + 2 * g + 1] = Q[i] / lQ;
+  }
+  if (l == 0) {
+    lam[2 * g] = lP;
+    lam[2 * g + 1] = lQ;
+  }
+  __syncthreads();
+  if (tid < MPD) sr[tid] = sqrtf(float(m - 1) / lam[tid]);
+  // ---- wbar = A^-1 c by iterative refinement ----
+  for (int it = 0; it < GL_REFINE; ++it) {
+    if (tid < MPD) {                              // r = c - A w (FP64)
+      double s = c64[tid];
+      for (int j = 0; j < MPD; ++j) s = fma(-A[tid * LD + j], w64[j], s);
+      r64[tid] = s;
+    }
+    __syncthreads();
+    if (tid < MPD) {                              // t = Lambda^-1 Q^T r
+      float s = 0.f;
+      for (int j = 0; j < MPD; ++j) s = fmaf(Qs[j * LD + tid], (float)r64[j], s);
+      tv[tid] = s / lam[tid];
+    }
+    __syncthreads();
+    if (tid < MPD) {                              // w += Q t
+      float s = 0.f;
+      for (int c = 0; c < MPD; ++c) s = fmaf(Qs[tid * LD + c], tv[c], s);
+      w64[tid] += (double)s;
+    }
+    __syncthreads();
+  }
+  // ---- T = wbar 1^T + Q diag(sroot) Q^T ----
+  for (int e = tid; e < m * m; e += NT) {
+    const int i = e / m, j = e - i * m;
+    float s = 0.f;
+    for (int c = 0; c < MPD; ++c) s = fmaf(Qs[i * LD + c] * sr[c], Qs[j * LD + c], s);
+    T[e] = (float)w64[i] + s;
+  }
+}
+
+// Xa_r = xbar_r + X'_r T for 16 state rows per CTA (rows = node-major, 2 per node).
+__global__ void __launch_bounds__(256)
+    global_apply_kernel(const LkInst *__restrict__ insts, const float *__restrict__ T,
+                        float *__restrict__ mean, float *__restrict__ spread,
+                        int *__restrict__ counters) {
+  extern __shared__ __align__(16) float asm_[];
+  lk_pdl_wait();
+  const LkInst &I = insts[0];
+  const int m = I.m, tid = threadIdx.x;
+  float *Ts = asm_;                               // [m][m]
+  float *xr = Ts + m * m;                         // [16][m]
+  for (int e = tid; e < m * m; e += blockDim.x) Ts[e] = T[e];
+  const long long r0 = (long long)blockIdx.x * 16, nrows = 2LL * I.n_pts;
+  float *X = static_cast<float *>(I.X);
+  for (int e = tid; e < 16 * m; e += blockDim.x) {
+    const long long r = r0 + e / m;
+    xr[e] = r < nrows ? X[r * m + e % m] : 0.f;
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  const float inv_m = 1.f / float(m);
+  for (int q = warp; q < 16; q += 8) {
+    const long long r = r0 + q;
+    if (r >= nrows) break;
+    float s = 0.f;
+    for (int j = lane; j < m; j += 32) s += xr[q * m + j];
+    const float xbar = lk_warp_sum(s) * inv_m;
+    float sum = 0.f;
+    for (int j = lane; j < m; j += 32) {
+      float acc = 0.f;
+      for (int i = 0; i < m; ++i) acc = fmaf(xr[q * m + i] - xbar, Ts[i * m + j], acc);
+      const float xa = xbar + acc;
+      X[r * m + j] = xa;
+      sum += xa;
+    }
+    const float mu = lk_warp_sum(sum) * inv_m;
+    float sq = 0.f;
+    for (int j = lane; j < m; j += 32) {
+      const float dv = X[r * m + j] - mu;
+      sq = fmaf(dv, dv, sq);
+    }
+    const float sp = sqrtf(lk_warp_sum(sq) / float(m - 1));
+    if (lane == 0) {
+      if (mean) mean[r] = mu;
+      if (spread) spread[r] = sp;
+      if (!isfinite(mu) || !isfinite(sp)) atomicOr(&counters[0], LK_BIT_NONFINITE);
+    }
+  }
+}
+
+constexpr int gl_mpt(int mpd) { return ((mpd + GL_TILE - 1) / GL_TILE) * GL_TILE; }
+
+template <int RPL>
+cudaError_t launch_global_rpl(letkf_ctx *h, void *mean, void *spread) {
+  const LkDom &D = *h->dom;
+  const LkInst &I = h->inst[0];
+  constexpr int MPT = gl_mpt(8 * RPL), NT = MPT / GL_TILE;
+  cudaError_t e = lk_launch_pdl(global_gram_kernel, dim3(NT * (NT + 1) / 2, D.kchunks), 256, 0,
+                                h->stream, h->d_inst, (const int *)D.obs_slot,
+                                (const float *)D.obs_w, D.max_obs, MPT, D.gpart, D.cpart);
+  if (e != cudaSuccess) return e;
+  e = lk_launch_pdl(global_solve_kernel<RPL>, 1, 32 * RPL, global_solve_smem<RPL>(), h->stream,
+                    h->d_inst, (const double *)D.gpart, (const double *)D.cpart, D.kchunks, MPT,
+                    D.T, (float)h->tol32, (float)(h->stop32 > h->tol32 ? h->stop32 : h->tol32),
+                    h->max_sweeps, h->counters);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((2LL * I.n_pts + 15) / 16);
+  return lk_launch_pdl(global_apply_kernel, blocks, 256,
+                       sizeof(float) * ((size_t)I.m * I.m + 16 * (size_t)I.m), h->stream,
+                       h->d_inst, (const float *)D.T, static_cast<float *>(mean),
+                       static_cast<float *>(spread), h->counters);
+}
+
+template <int RPL>
+cudaError_t setup_global_rpl(const LkDom &D, int m) {
+  cudaError_t e = cudaFuncSetAttribute(global_solve_kernel<RPL>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)global_solve_smem<RPL>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(global_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float) * ((size_t)m * m + 16 * (size_t)m)));
+  (void)D;
+  return e;
+}
+
 template <int RPL>
 cudaError_t launch_rpl(letkf_ctx *h, const DomArgs &a) {
   const LkDom &D = *h->dom;
@@ -509,11 +817,12 @@ letkf_status lk_domains_build(letkf_ctx *h, const letkf_config &c, const std::ve
     }
   D->n_dom = (int)node_off.size() - 1;
   D->rpl = rpl_of(c.m);
+  D->global = P == 1;
   const int mpd = 8 * D->rpl;
   const size_t smem = (size_t)dom_layout(mpd, D->max_obs, 2 * D->max_nodes).total * sizeof(float);
   int dev_smem = 0;
   cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-  if (smem > (size_t)dev_smem) {
+  if (!D->global && smem > (size_t)dev_smem) {
     err = "local domains too large for one CTA's shared memory (fewer nodes per domain, a "
           "smaller window or fewer members)";
     return LETKF_ERR_ARG;
@@ -607,7 +916,25 @@ letkf_status lk_domains_build(letkf_ctx *h, const letkf_config &c, const std::ve
   if (e == cudaSuccess) e = dup(&D->KT, KT);
   if (e == cudaSuccess) e = cudaMalloc((void **)&D->delta, pts.size() * 2 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void **)&D->cpist, (size_t)Dn * 2 * sizeof(float));
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && D->global) {
+    const int mpt = gl_mpt(mpd);
+    D->kchunks = (D->max_obs + GL_KC - 1) / GL_KC;
+    if (D->kchunks < 1) D->kchunks = 1;
+    e = cudaMalloc((void **)&D->gpart, (size_t)D->kchunks * mpt * mpt * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(D->gpart, 0, (size_t)D->kchunks * mpt * mpt * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&D->cpart, (size_t)D->kchunks * mpt * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(D->cpart, 0, (size_t)D->kchunks * mpt * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&D->T, (size_t)c.m * c.m * sizeof(float));
+    if (e == cudaSuccess) {
+      switch (D->rpl) {
+        case 2: e = setup_global_rpl<2>(*D, c.m); break;
+        case 4: e = setup_global_rpl<4>(*D, c.m); break;
+        case 8: e = setup_global_rpl<8>(*D, c.m); break;
+        case 13: e = setup_global_rpl<13>(*D, c.m); break;
+        default: e = setup_global_rpl<16>(*D, c.m); break;
+      }
+    }
+  } else if (e == cudaSuccess) {
     switch (D->rpl) {
       case 2: e = setup_rpl<2>(*D); break;
       case 4: e = setup_rpl<4>(*D); break;
@@ -635,7 +962,8 @@ void lk_domains_release(letkf_ctx *h) {
   LkDom *D = h->dom;
   if (!D) return;
   void *bufs[] = {D->node_off, D->node_ids, D->obs_off, D->obs_slot, D->obs_w, D->node_dom,
-                  D->edges,    D->dedge_off, D->dedge,   D->KT,       D->delta, D->cpist};
+                  D->edges,    D->dedge_off, D->dedge,   D->KT,       D->delta, D->cpist,
+                  D->gpart,    D->cpart,     D->T};
   for (void *p : bufs)
     if (p) cudaFree(p);
   delete D;
@@ -664,6 +992,15 @@ int lk_domain_obs_counts(const letkf_ctx *h, int *obs_host) {
 // constants and their application.
 cudaError_t lk_launch_domains(letkf_ctx *h, void *mean, void *spread) {
   const LkDom &D = *h->dom;
+  if (D.global) {
+    switch (D.rpl) {
+      case 2: return launch_global_rpl<2>(h, mean, spread);
+      case 4: return launch_global_rpl<4>(h, mean, spread);
+      case 8: return launch_global_rpl<8>(h, mean, spread);
+      case 13: return launch_global_rpl<13>(h, mean, spread);
+      default: return launch_global_rpl<16>(h, mean, spread);
+    }
+  }
   DomArgs a;
   a.node_off = D.node_off;
   a.node_ids = D.node_ids;

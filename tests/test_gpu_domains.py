@@ -167,3 +167,30 @@ def test_domain_handles_refuse_what_they_do_not_support():
     with pytest.raises(LetkfError, match="LETKF_ERR_STATE"):
         f.grad(3, y, t)
     f.close()
+
+
+@pytest.mark.parametrize("frames", [0, 3], ids=["prior-draw", "f3"])
+def test_global_etkf_at_paper_size(frames):
+    """One domain over the 16 m pupil (partition 1: every slope observed by
+    every node, the global ETKF of Section 3.1.1) with m = 101: p = 1624
+    slopes, n = 1754 state rows, kappa_hat of 1e4-1e5; the mean solve is
+    refined in FP64 and every frame matches the oracle."""
+    w = replace(W.DOM_16M, name="global-16m-m101", partition=1, piston=0, taper=0)
+    inp = synth.make_loop_inputs(w, frames=frames + 2)
+    dg = LD.build_domains(inp.subap_mask, 1, w.window, 0)
+    assert dg.n_dom == 1 and len(dg.dom_obs[0]) == dg.geom.p == 1624
+    X = inp.X0.copy()
+    for k in range(frames):
+        Xa, _, _ = LD.analysis_domains(dg, X, inp.slopes[k], w.sigma2, w.rho)
+        X = oracle.forecast(Xa, oracle.bank_noise(inp.bank, dg.geom.points, w.m, w.seeds[2], k,
+                                                  w.noise_std), w.a_ar1)
+    Xb = X.astype(np.float32)
+    y = inp.slopes[frames].astype(np.float32)
+    (Xa, mean, spread), _ = gpu_analysis(w, inp, Xb, y)
+    rXa, rmean, rspread = LD.analysis_domains(dg, Xb.astype(np.float64), y.astype(np.float64),
+                                              w.sigma2, w.rho)
+    assert rel(mean, rmean) <= 1e-4, rel(mean, rmean)
+    assert rel(spread, rspread) <= 1e-3, rel(spread, rspread)
+    assert rel(anoms(Xa), anoms(rXa)) <= 1e-3, rel(anoms(Xa), anoms(rXa))
+    xbar = Xb.astype(np.float64).mean(-1)
+    assert rel(mean - xbar, rmean - xbar) <= 1e-3, rel(mean - xbar, rmean - xbar)
