@@ -311,17 +311,22 @@ def domains_arm(torch, L, K: int = 200, Wm: int = 20):
     """Multi-actuator local domains (Section 4) at the paper's sizes: the 16 m
     telescope with a 9 x 9 partition and the 40 m telescope (80 x 80) with a
     21 x 21 partition (373 domains), m = 101, n_d <= 32, p_d <= 128, with the
-    differential-piston least squares. Per frame: the update of every domain
-    (one CTA each) and the piston kernels timed with CUDA events, the whole
+    differential-piston least squares; and the global ETKF (Section 3.1.1:
+    partition 1, all 1624 slopes) of the 16 m telescope at m = 101. Per frame:
+    the update (one CTA per domain and the piston kernels, or the global
+    pipeline) timed with CUDA events; for the partitions also the whole
     closed-loop frame (residual, observation, update, forecast) as one launch
-    of K frames with in-graph stamps. Returns the 'domains' object of the
-    JSON line (the paper's own CPU figures are quoted as context)."""
+    of K frames with in-graph stamps. The global update is timed on the prior
+    draw (its closed loop is not stable at m = 101, as the paper's Fig. 4 shows
+    for the ETKF below ~600 members). Returns the 'domains' object of the JSON
+    line (the paper's own CPU figures are quoted as context)."""
     import numpy as np
-    from paper_1408_7069_gb300 import opcount, synth, workloads as W
     from dataclasses import replace
+    from paper_1408_7069_gb300 import opcount, synth, workloads as W
     out = {}
     glob = replace(W.DOM_16M, name="global-16m-32x32-m101", partition=1, piston=0, taper=0)
     for w in (W.DOM_16M, W.DOM_40M, glob):
+        loop = w.partition > 1
         inp = synth.make_loop_inputs(w, frames=Wm + K + 1)
         f = L.Letkf.from_workload(w, bank=inp.bank)
         h, s = f.h, f.stream
@@ -329,52 +334,62 @@ def domains_arm(torch, L, K: int = 200, Wm: int = 20):
         y = torch.from_numpy(inp.slopes.astype(np.float32)).cuda()
         t = torch.from_numpy(inp.truth.astype(np.float32)).cuda()
         f.set_state(X0)
-        rv = f.run(Wm, y, t, use_graph=True)
+        if loop:
+            f.run(Wm, y, t, use_graph=True)
         torch.cuda.synchronize()
         nd, pd = f.domain_sizes()
         ops = sum(opcount.update_ops(w.m, int(a), int(b)) for a, b in zip(nd, pd))
+        rv = torch.zeros(1, dtype=torch.float64, device="cuda")
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(K)]
         with torch.cuda.stream(s):
             for i in range(K):
                 k = Wm + i
-                L.letkf_residual(h, t[k], rv[0:1])
+                if loop:
+                    L.letkf_residual(h, t[k], rv)
+                else:
+                    L.letkf_set_state(h, X0)
                 ev[i][0].record(s)
-                L.letkf_analyze(h, y[k], None, None)
+                L.letkf_analyze(h, y[k] if loop else y[1], None, None)
                 ev[i][1].record(s)
-                L.letkf_forecast(h)
+                if loop:
+                    L.letkf_forecast(h)
         torch.cuda.synchronize()
-        upd = [a.elapsed_time(b) * 1e3 for a, b in ev]
-        f.set_state(X0)
-        f.set_frame(0)
-        f.run(Wm, y, t, use_graph=True)
-        stamps = torch.zeros(K + 1, dtype=torch.int64, device="cuda")
-        resv = torch.zeros(K, dtype=torch.float64, device="cuda")
-        for rep in range(2):                          # the first call instantiates the graph
-            f.set_state(X0)
-            f.set_frame(0)
-            f.run(Wm, y, t, use_graph=True)
-            torch.cuda.synchronize()
-            L.letkf_run_graph(h, K, y[Wm:], t[Wm:], resv, stamps)
-            torch.cuda.synchronize()
         f.sync()
-        fus = np.diff(stamps.cpu().numpy().astype(np.float64)) / 1e3
-        n_dom = len(nd)
+        upd = [a.elapsed_time(b) * 1e3 for a, b in ev]
         upd_mean = statistics.mean(upd)
-        out[w.name] = {
-            "n_pts": int(f.n_pts), "m": w.m, "partition": w.partition, "domains": n_dom,
+        entry = {
+            "n_pts": int(f.n_pts), "m": w.m, "partition": w.partition, "domains": len(nd),
             "n_max": int(nd.max()), "p_max": int(pd.max()), "ops_per_frame_table1": ops,
             "update_us_mean": upd_mean, "update_us_p50": percentile(upd, 50),
             "update_us_p99": percentile(upd, 99),
-            "update_tflops_table1": ops / (upd_mean * 1e-6) / 1e12,
-            "frame_us_p50": percentile(list(fus), 50), "frame_us_p99": percentile(list(fus), 99),
-            "frames_per_s": 1e6 / float(np.mean(fus)),
-            "resvar_last": float(resv[-1].item()),
-            "paper_context": "Section 5.3, Table 2 (2 x Xeon E5-2680 v2): update of one domain "
-                             "0.94 ms on one core; full 16 m cycle 1.18 ms with >= 69 cores; "
-                             "40 m: 2.64 ms plus ~2 ms of cluster communication",
-            "launch": "update: one CTA per domain + piston solve + piston apply; frames: "
-                      "letkf_run_graph (one launch, in-graph stamps)"}
+            "update_tflops_table1": ops / (upd_mean * 1e-6) / 1e12}
+        if loop:
+            stamps = torch.zeros(K + 1, dtype=torch.int64, device="cuda")
+            resv = torch.zeros(K, dtype=torch.float64, device="cuda")
+            for rep in range(2):                      # the first call instantiates the graph
+                f.set_state(X0)
+                f.set_frame(0)
+                f.run(Wm, y, t, use_graph=True)
+                torch.cuda.synchronize()
+                L.letkf_run_graph(h, K, y[Wm:], t[Wm:], resv, stamps)
+                torch.cuda.synchronize()
+            f.sync()
+            fus = np.diff(stamps.cpu().numpy().astype(np.float64)) / 1e3
+            entry.update({"frame_us_p50": percentile(list(fus), 50),
+                          "frame_us_p99": percentile(list(fus), 99),
+                          "frames_per_s": 1e6 / float(np.mean(fus)),
+                          "resvar_last": float(resv[-1].item())})
+            entry["launch"] = ("update: one CTA per domain + piston solve + piston apply; "
+                               "frames: letkf_run_graph (one launch, in-graph stamps)")
+        else:
+            entry["launch"] = ("update: FP64 Gram (split over slope chunks), one-CTA FP32 "
+                               "Jacobi with FP64-refined mean solve, row-blocked apply; "
+                               "timed on the prior draw")
+        entry["paper_context"] = ("Section 5.3, Table 2 (2 x Xeon E5-2680 v2): update of one "
+                                  "domain 0.94 ms on one core; full 16 m cycle 1.18 ms with "
+                                  ">= 69 cores; 40 m: 2.64 ms plus ~2 ms of cluster communication")
+        out[w.name] = entry
         f.close()
     return out
 
