@@ -261,3 +261,36 @@ def random_ensemble(seed: int, n_pts: int, m: int, scale: float = 1.0,
     rng = np.random.default_rng(seed)
     mean = offset_scale * rng.standard_normal((n_pts, 2, 1))
     return mean + scale * rng.standard_normal((n_pts, 2, m))
+
+
+# --------------------------------------------------------------------------
+# Deformable mirror calibration (the DM model the loop is simulated with)
+# --------------------------------------------------------------------------
+def dm_calibration(subap_mask: np.ndarray, coupling: float = 0.3, support: int = 2,
+                   drop: float = 1e-6):
+    """The simulated DM's calibration matrices over the valid nodes (row-major
+    node order, actuators at the nodes): influence matrix N with
+    N[b, a] = coupling^(di^2 + dj^2) for node offsets |di|, |dj| <= support, and
+    the least-squares command matrix (N^T N)^-1 N^T with entries below `drop`
+    times the largest magnitude dropped, as a controller would load them.
+    Returns (N, P) as scipy CSR float64 matrices."""
+    import scipy.sparse
+    nodes = node_mask_of(subap_mask)
+    pts = np.argwhere(nodes)
+    index = -np.ones(nodes.shape, int)
+    index[nodes] = np.arange(len(pts))
+    rows, cols, vals = [], [], []
+    for a, (i, j) in enumerate(pts):
+        for di in range(-support, support + 1):
+            for dj in range(-support, support + 1):
+                ii, jj = i + di, j + dj
+                if 0 <= ii < nodes.shape[0] and 0 <= jj < nodes.shape[1] and index[ii, jj] >= 0:
+                    rows.append(index[ii, jj])
+                    cols.append(a)
+                    vals.append(coupling ** (di * di + dj * dj))
+    n = len(pts)
+    N = scipy.sparse.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    Nd = N.toarray()
+    full = np.linalg.lstsq(Nd, np.eye(n), rcond=None)[0]
+    P = scipy.sparse.csr_matrix(np.where(np.abs(full) >= drop * np.abs(full).max(), full, 0.0))
+    return N, P
