@@ -196,6 +196,47 @@ letkf_status letkf_run(letkf_t h, int32_t frames, const void *y_seq_dev, const v
 letkf_status letkf_run_graph(letkf_t h, int32_t frames, const void *y_seq_dev,
                              const void *truth_seq_dev, double *resvar_dev, uint64_t *stamps_dev);
 
+/* Deformable mirror of a single-instance per-node handle (Section 2.1, Eqs.
+ * Eq_Obs and Eq_Cor; Section 2.2; Appendix B.3): n = n_pts; N is the influence
+ * matrix (row b, column a: the phase at node b per unit command of actuator
+ * a; actuators at the nodes) and P the command matrix (the least-squares
+ * projection (N^T N)^-1 N^T of Appendix B.3, as the caller calibrated it),
+ * both host CSR: int32 row pointers [n + 1], int32 column indices, double
+ * values; copied (to the handle's real type). The library forms D1 N (at
+ * most 36 nonzeros per row for a 5 x 5 influence support) and zeroes the
+ * commands. From then on
+ *  - letkf_analyze takes y as the measurement of the residual phase, y_k =
+ *    D1 (phi^tur_{k-1} - N u_{k-2}) + w_k, and analyses the pseudo-open-loop
+ *    slopes y_k + D1 N u_{k-2} (ybar of Section 3.1.1 with its D1 N term);
+ *  - every forecast is followed by the command u_k = P phihat_{k+1/k}, the
+ *    predicted turbulent phase (row 0 mean) projected on the mirror;
+ *  - letkf_residual measures phi^tur_k - N u_{k-1}, the residual phase left
+ *    by the applied correction;
+ * the commands live on the device in a ring of three indexed by the forecast
+ * counter (so frames stay graph-capturable; letkf_set_frame moves it too).
+ * n_ptr NULL removes the mirror (the pseudo-open-loop form: the correction
+ * is the prediction itself). LETKF_ERR_ARG for a batch or domain handle or
+ * malformed CSR. Synchronises. */
+letkf_status letkf_set_dm(letkf_t h, int32_t n, const int32_t *n_ptr, const int32_t *n_idx,
+                          const double *n_val, const int32_t *p_ptr, const int32_t *p_idx,
+                          const double *p_val);
+
+/* The latest command u (the one computed after the last forecast), device
+ * [n_pts] real: what a controller sends to the mirror. Stream-ordered. */
+letkf_status letkf_get_command(letkf_t h, void *u_dev);
+
+/* The simulated true closed loop with the handle's deformable mirror over
+ * `frames` frames: for frame k the residual variance of phi^tur_k - N u_{k-1}
+ * into resvar[k] (if not NULL), the measurement y_k = D1 (phi^tur_{k-1} -
+ * N u_{k-2}) + w_k (phi^tur_{k-1} = truth_seq[k - 1], zero for the call's first
+ * frame), the analysis, the forecast with bank noise and the command.
+ * truth_seq_dev: device [frames][n_pts] real; wnoise_seq_dev: device
+ * [frames][p] real (w_k); resvar_dev: device double[frames] or NULL.
+ * use_graph != 0 replays one captured frame. LETKF_ERR_STATE without a mirror
+ * or a noise bank. */
+letkf_status letkf_run_dm(letkf_t h, int32_t frames, const void *truth_seq_dev,
+                          const void *wnoise_seq_dev, double *resvar_dev, int32_t use_graph);
+
 /* Change instance i's inflation rho, slope noise variance sigma2 and taper
  * half-support loc_len (<= 0: window / 4) in place (Section 4.2: A = (m-1)/rho I
  * + Yb^T R^-1 Yb with R^-1 = diag(tau_j / sigma2)); the next analysis uses them.

@@ -836,6 +836,8 @@ extern "C" letkf_status letkf_grad(letkf_t h, int32_t frames, const void *y_seq_
     return gfail(h, LETKF_ERR_ARG, "y_seq_dev and truth_seq_dev are required");
   if (h->n_inst != 1) return gfail(h, LETKF_ERR_ARG, "letkf_grad takes a single-instance handle");
   if (h->dom) return gfail(h, LETKF_ERR_STATE, "letkf_grad has no local-domain form");
+  if (h->inst[0].dm)
+    return gfail(h, LETKF_ERR_STATE, "letkf_grad differentiates the pseudo-open-loop form only");
   const LkInst &I = h->inst[0];
   if (I.mp > 32) return gfail(h, LETKF_ERR_ARG, "letkf_grad supports m <= 32");
   if (!I.bank) return gfail(h, LETKF_ERR_STATE, "letkf_grad needs the instance's noise bank");

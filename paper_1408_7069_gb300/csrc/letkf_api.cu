@@ -64,6 +64,8 @@ void drop_graphs(letkf_ctx *h) {
 void release(letkf_ctx *h) {
   drop_graphs(h);
   lk_domains_release(h);
+  if (h->dm_buf) cudaFree(h->dm_buf);
+  h->dm_buf = nullptr;
   for (cudaEvent_t ev : {h->ev_fork, h->ev_join, h->ev_out})
     if (ev) cudaEventDestroy(ev);
   if (h->side) cudaStreamDestroy(h->side);
@@ -404,10 +406,12 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   if (e == cudaSuccess) e = cudaMemset(h->frame, 0, 2 * sizeof(long long));
   if (e == cudaSuccess) e = cudaMemset(h->tickets, 0, (size_t)(n + 1) * sizeof(int));
   if (e != cudaSuccess) LK_TRY(cuda_fail(h, e, "cudaMemset"));
-  if (cfgs[0].partition > 0) {
+  if (n == 1) {
     h->dom_pid = geo[0].pid;
     h->dom_pts = geo[0].pts;
     h->dom_saps = geo[0].saps;
+  }
+  if (cfgs[0].partition > 0) {
     letkf_status ds = lk_domains_build(h, cfgs[0], h->dom_pid, h->dom_pts, h->dom_saps, h->err);
     if (ds != LETKF_OK && h->err.empty()) h->err = "local-domain set-up failed";
     LK_TRY(ds);
@@ -473,6 +477,20 @@ letkf_status enqueue_step(letkf_ctx *h, bool with_truth) {
   LK_CUDA(h, cudaMemcpyAsync(mp, md, down, cudaMemcpyDeviceToHost, h->stream));
   if (h->ev_out)
     LK_CUDA(h, cudaEventRecordWithFlags(h->ev_out, h->stream, cudaEventRecordExternal));
+  LK_CUDA(h, lk_launch_forecast(h, nullptr));
+  return LETKF_OK;
+}
+
+// One frame of the simulated closed loop with a deformable mirror: residual
+// against the correction, measurement of the residual phase, analysis of the
+// pseudo-open-loop slopes, forecast and command.
+letkf_status enqueue_frame_dm(letkf_ctx *h, const void *truth_seq, const void *wnoise_seq,
+                              double *resvar) {
+  const long long *ridx = h->frame + 1;
+  if (resvar) LK_CUDA(h, lk_launch_residual(h, truth_seq, resvar, ridx));
+  LK_CUDA(h, lk_launch_dm_wfs(h, truth_seq, wnoise_seq, ridx, h->dm_wfs_y));
+  LK_CUDA(h, lk_launch_obs(h, h->dm_wfs_y, nullptr));
+  LK_CUDA(h, lk_launch_analysis(h, nullptr, nullptr));
   LK_CUDA(h, lk_launch_forecast(h, nullptr));
   return LETKF_OK;
 }
@@ -676,6 +694,183 @@ letkf_status letkf_run_graph(letkf_t h, int32_t frames, const void *y_seq_dev,
   }
   LK_CUDA(h, cudaMemsetAsync(h->frame + 1, 0, sizeof(long long), h->stream));
   LK_CUDA(h, cudaGraphLaunch(h->mgraph, h->stream));
+  h->frame_host += frames;
+  return LETKF_OK;
+}
+
+letkf_status letkf_set_dm(letkf_t h, int32_t n, const int32_t *n_ptr, const int32_t *n_idx,
+                          const double *n_val, const int32_t *p_ptr, const int32_t *p_idx,
+                          const double *p_val) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (h->n_inst != 1 || h->dom)
+    return fail(h, LETKF_ERR_ARG, "a deformable mirror takes a single-instance per-node handle");
+  DeviceGuard dg(h->device);
+  LK_CUDA(h, cudaStreamSynchronize(h->stream));
+  LkInst &I = h->inst[0];
+  if (!n_ptr) {                                  // back to the pseudo-open-loop form
+    if (h->dm_buf) cudaFree(h->dm_buf);
+    h->dm_buf = nullptr;
+    h->dm_wfs_y = nullptr;
+    I.dm = 0;
+    drop_graphs(h);
+    return upload(h, h->d_inst, &I, sizeof(LkInst));
+  }
+  if (n != I.n_pts || !n_idx || !n_val || !p_ptr || !p_idx || !p_val)
+    return fail(h, LETKF_ERR_ARG, "N and P must be n_pts x n_pts CSR matrices");
+  auto valid = [n](const int32_t *ptr, const int32_t *idx) {
+    if (ptr[0] != 0) return false;
+    for (int r = 0; r < n; ++r)
+      if (ptr[r + 1] < ptr[r]) return false;
+    for (int q = 0; q < ptr[n]; ++q)
+      if (idx[q] < 0 || idx[q] >= n) return false;
+    return true;
+  };
+  if (!valid(n_ptr, n_idx) || !valid(p_ptr, p_idx))
+    return fail(h, LETKF_ERR_ARG, "malformed CSR (row pointers or column indices)");
+  // D1 N: the Fried slopes of every row of N (Appendix B)
+  const int nn = I.nsub + 1, ns = I.n_sap;
+  std::vector<int32_t> dn_ptr{0}, dn_idx;
+  std::vector<double> dn_val, acc(n, 0.0);
+  std::vector<int> touched;
+  std::vector<char> mark(n, 0);
+  for (int r = 0; r < 2 * ns; ++r) {
+    const int2 st = h->dom_saps[r % ns];
+    const int q00 = h->dom_pid[(size_t)st.x * nn + st.y];
+    const int q10 = h->dom_pid[(size_t)(st.x + 1) * nn + st.y];
+    const int q01 = h->dom_pid[(size_t)st.x * nn + st.y + 1];
+    const int q11 = h->dom_pid[(size_t)(st.x + 1) * nn + st.y + 1];
+    const int rows[4] = {q00, q10, q01, q11};
+    const double wx[4] = {-0.5, 0.5, -0.5, 0.5}, wy[4] = {-0.5, -0.5, 0.5, 0.5};
+    for (int c = 0; c < 4; ++c) {
+      const double wc = r < ns ? wx[c] : wy[c];
+      for (int q = n_ptr[rows[c]]; q < n_ptr[rows[c] + 1]; ++q) {
+        const int a = n_idx[q];
+        if (!mark[a]) {
+          mark[a] = 1;
+          touched.push_back(a);
+        }
+        acc[a] += wc * n_val[q];
+      }
+    }
+    std::sort(touched.begin(), touched.end());
+    for (int a : touched) {
+      if (acc[a] != 0.0) {
+        dn_idx.push_back(a);
+        dn_val.push_back(acc[a]);
+      }
+      acc[a] = 0.0;
+      mark[a] = 0;
+    }
+    touched.clear();
+    dn_ptr.push_back((int32_t)dn_idx.size());
+  }
+  // one allocation: int arrays, then real arrays (each 256-byte aligned)
+  const size_t rs = h->rsz, nzN = n_ptr[n], nzP = p_ptr[n], nzD = dn_idx.size();
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off = 0;
+  const size_t o_nptr = off; off = al(off + (n + 1) * 4);
+  const size_t o_nidx = off; off = al(off + nzN * 4);
+  const size_t o_pptr = off; off = al(off + (n + 1) * 4);
+  const size_t o_pidx = off; off = al(off + nzP * 4);
+  const size_t o_dptr = off; off = al(off + (2 * ns + 1) * 4);
+  const size_t o_didx = off; off = al(off + nzD * 4);
+  const size_t o_nval = off; off = al(off + nzN * rs);
+  const size_t o_pval = off; off = al(off + nzP * rs);
+  const size_t o_dval = off; off = al(off + nzD * rs);
+  const size_t o_u = off; off = al(off + 3 * (size_t)n * rs);
+  const size_t o_pm = off; off = al(off + (size_t)n * rs);
+  const size_t o_cor = off; off = al(off + (size_t)n * rs);
+  const size_t o_y = off; off = al(off + (size_t)2 * ns * rs);
+  if (h->dm_buf) cudaFree(h->dm_buf);
+  h->dm_buf = nullptr;
+  LK_CUDA(h, cudaMalloc(&h->dm_buf, off));
+  unsigned char *b = static_cast<unsigned char *>(h->dm_buf);
+  auto put_real = [&](size_t o, const double *v, size_t cnt) -> cudaError_t {
+    if (h->precision == 1) return cudaMemcpy(b + o, v, cnt * 8, cudaMemcpyHostToDevice);
+    std::vector<float> f(v, v + cnt);
+    return cudaMemcpy(b + o, f.data(), cnt * 4, cudaMemcpyHostToDevice);
+  };
+  LK_CUDA(h, cudaMemcpy(b + o_nptr, n_ptr, (n + 1) * 4, cudaMemcpyHostToDevice));
+  LK_CUDA(h, cudaMemcpy(b + o_nidx, n_idx, nzN * 4, cudaMemcpyHostToDevice));
+  LK_CUDA(h, cudaMemcpy(b + o_pptr, p_ptr, (n + 1) * 4, cudaMemcpyHostToDevice));
+  LK_CUDA(h, cudaMemcpy(b + o_pidx, p_idx, nzP * 4, cudaMemcpyHostToDevice));
+  LK_CUDA(h, cudaMemcpy(b + o_dptr, dn_ptr.data(), dn_ptr.size() * 4, cudaMemcpyHostToDevice));
+  LK_CUDA(h, cudaMemcpy(b + o_didx, dn_idx.data(), nzD * 4, cudaMemcpyHostToDevice));
+  LK_CUDA(h, put_real(o_nval, n_val, nzN));
+  LK_CUDA(h, put_real(o_pval, p_val, nzP));
+  LK_CUDA(h, put_real(o_dval, dn_val.data(), nzD));
+  LK_CUDA(h, cudaMemset(b + o_u, 0, 3 * (size_t)n * rs));
+  LK_CUDA(h, cudaMemset(b + o_pm, 0, (size_t)n * rs));
+  LK_CUDA(h, cudaMemset(b + o_cor, 0, (size_t)n * rs));
+  I.dm = 1;
+  I.n_ptr = reinterpret_cast<const int *>(b + o_nptr);
+  I.n_idx = reinterpret_cast<const int *>(b + o_nidx);
+  I.p_ptr = reinterpret_cast<const int *>(b + o_pptr);
+  I.p_idx = reinterpret_cast<const int *>(b + o_pidx);
+  I.dn_ptr = reinterpret_cast<const int *>(b + o_dptr);
+  I.dn_idx = reinterpret_cast<const int *>(b + o_didx);
+  I.n_val = b + o_nval;
+  I.p_val = b + o_pval;
+  I.dn_val = b + o_dval;
+  I.u = b + o_u;
+  I.pmean = b + o_pm;
+  I.cor = b + o_cor;
+  I.fcount = h->frame;
+  h->dm_wfs_y = b + o_y;
+  drop_graphs(h);
+  return upload(h, h->d_inst, &I, sizeof(LkInst));
+}
+
+letkf_status letkf_get_command(letkf_t h, void *u_dev) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (!u_dev) return fail(h, LETKF_ERR_ARG, "u_dev is NULL");
+  if (!h->inst[0].dm) return fail(h, LETKF_ERR_STATE, "no deformable mirror (letkf_set_dm)");
+  DeviceGuard dg(h->device);
+  LK_CUDA(h, lk_launch_dm_get(h, u_dev));
+  return LETKF_OK;
+}
+
+letkf_status letkf_run_dm(letkf_t h, int32_t frames, const void *truth_seq_dev,
+                          const void *wnoise_seq_dev, double *resvar_dev, int32_t use_graph) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (frames < 0) return fail(h, LETKF_ERR_ARG, "frames < 0");
+  if (!truth_seq_dev || !wnoise_seq_dev)
+    return fail(h, LETKF_ERR_ARG, "truth_seq_dev and wnoise_seq_dev are required");
+  if (!h->inst[0].dm) return fail(h, LETKF_ERR_STATE, "no deformable mirror (letkf_set_dm)");
+  if (!all_have_banks(h)) return fail(h, LETKF_ERR_STATE, "letkf_run_dm needs a noise bank");
+  if (use_graph && h->stream == nullptr)
+    return fail(h, LETKF_ERR_STATE, "graph capture needs a non-default stream");
+  DeviceGuard dg(h->device);
+  LK_CUDA(h, cudaMemsetAsync(h->frame + 1, 0, sizeof(long long), h->stream));
+  if (frames == 0) return LETKF_OK;
+  if (use_graph) {
+    if (h->graph) {                              // the one-frame graph of this call's form
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+    }
+    LK_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    letkf_status st = enqueue_frame_dm(h, truth_seq_dev, wnoise_seq_dev, resvar_dev);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (st != LETKF_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    h->graph_y = h->graph_truth = nullptr;       // not letkf_run's graph
+    h->graph_resvar = nullptr;
+    for (int k = 0; k < frames; ++k) LK_CUDA(h, cudaGraphLaunch(h->graph, h->stream));
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  } else {
+    for (int k = 0; k < frames; ++k) {
+      letkf_status st = enqueue_frame_dm(h, truth_seq_dev, wnoise_seq_dev, resvar_dev);
+      if (st != LETKF_OK) return st;
+    }
+  }
   h->frame_host += frames;
   return LETKF_OK;
 }

@@ -63,6 +63,16 @@ struct LkInst {
   long long node_off;       // ... in concatenated node arrays (truth, mean/spread rows)
   long long noise_off;      // ... in concatenated [n_pts][m] noise
   long long state_off;      // ... in the concatenated ensemble
+  // Deformable mirror (letkf_set_dm; dm = 0: none, the pseudo-open-loop form):
+  // influence matrix N, command matrix P and D1 N as CSR over the nodes, the
+  // commands u [3][n_pts] (slot f % 3 holds the command computed after
+  // forecast number f, f the forecast counter *fcount), the predicted phase
+  // pmean [n_pts] (written by the forecast) and the correction cor = N u_{k-1}.
+  int dm;
+  const int *n_ptr, *n_idx, *p_ptr, *p_idx, *dn_ptr, *dn_idx;
+  const void *n_val, *p_val, *dn_val;
+  void *u, *pmean, *cor;
+  const long long *fcount;
 };
 
 // Work items.
@@ -145,6 +155,10 @@ struct letkf_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr;
 
+  // deformable-mirror buffers (letkf_set_dm), single allocation per kind
+  void *dm_buf = nullptr;           // N, P, D1 N (CSR) and u, pmean, cor
+  unsigned char *dm_wfs_y = nullptr;   // letkf_run_dm: the simulated measurement [p]
+
   std::string err;
 };
 
@@ -163,6 +177,14 @@ cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
 cudaError_t lk_launch_residual_on(letkf_ctx *h, cudaStream_t stream, const void *truth,
                                   double *resvar, const long long *run_idx, double *piston);
 cudaError_t lk_launch_basis_reset(letkf_ctx *h);   // warm-start eigenbases -> identity
+// Deformable mirror (letkf_dm.cu): cor = N u_{k-1} on `stream` (before a
+// residual), u_k = P pmean (after a forecast), and the simulated measurement
+// y_k = D1 (phi_prev - N u_{k-2}) + w_k of a closed loop (phi_prev NULL: zero).
+cudaError_t lk_launch_dm_cor(letkf_ctx *h, cudaStream_t stream);
+cudaError_t lk_launch_dm_control(letkf_ctx *h);
+cudaError_t lk_launch_dm_wfs(letkf_ctx *h, const void *truth_seq, const void *wnoise_seq,
+                             const long long *run_idx, void *y_out);
+cudaError_t lk_launch_dm_get(letkf_ctx *h, void *out);
 // Writes the global timer (ns) into *dst once the preceding work has completed.
 cudaError_t lk_launch_stamp(letkf_ctx *h, unsigned long long *dst);
 cudaError_t lk_setup_analysis(letkf_ctx *h);

@@ -65,8 +65,18 @@ __global__ void __launch_bounds__(LK_WARP_CTA) obs_kernel(const LkInst *__restri
   if (lane == 0) {
     const S ybx = S(0.5) * ((u10 + u11) - (u00 + u01));
     const S yby = S(0.5) * ((u01 + u11) - (u00 + u10));
-    const S dx = y[k] - ybx;
-    const S dy = y[I.n_sap + k] - yby;
+    S yx = y[k], yy = y[I.n_sap + k];
+    if (I.dm) {
+      // the measurement sees the residual phase: the analysis takes the
+      // pseudo-open-loop slopes y + D1 N u_{k-2} (Section 3.1.1, ybar)
+      const S *u2 = static_cast<const S *>(I.u) + (size_t)((*I.fcount + 1) % 3) * I.n_pts;
+      const S *dv = static_cast<const S *>(I.dn_val);
+      for (int q = I.dn_ptr[k]; q < I.dn_ptr[k + 1]; ++q) yx += dv[q] * u2[I.dn_idx[q]];
+      for (int q = I.dn_ptr[I.n_sap + k]; q < I.dn_ptr[I.n_sap + k + 1]; ++q)
+        yy += dv[q] * u2[I.dn_idx[q]];
+    }
+    const S dx = yx - ybx;
+    const S dy = yy - yby;
     dp[cell * 2 + 0] = dx;
     dp[cell * 2 + 1] = dy;
     if (!isfinite(dx) || !isfinite(dy)) atomicOr(&counters[0], LK_BIT_NONFINITE);
@@ -82,6 +92,7 @@ __device__ __forceinline__ void forecast_node(const LkInst *__restrict__ insts, 
   S *row0 = static_cast<S *>(I.X) + (size_t)gpt * 2 * m;
   const S a = S(I.a_ar1), q = S(I.noise_std);
   const int2 ij = I.pts[gpt];
+  S psum = S(0);
   for (int i = lane; i < m; i += 32) {
     const S x0 = row0[i];
     S v;
@@ -98,6 +109,11 @@ __device__ __forceinline__ void forecast_node(const LkInst *__restrict__ insts, 
     }
     row0[m + i] = x0;
     row0[i] = a * x0 + v;
+    psum += row0[i];
+  }
+  if (I.dm) {                       // the predicted phase, for the command u = P phihat
+    psum = lk_warp_sum(psum);
+    if (lane == 0) static_cast<S *>(I.pmean)[gpt] = psum / S(m);
   }
 }
 
@@ -172,7 +188,9 @@ __global__ void __launch_bounds__(64) residual_kernel(const LkInst *__restrict__
     } else {
       for (int i = 0; i < m; ++i) x += (double)row[i];
     }
-    const double r = (double)tr[g] - x * inv_m;
+    // with a deformable mirror the residual phase is phi^tur_k - N u_{k-1}
+    // (Section 2.1, Eq. Eq_Cor); without, the prediction is the correction
+    const double r = (double)tr[g] - (I.dm ? (double)static_cast<const S *>(I.cor)[g] : x * inv_m);
     s1 += r;
     s2 += r * r;
   }
@@ -252,11 +270,16 @@ cudaError_t lk_launch_obs(letkf_ctx *h, const void *y, const long long *run_idx)
 cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise) {
   const int blocks = warp_blocks(h->n_pts_total);
   int *ticket = h->tickets + h->n_inst;
+  cudaError_t e;
   if (h->precision == 1)
-    return lk_launch_pdl(forecast_kernel<double>, blocks, LK_WARP_CTA, 0, h->stream, h->d_inst,
-                         h->node_items, h->n_pts_total, (const double *)noise, h->frame, ticket);
-  return lk_launch_pdl(forecast_kernel<float>, blocks, LK_WARP_CTA, 0, h->stream, h->d_inst,
-                       h->node_items, h->n_pts_total, (const float *)noise, h->frame, ticket);
+    e = lk_launch_pdl(forecast_kernel<double>, blocks, LK_WARP_CTA, 0, h->stream, h->d_inst,
+                      h->node_items, h->n_pts_total, (const double *)noise, h->frame, ticket);
+  else
+    e = lk_launch_pdl(forecast_kernel<float>, blocks, LK_WARP_CTA, 0, h->stream, h->d_inst,
+                      h->node_items, h->n_pts_total, (const float *)noise, h->frame, ticket);
+  // with a deformable mirror, the command of the new prediction
+  if (e == cudaSuccess && h->inst[0].dm) e = lk_launch_dm_control(h);
+  return e;
 }
 
 cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
@@ -267,6 +290,10 @@ cudaError_t lk_launch_residual(letkf_ctx *h, const void *truth, double *resvar,
 cudaError_t lk_launch_residual_on(letkf_ctx *h, cudaStream_t stream, const void *truth,
                                   double *resvar, const long long *run_idx, double *piston) {
   const dim3 grid(LK_RES_BLOCKS, h->n_inst);
+  if (h->inst[0].dm) {              // the correction N u_{k-1} the residual is taken against
+    cudaError_t e = lk_launch_dm_cor(h, stream);
+    if (e != cudaSuccess) return e;
+  }
   if (h->precision == 1)
     return lk_launch_pdl(residual_kernel<double>, grid, 64, 0, stream, h->d_inst, h->n_pts_total,
                          (const double *)truth, run_idx, h->partial, h->tickets, h->n_inst,

@@ -54,6 +54,10 @@ _SIGS = {
     "letkf_residual": [c_void_p, c_void_p, c_void_p],
     "letkf_run": [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32],
     "letkf_run_graph": [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p],
+    "letkf_set_dm": [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                     c_void_p],
+    "letkf_get_command": [c_void_p, c_void_p],
+    "letkf_run_dm": [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32],
     "letkf_sync": [c_void_p],
     "letkf_stats": [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)],
     "letkf_analyze_noalloc": [POINTER(letkf_config), c_void_p, c_void_p, c_void_p, c_void_p,
@@ -508,6 +512,43 @@ class Letkf:
             t = st.cpu().numpy().astype(np.float64)
             us = np.diff(t) / 1e3
         return resvar, us
+
+    def set_dm(self, N=None, P=None):
+        """Deformable mirror (letkf_set_dm) from scipy CSR matrices N and P
+        (n_pts x n_pts); None removes it."""
+        if N is None:
+            _check(lib().letkf_set_dm(self.h, 0, None, None, None, None, None, None), self.h)
+            return
+        arrs = []
+        for M in (N, P):
+            M = M.tocsr()
+            arrs += [np.ascontiguousarray(M.indptr, np.int32),
+                     np.ascontiguousarray(M.indices, np.int32),
+                     np.ascontiguousarray(M.data, np.float64)]
+        self._dm_keep = arrs
+        _check(lib().letkf_set_dm(self.h, self.n_pts, *[a.ctypes.data for a in arrs]), self.h)
+
+    def command(self):
+        """The latest DM command u [n_pts] (device tensor)."""
+        u = self.new(self.n_pts)
+        self._enter()
+        _check(lib().letkf_get_command(self.h, _ptr(u)), self.h)
+        self._leave()
+        return u
+
+    def run_dm(self, frames: int, truth_seq, wnoise_seq, use_graph: bool = True):
+        """The simulated closed loop with the mirror (letkf_run_dm); returns
+        the residual variance per frame (device FP64 tensor)."""
+        self._t(truth_seq, (truth_seq.shape[0], self.n_pts))
+        self._t(wnoise_seq, (wnoise_seq.shape[0], self.p))
+        if truth_seq.shape[0] < frames or wnoise_seq.shape[0] < frames:
+            raise ValueError("sequences shorter than frames")
+        resvar = self._torch.zeros(frames, dtype=self._torch.float64, device="cuda")
+        self._enter()
+        _check(lib().letkf_run_dm(self.h, int(frames), _ptr(truth_seq), _ptr(wnoise_seq),
+                                  _ptr(resvar), 1 if use_graph else 0), self.h)
+        self._leave()
+        return resvar
 
     def set_params(self, rho: float, sigma2: float, loc_len: float, instance: int = 0):
         letkf_set_params(self.h, instance, rho, sigma2, loc_len)
