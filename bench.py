@@ -307,6 +307,50 @@ def small_configs_arm(torch, L, K: int = 500, Wm: int = 20):
     return out
 
 
+# --------------------------------------------------------------------------- deformable mirror
+def dm_arm(torch, L, K: int = 500, Wm: int = 20):
+    """The 16 m system's true closed loop with the deformable mirror
+    (coupling 0.3, least-squares commands): per frame the residual against
+    N u_{k-1}, the simulated measurement of the residual phase, the analysis of
+    the pseudo-open-loop slopes, the forecast and the command, one CUDA-graph
+    replay per frame (letkf_run_dm). Returns the 'dm' object of the JSON line."""
+    import numpy as np
+    from paper_1408_7069_gb300 import synth, workloads as W
+    w = W.TEL_16M
+    inp = synth.make_loop_inputs(w, frames=Wm + K)
+    Nm, Pm = synth.dm_calibration(inp.subap_mask)
+    # w_k of the synthetic slopes: y_k - D1 phi_{k-1} (phi_{-1} = 0), by the
+    # Fried formula on the node grid
+    mask = inp.subap_mask.astype(bool)
+    nodes = synth.node_mask_of(inp.subap_mask)
+    grid = np.zeros((Wm + K, w.nsub + 1, w.nsub + 1))
+    grid[:, nodes] = inp.truth
+    prev = np.concatenate([np.zeros_like(grid[:1]), grid[:-1]])
+    wn = inp.slopes - synth.wfs_slopes(prev, mask)
+    f = L.Letkf.from_workload(w, bank=inp.bank)
+    f.set_state(torch.from_numpy(inp.X0.astype(np.float32)).cuda())
+    f.set_dm(Nm, Pm)
+    t = torch.from_numpy(inp.truth.astype(np.float32)).cuda()
+    wd = torch.from_numpy(wn.astype(np.float32)).cuda()
+    f.run_dm(Wm, t, wd)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(f.stream)
+    rv = f.run_dm(K, t[Wm:], wd[Wm:])
+    e1.record(f.stream)
+    torch.cuda.synchronize()
+    f.sync()
+    ms = e0.elapsed_time(e1)
+    out = {"workload": w.name, "frames": K, "frames_per_s": K / (ms / 1e3),
+           "us_per_frame": 1e3 * ms / K, "n_pts": int(f.n_pts),
+           "nnz_N": int(Nm.nnz), "nnz_P": int(Pm.nnz),
+           "resvar_last": float(rv[-1].item()),
+           "launch": "letkf_run_dm: one CUDA-graph replay per frame (residual vs N u, simulated "
+                     "WFS, observation with D1 N u, analysis, forecast, command u = P phihat)"}
+    f.close()
+    return out
+
+
 # --------------------------------------------------------------------------- local domains
 def domains_arm(torch, L, K: int = 200, Wm: int = 20):
     """Multi-actuator local domains (Section 4) at the paper's sizes: the 16 m
@@ -879,6 +923,7 @@ def gpu_arm(args):
         line["adjoint"] = adjoint_arm(torch, L)
     if rank == 0 and not args.no_domains:
         line["domains"] = domains_arm(torch, L)
+        line["dm"] = dm_arm(torch, L)
     if rank == 0:
         line["clocks"] = clk.summary()
         if world == 1 and not args.no_cpu_baseline:
