@@ -49,6 +49,9 @@ def parse_args(argv=None):
                     help="skip the reverse-mode (letkf_grad) measurement")
     ap.add_argument("--no-domains", action="store_true",
                     help="skip the multi-actuator local-domain measurement")
+    ap.add_argument("--only-domains", action="store_true",
+                    help="run only the local-domain measurement (K = --steps frames after "
+                         "--warmup) and print its JSON")
     ap.add_argument("--phase-split", action="store_true",
                     help="print where the FP32 analysis kernel spends its cycles (builds and "
                          "loads the phase-clock variant of the library) instead of the bench line")
@@ -947,6 +950,12 @@ def main(argv=None):
         return 0
     if args.phase_worker:
         return phase_worker(args)
+    if args.only_domains:
+        import torch
+        from paper_1408_7069_gb300 import letkf as L
+        torch.cuda.set_device(0)
+        print(json.dumps(domains_arm(torch, L, K=args.steps, Wm=args.warmup)))
+        return 0
     if args.phase_split:
         return phase_split(args)
     if args.impl == "reference":
