@@ -82,8 +82,9 @@ typedef struct {
   int32_t bank_B, bank_G;      /* bank shape (ignored when noise_bank is NULL) */
   int32_t max_sweeps;          /* Jacobi sweep limit per node; <= 0 -> 20 */
   int32_t partition;           /* 0: every node is its own local domain (the per-node analysis);
-                                  P in 1..64: multi-actuator local domains of a P x P partition
-                                  of the node grid (Section 4.1), single instance, FP32, m 2..128 */
+                                  P in 2..64: multi-actuator local domains of a P x P partition
+                                  of the node grid (Section 4.1), single instance, FP32, m 2..128;
+                                  1: one domain, the global ETKF (Section 3.1.1), m 2..1024 */
   int32_t piston;              /* with partition > 0: nonzero = remove the differential pistons
                                   between domains by least squares (Section 4.4) */
 } letkf_config;

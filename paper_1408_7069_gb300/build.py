@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libletkf.so")
 PHASE_LIB = os.path.join(PKG, "libletkf_phase.so")
 SOURCES = ["letkf_api.cu", "letkf_kernels.cu", "letkf_analysis.cu", "letkf_adjoint.cu", "letkf_pair.cu",
            "letkf_node64.cu", "letkf_peaks.cu", "letkf_domains.cu",
-           "letkf_dm.cu"]
+           "letkf_dm.cu", "letkf_global.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

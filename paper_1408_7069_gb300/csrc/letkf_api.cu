@@ -97,8 +97,10 @@ letkf_status check_config(const letkf_config &c) {
   if (!c.subap_mask) return fail(nullptr, LETKF_ERR_ARG, "subap_mask is NULL");
   if (c.partition < 0 || c.partition > 64)
     return fail(nullptr, LETKF_ERR_ARG, "partition must be in 0..64");
-  if (c.partition > 0 && (c.m < 2 || c.m > 128))
+  if (c.partition > 1 && (c.m < 2 || c.m > 128))
     return fail(nullptr, LETKF_ERR_ARG, "m must be in 2..128 with local domains");
+  if (c.partition == 1 && (c.m < 2 || c.m > 1024))
+    return fail(nullptr, LETKF_ERR_ARG, "m must be in 2..1024 for the global ETKF");
   if (c.partition > 0 && c.precision != 0)
     return fail(nullptr, LETKF_ERR_ARG, "local domains are analysed in FP32 (precision 0)");
   if (c.partition == 0 && (c.m < 2 || c.m > 64))

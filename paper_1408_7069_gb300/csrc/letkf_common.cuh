@@ -222,6 +222,13 @@ int lk_domain_count(const letkf_ctx *h);
 int lk_domain_of_nodes(const letkf_ctx *h, int *node_dom_host);
 int lk_domain_obs_counts(const letkf_ctx *h, int *obs_host);
 cudaError_t lk_launch_domains(letkf_ctx *h, void *mean, void *spread);
+// The global ETKF for m > 128 (letkf_global.cu): Newton-Schulz root, refined
+// mean, matrix-product apply, from the FP64 Gram partials.
+int lk_ns_tile();
+size_t lk_ns_workspace_bytes(int mpt, long long n_pad);
+cudaError_t lk_launch_ns_global(letkf_ctx *h, const double *gpart, const double *cpart,
+                                int kchunks, int mpt, int iters, void *ws, void *mean,
+                                void *spread);
 
 // ---------------------------------------------------------------------------
 // Device helpers

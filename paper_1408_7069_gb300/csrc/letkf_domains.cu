@@ -52,7 +52,8 @@ struct LkDom {
   float *cpist = nullptr;                         // [D][2] piston constants
   std::vector<double> tau;                        // host: tau of each observed slope
   // one domain covering the grid (partition 1): the global ETKF pipeline
-  int global = 0, kchunks = 0;
+  int global = 0, kchunks = 0, mpt = 0;
+  void *ns_ws = nullptr;                          // Newton-Schulz workspace (m > 128)
   double *gpart = nullptr;                        // [kchunks][MPD][MPD] Gram partial sums
   double *cpart = nullptr;                        // [kchunks][MPD]
   float *T = nullptr;                             // [m][m] transform wbar 1^T + W
@@ -706,9 +707,13 @@ cudaError_t setup_rpl(const LkDom &D) {
                               (int)smem);
 }
 
+// Rows per lane of the Jacobi layout (MPD = 8 RPL columns); 0: wider than the
+// one-CTA layout takes (the global ETKF's Newton-Schulz path, letkf_global.cu).
 int rpl_of(int m) {
-  return m <= 16 ? 2 : m <= 32 ? 4 : m <= 64 ? 8 : m <= 104 ? 13 : 16;
+  return m <= 16 ? 2 : m <= 32 ? 4 : m <= 64 ? 8 : m <= 104 ? 13 : m <= 128 ? 16 : 0;
 }
+
+constexpr int NS_ITERS = 40;      // Newton-Schulz iterations of the wide global path
 
 template <typename T>
 cudaError_t dup(T **dst, const std::vector<T> &src) {
@@ -818,7 +823,11 @@ letkf_status lk_domains_build(letkf_ctx *h, const letkf_config &c, const std::ve
   D->n_dom = (int)node_off.size() - 1;
   D->rpl = rpl_of(c.m);
   D->global = P == 1;
-  const int mpd = 8 * D->rpl;
+  if (D->rpl == 0 && !D->global) {
+    err = "local domains of more than one take m <= 128";
+    return LETKF_ERR_ARG;
+  }
+  const int mpd = D->rpl ? 8 * D->rpl : ((c.m + 63) / 64) * 64;
   const size_t smem = (size_t)dom_layout(mpd, D->max_obs, 2 * D->max_nodes).total * sizeof(float);
   int dev_smem = 0;
   cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
@@ -917,7 +926,8 @@ letkf_status lk_domains_build(letkf_ctx *h, const letkf_config &c, const std::ve
   if (e == cudaSuccess) e = cudaMalloc((void **)&D->delta, pts.size() * 2 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void **)&D->cpist, (size_t)Dn * 2 * sizeof(float));
   if (e == cudaSuccess && D->global) {
-    const int mpt = gl_mpt(mpd);
+    const int mpt = D->rpl ? gl_mpt(mpd) : mpd;
+    D->mpt = mpt;
     D->kchunks = (D->max_obs + GL_KC - 1) / GL_KC;
     if (D->kchunks < 1) D->kchunks = 1;
     e = cudaMalloc((void **)&D->gpart, (size_t)D->kchunks * mpt * mpt * sizeof(double));
@@ -925,7 +935,11 @@ letkf_status lk_domains_build(letkf_ctx *h, const letkf_config &c, const std::ve
     if (e == cudaSuccess) e = cudaMalloc((void **)&D->cpart, (size_t)D->kchunks * mpt * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(D->cpart, 0, (size_t)D->kchunks * mpt * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void **)&D->T, (size_t)c.m * c.m * sizeof(float));
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && D->rpl == 0) {
+      const long long n_pad = ((2LL * (long long)pts.size() + lk_ns_tile() - 1) / lk_ns_tile()) *
+                              lk_ns_tile();
+      e = cudaMalloc(&D->ns_ws, lk_ns_workspace_bytes(mpt, n_pad));
+    } else if (e == cudaSuccess) {
       switch (D->rpl) {
         case 2: e = setup_global_rpl<2>(*D, c.m); break;
         case 4: e = setup_global_rpl<4>(*D, c.m); break;
@@ -963,7 +977,7 @@ void lk_domains_release(letkf_ctx *h) {
   if (!D) return;
   void *bufs[] = {D->node_off, D->node_ids, D->obs_off, D->obs_slot, D->obs_w, D->node_dom,
                   D->edges,    D->dedge_off, D->dedge,   D->KT,       D->delta, D->cpist,
-                  D->gpart,    D->cpart,     D->T};
+                  D->gpart,    D->cpart,     D->T,       D->ns_ws};
   for (void *p : bufs)
     if (p) cudaFree(p);
   delete D;
@@ -992,6 +1006,15 @@ int lk_domain_obs_counts(const letkf_ctx *h, int *obs_host) {
 // constants and their application.
 cudaError_t lk_launch_domains(letkf_ctx *h, void *mean, void *spread) {
   const LkDom &D = *h->dom;
+  if (D.global && D.rpl == 0) {
+    const int nt = D.mpt / GL_TILE;
+    cudaError_t e = lk_launch_pdl(global_gram_kernel, dim3(nt * (nt + 1) / 2, D.kchunks), 256, 0,
+                                  h->stream, h->d_inst, (const int *)D.obs_slot,
+                                  (const float *)D.obs_w, D.max_obs, D.mpt, D.gpart, D.cpart);
+    if (e != cudaSuccess) return e;
+    return lk_launch_ns_global(h, D.gpart, D.cpart, D.kchunks, D.mpt, NS_ITERS, D.ns_ws, mean,
+                               spread);
+  }
   if (D.global) {
     switch (D.rpl) {
       case 2: return launch_global_rpl<2>(h, mean, spread);

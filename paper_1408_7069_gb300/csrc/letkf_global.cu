@@ -1,0 +1,315 @@
+// The global ETKF (Section 3.1.1: one domain observing every slope, partition
+// 1) for ensembles too wide for the one-CTA Jacobi (m > 128; the paper's
+// global curves reach m ~ 626, Section 5.1). The transform needs only
+// A^-1/2 and A^-1 c, so the eigendecomposition is replaced by matrix products:
+//   Gram     A = (m-1)/rho I + S^T S, c = S^T s in FP64 (the split-K Gram of
+//            letkf_domains.cu), s_A = |A|_F >= lambda_max
+//   root     coupled Newton-Schulz on Y0 = A / s_A, Z0 = I:
+//            T = (3 I - Z Y) / 2, Y <- Y T, Z <- T Z, converging to
+//            Y -> (A/s_A)^1/2 and Z -> (A/s_A)^-1/2 (the spectrum of A / s_A
+//            lies in (0, 1]); a fixed number of iterations, FP32 matrix
+//            products on a 64 x 64 tiled kernel, and a check of |I - Z Y|
+//   mean     wbar = A^-1 c by iterative refinement: residual c - A wbar in
+//            FP64, correction Z (Z r) / s_A in FP32
+//   apply    T = wbar 1^T + sqrt((m-1) / s_A) Z, Xa = xbar + X' T (the same
+//            matrix-product kernel over all state rows), mean and spread
+#include <math.h>
+
+#include <vector>
+
+#include "letkf_device.cuh"
+
+namespace {
+
+constexpr int NS_TILE = 64, NS_KT = 16, NS_THREADS = 256;
+
+// C = alpha A B + beta I (beta on the diagonal only), all row-major,
+// M, N, K multiples of 64. 64 x 64 tile per CTA, 4 x 4 outputs per thread.
+__global__ void __launch_bounds__(NS_THREADS)
+    ns_gemm_kernel(int K, const float *__restrict__ A, int lda, const float *__restrict__ B,
+                   int ldb, float *__restrict__ C, int ldc, float alpha, float beta) {
+  __shared__ float As[NS_KT][NS_TILE + 4], Bs[NS_KT][NS_TILE + 4];
+  lk_pdl_wait();
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+  const int row0 = blockIdx.y * NS_TILE, col0 = blockIdx.x * NS_TILE;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += NS_KT) {
+    for (int e = threadIdx.x; e < NS_KT * NS_TILE; e += NS_THREADS) {
+      const int r = e / NS_KT, k = e % NS_KT;              // A tile, transposed into As[k][r]
+      As[k][r] = A[(size_t)(row0 + r) * lda + k0 + k];
+      const int kb = e / NS_TILE, cb = e % NS_TILE;
+      Bs[kb][cb] = B[(size_t)(k0 + kb) * ldb + col0 + cb];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NS_KT; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][tr * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tc * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = row0 + tr * 4 + i, c = col0 + tc * 4 + j;
+      C[(size_t)r * ldc + c] = alpha * acc[i][j] + (r == c ? beta : 0.f);
+    }
+}
+
+// A (FP64) = (m-1)/rho I + the Gram partials, and the row sums of squares;
+// a CTA per row.
+__global__ void __launch_bounds__(256)
+    ns_assemble_kernel(const LkInst *__restrict__ insts, const double *__restrict__ gpart,
+                       const double *__restrict__ cpart, int kchunks, int mpt,
+                       double *__restrict__ A64, double *__restrict__ c64,
+                       double *__restrict__ rowsq) {
+  lk_pdl_wait();
+  const LkInst &I = insts[0];
+  const int i = blockIdx.x;
+  double sq = 0.0;
+  for (int j = threadIdx.x; j < mpt; j += blockDim.x) {
+    const int a = i <= j ? i : j, b = i <= j ? j : i;
+    double s = 0.0;
+    for (int k = 0; k < kchunks; ++k) s += gpart[((size_t)k * mpt + a) * mpt + b];
+    if (i == j) s += i < I.m ? I.alpha : 1.0;
+    A64[(size_t)i * mpt + j] = s;
+    sq = fma(s, s, sq);
+  }
+  __shared__ double red[8];
+  sq = lk_warp_sum(sq);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    rowsq[i] = t;
+    double c = 0.0;
+    for (int k = 0; k < kchunks; ++k) c += cpart[(size_t)k * mpt + i];
+    c64[i] = c;
+  }
+}
+
+// s_A = |A|_F (fixed summation order); Y = A / s_A, Z = I; wbar = 0.
+__global__ void __launch_bounds__(256)
+    ns_start_kernel(int mpt, const double *__restrict__ A64, const double *__restrict__ rowsq,
+                    double *__restrict__ scale, float *__restrict__ Y, float *__restrict__ Z,
+                    double *__restrict__ w64) {
+  lk_pdl_wait();
+  double t = 0.0;
+  for (int i = 0; i < mpt; ++i) t += rowsq[i];
+  const double s = sqrt(t);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *scale = s;
+  const double inv = 1.0 / s;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)mpt * mpt;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / mpt), j = (int)(e % mpt);
+    Y[e] = (float)(A64[e] * inv);
+    Z[e] = i == j ? 1.f : 0.f;
+    if (e < mpt) w64[e] = 0.0;
+  }
+}
+
+// max |I - Z Y| of the converged iteration (R = Z Y given) into the status
+// word: NOCONVERGE above 1e-3.
+__global__ void __launch_bounds__(256)
+    ns_check_kernel(int mpt, const float *__restrict__ R, int *__restrict__ counters) {
+  lk_pdl_wait();
+  float mx = 0.f;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)mpt * mpt;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / mpt), j = (int)(e % mpt);
+    mx = fmaxf(mx, fabsf((i == j ? 1.f : 0.f) - R[e]));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+  if ((threadIdx.x & 31) == 0 && !(mx <= 1e-3f)) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
+}
+
+// r = c - A w (FP64), thread per row.
+__global__ void __launch_bounds__(128)
+    ns_residual_kernel(int mpt, const double *__restrict__ A64, const double *__restrict__ c64,
+                       const double *__restrict__ w64, float *__restrict__ r) {
+  lk_pdl_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= mpt) return;
+  double s = c64[i];
+  for (int j = 0; j < mpt; ++j) s = fma(-A64[(size_t)j * mpt + i], w64[j], s);   // A symmetric
+  r[i] = (float)s;
+}
+
+// out = Z v (FP32), thread per row; with `w`, w += out / s_A (FP64).
+__global__ void __launch_bounds__(128)
+    ns_matvec_kernel(int mpt, const float *__restrict__ Z, const float *__restrict__ v,
+                     float *__restrict__ out, double *__restrict__ w,
+                     const double *__restrict__ scale) {
+  lk_pdl_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= mpt) return;
+  float s = 0.f;
+  for (int j = 0; j < mpt; ++j) s = fmaf(Z[(size_t)j * mpt + i], v[j], s);      // Z symmetric
+  if (w)
+    w[i] += (double)s / *scale;
+  else
+    out[i] = s;
+}
+
+// T = wbar 1^T + sqrt((m-1) / s_A) Z on the m x m block, zero elsewhere.
+__global__ void __launch_bounds__(256)
+    ns_transform_kernel(const LkInst *__restrict__ insts, int mpt, const float *__restrict__ Z,
+                        const double *__restrict__ w64, const double *__restrict__ scale,
+                        float *__restrict__ T) {
+  lk_pdl_wait();
+  const LkInst &I = insts[0];
+  const float f = (float)sqrt((I.m - 1) / *scale);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)mpt * mpt;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / mpt), j = (int)(e % mpt);
+    T[e] = (i < I.m && j < I.m) ? (float)w64[i] + f * Z[e] : 0.f;
+  }
+}
+
+// Anomalies of every state row into Xp [n_pad][mpt] (zero padding), means into xm.
+__global__ void __launch_bounds__(LK_WARP_CTA)
+    ns_anom_kernel(const LkInst *__restrict__ insts, int mpt, long long n_pad,
+                   float *__restrict__ Xp, float *__restrict__ xm) {
+  lk_pdl_wait();
+  const LkInst &I = insts[0];
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, m = I.m;
+  if (r >= n_pad) return;
+  const bool real = r < 2LL * I.n_pts;
+  const float *x = static_cast<const float *>(I.X) + r * m;
+  float s = 0.f;
+  if (real)
+    for (int j = lane; j < m; j += 32) s += x[j];
+  s = lk_warp_sum(s) / float(m);
+  for (int j = lane; j < mpt; j += 32) Xp[r * mpt + j] = (real && j < m) ? x[j] - s : 0.f;
+  if (lane == 0) xm[r] = s;
+}
+
+// Xa = xbar + (X' T), mean and spread, warp per state row.
+__global__ void __launch_bounds__(LK_WARP_CTA)
+    ns_finish_kernel(const LkInst *__restrict__ insts, int mpt, const float *__restrict__ P,
+                     const float *__restrict__ xm, float *__restrict__ mean,
+                     float *__restrict__ spread, int *__restrict__ counters) {
+  lk_pdl_wait();
+  const LkInst &I = insts[0];
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, m = I.m;
+  if (r >= 2LL * I.n_pts) return;
+  float *x = static_cast<float *>(I.X) + r * m;
+  float sum = 0.f;
+  for (int j = lane; j < m; j += 32) {
+    const float xa = xm[r] + P[r * mpt + j];
+    x[j] = xa;
+    sum += xa;
+  }
+  const float mu = lk_warp_sum(sum) / float(m);
+  float sq = 0.f;
+  for (int j = lane; j < m; j += 32) {
+    const float d = x[j] - mu;
+    sq = fmaf(d, d, sq);
+  }
+  const float sp = sqrtf(lk_warp_sum(sq) / float(m - 1));
+  if (lane == 0) {
+    if (mean) mean[r] = mu;
+    if (spread) spread[r] = sp;
+    if (!isfinite(mu) || !isfinite(sp)) atomicOr(&counters[0], LK_BIT_NONFINITE);
+  }
+}
+
+cudaError_t gemm(cudaStream_t st, int M, int N, int K, const float *A, int lda, const float *B,
+                 int ldb, float *C, int ldc, float alpha, float beta) {
+  return lk_launch_pdl(ns_gemm_kernel, dim3(N / NS_TILE, M / NS_TILE), NS_THREADS, 0, st, K, A,
+                       lda, B, ldb, C, ldc, alpha, beta);
+}
+
+}  // namespace
+
+int lk_ns_tile() { return NS_TILE; }
+
+// Workspace (one allocation): A64, c64, w64, rowsq, scale (FP64); Y, Z, T, U
+// (FP32 [mpt][mpt]); r, v (FP32 [mpt]); Xp and the product (FP32 [n_pad][mpt]),
+// xm [n_pad].
+size_t lk_ns_workspace_bytes(int mpt, long long n_pad) {
+  const size_t d = (size_t)mpt * mpt * 8 + 3 * (size_t)mpt * 8 + 8;
+  const size_t f = 4 * (size_t)mpt * mpt * 4 + 2 * (size_t)mpt * 4 +
+                   2 * (size_t)n_pad * mpt * 4 + (size_t)n_pad * 4;
+  return d + f + 1024;
+}
+
+cudaError_t lk_launch_ns_global(letkf_ctx *h, const double *gpart, const double *cpart,
+                                int kchunks, int mpt, int iters, void *ws, void *mean,
+                                void *spread) {
+  const LkInst &I = h->inst[0];
+  const long long n_pad = ((2LL * I.n_pts + NS_TILE - 1) / NS_TILE) * NS_TILE;
+  unsigned char *b = static_cast<unsigned char *>(ws);
+  double *A64 = reinterpret_cast<double *>(b);
+  double *c64 = A64 + (size_t)mpt * mpt, *w64 = c64 + mpt, *rowsq = w64 + mpt;
+  double *scale = rowsq + mpt;
+  float *Y = reinterpret_cast<float *>(scale + 1);
+  float *Z = Y + (size_t)mpt * mpt, *T = Z + (size_t)mpt * mpt, *U = T + (size_t)mpt * mpt;
+  float *rv = U + (size_t)mpt * mpt, *vv = rv + mpt;
+  float *Xp = vv + mpt, *Pr = Xp + (size_t)n_pad * mpt, *xm = Pr + (size_t)n_pad * mpt;
+  cudaStream_t st = h->stream;
+  cudaError_t e = lk_launch_pdl(ns_assemble_kernel, (unsigned)mpt, 256, 0, st,
+                                (const LkInst *)h->d_inst, gpart, cpart, kchunks, mpt, A64, c64,
+                                rowsq);
+  const unsigned eb = (unsigned)(((long long)mpt * mpt + 255) / 256 < 2048
+                                     ? ((long long)mpt * mpt + 255) / 256
+                                     : 2048);
+  if (e == cudaSuccess)
+    e = lk_launch_pdl(ns_start_kernel, eb, 256, 0, st, mpt, (const double *)A64,
+                      (const double *)rowsq, scale, Y, Z, w64);
+  // Newton-Schulz, buffers rotating: T = 1.5 I - 0.5 Z Y; U = Y T; Y' = U;
+  // Z' = T Z written into the old Y
+  for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+    e = gemm(st, mpt, mpt, mpt, Z, mpt, Y, mpt, T, mpt, -0.5f, 1.5f);
+    if (e == cudaSuccess) e = gemm(st, mpt, mpt, mpt, Y, mpt, T, mpt, U, mpt, 1.f, 0.f);
+    if (e == cudaSuccess) e = gemm(st, mpt, mpt, mpt, T, mpt, Z, mpt, Y, mpt, 1.f, 0.f);
+    float *nY = U, *nZ = Y;
+    U = Z;
+    Y = nY;
+    Z = nZ;
+  }
+  if (e == cudaSuccess) e = gemm(st, mpt, mpt, mpt, Z, mpt, Y, mpt, T, mpt, 1.f, 0.f);
+  if (e == cudaSuccess)
+    e = lk_launch_pdl(ns_check_kernel, eb, 256, 0, st, mpt, (const float *)T, h->counters);
+  // wbar = A^-1 c by refinement with A^-1 ~ Z Z / s_A
+  const unsigned vb = (unsigned)((mpt + 127) / 128);
+  for (int it = 0; it < 4 && e == cudaSuccess; ++it) {
+    e = lk_launch_pdl(ns_residual_kernel, vb, 128, 0, st, mpt, (const double *)A64,
+                      (const double *)c64, (const double *)w64, rv);
+    if (e == cudaSuccess)
+      e = lk_launch_pdl(ns_matvec_kernel, vb, 128, 0, st, mpt, (const float *)Z,
+                        (const float *)rv, vv, (double *)nullptr, (const double *)scale);
+    if (e == cudaSuccess)
+      e = lk_launch_pdl(ns_matvec_kernel, vb, 128, 0, st, mpt, (const float *)Z,
+                        (const float *)vv, rv, w64, (const double *)scale);
+  }
+  if (e == cudaSuccess)
+    e = lk_launch_pdl(ns_transform_kernel, eb, 256, 0, st, (const LkInst *)h->d_inst, mpt,
+                      (const float *)Z, (const double *)w64, (const double *)scale, T);
+  const unsigned rb = (unsigned)((n_pad * 32 + LK_WARP_CTA - 1) / LK_WARP_CTA);
+  if (e == cudaSuccess)
+    e = lk_launch_pdl(ns_anom_kernel, rb, LK_WARP_CTA, 0, st, (const LkInst *)h->d_inst, mpt,
+                      n_pad, Xp, xm);
+  if (e == cudaSuccess) e = gemm(st, (int)n_pad, mpt, mpt, Xp, mpt, T, mpt, Pr, mpt, 1.f, 0.f);
+  const unsigned fb = (unsigned)((2LL * I.n_pts * 32 + LK_WARP_CTA - 1) / LK_WARP_CTA);
+  if (e == cudaSuccess)
+    e = lk_launch_pdl(ns_finish_kernel, fb, LK_WARP_CTA, 0, st, (const LkInst *)h->d_inst, mpt,
+                      (const float *)Pr, (const float *)xm, static_cast<float *>(mean),
+                      static_cast<float *>(spread), h->counters);
+  return e;
+}

@@ -157,7 +157,9 @@ def test_domain_handles_refuse_what_they_do_not_support():
     with pytest.raises(LetkfError, match="LETKF_ERR_ARG"):
         Letkf.from_workload(replace(w, precision=1))
     with pytest.raises(LetkfError, match="LETKF_ERR_ARG"):
-        Letkf.from_workload(replace(w, m=129))
+        Letkf.from_workload(replace(w, m=129))          # a partition of more than one domain
+    with pytest.raises(LetkfError, match="LETKF_ERR_ARG"):
+        Letkf.from_workload(replace(w, partition=1, m=1025))
     with pytest.raises(LetkfError, match="LETKF_ERR_ARG"):
         Letkf.batch([w, w], [None, None])
     inp = synth.make_loop_inputs(w, frames=3)
@@ -179,6 +181,32 @@ def test_global_etkf_at_paper_size(frames):
     inp = synth.make_loop_inputs(w, frames=frames + 2)
     dg = LD.build_domains(inp.subap_mask, 1, w.window, 0)
     assert dg.n_dom == 1 and len(dg.dom_obs[0]) == dg.geom.p == 1624
+    X = inp.X0.copy()
+    for k in range(frames):
+        Xa, _, _ = LD.analysis_domains(dg, X, inp.slopes[k], w.sigma2, w.rho)
+        X = oracle.forecast(Xa, oracle.bank_noise(inp.bank, dg.geom.points, w.m, w.seeds[2], k,
+                                                  w.noise_std), w.a_ar1)
+    Xb = X.astype(np.float32)
+    y = inp.slopes[frames].astype(np.float32)
+    (Xa, mean, spread), _ = gpu_analysis(w, inp, Xb, y)
+    rXa, rmean, rspread = LD.analysis_domains(dg, Xb.astype(np.float64), y.astype(np.float64),
+                                              w.sigma2, w.rho)
+    assert rel(mean, rmean) <= 1e-4, rel(mean, rmean)
+    assert rel(spread, rspread) <= 1e-3, rel(spread, rspread)
+    assert rel(anoms(Xa), anoms(rXa)) <= 1e-3, rel(anoms(Xa), anoms(rXa))
+    xbar = Xb.astype(np.float64).mean(-1)
+    assert rel(mean - xbar, rmean - xbar) <= 1e-3, rel(mean - xbar, rmean - xbar)
+
+
+@pytest.mark.parametrize("m,frames", [(200, 0), (200, 2), (626, 0)],
+                         ids=["m200-prior", "m200-f2", "m626-prior"])
+def test_global_etkf_wide_ensembles(m, frames):
+    """The global ETKF beyond the one-CTA eigensolver (m > 128, up to the
+    paper's 626 members): Newton-Schulz root and FP64-refined mean solve
+    against the oracle's eigendecomposition, 16 m pupil, all 1624 slopes."""
+    w = replace(W.DOM_16M, name=f"global-16m-m{m}", m=m, partition=1, piston=0, taper=0)
+    inp = synth.make_loop_inputs(w, frames=frames + 2)
+    dg = LD.build_domains(inp.subap_mask, 1, w.window, 0)
     X = inp.X0.copy()
     for k in range(frames):
         Xa, _, _ = LD.analysis_domains(dg, X, inp.slopes[k], w.sigma2, w.rho)
