@@ -797,6 +797,9 @@ def gpu_arm(args):
     torch.cuda.synchronize()
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    import gc
+    gc.collect()
+    gc.disable()                   # no collector pause between a frame's launches
     with ClockSampler(local) as clk:
         t_wall0 = time.perf_counter()
         with torch.cuda.stream(s):
@@ -813,6 +816,7 @@ def gpu_arm(args):
                 e[3].record(s)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
+    gc.enable()
     L.letkf_sync(h)
     nfp64, sweeps, total_sweeps = L.letkf_stats(h)
     frame_ms = [e[0].elapsed_time(e[3]) for e in ev]
