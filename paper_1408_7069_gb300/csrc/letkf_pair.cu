@@ -59,10 +59,7 @@ struct PairCfg {
   static constexpr int NPW = MP <= 32 ? 32 / LPN : 1;     // nodes per warp
   static constexpr int GL = NPW > 1 ? LPN : 32;           // lanes of a node's group (power of 2)
   static constexpr int K2 = MP / 2;                       // float2 per column
-  // floats per halo cell: +4 shifts consecutive cells by four banks; MP = 32
-  // (tensor-core Gram) shifts them by eight, so that the four cells a k-step
-  // reads land on disjoint banks
-  static constexpr int CELLF = 2 * MP + (MP == 32 ? 8 : 4);
+  static constexpr int CELLF = 2 * MP + 4;                // floats per halo cell (+4: bank shift)
   static constexpr int NODE_SCR = 3 * MP + 4;             // scratch floats per node
 };
 
@@ -70,20 +67,12 @@ struct PairCfg {
 struct PairLayout {
   size_t dh, tap, scr, total;
 };
-// MP = 32: after the Gram every warp reuses the halo region as a [32][34]
-// buffer for its nodes' Gram matrices, so the region holds at least that.
-constexpr int GRAM_LD = 34;
 template <int MP, int TI, int TJ>
 __host__ __device__ PairLayout pair_layout(int w) {
   using C = PairCfg<MP>;
   PairLayout L;
   const size_t ncell = (size_t)(TI + w - 1) * (TJ + w - 1);
-  size_t region = ncell * C::CELLF;
-  if (MP == 32) {
-    const size_t gb = (size_t)(TI * TJ / C::NPW) * 32 * GRAM_LD;
-    region = gb > region ? gb : region;
-  }
-  L.dh = align16(region * sizeof(float));
+  L.dh = align16(ncell * C::CELLF * sizeof(float));
   L.tap = align16(L.dh + ncell * 2 * sizeof(float));
   L.scr = align16(L.tap + (size_t)w * w * sizeof(float));
   L.total = L.scr + (size_t)TI * TJ * C::NODE_SCR * sizeof(float);
@@ -190,144 +179,6 @@ __device__ __forceinline__ float2 reduce_scatter(float2 (&v)[GL], int li) {
   return v[0];
 }
 
-// ---------------------------------------------------------------------------
-// Tensor-core Gram for MP = 32 (Section 4.2's S^T S, the dense contraction of
-// the update): per node G = sum_j tau_j y_j y_j^T over the window's slopes as
-// warp-level mma.sync m16n8k8 TF32 products, A = Y (members x slopes), B = tau Y
-// (slopes x members), two 16-row tiles by four 8-column tiles, eight slopes
-// (four cells, both components) per k-step. Each FP32 operand is split into
-// TF32 high and low parts and three products (lo*hi, hi*lo, hi*hi) accumulate in
-// FP32, which keeps the Gram at FP32 accuracy (the dropped lo*lo term is about
-// 2^-22 of each product). One lane loads, per k-step, members g, g+8, g+16,
-// g+24 (g = lane / 4) of both slopes of cell t = lane % 4: the same four values
-// feed its A and B fragments. The warp does its two nodes in turn, then
-// (after a CTA barrier: the halo is no longer read) writes each Gram through a
-// per-warp [32][34] buffer in the halo region, from which lane i of the node
-// takes rows 2i and 2i+1 (= columns, G is symmetric) in the pair layout.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned tf32_hi(float v) {
-  unsigned r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return r;
-}
-
-__device__ __forceinline__ void split_tf32(float v, unsigned &hi, unsigned &lo) {
-  hi = tf32_hi(v);
-  lo = tf32_hi(v - __uint_as_float(hi));
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2,
-                                         unsigned a3, unsigned b0, unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-template <int TJ>
-__device__ __forceinline__ void gram_mma32(const float *halo, const float *dh, const float *tap,
-                                           int w, int HJ, int warp, int lane, float2 (&P)[16],
-                                           float2 (&Q)[16], float &diag, float &cd0, float &cd1) {
-  constexpr int CELLF = PairCfg<32>::CELLF;
-  const int g = lane >> 2, t = lane & 3;
-  const int ncell = w * w, ksteps = (ncell + 3) / 4;
-  float acc[2][2][4][4];
-  float cdp[2][4];
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) cdp[s][q] = 0.f;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[s][mt][nt][c] = 0.f;
-  }
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const int node = warp * 2 + s;
-    const int nti = node / TJ, ntj = node - (node / TJ) * TJ;
-    const float *hw = halo + (size_t)(nti * HJ + ntj) * CELLF;
-    const float *dw = dh + (size_t)(nti * HJ + ntj) * 2;
-    for (int ks = 0; ks < ksteps; ++ks) {
-      const int j = 4 * ks + t;
-      const bool valid = j < ncell;
-      const int ds = valid ? j / w : 0, dt = valid ? j - (j / w) * w : 0;
-      const int cell = ds * HJ + dt;
-      const float tw = valid ? tap[j] : 0.f;
-      const float *base = hw + (size_t)cell * CELLF;
-      float v0[4], v1[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        v0[q] = valid ? base[g + 8 * q] : 0.f;
-        v1[q] = valid ? base[32 + g + 8 * q] : 0.f;
-      }
-      const float d0 = valid ? dw[cell * 2] : 0.f, d1 = valid ? dw[cell * 2 + 1] : 0.f;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) cdp[s][q] = fmaf(tw, fmaf(v0[q], d0, v1[q] * d1), cdp[s][q]);
-      unsigned ah0[4], al0[4], ah1[4], al1[4], bh0[4], bl0[4], bh1[4], bl1[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        split_tf32(v0[q], ah0[q], al0[q]);
-        split_tf32(v1[q], ah1[q], al1[q]);
-        split_tf32(tw * v0[q], bh0[q], bl0[q]);
-        split_tf32(tw * v1[q], bh1[q], bl1[q]);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          float(&d)[4] = acc[s][mt][nt];
-          mma_tf32(d, al0[2 * mt], al0[2 * mt + 1], al1[2 * mt], al1[2 * mt + 1], bh0[nt], bh1[nt]);
-          mma_tf32(d, ah0[2 * mt], ah0[2 * mt + 1], ah1[2 * mt], ah1[2 * mt + 1], bl0[nt], bl1[nt]);
-          mma_tf32(d, ah0[2 * mt], ah0[2 * mt + 1], ah1[2 * mt], ah1[2 * mt + 1], bh0[nt], bh1[nt]);
-        }
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      cdp[s][q] += __shfl_xor_sync(FULL, cdp[s][q], 1);
-      cdp[s][q] += __shfl_xor_sync(FULL, cdp[s][q], 2);
-    }
-  __syncthreads();                                   // the halo is read no more
-  float *gb = const_cast<float *>(halo) + (size_t)warp * 32 * GRAM_LD;
-  const int grp = lane >> 4, li = lane & 15;
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const float(&d)[4] = acc[s][mt][nt];
-        *reinterpret_cast<float2 *>(gb + (16 * mt + g) * GRAM_LD + 8 * nt + 2 * t) =
-            make_float2(d[0], d[1]);
-        *reinterpret_cast<float2 *>(gb + (16 * mt + g + 8) * GRAM_LD + 8 * nt + 2 * t) =
-            make_float2(d[2], d[3]);
-      }
-    if (t == 0) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) gb[(g + 8 * q) * GRAM_LD + 32] = cdp[s][q];
-    }
-    __syncwarp();
-    if (grp == s) {
-      const float *r0 = gb + (2 * li) * GRAM_LD, *r1 = r0 + GRAM_LD;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        P[k] = reinterpret_cast<const float2 *>(r0)[k];
-        Q[k] = reinterpret_cast<const float2 *>(r1)[k];
-      }
-      diag = r0[2 * li] + r1[2 * li + 1];
-      cd0 = r0[32];
-      cd1 = r1[32];
-    }
-    __syncwarp();
-  }
-}
-
 // Stages the tile's halo (slope anomalies and innovations) and the taper table.
 template <int MP, int TI, int TJ>
 __device__ __forceinline__ void stage_pair_tile(const LkInst &I, int i0, int j0, float *halo,
@@ -428,9 +279,6 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
   const float *hwin = halo + (size_t)(ti * HJ + tj) * C::CELLF;
   const float *dwin = dh + (size_t)(ti * HJ + tj) * 2;
   const int lr = live ? li : 0;                      // idle lanes read row pair 0, then drop it
-  if constexpr (MP == 32) {
-    gram_mma32<TJ>(halo, dh, tap, w, HJ, threadIdx.x >> 5, lane, P, Q, diag, cd0, cd1);
-  } else {
   for (int ds = 0; ds < w; ++ds) {
     for (int dt = 0; dt < w; ++dt) {
       const int cell = ds * HJ + dt;
@@ -456,7 +304,6 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
         }
       }
     }
-  }
   }
   if (!live) diag = cd0 = cd1 = 0.f;
   const float alpha = float(I.alpha);
