@@ -21,51 +21,78 @@
 
 namespace {
 
-constexpr int NS_TILE = 64, NS_KT = 16, NS_THREADS = 256;
+constexpr int NS_TILE = 64, NS_KT = 32, NS_THREADS = 256;
 
-// C = alpha A B + beta I (beta on the diagonal only), all row-major,
-// M, N, K multiples of 64. 64 x 64 tile per CTA, 4 x 4 outputs per thread.
+// C = alpha A B + beta I (beta on the diagonal only), all row-major, M, N, K
+// multiples of 64, leading dimensions multiples of 4 floats. A 64 x 64 tile
+// per CTA, 4 x 4 outputs per thread; the next 32-deep slice of A and B is
+// loaded into registers (float4) while the current one, in shared memory (A
+// transposed), is multiplied.
 __global__ void __launch_bounds__(NS_THREADS)
     ns_gemm_kernel(int K, const float *__restrict__ A, int lda, const float *__restrict__ B,
                    int ldb, float *__restrict__ C, int ldc, float alpha, float beta) {
-  __shared__ float As[NS_KT][NS_TILE + 4], Bs[NS_KT][NS_TILE + 4];
+  __shared__ __align__(16) float As[NS_KT][NS_TILE + 4];
+  __shared__ __align__(16) float Bs[NS_KT][NS_TILE + 4];
   lk_pdl_wait();
-  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+  const int tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
   const int row0 = blockIdx.y * NS_TILE, col0 = blockIdx.x * NS_TILE;
+  // slice loads: A 64 x 32 (two float4 per thread: row ar + 32 q, columns ak .. ak+3),
+  // B 32 x 64 (two float4 per thread: row bk + 16 q, columns bc .. bc+3)
+  const int ar = tid / 8, ak = (tid % 8) * 4;
+  const int bk = tid / 16, bc = (tid % 16) * 4;
+  float4 ra[2], rb[2];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      ra[q] = *reinterpret_cast<const float4 *>(A + (size_t)(row0 + ar + 32 * q) * lda + k0 + ak);
+      rb[q] = *reinterpret_cast<const float4 *>(B + (size_t)(k0 + bk + 16 * q) * ldb + col0 + bc);
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int r = ar + 32 * q;
+      As[ak + 0][r] = ra[q].x;
+      As[ak + 1][r] = ra[q].y;
+      As[ak + 2][r] = ra[q].z;
+      As[ak + 3][r] = ra[q].w;
+      *reinterpret_cast<float4 *>(&Bs[bk + 16 * q][bc]) = rb[q];
+    }
+  };
   float acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  load(0);
   for (int k0 = 0; k0 < K; k0 += NS_KT) {
-    for (int e = threadIdx.x; e < NS_KT * NS_TILE; e += NS_THREADS) {
-      const int r = e / NS_KT, k = e % NS_KT;              // A tile, transposed into As[k][r]
-      As[k][r] = A[(size_t)(row0 + r) * lda + k0 + k];
-      const int kb = e / NS_TILE, cb = e % NS_TILE;
-      Bs[kb][cb] = B[(size_t)(k0 + kb) * ldb + col0 + cb];
-    }
+    store();
     __syncthreads();
+    if (k0 + NS_KT < K) load(k0 + NS_KT);
 #pragma unroll
     for (int k = 0; k < NS_KT; ++k) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[k][tr * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tc * 4 + j];
+      const float4 a = *reinterpret_cast<const float4 *>(&As[k][tr * 4]);
+      const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tc * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 4; ++i) {
+    const int r = row0 + tr * 4 + i;
+    float4 o;
+    float *ov = &o.x;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int r = row0 + tr * 4 + i, c = col0 + tc * 4 + j;
-      C[(size_t)r * ldc + c] = alpha * acc[i][j] + (r == c ? beta : 0.f);
+      const int c = col0 + tc * 4 + j;
+      ov[j] = alpha * acc[i][j] + (r == c ? beta : 0.f);
     }
+    *reinterpret_cast<float4 *>(C + (size_t)r * ldc + col0 + tc * 4) = o;
+  }
 }
 
 // A (FP64) = (m-1)/rho I + the Gram partials, and the row sums of squares;
@@ -242,11 +269,15 @@ int lk_ns_tile() { return NS_TILE; }
 // Workspace (one allocation): A64, c64, w64, rowsq, scale (FP64); Y, Z, T, U
 // (FP32 [mpt][mpt]); r, v (FP32 [mpt]); Xp and the product (FP32 [n_pad][mpt]),
 // xm [n_pad].
+// (the FP32 part starts 256-byte aligned: the matrix products load float4)
+static size_t ns_fp64_bytes(int mpt) {
+  return (((size_t)mpt * mpt * 8 + 3 * (size_t)mpt * 8 + 8) + 255) & ~size_t(255);
+}
+
 size_t lk_ns_workspace_bytes(int mpt, long long n_pad) {
-  const size_t d = (size_t)mpt * mpt * 8 + 3 * (size_t)mpt * 8 + 8;
   const size_t f = 4 * (size_t)mpt * mpt * 4 + 2 * (size_t)mpt * 4 +
                    2 * (size_t)n_pad * mpt * 4 + (size_t)n_pad * 4;
-  return d + f + 1024;
+  return ns_fp64_bytes(mpt) + f + 1024;
 }
 
 cudaError_t lk_launch_ns_global(letkf_ctx *h, const double *gpart, const double *cpart,
@@ -258,7 +289,7 @@ cudaError_t lk_launch_ns_global(letkf_ctx *h, const double *gpart, const double 
   double *A64 = reinterpret_cast<double *>(b);
   double *c64 = A64 + (size_t)mpt * mpt, *w64 = c64 + mpt, *rowsq = w64 + mpt;
   double *scale = rowsq + mpt;
-  float *Y = reinterpret_cast<float *>(scale + 1);
+  float *Y = reinterpret_cast<float *>(b + ns_fp64_bytes(mpt));
   float *Z = Y + (size_t)mpt * mpt, *T = Z + (size_t)mpt * mpt, *U = T + (size_t)mpt * mpt;
   float *rv = U + (size_t)mpt * mpt, *vv = rv + mpt;
   float *Xp = vv + mpt, *Pr = Xp + (size_t)n_pad * mpt, *xm = Pr + (size_t)n_pad * mpt;
