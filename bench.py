@@ -263,8 +263,9 @@ def small_configs_arm(torch, L, K: int = 500, Wm: int = 20):
     one CUDA-graph replay per frame. Returns the 'configs' object of the JSON line."""
     import numpy as np
     from paper_1408_7069_gb300 import synth, workloads as W
+    from dataclasses import replace
     out = {}
-    for w in (W.TOY_8X8, W.TEL_16M):
+    for w in (W.TOY_8X8, W.TEL_16M, replace(W.TEL_16M, row_split=2)):
         rt = np.float32 if w.precision == 0 else np.float64
         inp = synth.make_loop_inputs(w, frames=Wm + K + 1)
         f = L.Letkf.from_workload(w, bank=inp.bank)
@@ -299,13 +300,14 @@ def small_configs_arm(torch, L, K: int = 500, Wm: int = 20):
         g1.record(s)
         torch.cuda.synchronize()
         f.sync()
-        out[w.name] = {"n_pts": int(f.n_pts), "m": w.m, "window": w.window,
-                       "dtype": "f32" if w.precision == 0 else "f64",
-                       # FP64 handles run one CTA per node: no tile shape applies
-                       "tile_shape": tune.get("tiles") if w.precision == 0 else None,
-                       "frames_per_s": K / (sum(ms) / 1e3), "p50_us": 1e3 * percentile(ms, 50),
-                       "p99_us": 1e3 * percentile(ms, 99),
-                       "graph_frames_per_s": K / (g0.elapsed_time(g1) / 1e3)}
+        key = w.name if w.row_split == 1 else f"{w.name}-rowsplit{w.row_split}"
+        out[key] = {"n_pts": int(f.n_pts), "m": w.m, "window": w.window,
+                    "dtype": "f32" if w.precision == 0 else "f64", "row_split": w.row_split,
+                    # FP64 handles run one CTA per node: no tile shape applies
+                    "tile_shape": tune.get("tiles") if w.precision == 0 else None,
+                    "frames_per_s": K / (sum(ms) / 1e3), "p50_us": 1e3 * percentile(ms, 50),
+                    "p99_us": 1e3 * percentile(ms, 99),
+                    "graph_frames_per_s": K / (g0.elapsed_time(g1) / 1e3)}
         f.close()
     return out
 

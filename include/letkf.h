@@ -330,6 +330,22 @@ letkf_status letkf_set_tile_shape(letkf_t h, int32_t width_class, int32_t shape)
 letkf_status letkf_autotune(letkf_t h, const void *y_dev, int32_t reps, int32_t *shapes_out,
                             float *us_out);
 
+/* Row split of the FP32 per-node analysis (Section 4.2's eigensolve and
+ * transform), per width class: split = 1 (the default) gives each lane two
+ * whole columns of the node's matrix; split = 2 gives each lane the rows of
+ * one half of two columns, so a node takes twice the lanes (2 nodes per warp
+ * for m <= 16, 1 for m <= 32), every dot product of the one-sided Jacobi adds
+ * its partner lane's half, and a rotation round's dependent chain is about
+ * half as long. It pays on systems whose nodes fill few warps per SM (a few
+ * thousand nodes or fewer on 152 SMs) and costs issue slots on large ones.
+ * The results differ from split 1 by rounding only (sums in another order);
+ * for fixed settings they are bitwise reproducible. Width classes 0 and 1 of
+ * FP32 per-node handles only, with the class's current tile shape holding
+ * whole warps of nodes in the split form; LETKF_ERR_ARG otherwise (FP64 and
+ * domain handles, class 2, split not 1 or 2). Synchronises; drops the cached
+ * CUDA graphs. letkf_autotune keeps the split and times the shapes it allows. */
+letkf_status letkf_set_row_split(letkf_t h, int32_t width_class, int32_t split);
+
 /* Synchronise the stream, return and clear the first error recorded on the
  * device since the last call (LETKF_OK if none). */
 letkf_status letkf_sync(letkf_t h);
@@ -400,6 +416,14 @@ letkf_status letkf_fma_peaks(double *out);
  * apply (Section 4.2's steps), and the number of warps. Synchronises the
  * device and resets the counts. The paper has no counterpart. */
 letkf_status letkf_phase_clocks(uint64_t *out);
+
+/* The same for the reverse mode's node kernel (letkf_grad): SM cycles summed
+ * over its nodes since the last call, out: host uint64_t[6] = window staging,
+ * Gram and the start of the eigensolve (B = A U0, or the FP64 warm basis),
+ * Jacobi sweeps, the adjoint of the transform up to A_bar, the window slopes'
+ * adjoints, and the number of nodes. LETKF_ERR_STATE without phase clocks.
+ * Synchronises the device and resets the counts. */
+letkf_status letkf_adjoint_phase_clocks(uint64_t *out);
 
 /* Text of the last error on this handle (or of the last failed create when h is NULL). */
 const char *letkf_last_error(letkf_t h);

@@ -69,6 +69,17 @@ struct LkAdjWork {
   const void *graph_y = nullptr, *graph_truth = nullptr;
 };
 
+// Phase clocks (a library built with -DLK_PHASE_CLOCKS only): lane 0 of every
+// node adds the SM cycles of each phase of adjoint_node_kernel: [0] window
+// staging, [1] Gram and the start of the eigensolve, [2] Jacobi sweeps,
+// [3] adjoint of the transform up to A_bar, [4] window slopes, [5] nodes.
+#ifdef LK_PHASE_CLOCKS
+__device__ unsigned long long g_lk_adj_clocks[6];
+#define LK_ADJ_STAMP(t) const long long t = clock64()
+#else
+#define LK_ADJ_STAMP(t)
+#endif
+
 namespace {
 
 // One warp per CTA: the node kernels are bound by their SM's FP64 and dependency
@@ -122,6 +133,7 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
                         float kappa_thr, int2 *__restrict__ queue, int *__restrict__ queue_len,
                         T tol, AdjArgs a) {
   constexpr bool kWarm = std::is_same<T, float>::value;
+  LK_ADJ_STAMP(ph0);
   extern __shared__ __align__(16) unsigned char smem[];
   const LkInst &I = insts[0];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -175,8 +187,12 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
     dtap[e] = a.dtap[e];
   }
   __syncwarp();
+  LK_ADJ_STAMP(ph1);
 
   // ---- A, b and the eigendecomposition A = V diag(lam) V^T ----
+#ifdef LK_PHASE_CLOCKS
+  long long ph2 = 0;
+#endif
   T b[MP], diag, cd;
   gram<MP, S, T>(win, dwin, w, tap, w, m, T(I.alpha), b, diag, cd);
   T v[MP];
@@ -205,11 +221,15 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
       b[i] = s;
     }
     __syncwarp();
+    LK_ADJ_STAMP(ph2w);
     // U0 is this frame's converged basis, so the first sweep's rotations are at
     // rounding level: stop after the first sweep whose cosines all stay below
     // 1e-3 (one sweep, leaving pairs within about 1e-6) instead of running a
     // second sweep only to find no rotation
     jacobi<MP, T, false>(b, v, tol, a.max_sweeps, a.counters, T(1e-3));
+#ifdef LK_PHASE_CLOCKS
+    ph2 = ph2w;
+#endif
   } else {
     if (U0) {
       warm_basis<MP, T>(b, v, U0 + (size_t)pid * MP * MP, Ms, Vs);
@@ -217,8 +237,12 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
 #pragma unroll
       for (int k = 0; k < MP; ++k) v[k] = (k == lane) ? T(1) : T(0);
     }
+#ifdef LK_PHASE_CLOCKS
+    ph2 = clock64();
+#endif
     jacobi<MP, T, true>(b, v, tol, a.max_sweeps, a.counters, U0 ? T(LK_WARM_STOP64) : T(0));
   }
+  LK_ADJ_STAMP(ph3);
   const T nrm = dot4<MP, T>(b, b);
   const T lam = (col && nrm > T(0)) ? sqrt(nrm) : T(1);   // |A v_j| = lambda_j
   if constexpr (kWarm) {
@@ -356,6 +380,7 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
     }
   }
   const double alpha_bar = double(lk_warp_sum(dg));   // d/d((m-1)/rho) = tr(A_bar)
+  LK_ADJ_STAMP(ph4);
 
   // ---- window slopes: y_bar_j = 2 c_j A_bar y_j + c_j d_j b_bar, d_bar_j, c_bar_j ----
   // sum_j c_bar_j c_j and sum_j c_bar_j dc_j/dL, whose terms cancel strongly
@@ -402,6 +427,18 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
     a.theta[(size_t)pid * 3 + 1] = -gs2 / a.sigma2;
     a.theta[(size_t)pid * 3 + 2] = gL;
   }
+#ifdef LK_PHASE_CLOCKS
+  __syncwarp();
+  LK_ADJ_STAMP(ph5);
+  if (lane == 0) {
+    atomicAdd(&g_lk_adj_clocks[0], (unsigned long long)(ph1 - ph0));
+    atomicAdd(&g_lk_adj_clocks[1], (unsigned long long)(ph2 - ph1));
+    atomicAdd(&g_lk_adj_clocks[2], (unsigned long long)(ph3 - ph2));
+    atomicAdd(&g_lk_adj_clocks[3], (unsigned long long)(ph4 - ph3));
+    atomicAdd(&g_lk_adj_clocks[4], (unsigned long long)(ph5 - ph4));
+    atomicAdd(&g_lk_adj_clocks[5], 1ull);
+  }
+#endif
 }
 
 // Warp per valid subaperture (s, t): sums the slope adjoints the nodes whose
@@ -922,4 +959,21 @@ extern "C" letkf_status letkf_grad(letkf_t h, int32_t frames, const void *y_seq_
   if (grad_out)
     for (int c = 0; c < 3; ++c) grad_out[c] = acc[c];
   return LETKF_OK;
+}
+
+extern "C" letkf_status letkf_adjoint_phase_clocks(uint64_t *out) {
+#ifdef LK_PHASE_CLOCKS
+  if (!out) return LETKF_ERR_ARG;
+  unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(v, g_lk_adj_clocks, sizeof(v));
+  const unsigned long long z[6] = {0, 0, 0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_lk_adj_clocks, z, sizeof(z));
+  if (e != cudaSuccess) return LETKF_ERR_CUDA;
+  for (int i = 0; i < 6; ++i) out[i] = v[i];
+  return LETKF_OK;
+#else
+  (void)out;
+  return LETKF_ERR_STATE;
+#endif
 }

@@ -1012,12 +1012,27 @@ letkf_status letkf_set_tile_shape(letkf_t h, int32_t width_class, int32_t shape)
     return fail(h, LETKF_ERR_ARG, "width class or tile shape out of range");
   if (!lk_shape_ok(h, width_class, shape))
     return fail(h, LETKF_ERR_ARG,
-                "FP32 tiles hold whole warps of nodes (4 per warp for m <= 16, 2 for m <= 32) "
-                "and ensembles of 33..64 members at most 8 nodes");
+                "FP32 tiles hold whole warps of nodes (4 per warp for m <= 16, 2 for m <= 32; "
+                "2 and 1 with the row split) and ensembles of 33..64 members at most 8 nodes");
   DeviceGuard dg(h->device);
   LK_CUDA(h, cudaStreamSynchronize(h->stream));
   h->tile_shape[width_class] = shape;
   return rebuild_tiles(h, width_class);
+}
+
+letkf_status letkf_set_row_split(letkf_t h, int32_t width_class, int32_t split) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (width_class < 0 || width_class > 2 || (split != 1 && split != 2))
+    return fail(h, LETKF_ERR_ARG, "width class out of range or split not 1 or 2");
+  if (h->dom || !lk_shape_split_ok(h, width_class, h->tile_shape[width_class], split))
+    return fail(h, LETKF_ERR_ARG,
+                "the row split needs an FP32 per-node handle, width class 0 or 1, and a tile "
+                "of whole warps (an even node count in class 0)");
+  DeviceGuard dg(h->device);
+  LK_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->row_split[width_class] != split) drop_graphs(h);   // they hold the other kernel
+  h->row_split[width_class] = split;
+  return LETKF_OK;
 }
 
 letkf_status letkf_autotune(letkf_t h, const void *y_dev, int32_t reps, int32_t *shapes_out,

@@ -108,6 +108,7 @@ struct letkf_ctx {
   int n_tiles[3] = {0, 0, 0};
   int tile_shape[3] = {0, 0, 0};    // index into the compiled tile shapes, per class
   int tile_split[3] = {0, 0, 0};    // class 2: leading tiles of MP = 64 instances (MP = 48 after)
+  int row_split[3] = {1, 1, 1};     // 2: each column's rows on two lanes (classes 0 and 1, FP32)
   std::vector<LkTile> tiles_host[3];
 
   // device buffers (single allocations sliced per instance)
@@ -203,6 +204,7 @@ cudaError_t lk_setup_node64w();
 // handles need whole warps of nodes and, in class 2 (one node per warp), at
 // most 8 nodes per tile. (FP64 handles take any shape, which they ignore.)
 bool lk_shape_ok(const letkf_ctx *h, int cls, int shape);
+bool lk_shape_split_ok(const letkf_ctx *h, int cls, int shape, int split);
 int lk_num_tile_shapes();
 void lk_tile_shape(int s, int *ti, int *tj);
 int lk_width_class(int m);          // 0: m <= 16, 1: m <= 32, 2: m <= 64

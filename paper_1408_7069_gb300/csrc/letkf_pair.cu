@@ -107,13 +107,23 @@ __device__ __forceinline__ float dotk(const float2 (&a)[K2], const float2 (&b)[K
   return s[0].x + s[0].y;
 }
 
+// Adds the partner lane's partial sum (XO > 0: the columns' rows are split
+// between lanes XO apart). Float addition commutes, so both lanes get the
+// same bits.
+template <int XO>
+__device__ __forceinline__ float combine(float v) {
+  if constexpr (XO > 0) v += __shfl_xor_sync(FULL, v, XO);
+  return v;
+}
+
 // One round on this lane's pair (P, Q) with tracked squared norms. `idle`:
-// the end slot of an odd round, which swaps instead of rotating. Returns
-// whether the pair was rotated.
-template <int K2>
+// the end slot of an odd round, which swaps instead of rotating. XO > 0: the
+// lane holds half of the pair's rows, the other half is on lane ^ XO, which
+// computes the same rotation. Returns whether the pair was rotated.
+template <int K2, int XO = 0>
 __device__ __forceinline__ int pair_round(float2 (&P)[K2], float2 (&Q)[K2], float &nP, float &nQ,
                                           float tol2, float stop2, bool idle, bool frozen) {
-  const float dot = dotk<K2>(P, Q);
+  const float dot = combine<XO>(dotk<K2>(P, Q));
   // The rotation that makes the pair orthogonal, |theta| <= pi/4, from
   // x = |q|^2 - |p|^2, y = 2 p.q and h = sqrt(x^2 + y^2): cos 2theta = |x|/h,
   // sin 2theta = sign(x) y / h, c = sqrt((1 + cos 2theta)/2) >= 1/sqrt(2),
@@ -515,6 +525,301 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
 #endif
 }
 
+// ---------------------------------------------------------------------------
+// Row-split form (MP = 16 and 32): each column's rows are split between two
+// lanes, so a node takes 2 MP/2 = MP lanes: lane (h, li) of the node, h = 0, 1
+// the row half and li = 0 .. MP/2 - 1 the column pair, holds rows
+// [MP h / 2, MP (h + 1) / 2) of columns 2li and 2li + 1. The odd-even network
+// runs on each half as on the whole columns; every dot product adds the
+// partner half's partial sum (lane ^ MP/2), so both halves compute the same
+// rotation. A round's chain (dot product, rotation, column shuffle) is half as
+// long and a system has twice as many warps: this pays where the nodes fill
+// few warps per SM (latency-bound systems), not where the SMs are full.
+template <int MP>
+struct SplitCfg {
+  static_assert(MP == 16 || MP == 32, "row split for MP = 16 and 32");
+  static constexpr int LPN = MP / 2;      // column-pair lanes per half
+  static constexpr int GL = MP;           // lanes of a node
+  static constexpr int NPW = 32 / GL;     // nodes per warp
+  static constexpr int KH = MP / 4;       // float2 per column and lane
+};
+
+template <int MP, int TI, int TJ>
+struct SplitLaunch {
+  static constexpr int threads = TI * TJ * SplitCfg<MP>::GL;
+  static constexpr int min_ctas = 65536 / (threads * 128) > 0 ? 65536 / (threads * 128) : 1;
+};
+
+template <int MP, int TI, int TJ>
+__global__ void __launch_bounds__(SplitLaunch<MP, TI, TJ>::threads, SplitLaunch<MP, TI, TJ>::min_ctas)
+    analysis_split_kernel(const LkInst *__restrict__ insts, const LkTile *__restrict__ tiles,
+                          float *__restrict__ mean, float *__restrict__ spread, float tol,
+                          float stop, int max_sweeps, float kappa_thr, int *__restrict__ counters,
+                          int *__restrict__ queue, int2 *__restrict__ worklist, int keep_basis) {
+  lk_pdl_wait();
+  LK_PHASE_STAMP(ph0);
+  using C = PairCfg<MP>;
+  using S = SplitCfg<MP>;
+  constexpr int KH = S::KH, LPN = S::LPN, GL = S::GL;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const LkTile tl = tiles[blockIdx.x];
+  const LkInst &I = insts[tl.inst];
+  const int w = I.w, m = I.m;
+  const PairLayout Ly = pair_layout<MP, TI, TJ>(w);
+  const int HJ = TJ + w - 1;
+  float *halo = reinterpret_cast<float *>(smem);
+  float *dh = reinterpret_cast<float *>(smem + Ly.dh);
+  float *tap = reinterpret_cast<float *>(smem + Ly.tap);
+  stage_pair_tile<MP, TI, TJ>(I, tl.i0, tl.j0, halo, dh, tap);
+  __syncthreads();
+  LK_PHASE_STAMP(ph1);
+
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / GL, gl = lane - grp * GL;   // node of the warp, lane within the node
+  const int hh = gl / LPN, li = gl - hh * LPN;       // row half, column pair
+  const int node = (threadIdx.x >> 5) * S::NPW + grp;
+  const int ti = node / TJ, tj = node - (node / TJ) * TJ;
+  const int gi = tl.i0 + ti, gj = tl.j0 + tj;
+  int pid = -1;
+  if (gi <= I.nsub && gj <= I.nsub) pid = I.pid_map[gi * (I.nsub + 1) + gj];
+  float *scr = reinterpret_cast<float *>(smem + Ly.scr) + (size_t)node * C::NODE_SCR;
+
+  // ---- Gram: this half's rows of columns 2li and 2li+1 of A, C d, diagonal of G ----
+  float2 P[KH], Q[KH];
+#pragma unroll
+  for (int k = 0; k < KH; ++k) {
+    P[k] = f2(0.f);
+    Q[k] = f2(0.f);
+  }
+  float diag = 0.f, cd0 = 0.f, cd1 = 0.f;
+  const float *hwin = halo + (size_t)(ti * HJ + tj) * C::CELLF;
+  const float *dwin = dh + (size_t)(ti * HJ + tj) * 2;
+  for (int ds = 0; ds < w; ++ds) {
+    for (int dt = 0; dt < w; ++dt) {
+      const int cell = ds * HJ + dt;
+      const float tw = tap[ds * w + dt];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float *yv = hwin + (size_t)cell * C::CELLF + c * MP;
+        const float2 yl = reinterpret_cast<const float2 *>(yv)[li];
+        const float cy0 = tw * yl.x, cy1 = tw * yl.y;
+        diag = fmaf(cy0, yl.x, fmaf(cy1, yl.y, diag));
+        const float dj = dwin[cell * 2 + c];
+        cd0 = fmaf(cy0, dj, cd0);
+        cd1 = fmaf(cy1, dj, cd1);
+        const float2 c0 = f2(cy0), c1 = f2(cy1);
+        const float4 *y4p = reinterpret_cast<const float4 *>(yv) + hh * (KH / 2);
+#pragma unroll
+        for (int k = 0; k < KH / 2; ++k) {
+          const float4 y4 = y4p[k];
+          const float2 ya = make_float2(y4.x, y4.y), yb = make_float2(y4.z, y4.w);
+          P[2 * k] = fma2(c0, ya, P[2 * k]);
+          P[2 * k + 1] = fma2(c0, yb, P[2 * k + 1]);
+          Q[2 * k] = fma2(c1, ya, Q[2 * k]);
+          Q[2 * k + 1] = fma2(c1, yb, Q[2 * k + 1]);
+        }
+      }
+    }
+  }
+  const float alpha = float(I.alpha);
+  const bool active = pid >= 0;
+  bool queued = false;
+  if (queue) {
+    const float trg = group_sum<LPN>(diag);          // the same in both halves
+    if (active && 1.f + trg / alpha > kappa_thr) {
+      if (gl == 0) {
+        worklist[atomicAdd(queue, 1)] = make_int2(tl.inst, pid);
+        atomicAdd(&counters[1], 1);
+      }
+      queued = true;
+    }
+  }
+  const float dP = (2 * li < m) ? alpha : 1.f, dQ = (2 * li + 1 < m) ? alpha : 1.f;
+#pragma unroll
+  for (int k = 0; k < KH; ++k) {
+    if (!active) {
+      P[k] = f2(0.f);
+      Q[k] = f2(0.f);
+    }
+    if (hh * KH + k == li) {
+      P[k].x = active ? P[k].x + dP : 1.f;
+      Q[k].y = active ? Q[k].y + dQ : 1.f;
+    }
+  }
+
+  // ---- Jacobi sweeps ----
+  LK_PHASE_STAMP(ph2);
+  const float tol2 = tol * tol, stop2 = stop * stop;
+  const int base = grp * GL + hh * LPN;
+  const int up = base + (li + 1) % LPN;
+  const int dn = base + (li + LPN - 1) % LPN;
+  bool conv = !active;
+  int sweeps = 0;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (__all_sync(FULL, conv)) break;
+    float nP = combine<LPN>(dotk<KH>(P, P)), nQ = combine<LPN>(dotk<KH>(Q, Q));
+    int rotated = 0;
+    const int su = conv ? lane : up, sd = conv ? lane : dn;
+#pragma unroll 2
+    for (int r = 0; r < MP / 2; ++r) {
+      rotated |= pair_round<KH, LPN>(P, Q, nP, nQ, tol2, stop2, false, conv);
+      shfl_cols<KH>(Q, su);
+      nQ = __shfl_sync(FULL, nQ, su);
+      rotated |= pair_round<KH, LPN>(P, Q, nP, nQ, tol2, stop2, li == LPN - 1, conv);
+      shfl_cols<KH>(P, sd);
+      nP = __shfl_sync(FULL, nP, sd);
+    }
+    const unsigned big = __ballot_sync(FULL, rotated & 2);
+    const unsigned gmask = (GL == 32) ? 0xffffffffu : (((1u << GL) - 1u) << (grp * GL));
+    if (!conv) {
+      sweeps = sweep + 1;
+      if ((big & gmask) == 0u) conv = true;
+    }
+  }
+  if (active && gl == 0) {
+    atomicMax(&counters[2], sweeps);
+    atomicAdd(&counters[3], sweeps);
+    if (!conv) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
+  }
+
+  // ---- eigenpairs: lambda = |b|, v = b / lambda ----
+  LK_PHASE_STAMP(ph3);
+  const float lP = sqrtf(combine<LPN>(dotk<KH>(P, P)));
+  const float lQ = sqrtf(combine<LPN>(dotk<KH>(Q, Q)));
+  {
+    const float iP = 1.f / lP, iQ = 1.f / lQ;
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      P[k] = mul2(f2(iP), P[k]);
+      Q[k] = mul2(f2(iQ), Q[k]);
+    }
+  }
+  {
+    // finite on both halves of the two columns: the shuffle runs on every lane
+    // (two nodes share a warp when MP = 16, and only one of them may store)
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < KH; ++k)
+      ok = ok && isfinite(P[k].x) && isfinite(P[k].y) && isfinite(Q[k].x) && isfinite(Q[k].y);
+    ok = __shfl_xor_sync(FULL, (int)ok, LPN) && ok;
+    if ((keep_basis || queued) && active) {
+      float *U = I.basis + (size_t)pid * MP * MP;
+#pragma unroll
+      for (int k = 0; k < KH; ++k) {
+        const int r = hh * KH + k;
+        const float2 r0 = ok ? make_float2(P[k].x, Q[k].x) : make_float2(r == li ? 1.f : 0.f, 0.f);
+        const float2 r1 = ok ? make_float2(P[k].y, Q[k].y) : make_float2(0.f, r == li ? 1.f : 0.f);
+        reinterpret_cast<float2 *>(U + (2 * r) * MP)[li] = r0;
+        reinterpret_cast<float2 *>(U + (2 * r + 1) * MP)[li] = r1;
+      }
+    }
+  }
+
+  // ---- transform and apply (Section 4.2): Xa_r = xbar_r + X'_r wbar + X'_r W ----
+  float *vcd = scr;
+  float *vx0 = vcd + MP;
+  float *vx1 = vx0 + MP;
+  const bool wr = active && !queued;
+  float *xrow = wr ? static_cast<float *>(I.X) + (size_t)pid * 2 * m : nullptr;
+  const bool in0 = 2 * li < m, in1 = 2 * li + 1 < m;
+  const float x00 = (wr && in0) ? xrow[2 * li] : 0.f;
+  const float x01 = (wr && in1) ? xrow[2 * li + 1] : 0.f;
+  const float x10 = (wr && in0) ? xrow[m + 2 * li] : 0.f;
+  const float x11 = (wr && in1) ? xrow[m + 2 * li + 1] : 0.f;
+  const float inv_m = 1.f / float(m);
+  const float xb0 = group_sum<LPN>(x00 + x01) * inv_m;
+  const float xb1 = group_sum<LPN>(x10 + x11) * inv_m;
+  if (hh == 0) {
+    reinterpret_cast<float2 *>(vcd)[li] = make_float2(cd0, cd1);
+    reinterpret_cast<float2 *>(vx0)[li] = make_float2(in0 ? x00 - xb0 : 0.f, in1 ? x01 - xb0 : 0.f);
+    reinterpret_cast<float2 *>(vx1)[li] = make_float2(in0 ? x10 - xb1 : 0.f, in1 ? x11 - xb1 : 0.f);
+  }
+  __syncwarp();
+  float2 uP = f2(0.f), uQ = f2(0.f), a0P = f2(0.f), a0Q = f2(0.f), a1P = f2(0.f), a1Q = f2(0.f);
+#pragma unroll
+  for (int k = 0; k < KH; ++k) {
+    const int r = hh * KH + k;
+    const float2 cdv = reinterpret_cast<const float2 *>(vcd)[r];
+    const float2 x0v = reinterpret_cast<const float2 *>(vx0)[r];
+    const float2 x1v = reinterpret_cast<const float2 *>(vx1)[r];
+    uP = fma2(P[k], cdv, uP);
+    uQ = fma2(Q[k], cdv, uQ);
+    a0P = fma2(P[k], x0v, a0P);
+    a0Q = fma2(Q[k], x0v, a0Q);
+    a1P = fma2(P[k], x1v, a1P);
+    a1Q = fma2(Q[k], x1v, a1Q);
+  }
+  const float gP0 = combine<LPN>(a0P.x + a0P.y), gQ0 = combine<LPN>(a0Q.x + a0Q.y);
+  const float gP1 = combine<LPN>(a1P.x + a1P.y), gQ1 = combine<LPN>(a1Q.x + a1Q.y);
+  const float zP = combine<LPN>(uP.x + uP.y) / lP, zQ = combine<LPN>(uQ.x + uQ.y) / lQ;
+  const float w0 = group_sum<LPN>(gP0 * zP + gQ0 * zQ);    // X'_0 wbar
+  const float w1 = group_sum<LPN>(gP1 * zP + gQ1 * zQ);    // X'_1 wbar
+  const float rP = sqrtf(float(m - 1) / lP), rQ = sqrtf(float(m - 1) / lQ);
+  // X'_r W: this lane's terms on its half's rows, summed over the half's LPN
+  // lanes; lane li < KH of half h ends with row pair h KH + li
+  float2 v0[KH], v1[KH];
+  {
+    const float2 hP0 = f2(gP0 * rP), hQ0 = f2(gQ0 * rQ), hP1 = f2(gP1 * rP), hQ1 = f2(gQ1 * rQ);
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      v0[k] = fma2(hP0, P[k], mul2(hQ0, Q[k]));
+      v1[k] = fma2(hP1, P[k], mul2(hQ1, Q[k]));
+    }
+  }
+  float2 q0 = reduce_scatter<KH>(v0, li), q1 = reduce_scatter<KH>(v1, li);
+  q0.x += __shfl_xor_sync(FULL, q0.x, KH);
+  q0.y += __shfl_xor_sync(FULL, q0.y, KH);
+  q1.x += __shfl_xor_sync(FULL, q1.x, KH);
+  q1.y += __shfl_xor_sync(FULL, q1.y, KH);
+  const int r0 = hh * KH + (li & (KH - 1));
+  const bool own = li < KH;
+  const bool o0 = own && 2 * r0 < m, o1 = own && 2 * r0 + 1 < m;
+  const float xa00 = xb0 + w0 + q0.x, xa01 = xb0 + w0 + q0.y;
+  const float xa10 = xb1 + w1 + q1.x, xa11 = xb1 + w1 + q1.y;
+  if (wr) {
+    if (o0) {
+      xrow[2 * r0] = xa00;
+      xrow[m + 2 * r0] = xa10;
+    }
+    if (o1) {
+      xrow[2 * r0 + 1] = xa01;
+      xrow[m + 2 * r0 + 1] = xa11;
+    }
+  }
+  const float e00 = o0 ? xa00 : 0.f, e01 = o1 ? xa01 : 0.f;
+  const float e10 = o0 ? xa10 : 0.f, e11 = o1 ? xa11 : 0.f;
+  const float mu0 = group_sum<GL>(e00 + e01) * inv_m;
+  const float mu1 = group_sum<GL>(e10 + e11) * inv_m;
+  const float d00 = o0 ? xa00 - mu0 : 0.f, d01 = o1 ? xa01 - mu0 : 0.f;
+  const float d10 = o0 ? xa10 - mu1 : 0.f, d11 = o1 ? xa11 - mu1 : 0.f;
+  const float sp0 = sqrtf(group_sum<GL>(d00 * d00 + d01 * d01) / float(m - 1));
+  const float sp1 = sqrtf(group_sum<GL>(d10 * d10 + d11 * d11) / float(m - 1));
+  if (wr && gl == 0) {
+    const long long row = I.node_off + pid;
+    if (mean) {
+      mean[2 * row] = mu0;
+      mean[2 * row + 1] = mu1;
+    }
+    if (spread) {
+      spread[2 * row] = sp0;
+      spread[2 * row + 1] = sp1;
+    }
+    if (!isfinite(mu0) || !isfinite(mu1) || !isfinite(sp0) || !isfinite(sp1))
+      atomicOr(&counters[0], LK_BIT_NONFINITE);
+  }
+#ifdef LK_PHASE_CLOCKS
+  __syncwarp();
+  LK_PHASE_STAMP(ph4);
+  if (lane == 0) {
+    atomicAdd(&g_lk_phase_clocks[0], (unsigned long long)(ph1 - ph0));
+    atomicAdd(&g_lk_phase_clocks[1], (unsigned long long)(ph2 - ph1));
+    atomicAdd(&g_lk_phase_clocks[2], (unsigned long long)(ph3 - ph2));
+    atomicAdd(&g_lk_phase_clocks[3], (unsigned long long)(ph4 - ph3));
+    atomicAdd(&g_lk_phase_clocks[4], 1ull);
+  }
+#endif
+}
+
 // A tile fills whole warps (its node count is a multiple of the nodes per
 // warp), and wide problems (one node per warp) take tiles of at most 8 nodes:
 // a 16-warp CTA would leave fewer registers per thread than the two columns need.
@@ -522,12 +827,18 @@ template <int MP, int TI, int TJ>
 constexpr bool shape_ok() {
   return (TI * TJ) % PairCfg<MP>::NPW == 0 && (PairCfg<MP>::NPW > 1 || TI * TJ <= 8);
 }
-
+// The row-split form: whole warps of nodes (two per warp for MP = 16).
 template <int MP, int TI, int TJ>
+constexpr bool split_shape_ok() {
+  if constexpr (MP > 32) return false;
+  else return (TI * TJ) % SplitCfg<MP>::NPW == 0;
+}
+
+template <int MP, int TI, int TJ, bool SPLIT>
 cudaError_t launch_shape(letkf_ctx *h, const LkTile *tiles, int n_tiles, float *mean,
                          float *spread, float kthr, int *queue, int2 *worklist) {
   if (n_tiles == 0) return cudaSuccess;
-  if constexpr (!shape_ok<MP, TI, TJ>()) {
+  if constexpr (SPLIT ? !split_shape_ok<MP, TI, TJ>() : !shape_ok<MP, TI, TJ>()) {
     return cudaErrorInvalidConfiguration;
   } else {
   size_t need = 0;
@@ -536,10 +847,16 @@ cudaError_t launch_shape(letkf_ctx *h, const LkTile *tiles, int n_tiles, float *
       const size_t b = pair_layout<MP, TI, TJ>(I.w).total;
       need = b > need ? b : need;
     }
-  return lk_launch_pdl(analysis_pair_kernel<MP, TI, TJ>, n_tiles,
-                       TI * TJ * 32 / PairCfg<MP>::NPW, need, h->stream, h->d_inst, tiles, mean,
-                       spread, (float)h->tol32, (float)h->stop32, h->max_sweeps, kthr, h->counters,
-                       queue, worklist, h->keep_basis);
+  if constexpr (SPLIT)
+    return lk_launch_pdl(analysis_split_kernel<MP, TI, TJ>, n_tiles,
+                         SplitLaunch<MP, TI, TJ>::threads, need, h->stream, h->d_inst, tiles, mean,
+                         spread, (float)h->tol32, (float)h->stop32, h->max_sweeps, kthr,
+                         h->counters, queue, worklist, h->keep_basis);
+  else
+    return lk_launch_pdl(analysis_pair_kernel<MP, TI, TJ>, n_tiles,
+                         TI * TJ * 32 / PairCfg<MP>::NPW, need, h->stream, h->d_inst, tiles, mean,
+                         spread, (float)h->tol32, (float)h->stop32, h->max_sweeps, kthr,
+                         h->counters, queue, worklist, h->keep_basis);
   }
 }
 
@@ -549,10 +866,14 @@ cudaError_t launch_mp(letkf_ctx *h, int cls, const LkTile *tiles, int n_tiles, f
   const float kthr = h->fp64_kappa > 0 ? (float)h->fp64_kappa : 0.f;
   int *queue = kthr > 0.f ? h->counters + 4 + cls : nullptr;
   int2 *wl = h->worklist + (size_t)cls * h->n_pts_total;
+  const bool split = MP <= 32 && h->row_split[cls] == 2;
   switch (h->tile_shape[cls]) {
-#define LK_CASE(id, ti, tj) \
-  case id:                  \
-    return launch_shape<MP, ti, tj>(h, tiles, n_tiles, mean, spread, kthr, queue, wl);
+#define LK_CASE(id, ti, tj)                                                                   \
+  case id:                                                                                    \
+    return split ? launch_shape<MP, ti, tj, true>(h, tiles, n_tiles, mean, spread, kthr, queue, \
+                                                  wl)                                         \
+                 : launch_shape<MP, ti, tj, false>(h, tiles, n_tiles, mean, spread, kthr, queue, \
+                                                   wl);
     LK_FOR_SHAPES(LK_CASE)
 #undef LK_CASE
   }
@@ -561,13 +882,16 @@ cudaError_t launch_mp(letkf_ctx *h, int cls, const LkTile *tiles, int n_tiles, f
 
 template <int MP, int TI, int TJ>
 cudaError_t set_shape_smem(int w) {
-  if constexpr (!shape_ok<MP, TI, TJ>()) {
-    return cudaSuccess;
-  } else {
-    return cudaFuncSetAttribute(analysis_pair_kernel<MP, TI, TJ>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pair_layout<MP, TI, TJ>(w).total);
-  }
+  const int bytes = (int)pair_layout<MP, TI, TJ>(w).total;
+  cudaError_t e = cudaSuccess;
+  if constexpr (shape_ok<MP, TI, TJ>())
+    e = cudaFuncSetAttribute(analysis_pair_kernel<MP, TI, TJ>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if constexpr (split_shape_ok<MP, TI, TJ>())
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(analysis_split_kernel<MP, TI, TJ>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
 }
 
 template <int MP>
@@ -600,9 +924,20 @@ cudaError_t lk_launch_pair(letkf_ctx *h, int cls, void *mean, void *spread) {
 }
 
 bool lk_shape_ok(const letkf_ctx *h, int cls, int shape) {
+  return lk_shape_split_ok(h, cls, shape, h->row_split[cls]);
+}
+
+bool lk_shape_split_ok(const letkf_ctx *h, int cls, int shape, int split) {
   int ti, tj;
   lk_tile_shape(shape, &ti, &tj);
-  if (h->precision == 1) return true;     // FP64 handles analyse one node per CTA
+  if (h->precision == 1) return split == 1;   // FP64 handles analyse one node per CTA
+  if (split == 2) {
+    switch (cls) {
+      case 0: return (ti * tj) % SplitCfg<16>::NPW == 0;
+      case 1: return (ti * tj) % SplitCfg<32>::NPW == 0;
+      default: return false;
+    }
+  }
   switch (cls) {
     case 0: return (ti * tj) % PairCfg<16>::NPW == 0;
     case 1: return (ti * tj) % PairCfg<32>::NPW == 0;

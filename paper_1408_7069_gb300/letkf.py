@@ -65,11 +65,13 @@ _SIGS = {
     "letkf_noalloc_status": [c_void_p, POINTER(c_int32)],
     "letkf_fma_peaks": [c_void_p],
     "letkf_phase_clocks": [c_void_p],
+    "letkf_adjoint_phase_clocks": [c_void_p],
     "letkf_create_batch": [POINTER(letkf_config), c_int32, c_void_p, POINTER(c_void_p)],
     "letkf_query_instance": [c_void_p, c_int32, POINTER(c_int32), POINTER(c_int32),
                              POINTER(c_int32), POINTER(c_int32)],
     "letkf_tile_shape": [c_int32, POINTER(c_int32), POINTER(c_int32)],
     "letkf_set_tile_shape": [c_void_p, c_int32, c_int32],
+    "letkf_set_row_split": [c_void_p, c_int32, c_int32],
     "letkf_autotune": [c_void_p, c_void_p, c_int32, POINTER(c_int32), POINTER(ctypes.c_float)],
     "letkf_set_params": [c_void_p, c_int32, c_double, c_double, c_double],
     "letkf_set_frame": [c_void_p, ctypes.c_int64],
@@ -162,6 +164,10 @@ def tile_shapes() -> list:
 
 def letkf_set_tile_shape(h, width_class: int, shape: int) -> None:
     _check(lib().letkf_set_tile_shape(h, width_class, shape), h)
+
+
+def letkf_set_row_split(h, width_class: int, split: int) -> None:
+    _check(lib().letkf_set_row_split(h, width_class, split), h)
 
 
 def letkf_autotune(h, y, reps: int = 3):
@@ -298,6 +304,18 @@ def letkf_phase_clocks():
     return list(out)
 
 
+def letkf_adjoint_phase_clocks():
+    """Cycles of the reverse-mode node kernel's phases (staging, Gram and
+    start, Jacobi, transform adjoint, window slopes) and its node count since
+    the last call, or None without phase clocks."""
+    out = (ctypes.c_uint64 * 6)()
+    st = lib().letkf_adjoint_phase_clocks(out)
+    if st == 6:
+        return None
+    _check(st, None)
+    return list(out)
+
+
 def letkf_last_error(h=None) -> str:
     msg = lib().letkf_last_error(h)
     return msg.decode() if msg else ""
@@ -373,7 +391,14 @@ class Letkf:
 
     @classmethod
     def from_workload(cls, w, bank=None, stream=None, **kw):
-        return cls(stream=stream, _configs=[workload_config(w, bank, **kw)])
+        f = cls(stream=stream, _configs=[workload_config(w, bank, **kw)])
+        if getattr(w, "row_split", 1) != 1:
+            try:
+                f.set_row_split(0 if w.m <= 16 else 1, w.row_split)
+            except BaseException:
+                f.close()
+                raise
+        return f
 
     @classmethod
     def batch(cls, workloads, banks, stream=None, **kw):
@@ -604,6 +629,12 @@ class Letkf:
 
     def set_tile_shape(self, width_class: int, shape: int):
         letkf_set_tile_shape(self.h, width_class, shape)
+
+    def set_row_split(self, width_class: int, split: int):
+        """1: two whole columns per lane; 2: each column's rows on two lanes
+        (classes 0 and 1 of FP32 per-node handles; for systems that fill few
+        warps per SM)."""
+        letkf_set_row_split(self.h, width_class, split)
 
     def sync(self):
         letkf_sync(self.h)

@@ -37,6 +37,7 @@ class Workload:
     bank_count: int = 16
     partition: int = 0        # 0: per-node analysis; P: local domains of a P x P node partition
     piston: int = 0           # with a partition: differential-piston least squares
+    row_split: int = 1        # FP32 per-node analysis: 2 = each column's rows on two lanes
 
     @property
     def sigma2(self) -> float:
