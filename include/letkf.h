@@ -346,6 +346,18 @@ letkf_status letkf_autotune(letkf_t h, const void *y_dev, int32_t reps, int32_t 
  * CUDA graphs. letkf_autotune keeps the split and times the shapes it allows. */
 letkf_status letkf_set_row_split(letkf_t h, int32_t width_class, int32_t split);
 
+/* Start of the FP64 eigensolve on FP64 handles (Section 4.2's EVD): warm = 1
+ * (the default) runs the FP32 two-columns-per-lane eigensolve on the window
+ * rounded to FP32 first and starts each node's FP64 one-sided Jacobi from that
+ * basis, made orthonormal to FP64 rounding by two Newton-Schulz steps, stopping after a
+ * sweep whose cosines all stay below 1e-8 (the next would rotate by about its
+ * square); warm = 0 starts from the identity and stops after a sweep without
+ * rotations. Both give FP64 results (they differ by rounding). FP64 per-node
+ * handles only (LETKF_ERR_ARG otherwise). The FP32 pass takes the class's
+ * tile shape, so FP64 handles take the shapes of the whole-column FP32 form.
+ * Synchronises; drops the cached CUDA graphs. */
+letkf_status letkf_set_fp64_start(letkf_t h, int32_t warm);
+
 /* Synchronise the stream, return and clear the first error recorded on the
  * device since the last call (LETKF_OK if none). */
 letkf_status letkf_sync(letkf_t h);

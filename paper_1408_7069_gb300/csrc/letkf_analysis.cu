@@ -209,13 +209,20 @@ __device__ __forceinline__ void stage_tile(const LkInst &I, int i0, int j0, S *h
   for (int e = threadIdx.x; e < w * w; e += blockDim.x) tap[e] = T(taper[e]);
 }
 
-// One width class: FP64 handles run one CTA per node (letkf_node64.cu); FP32
-// handles the two-columns-per-lane kernel (letkf_pair.cu), then the FP64
-// analysis of the nodes it queued.
+// One width class: FP64 handles run the FP32 basis pass of the pair kernel
+// (unless switched off) and one CTA per node (letkf_node64.cu); FP32 handles
+// the two-columns-per-lane kernel (letkf_pair.cu), then the FP64 analysis of
+// the nodes it queued.
 template <int MP>
 cudaError_t launch_class(letkf_ctx *h, int cls, void *mean, void *spread) {
   if (h->n_tiles[cls] == 0) return cudaSuccess;
-  if (h->precision == 1) return lk_launch_node64(h, cls, mean, spread);
+  if (h->precision == 1) {
+    if (h->fp64_warm) {
+      const cudaError_t e = lk_launch_pair_basis(h, cls);
+      if (e != cudaSuccess) return e;
+    }
+    return lk_launch_node64(h, cls, mean, spread);
+  }
   cudaError_t e = lk_launch_pair(h, cls, mean, spread);
   if (e != cudaSuccess || h->fp64_kappa <= 0) return e;
   return lk_launch_list64(h, cls, mean, spread);

@@ -207,13 +207,19 @@ letkf_status build_tiles(letkf_ctx *h, int cls, const std::vector<std::vector<in
         if (any) tl.push_back(LkTile{k, i0, j0, (int)(cost * I.mp * I.mp / 32)});
       }
   }
-  // class 2 runs as two launches (MP = 64, then MP = 48): group by width first
-  auto wide = [h](const LkTile &t) { return h->inst[t.inst].mp == 64; };
+  // class 2 runs as two launches (MP = 64, then MP = 48), and class 1 of FP32
+  // handles in the whole-column form too (ensembles of at most 24 members on
+  // 24 columns, then the rest on 32): group by width first
+  const bool narrow24 = cls == 1 && h->precision == 0 && h->row_split[1] == 1;
+  auto first = [h, cls, narrow24](const LkTile &t) {
+    const LkInst &I = h->inst[t.inst];
+    return cls == 2 ? I.mp == 64 : (narrow24 && I.m <= 24);
+  };
   std::stable_sort(tl.begin(), tl.end(), [&](const LkTile &a, const LkTile &b) {
-    if (wide(a) != wide(b)) return wide(a);
+    if (first(a) != first(b)) return first(a);
     return a.cost > b.cost;
   });
-  h->tile_split[cls] = (int)std::count_if(tl.begin(), tl.end(), wide);
+  h->tile_split[cls] = (int)std::count_if(tl.begin(), tl.end(), first);
   if (h->tiles[cls]) cudaFree(h->tiles[cls]);
   h->tiles[cls] = nullptr;
   letkf_status st = dalloc(h, &h->tiles[cls], tl.size() * sizeof(LkTile));
@@ -1020,6 +1026,17 @@ letkf_status letkf_set_tile_shape(letkf_t h, int32_t width_class, int32_t shape)
   return rebuild_tiles(h, width_class);
 }
 
+letkf_status letkf_set_fp64_start(letkf_t h, int32_t warm) {
+  if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
+  if (h->precision != 1 || h->dom || (warm != 0 && warm != 1))
+    return fail(h, LETKF_ERR_ARG, "an FP64 per-node handle and warm = 0 or 1 are required");
+  DeviceGuard dg(h->device);
+  LK_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->fp64_warm != warm) drop_graphs(h);     // they hold the other launch sequence
+  h->fp64_warm = warm;
+  return LETKF_OK;
+}
+
 letkf_status letkf_set_row_split(letkf_t h, int32_t width_class, int32_t split) {
   if (!h) return fail(nullptr, LETKF_ERR_ARG, "handle is NULL");
   if (width_class < 0 || width_class > 2 || (split != 1 && split != 2))
@@ -1030,9 +1047,9 @@ letkf_status letkf_set_row_split(letkf_t h, int32_t width_class, int32_t split) 
                 "of whole warps (an even node count in class 0)");
   DeviceGuard dg(h->device);
   LK_CUDA(h, cudaStreamSynchronize(h->stream));
-  if (h->row_split[width_class] != split) drop_graphs(h);   // they hold the other kernel
+  if (h->row_split[width_class] == split) return LETKF_OK;
   h->row_split[width_class] = split;
-  return LETKF_OK;
+  return rebuild_tiles(h, width_class);    // class 1 groups its tiles by width only unsplit
 }
 
 letkf_status letkf_autotune(letkf_t h, const void *y_dev, int32_t reps, int32_t *shapes_out,

@@ -109,6 +109,7 @@ struct letkf_ctx {
   int tile_shape[3] = {0, 0, 0};    // index into the compiled tile shapes, per class
   int tile_split[3] = {0, 0, 0};    // class 2: leading tiles of MP = 64 instances (MP = 48 after)
   int row_split[3] = {1, 1, 1};     // 2: each column's rows on two lanes (classes 0 and 1, FP32)
+  int fp64_warm = 1;                // FP64 handles: FP32 basis pass, then the FP64 sweep from it
   std::vector<LkTile> tiles_host[3];
 
   // device buffers (single allocations sliced per instance)
@@ -205,6 +206,7 @@ cudaError_t lk_setup_node64w();
 // most 8 nodes per tile. (FP64 handles take any shape, which they ignore.)
 bool lk_shape_ok(const letkf_ctx *h, int cls, int shape);
 bool lk_shape_split_ok(const letkf_ctx *h, int cls, int shape, int split);
+cudaError_t lk_launch_pair_basis(letkf_ctx *h, int cls);
 int lk_num_tile_shapes();
 void lk_tile_shape(int s, int *ti, int *tj);
 int lk_width_class(int m);          // 0: m <= 16, 1: m <= 32, 2: m <= 64

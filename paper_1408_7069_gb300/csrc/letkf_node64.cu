@@ -18,8 +18,9 @@
 //
 //   Gram   A = (m-1)/rho I + sum_j tau_j/sigma2 Yb_j Yb_j^T, C d   (FP64, from the grid)
 //   EVD    one-sided Jacobi on the columns of B = A V, V accumulated: from the
-//          identity, or (queued FP32 nodes) from the stored FP32 eigenbasis made
-//          orthonormal by one Newton-Schulz step
+//          identity, or from a stored FP32 eigenbasis made orthonormal by
+//          Newton-Schulz steps (one for the queued nodes of FP32 handles, two
+//          for FP64 handles, whose FP32 basis pass precedes this kernel)
 //   apply  wbar = V Lambda^-1 V^T C d, W = V ((m-1) Lambda^-1)^(1/2) V^T,
 //          Xa_r = xbar_r + X'_r wbar + X'_r W for the node's two rows
 #include <math.h>
@@ -80,10 +81,17 @@ __device__ __forceinline__ double colsum(double x, double *red, int &buf) {
 // The node's analysis. S: storage type of the grid, ensemble and outputs;
 // WARM: start the sweep from the FP32 basis U (row-major MP x MP) instead of
 // the identity; stop: see jacobi().
+// WARM: ns_steps Newton-Schulz steps make the stored FP32 basis orthonormal
+// before the sweep. Each squares the orthogonality error: the FP32 eigensolve
+// leaves about 1e-6 (its last sweep rotated by cosines up to 1e-3), so one step
+// gives about 1e-12, enough for FP32 outputs, and two reach FP64 rounding,
+// which the FP64 outputs need (the Jacobi rotations keep whatever error V
+// starts with, and W = V Lambda^-1/2 V^T inherits it).
 template <int MP, typename S, bool WARM>
 __device__ void node64(const LkInst &I, int pid, S *__restrict__ mean_out,
                        S *__restrict__ spread_out, double tol, double stop, int max_sweeps,
-                       int *__restrict__ counters, double *smem, bool keep_basis = false) {
+                       int *__restrict__ counters, double *smem, bool keep_basis = false,
+                       int ns_steps = 1) {
   constexpr int NB = N64<MP>::NB, RB = N64<MP>::RB, LD = N64<MP>::LD;
   const int tid = threadIdx.x, c = tid % MP, rb = tid / MP, r0 = rb * RB;
   const int m = I.m, w = I.w;
@@ -123,7 +131,7 @@ __device__ void node64(const LkInst &I, int pid, S *__restrict__ mean_out,
 
   // ---- starting basis ----
   if constexpr (WARM) {
-    // V from the FP32 basis; V <- V (3I - V^T V)/2; B = A V
+    // V from the FP32 basis; ns_steps x (V <- V (3I - V^T V)/2); B = A V
     const float *U = I.basis + (size_t)pid * MP * MP;
 #pragma unroll
     for (int i = 0; i < RB; ++i) {
@@ -132,27 +140,29 @@ __device__ void node64(const LkInst &I, int pid, S *__restrict__ mean_out,
       sm.Vs[(r0 + i) * LD + c] = v[i];
     }
     __syncthreads();
+    for (int step = 0; step < ns_steps; ++step) {
 #pragma unroll
-    for (int i = 0; i < RB; ++i) {                   // G[j][c] = (V^T V)[j][c], j in my rows
-      const int j = r0 + i;
-      double g = 0.0;
+      for (int i = 0; i < RB; ++i) {                 // G[j][c] = (V^T V)[j][c], j in my rows
+        const int j = r0 + i;
+        double g = 0.0;
 #pragma unroll 8
-      for (int k = 0; k < MP; ++k) g = fma(sm.Vs[k * LD + j], sm.Vs[k * LD + c], g);
-      sm.Gs[j * LD + c] = g;
-    }
-    __syncthreads();
+        for (int k = 0; k < MP; ++k) g = fma(sm.Vs[k * LD + j], sm.Vs[k * LD + c], g);
+        sm.Gs[j * LD + c] = g;
+      }
+      __syncthreads();
 #pragma unroll
-    for (int i = 0; i < RB; ++i) {                   // V'[r][c] = 1.5 V[r][c] - 0.5 (V G)[r][c]
-      const int r = r0 + i;
-      double t = 0.0;
+      for (int i = 0; i < RB; ++i) {                 // V'[r][c] = 1.5 V[r][c] - 0.5 (V G)[r][c]
+        const int r = r0 + i;
+        double t = 0.0;
 #pragma unroll 8
-      for (int j = 0; j < MP; ++j) t = fma(sm.Vs[r * LD + j], sm.Gs[j * LD + c], t);
-      v[i] = fma(-0.5, t, 1.5 * v[i]);
-    }
-    __syncthreads();
+        for (int j = 0; j < MP; ++j) t = fma(sm.Vs[r * LD + j], sm.Gs[j * LD + c], t);
+        v[i] = fma(-0.5, t, 1.5 * v[i]);
+      }
+      __syncthreads();
 #pragma unroll
-    for (int i = 0; i < RB; ++i) sm.Vs[(r0 + i) * LD + c] = v[i];
-    __syncthreads();
+      for (int i = 0; i < RB; ++i) sm.Vs[(r0 + i) * LD + c] = v[i];
+      __syncthreads();
+    }
 #pragma unroll
     for (int i = 0; i < RB; ++i) {                   // B[r][c] = (A V')[r][c]
       const int r = r0 + i;
@@ -354,8 +364,12 @@ __device__ void node64(const LkInst &I, int pid, S *__restrict__ mean_out,
 }
 
 // FP64 handles: one CTA per node of width class MP (items: every node of the
-// handle; nodes of the other class leave at once).
-template <int MP, typename S>
+// handle; nodes of the other class leave at once). WARM: the sweep starts from
+// the FP32 eigenbasis the basis pass of the pair kernel stored (made
+// orthonormal to FP64 rounding by two Newton-Schulz steps) and stops after a
+// sweep whose cosines all stay below LK_WARM_STOP64; otherwise from the
+// identity, with a last sweep without rotations.
+template <int MP, typename S, bool WARM>
 __global__ void __launch_bounds__(N64_THREADS)
     node64_kernel(const LkInst *__restrict__ insts, const int2 *__restrict__ items,
                   S *__restrict__ mean, S *__restrict__ spread, double tol, int max_sweeps,
@@ -366,8 +380,9 @@ __global__ void __launch_bounds__(N64_THREADS)
   const LkInst &I = insts[it.x];
   if (I.mp != MP) return;
   const long long row = I.node_off + it.y;
-  node64<MP, S, false>(I, it.y, mean ? mean + 2 * row : nullptr, spread ? spread + 2 * row : nullptr,
-                       tol, 0.0, max_sweeps, counters, n64_smem, keep_basis != 0);
+  node64<MP, S, WARM>(I, it.y, mean ? mean + 2 * row : nullptr, spread ? spread + 2 * row : nullptr,
+                      tol, WARM ? LK_WARM_STOP64 : 0.0, max_sweeps, counters, n64_smem,
+                      keep_basis != 0, 2);
 }
 
 // FP32 handles: the nodes the pair kernel queued, a fixed grid of CTAs walking
@@ -728,8 +743,12 @@ int n64_sm_count(int device) {
 template <int MP>
 cudaError_t launch_node64(letkf_ctx *h, void *mean, void *spread) {
   const size_t smem = n64_smem_doubles<MP>() * sizeof(double);
-  return lk_launch_pdl(node64_kernel<MP, double>, (unsigned)h->n_pts_total, N64_THREADS, smem,
-                       h->stream, h->d_inst, h->node_items, (double *)mean, (double *)spread,
+  if (h->fp64_warm)
+    return lk_launch_pdl(node64_kernel<MP, double, true>, (unsigned)h->n_pts_total, N64_THREADS,
+                         smem, h->stream, h->d_inst, h->node_items, (double *)mean,
+                         (double *)spread, h->tol64, h->max_sweeps, h->counters, h->keep_basis);
+  return lk_launch_pdl(node64_kernel<MP, double, false>, (unsigned)h->n_pts_total, N64_THREADS,
+                       smem, h->stream, h->d_inst, h->node_items, (double *)mean, (double *)spread,
                        h->tol64, h->max_sweeps, h->counters, h->keep_basis);
 }
 

@@ -38,6 +38,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "letkf_device.cuh"
 
 // Phase clocks (a library built with -DLK_PHASE_CLOCKS only): lane 0 of every
@@ -53,14 +55,20 @@ __device__ unsigned long long g_lk_phase_clocks[5];
 
 namespace {
 
+constexpr int pow2_ceil(int x) { return x <= 1 ? 1 : 2 * pow2_ceil((x + 1) / 2); }
+
+// MP = 24 (ensembles of 17..24 members of the m <= 32 class) computes on 24
+// columns but keeps the class's 32 x 32 basis layout (MPS): its nodes' bases
+// are the 24 x 24 block of a 32 x 32 store whose padding stays the identity.
 template <int MP>
 struct PairCfg {
-  static constexpr int LPN = MP / 2;                      // lanes per node
-  static constexpr int NPW = MP <= 32 ? 32 / LPN : 1;     // nodes per warp
-  static constexpr int GL = NPW > 1 ? LPN : 32;           // lanes of a node's group (power of 2)
-  static constexpr int K2 = MP / 2;                       // float2 per column
-  static constexpr int CELLF = 2 * MP + 4;                // floats per halo cell (+4: bank shift)
-  static constexpr int NODE_SCR = 3 * MP + 4;             // scratch floats per node
+  static constexpr int LPN = MP / 2;                           // lanes per node
+  static constexpr int GL = MP <= 32 ? pow2_ceil(LPN) : 32;    // lanes of a node's group (power of 2)
+  static constexpr int NPW = 32 / GL;                          // nodes per warp
+  static constexpr int K2 = MP / 2;                            // float2 per column
+  static constexpr int CELLF = 2 * MP + 4;                     // floats per halo cell (+4: bank shift)
+  static constexpr int NODE_SCR = 3 * MP + 4;                  // scratch floats per node
+  static constexpr int MPS = MP == 24 ? 32 : MP;               // columns of the stored basis
 };
 
 // Shared-memory layout of one CTA (bytes).
@@ -190,17 +198,19 @@ __device__ __forceinline__ float2 reduce_scatter(float2 (&v)[GL], int li) {
 }
 
 // Stages the tile's halo (slope anomalies and innovations) and the taper table.
-template <int MP, int TI, int TJ>
+// S: the handle's storage type (double on FP64 handles, whose FP32 basis pass
+// rounds the window to float here).
+template <int MP, int TI, int TJ, typename S = float>
 __device__ __forceinline__ void stage_pair_tile(const LkInst &I, int i0, int j0, float *halo,
                                                 float *dh, float *tap) {
   using C = PairCfg<MP>;
   const int w = I.w, m = I.m;
   const int HJ = TJ + w - 1;
   const int ncell = (TI + w - 1) * HJ;
-  const float *Ybp = static_cast<const float *>(I.Ybp);
-  const float *dp = static_cast<const float *>(I.dp);
-  const float *taper = static_cast<const float *>(I.taper);
-  if (m == MP && (reinterpret_cast<uintptr_t>(Ybp) & 15) == 0) {
+  const S *Ybp = static_cast<const S *>(I.Ybp);
+  const S *dp = static_cast<const S *>(I.dp);
+  const S *taper = static_cast<const S *>(I.taper);
+  if (std::is_same<S, float>::value && m == MP && (reinterpret_cast<uintptr_t>(Ybp) & 15) == 0) {
     // a cell's two slope rows are 2 MP contiguous floats in the grid: float4 copies
     constexpr int Q4 = MP / 2;
     for (int e4 = threadIdx.x; e4 < ncell * Q4; e4 += blockDim.x) {
@@ -208,7 +218,7 @@ __device__ __forceinline__ void stage_pair_tile(const LkInst &I, int i0, int j0,
       const int hi = cell / HJ, hj = cell - hi * HJ;
       const size_t src = (size_t)(i0 + hi) * I.gs_cols + (j0 + hj);
       reinterpret_cast<float4 *>(halo + (size_t)cell * C::CELLF)[q] =
-          reinterpret_cast<const float4 *>(Ybp + src * 2 * MP)[q];
+          reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(Ybp) + src * 2 * MP)[q];
     }
   } else {
     for (int e = threadIdx.x; e < ncell * C::CELLF; e += blockDim.x) {
@@ -220,7 +230,7 @@ __device__ __forceinline__ void stage_pair_tile(const LkInst &I, int i0, int j0,
         const int mm = r - c * MP;
         const int hi = cell / HJ, hj = cell - hi * HJ;
         const size_t src = (size_t)(i0 + hi) * I.gs_cols + (j0 + hj);
-        if (mm < m) v = Ybp[(src * 2 + c) * m + mm];
+        if (mm < m) v = (float)Ybp[(src * 2 + c) * m + mm];
       }
       halo[e] = v;
     }
@@ -229,9 +239,9 @@ __device__ __forceinline__ void stage_pair_tile(const LkInst &I, int i0, int j0,
     const int cell = e >> 1;
     const int hi = cell / HJ, hj = cell - hi * HJ;
     const size_t src = (size_t)(i0 + hi) * I.gs_cols + (j0 + hj);
-    dh[e] = dp[src * 2 + (e & 1)];
+    dh[e] = (float)dp[src * 2 + (e & 1)];
   }
-  for (int e = threadIdx.x; e < w * w; e += blockDim.x) tap[e] = taper[e];
+  for (int e = threadIdx.x; e < w * w; e += blockDim.x) tap[e] = (float)taper[e];
 }
 
 // One CTA per tile of TI x TJ nodes of one instance; the nodes of the tile are
@@ -245,7 +255,10 @@ struct PairLaunch {
   static constexpr int min_ctas = MP <= 32 ? 65536 / (threads * 128) : 1;
 };
 
-template <int MP, int TI, int TJ>
+// BASIS (FP64 handles, S = double): the FP32 eigensolve alone, storing every
+// node's eigenbasis as the start of the FP64 sweep of node64_kernel; nothing
+// is queued and X is not touched.
+template <int MP, int TI, int TJ, typename S = float, bool BASIS = false>
 __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP, TI, TJ>::min_ctas)
     analysis_pair_kernel(const LkInst *__restrict__ insts, const LkTile *__restrict__ tiles,
                          float *__restrict__ mean, float *__restrict__ spread, float tol,
@@ -264,7 +277,7 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
   float *halo = reinterpret_cast<float *>(smem);
   float *dh = reinterpret_cast<float *>(smem + Ly.dh);
   float *tap = reinterpret_cast<float *>(smem + Ly.tap);
-  stage_pair_tile<MP, TI, TJ>(I, tl.i0, tl.j0, halo, dh, tap);
+  stage_pair_tile<MP, TI, TJ, S>(I, tl.i0, tl.j0, halo, dh, tap);
   __syncthreads();
   LK_PHASE_STAMP(ph1);
 
@@ -405,20 +418,22 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
     }
   }
   // ---- eigenbasis for the reverse mode and for queued nodes: U[k][2li], U[k][2li+1] ----
-  if ((keep_basis || queued) && active && live) {
+  if ((BASIS || keep_basis || queued) && active && live) {
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < K2; ++k)
       ok = ok && isfinite(P[k].x) && isfinite(P[k].y) && isfinite(Q[k].x) && isfinite(Q[k].y);
-    float *U = I.basis + (size_t)pid * MP * MP;
+    constexpr int MPS = C::MPS;
+    float *U = I.basis + (size_t)pid * MPS * MPS;
 #pragma unroll
     for (int k = 0; k < K2; ++k) {
       const float2 r0 = ok ? make_float2(P[k].x, Q[k].x) : make_float2(k == li ? 1.f : 0.f, 0.f);
       const float2 r1 = ok ? make_float2(P[k].y, Q[k].y) : make_float2(0.f, k == li ? 1.f : 0.f);
-      reinterpret_cast<float2 *>(U + (2 * k) * MP)[li] = r0;
-      reinterpret_cast<float2 *>(U + (2 * k + 1) * MP)[li] = r1;
+      reinterpret_cast<float2 *>(U + (2 * k) * MPS)[li] = r0;
+      reinterpret_cast<float2 *>(U + (2 * k + 1) * MPS)[li] = r1;
     }
   }
+  if constexpr (BASIS) return;
 
   // ---- transform and apply (Section 4.2): Xa_r = xbar_r + X'_r wbar + X'_r W ----
   float *vcd = scr;                     // C d
@@ -830,8 +845,17 @@ constexpr bool shape_ok() {
 // The row-split form: whole warps of nodes (two per warp for MP = 16).
 template <int MP, int TI, int TJ>
 constexpr bool split_shape_ok() {
-  if constexpr (MP > 32) return false;
+  if constexpr (MP != 16 && MP != 32) return false;
   else return (TI * TJ) % SplitCfg<MP>::NPW == 0;
+}
+
+// The instances a kernel of width MP serves: MP = 24 those of the m <= 32
+// class with at most 24 members, MP = 32 that class (its tile list decides
+// which), otherwise the instances padded to MP.
+template <int MP>
+bool serves(const LkInst &I) {
+  if constexpr (MP == 24) return I.mp == 32 && I.m <= 24;
+  else return I.mp == MP;
 }
 
 template <int MP, int TI, int TJ, bool SPLIT>
@@ -843,7 +867,7 @@ cudaError_t launch_shape(letkf_ctx *h, const LkTile *tiles, int n_tiles, float *
   } else {
   size_t need = 0;
   for (const LkInst &I : h->inst)
-    if (I.mp == MP) {
+    if (serves<MP>(I)) {
       const size_t b = pair_layout<MP, TI, TJ>(I.w).total;
       need = b > need ? b : need;
     }
@@ -866,7 +890,7 @@ cudaError_t launch_mp(letkf_ctx *h, int cls, const LkTile *tiles, int n_tiles, f
   const float kthr = h->fp64_kappa > 0 ? (float)h->fp64_kappa : 0.f;
   int *queue = kthr > 0.f ? h->counters + 4 + cls : nullptr;
   int2 *wl = h->worklist + (size_t)cls * h->n_pts_total;
-  const bool split = MP <= 32 && h->row_split[cls] == 2;
+  const bool split = (MP == 16 || MP == 32) && h->row_split[cls] == 2;
   switch (h->tile_shape[cls]) {
 #define LK_CASE(id, ti, tj)                                                                   \
   case id:                                                                                    \
@@ -880,15 +904,55 @@ cudaError_t launch_mp(letkf_ctx *h, int cls, const LkTile *tiles, int n_tiles, f
   return cudaErrorInvalidValue;
 }
 
+// FP64 handles: the FP32 basis pass over one width class (MP = 16 or 32).
 template <int MP, int TI, int TJ>
-cudaError_t set_shape_smem(int w) {
+cudaError_t launch_basis_shape(letkf_ctx *h, int cls) {
+  if (h->n_tiles[cls] == 0) return cudaSuccess;
+  if constexpr (!shape_ok<MP, TI, TJ>()) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    size_t need = 0;
+    for (const LkInst &I : h->inst)
+      if (I.mp == MP) {
+        const size_t b = pair_layout<MP, TI, TJ>(I.w).total;
+        need = b > need ? b : need;
+      }
+    return lk_launch_pdl(analysis_pair_kernel<MP, TI, TJ, double, true>, h->n_tiles[cls],
+                         TI * TJ * 32 / PairCfg<MP>::NPW, need, h->stream, h->d_inst,
+                         h->tiles[cls], (float *)nullptr, (float *)nullptr, (float)h->tol32,
+                         (float)h->stop32, h->max_sweeps, 0.f, h->counters, (int *)nullptr,
+                         (int2 *)nullptr, 1);
+  }
+}
+
+template <int MP>
+cudaError_t launch_basis(letkf_ctx *h, int cls) {
+  switch (h->tile_shape[cls]) {
+#define LK_CASE(id, ti, tj) \
+  case id:                  \
+    return launch_basis_shape<MP, ti, tj>(h, cls);
+    LK_FOR_SHAPES(LK_CASE)
+#undef LK_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int MP, int TI, int TJ>
+cudaError_t set_shape_smem(int w, bool fp64) {
   const int bytes = (int)pair_layout<MP, TI, TJ>(w).total;
   cudaError_t e = cudaSuccess;
-  if constexpr (shape_ok<MP, TI, TJ>())
+  if constexpr (shape_ok<MP, TI, TJ>()) {
+    if (fp64) {
+      if constexpr (MP == 16 || MP == 32)
+        e = cudaFuncSetAttribute(analysis_pair_kernel<MP, TI, TJ, double, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      return e;
+    }
     e = cudaFuncSetAttribute(analysis_pair_kernel<MP, TI, TJ>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  }
   if constexpr (split_shape_ok<MP, TI, TJ>())
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !fp64)
       e = cudaFuncSetAttribute(analysis_split_kernel<MP, TI, TJ>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;
@@ -898,11 +962,11 @@ template <int MP>
 cudaError_t setup_mp(letkf_ctx *h) {
   int wmax = 0;
   for (const LkInst &I : h->inst)
-    if (I.mp == MP) wmax = I.w > wmax ? I.w : wmax;
+    if (serves<MP>(I)) wmax = I.w > wmax ? I.w : wmax;
   if (wmax == 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
 #define LK_SET(id, ti, tj) \
-  if (e == cudaSuccess) e = set_shape_smem<MP, ti, tj>(wmax);
+  if (e == cudaSuccess) e = set_shape_smem<MP, ti, tj>(wmax, h->precision == 1);
   LK_FOR_SHAPES(LK_SET)
 #undef LK_SET
   return e;
@@ -910,12 +974,19 @@ cudaError_t setup_mp(letkf_ctx *h) {
 
 }  // namespace
 
-// Class 0: MP = 16; class 1: MP = 32; class 2: tiles of MP = 64 instances first
-// (tile_split of them), then MP = 48.
+// Class 0: MP = 16; class 1: tiles of instances with m <= 24 first (tile_split
+// of them, none in the row-split form) on MP = 24, then MP = 32; class 2: tiles
+// of MP = 64 instances first, then MP = 48.
 cudaError_t lk_launch_pair(letkf_ctx *h, int cls, void *mean, void *spread) {
   float *mo = static_cast<float *>(mean), *so = static_cast<float *>(spread);
   if (cls == 0) return launch_mp<16>(h, 0, h->tiles[0], h->n_tiles[0], mo, so);
-  if (cls == 1) return launch_mp<32>(h, 1, h->tiles[1], h->n_tiles[1], mo, so);
+  if (cls == 1) {
+    const int n24 = h->tile_split[1];
+    cudaError_t e = launch_mp<24>(h, 1, h->tiles[1], n24, mo, so);
+    if (e == cudaSuccess)
+      e = launch_mp<32>(h, 1, h->tiles[1] + n24, h->n_tiles[1] - n24, mo, so);
+    return e;
+  }
   const int split = h->tile_split[2];
   cudaError_t e = launch_mp<64>(h, 2, h->tiles[2], split, mo, so);
   if (e == cudaSuccess)
@@ -930,7 +1001,9 @@ bool lk_shape_ok(const letkf_ctx *h, int cls, int shape) {
 bool lk_shape_split_ok(const letkf_ctx *h, int cls, int shape, int split) {
   int ti, tj;
   lk_tile_shape(shape, &ti, &tj);
-  if (h->precision == 1) return split == 1;   // FP64 handles analyse one node per CTA
+  // FP64 handles analyse one node per CTA; their FP32 basis pass takes the
+  // tiles of the whole-column form
+  if (h->precision == 1 && split != 1) return false;
   if (split == 2) {
     switch (cls) {
       case 0: return (ti * tj) % SplitCfg<16>::NPW == 0;
@@ -945,9 +1018,15 @@ bool lk_shape_split_ok(const letkf_ctx *h, int cls, int shape, int split) {
   }
 }
 
+cudaError_t lk_launch_pair_basis(letkf_ctx *h, int cls) {
+  if (cls == 0) return launch_basis<16>(h, 0);
+  if (cls == 1) return launch_basis<32>(h, 1);
+  return cudaErrorInvalidValue;              // FP64 handles hold m <= 32
+}
+
 cudaError_t lk_setup_pair(letkf_ctx *h) {
-  if (h->precision != 0) return cudaSuccess;
   cudaError_t e = setup_mp<16>(h);
+  if (e == cudaSuccess && h->precision == 0) e = setup_mp<24>(h);
   if (e == cudaSuccess) e = setup_mp<32>(h);
   if (e == cudaSuccess) e = setup_mp<48>(h);
   if (e == cudaSuccess) e = setup_mp<64>(h);

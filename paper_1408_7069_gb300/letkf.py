@@ -72,6 +72,7 @@ _SIGS = {
     "letkf_tile_shape": [c_int32, POINTER(c_int32), POINTER(c_int32)],
     "letkf_set_tile_shape": [c_void_p, c_int32, c_int32],
     "letkf_set_row_split": [c_void_p, c_int32, c_int32],
+    "letkf_set_fp64_start": [c_void_p, c_int32],
     "letkf_autotune": [c_void_p, c_void_p, c_int32, POINTER(c_int32), POINTER(ctypes.c_float)],
     "letkf_set_params": [c_void_p, c_int32, c_double, c_double, c_double],
     "letkf_set_frame": [c_void_p, ctypes.c_int64],
@@ -168,6 +169,10 @@ def letkf_set_tile_shape(h, width_class: int, shape: int) -> None:
 
 def letkf_set_row_split(h, width_class: int, split: int) -> None:
     _check(lib().letkf_set_row_split(h, width_class, split), h)
+
+
+def letkf_set_fp64_start(h, warm: int) -> None:
+    _check(lib().letkf_set_fp64_start(h, warm), h)
 
 
 def letkf_autotune(h, y, reps: int = 3):
@@ -629,6 +634,11 @@ class Letkf:
 
     def set_tile_shape(self, width_class: int, shape: int):
         letkf_set_tile_shape(self.h, width_class, shape)
+
+    def set_fp64_start(self, warm: bool):
+        """FP64 handles: start the FP64 eigensolve from an FP32 basis (True,
+        the default) or from the identity (False)."""
+        letkf_set_fp64_start(self.h, 1 if warm else 0)
 
     def set_row_split(self, width_class: int, split: int):
         """1: two whole columns per lane; 2: each column's rows on two lanes

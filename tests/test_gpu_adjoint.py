@@ -93,11 +93,17 @@ def test_fp64_gradient_matches_oracle(w):
 
 def test_fp64_gradient_matches_gpu_finite_differences():
     """Central differences of the GPU loop itself (letkf_set_params + letkf_run),
-    Richardson-extrapolated, against letkf_grad."""
+    Richardson-extrapolated, against letkf_grad. The FP64 eigensolve starts
+    from the identity here: started from the FP32 basis pass, the last bits of
+    each analysis follow that basis, whose rotations change discontinuously with
+    the parameters, and J(theta) carries noise of about 1e-10 relative, which
+    the differences of step 1e-4 turn into about 2e-6 of the derivative. The
+    gradient of the default (warm) start is compared with this one beside it."""
     w = replace(W.TOY_8X8, name="toy-gc", m=10, loc_len=1.2)
     frames = 8
     inp = loop_inputs(w, frames)
     f = L.Letkf.from_workload(w, bank=inp.bank)
+    f.set_fp64_start(False)
     y = torch.from_numpy(inp.slopes[:frames]).cuda()
     t = torch.from_numpy(inp.truth[:frames]).cuda()
     X0 = torch.from_numpy(inp.X0).cuda()
@@ -124,9 +130,15 @@ def test_fp64_gradient_matches_gpu_finite_differences():
     num = [fd(k, 1e-4) for k in range(3)]
     f.set_params(*theta)
     J, g = gpu_grad(w, inp, frames, f=f)
+    f.set_fp64_start(True)
+    Jw, gw = gpu_grad(w, inp, frames, f=f)
     f.close()
     for k in range(3):
         assert abs(g[k] - num[k]) <= 1e-6 * max(abs(num[k]), 1e-9 * J), (g, num)
+    # the two starts differ by rounding, which the 8-frame loop amplifies
+    # (measured 7e-12 in J)
+    assert Jw == pytest.approx(J, rel=1e-10)
+    assert np.allclose(gw, g, rtol=1e-7, atol=0), (gw, g)
 
 
 def test_checkpoint_spacing_and_replay_are_bitwise_invariant():

@@ -15,7 +15,7 @@ torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
 from paper_1408_7069_gb300 import synth, workloads as W  # noqa: E402
-from paper_1408_7069_gb300.letkf import Letkf, LetkfError  # noqa: E402
+from paper_1408_7069_gb300.letkf import Letkf, LetkfError, tile_shapes  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -276,6 +276,75 @@ def test_edge_shapes(nsub, m, window, square):
     Xa = f.get_state().cpu().numpy().astype(np.float64)
     check_analysis(TOL[0], Xa, mean.cpu().numpy(), spread.cpu().numpy(), ref)
     f.close()
+
+
+@pytest.mark.parametrize("nsub,m,window,square", [(1, 2, 1, True), (3, 16, 9, True),
+                                                  (6, 17, 3, True), (10, 32, 5, False),
+                                                  (5, 5, 2, True)])
+def test_edge_shapes_fp64(nsub, m, window, square):
+    """The same shapes on FP64 handles, with the FP32 basis pass and the warm
+    FP64 sweep (the default) and with the cold sweep from the identity."""
+    mask = synth.pupil_subap_mask(nsub, 0.0 if square else 0.2, square)
+    geom = oracle.build_geometry(mask, window, 1, 0.0)
+    rng = np.random.default_rng(nsub * 100 + m + 7)
+    Xb = 3 * rng.standard_normal((geom.n_pts, 2, 1)) + 0.5 * rng.standard_normal((geom.n_pts, 2, m))
+    y = rng.standard_normal(geom.p)
+    ref = oracle.analysis(geom, Xb, y, 0.01, 1.03)
+    for warm in (True, False):
+        f = Letkf(mask, m=m, window=window, taper=1, rho=1.03, sigma2=0.01, precision=1)
+        f.set_fp64_start(warm)
+        f.set_state(torch.from_numpy(Xb).cuda())
+        mean, spread = f.analyze(torch.from_numpy(y).cuda())
+        f.sync()
+        Xa = f.get_state().cpu().numpy()
+        check_analysis(TOL[1], Xa, mean.cpu().numpy(), spread.cpu().numpy(), ref)
+        f.close()
+
+
+W16_64 = replace(W.TEL_16M, name="16m-fp64", precision=1)
+
+
+@pytest.mark.parametrize("w,k", [(W.TOY_8X8, 0), (W.TOY_8X8, 6), (W16_64, 0), (W16_64, 4)],
+                         ids=["8x8-f0", "8x8-f6", "16m-fp64-f0", "16m-fp64-f4"])
+def test_fp64_warm_and_cold_starts_match_oracle(w, k):
+    """FP64 handles: the FP64 sweep started from the FP32 basis pass (whose
+    FP32 eigenvectors carry errors up to about eps32 kappa at the prior draw)
+    and from the identity both meet the FP64 tolerances and agree with each
+    other to rounding."""
+    inp, geom = inputs(w, 8)
+    Xb = oracle_background(w, inp, geom, k) if k else inp.X0
+    y = inp.slopes[k]
+    ref = oracle.analysis(geom, Xb, y, w.sigma2, w.rho)
+    out = {}
+    for warm in (True, False):
+        f = Letkf.from_workload(w, bank=inp.bank)
+        f.set_fp64_start(warm)
+        f.set_state(torch.from_numpy(Xb).cuda())
+        mean, spread = f.analyze(torch.from_numpy(y).cuda())
+        f.sync()
+        Xa = f.get_state().cpu().numpy()
+        check_analysis(TOL[1], Xa, mean.cpu().numpy(), spread.cpu().numpy(), ref)
+        out[warm] = Xa
+        f.close()
+    # the ensembles' anomalies carry the eigenvectors' rounding, amplified by
+    # near-degenerate eigenvalues at the prior draw: the anomaly tolerance
+    assert rel(out[True], out[False]) <= TOL[1]["anom"], rel(out[True], out[False])
+
+
+def test_fp64_start_is_refused_on_fp32_handles():
+    w = W.TEL_16M
+    inp, _ = inputs(w, 8)
+    f = Letkf.from_workload(w, bank=inp.bank)
+    with pytest.raises(LetkfError, match="LETKF_ERR_ARG"):
+        f.set_fp64_start(True)
+    f.close()
+    g = Letkf.from_workload(W.TOY_8X8, bank=inputs(W.TOY_8X8, 8)[0].bank)
+    with pytest.raises(LetkfError, match="LETKF_ERR_ARG"):
+        g.set_row_split(0, 2)
+    one = [s for s, (a, b) in enumerate(tile_shapes()) if a * b == 1][0]
+    with pytest.raises(LetkfError, match="LETKF_ERR_ARG"):  # the FP32 basis pass fills warps
+        g.set_tile_shape(0, one)
+    g.close()
 
 
 def test_zero_spread_background_is_left_unchanged():
