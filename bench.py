@@ -52,6 +52,9 @@ def parse_args(argv=None):
     ap.add_argument("--only-domains", action="store_true",
                     help="run only the local-domain measurement (K = --steps frames after "
                          "--warmup) and print its JSON")
+    ap.add_argument("--only-small", action="store_true",
+                    help="run only the 8x8 FP64 and 16 m FP32 measurements (K = --steps frames "
+                         "after --warmup) and print their JSON")
     ap.add_argument("--phase-split", action="store_true",
                     help="print where the FP32 analysis kernel spends its cycles (builds and "
                          "loads the phase-clock variant of the library) instead of the bench line")
@@ -966,6 +969,12 @@ def main(argv=None):
         from paper_1408_7069_gb300 import letkf as L
         torch.cuda.set_device(0)
         print(json.dumps(domains_arm(torch, L, K=args.steps, Wm=args.warmup)))
+        return 0
+    if args.only_small:
+        import torch
+        from paper_1408_7069_gb300 import letkf as L
+        torch.cuda.set_device(0)
+        print(json.dumps(small_configs_arm(torch, L, K=args.steps, Wm=args.warmup)))
         return 0
     if args.phase_split:
         return phase_split(args)

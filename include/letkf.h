@@ -430,11 +430,13 @@ letkf_status letkf_fma_peaks(double *out);
 letkf_status letkf_phase_clocks(uint64_t *out);
 
 /* The same for the reverse mode's node kernel (letkf_grad): SM cycles summed
- * over its nodes since the last call, out: host uint64_t[6] = window staging,
- * Gram and the start of the eigensolve (B = A U0, or the FP64 warm basis),
- * Jacobi sweeps, the adjoint of the transform up to A_bar, the window slopes'
- * adjoints, and the number of nodes. LETKF_ERR_STATE without phase clocks.
- * Synchronises the device and resets the counts. */
+ * over its nodes since the last call, out: host uint64_t[12], [0..5] for its
+ * FP32 form and [6..11] for its FP64 form (FP64 handles and the queued nodes
+ * of FP32 handles) = window staging, Gram and the start of the eigensolve
+ * (B = A U0, or the FP64 warm basis), Jacobi sweeps, the adjoint of the
+ * transform up to A_bar, the window slopes' adjoints, and the number of nodes.
+ * LETKF_ERR_STATE without phase clocks. Synchronises the device and resets
+ * the counts. */
 letkf_status letkf_adjoint_phase_clocks(uint64_t *out);
 
 /* Text of the last error on this handle (or of the last failed create when h is NULL). */

@@ -70,11 +70,12 @@ struct LkAdjWork {
 };
 
 // Phase clocks (a library built with -DLK_PHASE_CLOCKS only): lane 0 of every
-// node adds the SM cycles of each phase of adjoint_node_kernel: [0] window
-// staging, [1] Gram and the start of the eigensolve, [2] Jacobi sweeps,
-// [3] adjoint of the transform up to A_bar, [4] window slopes, [5] nodes.
+// node adds the SM cycles of each phase of adjoint_node_kernel, [0..5] for the
+// FP32 form and [6..11] for the FP64 one: window staging, Gram and the start
+// of the eigensolve, Jacobi sweeps, adjoint of the transform up to A_bar,
+// window slopes, nodes.
 #ifdef LK_PHASE_CLOCKS
-__device__ unsigned long long g_lk_adj_clocks[6];
+__device__ unsigned long long g_lk_adj_clocks[12];
 #define LK_ADJ_STAMP(t) const long long t = clock64()
 #else
 #define LK_ADJ_STAMP(t)
@@ -431,12 +432,13 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
   __syncwarp();
   LK_ADJ_STAMP(ph5);
   if (lane == 0) {
-    atomicAdd(&g_lk_adj_clocks[0], (unsigned long long)(ph1 - ph0));
-    atomicAdd(&g_lk_adj_clocks[1], (unsigned long long)(ph2 - ph1));
-    atomicAdd(&g_lk_adj_clocks[2], (unsigned long long)(ph3 - ph2));
-    atomicAdd(&g_lk_adj_clocks[3], (unsigned long long)(ph4 - ph3));
-    atomicAdd(&g_lk_adj_clocks[4], (unsigned long long)(ph5 - ph4));
-    atomicAdd(&g_lk_adj_clocks[5], 1ull);
+    unsigned long long *pc = g_lk_adj_clocks + (kWarm ? 0 : 6);
+    atomicAdd(&pc[0], (unsigned long long)(ph1 - ph0));
+    atomicAdd(&pc[1], (unsigned long long)(ph2 - ph1));
+    atomicAdd(&pc[2], (unsigned long long)(ph3 - ph2));
+    atomicAdd(&pc[3], (unsigned long long)(ph4 - ph3));
+    atomicAdd(&pc[4], (unsigned long long)(ph5 - ph4));
+    atomicAdd(&pc[5], 1ull);
   }
 #endif
 }
@@ -964,13 +966,13 @@ extern "C" letkf_status letkf_grad(letkf_t h, int32_t frames, const void *y_seq_
 extern "C" letkf_status letkf_adjoint_phase_clocks(uint64_t *out) {
 #ifdef LK_PHASE_CLOCKS
   if (!out) return LETKF_ERR_ARG;
-  unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
+  unsigned long long v[12] = {};
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpyFromSymbol(v, g_lk_adj_clocks, sizeof(v));
-  const unsigned long long z[6] = {0, 0, 0, 0, 0, 0};
+  const unsigned long long z[12] = {};
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_lk_adj_clocks, z, sizeof(z));
   if (e != cudaSuccess) return LETKF_ERR_CUDA;
-  for (int i = 0; i < 6; ++i) out[i] = v[i];
+  for (int i = 0; i < 12; ++i) out[i] = v[i];
   return LETKF_OK;
 #else
   (void)out;

@@ -312,8 +312,9 @@ def letkf_phase_clocks():
 def letkf_adjoint_phase_clocks():
     """Cycles of the reverse-mode node kernel's phases (staging, Gram and
     start, Jacobi, transform adjoint, window slopes) and its node count since
-    the last call, or None without phase clocks."""
-    out = (ctypes.c_uint64 * 6)()
+    the last call, FP32 form then FP64 form (12 values), or None without
+    phase clocks."""
+    out = (ctypes.c_uint64 * 12)()
     st = lib().letkf_adjoint_phase_clocks(out)
     if st == 6:
         return None
