@@ -45,7 +45,8 @@
 struct LkAdjWork {
   int frames = 0, ckpt = 0, n_seg = 0;
   void *x_seg = nullptr;            // [ckpt][state] backgrounds of one segment
-  float *basis_seg = nullptr;       // [ckpt][n_pts][mp][mp] analysis eigenbases of one segment
+  void *basis_seg = nullptr;        // [ckpt][n_pts][mp][mp] analysis eigenbases of one segment
+                                    // (FP32; FP64 on FP64 handles)
   void *ckpt_x = nullptr;           // [n_seg][state]
   float *ckpt_basis = nullptr;      // [n_seg][n_pts][mp][mp] warm-start bases at segment start
   long long *ckpt_frame = nullptr;  // [n_seg][2] frame counters at segment start
@@ -131,8 +132,8 @@ template <int MP, typename S, typename T>
 __global__ void __launch_bounds__(ADJ_WARPS * 32)
     adjoint_node_kernel(const LkInst *__restrict__ insts, const int2 *__restrict__ list,
                         const int *__restrict__ list_len, const float *__restrict__ U0,
-                        float kappa_thr, int2 *__restrict__ queue, int *__restrict__ queue_len,
-                        T tol, AdjArgs a) {
+                        const double *__restrict__ U64, float kappa_thr,
+                        int2 *__restrict__ queue, int *__restrict__ queue_len, T tol, AdjArgs a) {
   constexpr bool kWarm = std::is_same<T, float>::value;
   LK_ADJ_STAMP(ph0);
   extern __shared__ __align__(16) unsigned char smem[];
@@ -230,6 +231,28 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
     jacobi<MP, T, false>(b, v, tol, a.max_sweeps, a.counters, T(1e-3));
 #ifdef LK_PHASE_CLOCKS
     ph2 = ph2w;
+#endif
+  } else if (U64) {
+    // FP64 handles: the forward analysis's FP64 eigenvectors V (orthonormal and
+    // converged to FP64 rounding) are taken as they are, B = A V, lambda = |A v|
+    if (col) {
+#pragma unroll
+      for (int k = 0; k < MP; ++k) Ms[lane * (MP + 1) + k] = b[k];
+    }
+    const double *u = U64 + (size_t)pid * MP * MP;
+#pragma unroll
+    for (int k = 0; k < MP; ++k) v[k] = col ? T(u[k * MP + lane]) : T(0);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < MP; ++i) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < MP; ++k) s = fma(Ms[i * (MP + 1) + k], v[k], s);
+      b[i] = s;
+    }
+    __syncwarp();
+#ifdef LK_PHASE_CLOCKS
+    ph2 = clock64();
 #endif
   } else {
     if (U0) {
@@ -633,25 +656,28 @@ size_t max_node_smem(const letkf_ctx *h) {
 }
 
 template <int MP>
-cudaError_t launch_nodes(letkf_ctx *h, LkAdjWork *W, const float *U0, const AdjArgs &a) {
+cudaError_t launch_nodes(letkf_ctx *h, LkAdjWork *W, const void *bk, const AdjArgs &a) {
   const LkInst &I = h->inst[0];
   const int blocks = (I.n_pts + ADJ_WARPS - 1) / ADJ_WARPS;
   if (h->precision == 1) {
-    // FP64 handles: refined from the eigenbasis the forward node64 kernel stored
+    // FP64 handles: the FP64 eigenbasis the forward node64 kernel stored
     adjoint_node_kernel<MP, double, double>
         <<<blocks, ADJ_WARPS * 32, node_smem<MP, double, double>(I), h->stream>>>(
-            h->d_inst, nullptr, nullptr, U0, 0.f, nullptr, nullptr, h->tol64, a);
+            h->d_inst, nullptr, nullptr, nullptr, static_cast<const double *>(bk), 0.f, nullptr,
+            nullptr, h->tol64, a);
     return cudaGetLastError();
   }
+  const float *U0 = static_cast<const float *>(bk);
   const float kthr = h->fp64_kappa > 0 ? (float)h->fp64_kappa : 0.f;
   adjoint_node_kernel<MP, float, float>
       <<<blocks, ADJ_WARPS * 32, node_smem<MP, float, float>(I), h->stream>>>(
-          h->d_inst, nullptr, nullptr, U0, kthr, W->queue, W->queue_len, (float)h->tol32, a);
+          h->d_inst, nullptr, nullptr, U0, nullptr, kthr, W->queue, W->queue_len,
+          (float)h->tol32, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || kthr <= 0.f) return e;
   adjoint_node_kernel<MP, float, double>
       <<<blocks, ADJ_WARPS * 32, node_smem<MP, float, double>(I), h->stream>>>(
-          h->d_inst, W->queue, W->queue_len, U0, 0.f, nullptr, nullptr, h->tol64, a);
+          h->d_inst, W->queue, W->queue_len, U0, nullptr, 0.f, nullptr, nullptr, h->tol64, a);
   return cudaGetLastError();
 }
 
@@ -684,11 +710,12 @@ letkf_status ensure_work(letkf_ctx *h, int frames, int ckpt) {
   const LkInst &I = h->inst[0];
   const size_t st = (size_t)h->state_total * h->rsz;
   const size_t bas = (size_t)I.n_pts * I.mp * I.mp * sizeof(float);
+  const size_t bas_seg = (size_t)I.n_pts * I.mp * I.mp * (h->precision == 1 ? 8 : 4);
   const size_t ns = (size_t)I.n_pts * 2 * I.m * sizeof(double);
   const size_t wc = (size_t)I.w * I.w;
   const size_t cells = (size_t)I.gs_rows * I.gs_cols;
   cudaError_t e = walloc(&W->x_seg, (size_t)ckpt * st);
-  if (e == cudaSuccess) e = walloc(&W->basis_seg, (size_t)ckpt * bas);
+  if (e == cudaSuccess) e = walloc(&W->basis_seg, (size_t)ckpt * bas_seg);
   if (e == cudaSuccess) e = walloc(&W->ckpt_x, (size_t)W->n_seg * st);
   if (e == cudaSuccess) e = walloc(&W->ckpt_basis, (size_t)W->n_seg * bas);
   if (e == cudaSuccess) e = walloc(&W->ckpt_frame, (size_t)W->n_seg * 2 * sizeof(long long));
@@ -749,9 +776,10 @@ cudaError_t load_state(letkf_ctx *h, const void *x, const float *basis, const lo
 }
 
 // One forward frame (prediction in h->X): optional residual, analysis (its
-// background kept in xk, its eigenbases in bk), forecast with the bank noise.
+// background kept in xk, its eigenbases in bk: FP64 on FP64 handles),
+// forecast with the bank noise.
 cudaError_t forward_frame(letkf_ctx *h, const void *y_seq, const void *truth_seq, double *resvar,
-                          void *xk, float *bk, bool forecast) {
+                          void *xk, void *bk, bool forecast) {
   const LkInst &I = h->inst[0];
   const long long *ridx = h->frame + 1;
   cudaError_t e = cudaSuccess;
@@ -760,9 +788,12 @@ cudaError_t forward_frame(letkf_ctx *h, const void *y_seq, const void *truth_seq
     e = cudaMemcpyAsync(xk, h->X, h->state_total * h->rsz, cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess) e = lk_launch_obs(h, y_seq, ridx);
   if (e == cudaSuccess) e = lk_launch_analysis(h, nullptr, nullptr);
+  const size_t nb = (size_t)I.n_pts * I.mp * I.mp;
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(bk, h->basis, (size_t)I.n_pts * I.mp * I.mp * sizeof(float),
-                        cudaMemcpyDeviceToDevice, h->stream);
+    e = h->basis64 ? cudaMemcpyAsync(bk, h->basis64, nb * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     h->stream)
+                   : cudaMemcpyAsync(bk, h->basis, nb * sizeof(float), cudaMemcpyDeviceToDevice,
+                                     h->stream);
   if (e == cudaSuccess && forecast) e = lk_launch_forecast(h, nullptr);
   return e;
 }
@@ -770,7 +801,7 @@ cudaError_t forward_frame(letkf_ctx *h, const void *y_seq, const void *truth_seq
 // One backward frame: background xk, analysis eigenbases bk, adjoint of the
 // analysis lam_in -> adjoint of the previous analysis lam_out.
 cudaError_t backward_frame(letkf_ctx *h, LkAdjWork *W, const void *y_k, const void *truth_k,
-                           const void *xk, const float *bk, const double *lam_in, double *lam_out,
+                           const void *xk, const void *bk, const double *lam_in, double *lam_out,
                            double crit_scale) {
   const LkInst &I = h->inst[0];
   cudaError_t e = cudaMemcpyAsync(h->X, xk, h->state_total * h->rsz, cudaMemcpyDeviceToDevice,
@@ -818,6 +849,8 @@ letkf_status enqueue_grad(letkf_ctx *h, int frames, const void *y_seq, const voi
   const int C = W->ckpt;
   const size_t st = (size_t)h->state_total * h->rsz;
   const size_t bas = (size_t)I.n_pts * I.mp * I.mp;   // floats
+  const size_t bseg = bas * (h->precision == 1 ? 8 : 4);  // bytes per frame in basis_seg
+  char *bs = static_cast<char *>(W->basis_seg);
   const char *ys = static_cast<const char *>(y_seq);
   const char *ts = static_cast<const char *>(truth_seq);
   char *xs = static_cast<char *>(W->x_seg);
@@ -830,7 +863,7 @@ letkf_status enqueue_grad(letkf_ctx *h, int frames, const void *y_seq, const voi
       LK_ACUDA(h, save_state(h, static_cast<char *>(W->ckpt_x) + (size_t)seg * st,
                              W->ckpt_basis + (size_t)seg * bas, W->ckpt_frame + 2 * seg));
     LK_ACUDA(h, forward_frame(h, y_seq, truth_seq, W->resvar, xs + (size_t)slot * st,
-                              W->basis_seg + (size_t)slot * bas, true));
+                              bs + (size_t)slot * bseg, true));
   }
   LK_ACUDA(h, save_state(h, W->fin_x, W->fin_basis, W->fin_frame));
   // ---- backward ----
@@ -845,12 +878,12 @@ letkf_status enqueue_grad(letkf_ctx *h, int frames, const void *y_seq, const voi
                              W->ckpt_basis + (size_t)seg * bas, W->ckpt_frame + 2 * seg));
       for (int k = s; k < e; ++k)
         LK_ACUDA(h, forward_frame(h, y_seq, nullptr, nullptr, xs + (size_t)(k - s) * st,
-                                  W->basis_seg + (size_t)(k - s) * bas, k + 1 < e));
+                                  bs + (size_t)(k - s) * bseg, k + 1 < e));
     }
     for (int k = e - 1; k >= s; --k) {
       LK_ACUDA(h, backward_frame(h, W, ys + (size_t)k * h->p_total * h->rsz,
                                  ts + (size_t)k * h->n_pts_total * h->rsz,
-                                 xs + (size_t)(k - s) * st, W->basis_seg + (size_t)(k - s) * bas,
+                                 xs + (size_t)(k - s) * st, bs + (size_t)(k - s) * bseg,
                                  W->lam[cur], W->lam[cur ^ 1], crit_scale));
       cur ^= 1;
     }

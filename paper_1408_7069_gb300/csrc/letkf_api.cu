@@ -72,7 +72,7 @@ void release(letkf_ctx *h) {
   if (h->step_pin) cudaFreeHost(h->step_pin);
   if (h->step_dev) cudaFree(h->step_dev);
   void *bufs[] = {h->X,          h->Ybp,      h->dp,       h->taper,    h->pid_map,
-                  h->pts,        h->saps,     h->bank,     h->basis,    h->counters,
+                  h->pts,        h->saps,     h->bank,     h->basis,    h->basis64,  h->counters,
                   h->worklist,   h->frame,    h->partial,  h->tickets,  h->d_inst,   h->obs_items,
                   h->node_items, h->tiles[0], h->tiles[1], h->tiles[2]};
   for (void *p : bufs)
@@ -337,6 +337,7 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   LK_TRY(dalloc(h, &h->pts, h->n_pts_total * sizeof(int2)));
   LK_TRY(dalloc(h, &h->saps, h->sap_total * sizeof(int2)));
   LK_TRY(dalloc(h, &h->basis, n_basis * sizeof(float)));
+  if (h->precision == 1) LK_TRY(dalloc(h, &h->basis64, n_basis * sizeof(double)));
   LK_TRY(dalloc(h, &h->bank, n_bank * sizeof(float)));
   LK_TRY(dalloc(h, &h->counters, 8 * sizeof(int)));
   LK_TRY(dalloc(h, &h->worklist, 3 * h->n_pts_total * sizeof(int2)));
@@ -369,6 +370,7 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
     I.pts = h->pts + o_pts;
     I.saps = h->saps + o_sap;
     I.basis = h->basis + o_basis;
+    I.basis64 = h->basis64 ? h->basis64 + o_basis : nullptr;
     LK_TRY(upload_taper(h, I, G.taper));
     LK_TRY(upload(h, (void *)I.pid_map, G.pid.data(), G.pid.size() * sizeof(int)));
     LK_TRY(upload(h, (void *)I.pts, G.pts.data(), G.pts.size() * sizeof(int2)));

@@ -54,6 +54,7 @@ struct LkInst {
   void *dp;                 // [gs_rows][gs_cols][2]
   const void *taper;        // [w*w] tau / sigma2
   float *basis;             // [n_pts][mp][mp] last eigenbasis (FP32 warm start)
+  double *basis64;          // FP64 handles: [n_pts][mp][mp] FP64 eigenbasis the reverse mode records
   const float *bank;        // [bank_B][bank_G][bank_G] or NULL
   int bank_B, bank_G;
   double alpha;             // (m - 1) / rho
@@ -117,6 +118,7 @@ struct letkf_ctx {
   int *pid_map = nullptr;
   int2 *pts = nullptr, *saps = nullptr;
   float *bank = nullptr, *basis = nullptr;
+  double *basis64 = nullptr;        // FP64 handles: the FP64 eigenbases the reverse mode records
   int *counters = nullptr;          // [0] status bits, [1] FP64 queue length, [2] max sweeps, [3] total sweeps
   int2 *worklist = nullptr;         // [n_pts_total] (inst, point) queued for FP64
   long long *frame = nullptr;       // [0] forecast counter, [1] frame index within letkf_run

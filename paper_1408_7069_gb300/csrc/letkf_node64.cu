@@ -45,12 +45,15 @@ struct N64 {
 // sums [2][NB][MP] and eight vectors of MP.
 template <int MP>
 __host__ __device__ constexpr size_t n64_smem_doubles() {
-  return 3 * (size_t)MP * N64<MP>::LD + 2 * (size_t)N64<MP>::NB * MP + 8 * (size_t)MP;
+  // A, V, G; the column sums; 8 vectors; FP32 copies of V and of I - G (one
+  // [MP][LD] double array holds both)
+  return 4 * (size_t)MP * N64<MP>::LD + 2 * (size_t)N64<MP>::NB * MP + 8 * (size_t)MP;
 }
 
 template <int MP>
 struct N64Smem {
   double *As, *Vs, *Gs, *red, *vec;
+  float *Vf, *Ef;
   __device__ explicit N64Smem(double *base) {
     constexpr int LD = N64<MP>::LD;
     As = base;
@@ -58,6 +61,8 @@ struct N64Smem {
     Gs = Vs + MP * LD;
     red = Gs + MP * LD;
     vec = red + 2 * N64<MP>::NB * MP;
+    Vf = reinterpret_cast<float *>(vec + 8 * MP);
+    Ef = Vf + MP * LD;
   }
 };
 
@@ -86,7 +91,11 @@ __device__ __forceinline__ double colsum(double x, double *red, int &buf) {
 // leaves about 1e-6 (its last sweep rotated by cosines up to 1e-3), so one step
 // gives about 1e-12, enough for FP32 outputs, and two reach FP64 rounding,
 // which the FP64 outputs need (the Jacobi rotations keep whatever error V
-// starts with, and W = V Lambda^-1/2 V^T inherits it).
+// starts with, and W = V Lambda^-1/2 V^T inherits it). A step is
+// V <- V + V E / 2 with E = I - V^T V: V^T V in FP64, since E is what is left of
+// it, but the product V E in FP32, since it is a correction of size |E| that
+// FP32 carries to |E| eps32 (1e-13 after the first step, 1e-19 after the second).
+// The FP64 FMAs of a step halve.
 template <int MP, typename S, bool WARM>
 __device__ void node64(const LkInst &I, int pid, S *__restrict__ mean_out,
                        S *__restrict__ spread_out, double tol, double stop, int max_sweeps,
@@ -151,12 +160,19 @@ __device__ void node64(const LkInst &I, int pid, S *__restrict__ mean_out,
       }
       __syncthreads();
 #pragma unroll
-      for (int i = 0; i < RB; ++i) {                 // V'[r][c] = 1.5 V[r][c] - 0.5 (V G)[r][c]
+      for (int i = 0; i < RB; ++i) {                 // FP32 copies of E = I - G and of V
+        const int j = r0 + i;
+        sm.Ef[j * LD + c] = (float)((j == c ? 1.0 : 0.0) - sm.Gs[j * LD + c]);
+        sm.Vf[j * LD + c] = (float)v[i];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {                 // V'[r][c] = V[r][c] + 0.5 (V E)[r][c]
         const int r = r0 + i;
-        double t = 0.0;
+        float t = 0.f;
 #pragma unroll 8
-        for (int j = 0; j < MP; ++j) t = fma(sm.Vs[r * LD + j], sm.Gs[j * LD + c], t);
-        v[i] = fma(-0.5, t, 1.5 * v[i]);
+        for (int j = 0; j < MP; ++j) t = fmaf(sm.Vf[r * LD + j], sm.Ef[j * LD + c], t);
+        v[i] = fma(0.5, (double)t, v[i]);
       }
       __syncthreads();
 #pragma unroll
@@ -261,13 +277,23 @@ __device__ void node64(const LkInst &I, int pid, S *__restrict__ mean_out,
     if (!converged) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
   }
   if (keep_basis) {
-    // the eigenvectors (rounded to FP32) for the reverse mode, which refines
-    // them in FP64 instead of sweeping from the identity again
-    float *U = I.basis + (size_t)pid * MP * MP;
+    // the eigenvectors for the reverse mode: in FP64 on FP64 handles (it takes
+    // them as they are), else rounded to FP32 (it refines them in FP64 instead
+    // of sweeping from the identity again)
+    if (I.basis64) {
+      double *U = I.basis64 + (size_t)pid * MP * MP;
 #pragma unroll
-    for (int i = 0; i < RB; ++i) {
-      const int r = r0 + i;
-      U[r * MP + c] = isfinite(v[i]) ? (float)v[i] : (r == c ? 1.f : 0.f);
+      for (int i = 0; i < RB; ++i) {
+        const int r = r0 + i;
+        U[r * MP + c] = isfinite(v[i]) ? v[i] : (r == c ? 1.0 : 0.0);
+      }
+    } else {
+      float *U = I.basis + (size_t)pid * MP * MP;
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        const int r = r0 + i;
+        U[r * MP + c] = isfinite(v[i]) ? (float)v[i] : (r == c ? 1.f : 0.f);
+      }
     }
   }
   __syncthreads();                           // rot (in vec) is reused below
