@@ -95,6 +95,81 @@ __global__ void __launch_bounds__(NS_THREADS)
   }
 }
 
+// The Newton-Schulz products: C = alpha A B + beta I, n x n, in 32 x 32 tiles
+// of 64 threads (4 x 4 outputs per thread): 400 CTAs at m = 626 instead of 100
+// CTAs of 64 x 64 tiles on 152 SMs. (Forming only the upper triangle of these
+// products of commuting symmetric matrices and mirroring it would halve the
+// flops, but it breaks the coupling of the iteration: in FP32 at the prior
+// draw's kappa ~ 1.5e5, m = 200, the symmetrised iteration overflows after 20
+// steps where the full one converges to |I - Z Y| ~ 3e-6.)
+constexpr int NSS_TILE = 32, NSS_KT = 32, NSS_THREADS = 64;
+
+__global__ void __launch_bounds__(NSS_THREADS)
+    ns_sq_gemm_kernel(int n, const float *__restrict__ A, const float *__restrict__ B,
+                      float *__restrict__ C, float alpha, float beta) {
+  __shared__ __align__(16) float As[NSS_KT][NSS_TILE + 4];
+  __shared__ __align__(16) float Bs[NSS_KT][NSS_TILE + 4];
+  lk_pdl_wait();
+  const int row0 = blockIdx.y * NSS_TILE, col0 = blockIdx.x * NSS_TILE;
+  const int tid = threadIdx.x, tr = tid / 8, tc = tid % 8;
+  // slice loads: A 32 x 32 (rows ar + 8q, columns ak .. ak+3), B 32 x 32
+  // (rows ar + 8q, columns ak .. ak+3), four float4 each per thread
+  const int ar = tid / 8, ak = (tid % 8) * 4;
+  float4 ra[4], rb[4];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ra[q] = *reinterpret_cast<const float4 *>(A + (size_t)(row0 + ar + 8 * q) * n + k0 + ak);
+      rb[q] = *reinterpret_cast<const float4 *>(B + (size_t)(k0 + ar + 8 * q) * n + col0 + ak);
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = ar + 8 * q;
+      As[ak + 0][r] = ra[q].x;
+      As[ak + 1][r] = ra[q].y;
+      As[ak + 2][r] = ra[q].z;
+      As[ak + 3][r] = ra[q].w;
+      *reinterpret_cast<float4 *>(&Bs[r][ak]) = rb[q];
+    }
+  };
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  load(0);
+  for (int k0 = 0; k0 < n; k0 += NSS_KT) {
+    store();
+    __syncthreads();
+    if (k0 + NSS_KT < n) load(k0 + NSS_KT);
+#pragma unroll
+    for (int k = 0; k < NSS_KT; ++k) {
+      const float4 a = *reinterpret_cast<const float4 *>(&As[k][tr * 4]);
+      const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tc * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float o[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = row0 + tr * 4 + i, c = col0 + tc * 4 + j;
+      o[i][j] = alpha * acc[i][j] + (r == c ? beta : 0.f);
+    }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    *reinterpret_cast<float4 *>(C + (size_t)(row0 + tr * 4 + i) * n + col0 + tc * 4) =
+        make_float4(o[i][0], o[i][1], o[i][2], o[i][3]);
+}
+
 // A (FP64) = (m-1)/rho I + the Gram partials, and the row sums of squares;
 // a CTA per row.
 __global__ void __launch_bounds__(256)
@@ -128,17 +203,22 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// s_A = |A|_F (fixed summation order); Y = A / s_A, Z = I; wbar = 0.
-__global__ void __launch_bounds__(256)
-    ns_start_kernel(int mpt, const double *__restrict__ A64, const double *__restrict__ rowsq,
-                    double *__restrict__ scale, float *__restrict__ Y, float *__restrict__ Z,
-                    double *__restrict__ w64) {
+// s_A = |A|_F from the row sums of squares, one warp in a fixed order.
+__global__ void __launch_bounds__(32)
+    ns_scale_kernel(int mpt, const double *__restrict__ rowsq, double *__restrict__ scale) {
   lk_pdl_wait();
   double t = 0.0;
-  for (int i = 0; i < mpt; ++i) t += rowsq[i];
-  const double s = sqrt(t);
-  if (blockIdx.x == 0 && threadIdx.x == 0) *scale = s;
-  const double inv = 1.0 / s;
+  for (int i = threadIdx.x; i < mpt; i += 32) t += rowsq[i];
+  t = lk_warp_sum(t);
+  if (threadIdx.x == 0) *scale = sqrt(t);
+}
+
+// Y = A / s_A, Z = I; wbar = 0.
+__global__ void __launch_bounds__(256)
+    ns_start_kernel(int mpt, const double *__restrict__ A64, const double *__restrict__ scale,
+                    float *__restrict__ Y, float *__restrict__ Z, double *__restrict__ w64) {
+  lk_pdl_wait();
+  const double inv = 1.0 / *scale;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)mpt * mpt;
        e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e / mpt), j = (int)(e % mpt);
@@ -163,28 +243,31 @@ __global__ void __launch_bounds__(256)
   if ((threadIdx.x & 31) == 0 && !(mx <= 1e-3f)) atomicOr(&counters[0], LK_BIT_NOCONVERGE);
 }
 
-// r = c - A w (FP64), thread per row.
+// r = c - A w (FP64), warp per row (lanes over the row, a fixed-order sum).
 __global__ void __launch_bounds__(128)
     ns_residual_kernel(int mpt, const double *__restrict__ A64, const double *__restrict__ c64,
                        const double *__restrict__ w64, float *__restrict__ r) {
   lk_pdl_wait();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= mpt) return;
-  double s = c64[i];
-  for (int j = 0; j < mpt; ++j) s = fma(-A64[(size_t)j * mpt + i], w64[j], s);   // A symmetric
-  r[i] = (float)s;
+  double s = 0.0;
+  for (int j = lane; j < mpt; j += 32) s = fma(A64[(size_t)i * mpt + j], w64[j], s);
+  s = lk_warp_sum(s);
+  if (lane == 0) r[i] = (float)(c64[i] - s);
 }
 
-// out = Z v (FP32), thread per row; with `w`, w += out / s_A (FP64).
+// out = Z v (FP32), warp per row; with `w`, w += out / s_A (FP64).
 __global__ void __launch_bounds__(128)
     ns_matvec_kernel(int mpt, const float *__restrict__ Z, const float *__restrict__ v,
                      float *__restrict__ out, double *__restrict__ w,
                      const double *__restrict__ scale) {
   lk_pdl_wait();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= mpt) return;
   float s = 0.f;
-  for (int j = 0; j < mpt; ++j) s = fmaf(Z[(size_t)j * mpt + i], v[j], s);      // Z symmetric
+  for (int j = lane; j < mpt; j += 32) s = fmaf(Z[(size_t)i * mpt + j], v[j], s);
+  s = lk_warp_sum(s);
+  if (lane != 0) return;
   if (w)
     w[i] += (double)s / *scale;
   else
@@ -262,6 +345,13 @@ cudaError_t gemm(cudaStream_t st, int M, int N, int K, const float *A, int lda, 
                        lda, B, ldb, C, ldc, alpha, beta);
 }
 
+cudaError_t sq_gemm(cudaStream_t st, int n, const float *A, const float *B, float *C, float alpha,
+                    float beta) {
+  const unsigned nt = (unsigned)(n / NSS_TILE);
+  return lk_launch_pdl(ns_sq_gemm_kernel, dim3(nt, nt), NSS_THREADS, 0, st, n, A, B, C, alpha,
+                       beta);
+}
+
 }  // namespace
 
 int lk_ns_tile() { return NS_TILE; }
@@ -301,24 +391,26 @@ cudaError_t lk_launch_ns_global(letkf_ctx *h, const double *gpart, const double 
                                      ? ((long long)mpt * mpt + 255) / 256
                                      : 2048);
   if (e == cudaSuccess)
+    e = lk_launch_pdl(ns_scale_kernel, 1u, 32, 0, st, mpt, (const double *)rowsq, scale);
+  if (e == cudaSuccess)
     e = lk_launch_pdl(ns_start_kernel, eb, 256, 0, st, mpt, (const double *)A64,
-                      (const double *)rowsq, scale, Y, Z, w64);
+                      (const double *)scale, Y, Z, w64);
   // Newton-Schulz, buffers rotating: T = 1.5 I - 0.5 Z Y; U = Y T; Y' = U;
   // Z' = T Z written into the old Y
   for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-    e = gemm(st, mpt, mpt, mpt, Z, mpt, Y, mpt, T, mpt, -0.5f, 1.5f);
-    if (e == cudaSuccess) e = gemm(st, mpt, mpt, mpt, Y, mpt, T, mpt, U, mpt, 1.f, 0.f);
-    if (e == cudaSuccess) e = gemm(st, mpt, mpt, mpt, T, mpt, Z, mpt, Y, mpt, 1.f, 0.f);
+    e = sq_gemm(st, mpt, Z, Y, T, -0.5f, 1.5f);
+    if (e == cudaSuccess) e = sq_gemm(st, mpt, Y, T, U, 1.f, 0.f);
+    if (e == cudaSuccess) e = sq_gemm(st, mpt, T, Z, Y, 1.f, 0.f);
     float *nY = U, *nZ = Y;
     U = Z;
     Y = nY;
     Z = nZ;
   }
-  if (e == cudaSuccess) e = gemm(st, mpt, mpt, mpt, Z, mpt, Y, mpt, T, mpt, 1.f, 0.f);
+  if (e == cudaSuccess) e = sq_gemm(st, mpt, Z, Y, T, 1.f, 0.f);
   if (e == cudaSuccess)
     e = lk_launch_pdl(ns_check_kernel, eb, 256, 0, st, mpt, (const float *)T, h->counters);
   // wbar = A^-1 c by refinement with A^-1 ~ Z Z / s_A
-  const unsigned vb = (unsigned)((mpt + 127) / 128);
+  const unsigned vb = (unsigned)((mpt * 32 + 127) / 128);
   for (int it = 0; it < 4 && e == cudaSuccess; ++it) {
     e = lk_launch_pdl(ns_residual_kernel, vb, 128, 0, st, mpt, (const double *)A64,
                       (const double *)c64, (const double *)w64, rv);
