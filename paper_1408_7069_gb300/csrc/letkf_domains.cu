@@ -713,7 +713,8 @@ int rpl_of(int m) {
   return m <= 16 ? 2 : m <= 32 ? 4 : m <= 64 ? 8 : m <= 104 ? 13 : m <= 128 ? 16 : 0;
 }
 
-constexpr int NS_ITERS = 40;      // Newton-Schulz iterations of the wide global path
+constexpr int NS_ITERS = 40;      // Newton-Schulz iterations of the wide global path (at most 64;
+                                  // converged iterations are skipped on the device)
 
 template <typename T>
 cudaError_t dup(T **dst, const std::vector<T> &src) {

@@ -102,16 +102,49 @@ __global__ void __launch_bounds__(NS_THREADS)
 // flops, but it breaks the coupling of the iteration: in FP32 at the prior
 // draw's kappa ~ 1.5e5, m = 200, the symmetrised iteration overflows after 20
 // steps where the full one converges to |I - Z Y| ~ 3e-6.)
+//
+// Early exit: the first product of iteration it (T = 1.5 I - 0.5 Z Y) records
+// max |Z Y - I| of its tiles in res[it] (non-negative floats compare as their
+// bit patterns); an iteration whose predecessors include one with
+// res <= NS_DONE is skipped, its three products turning into T = I, U = Y and
+// Y' = Z (what they give for T = I), so the buffers' rotation on the host stays
+// right. The iteration that reached NS_DONE still runs, and takes the residual
+// from about 1e-4 to FP32 rounding (it converges quadratically there).
 constexpr int NSS_TILE = 32, NSS_KT = 32, NSS_THREADS = 64;
+constexpr float NS_DONE = 1e-4f;
+enum { NSG_PLAIN = 0, NSG_T = 1, NSG_SKIP_COPY_A = 2, NSG_SKIP_COPY_B = 3 };
+
+__device__ __forceinline__ bool ns_skip(const unsigned *res, int it) {
+  for (int i = 0; i < it; ++i)
+    if (__uint_as_float(res[i]) <= NS_DONE) return true;
+  return false;
+}
 
 __global__ void __launch_bounds__(NSS_THREADS)
     ns_sq_gemm_kernel(int n, const float *__restrict__ A, const float *__restrict__ B,
-                      float *__restrict__ C, float alpha, float beta) {
+                      float *__restrict__ C, float alpha, float beta, int mode,
+                      unsigned *__restrict__ res, int it) {
   __shared__ __align__(16) float As[NSS_KT][NSS_TILE + 4];
   __shared__ __align__(16) float Bs[NSS_KT][NSS_TILE + 4];
   lk_pdl_wait();
   const int row0 = blockIdx.y * NSS_TILE, col0 = blockIdx.x * NSS_TILE;
   const int tid = threadIdx.x, tr = tid / 8, tc = tid % 8;
+  if (mode != NSG_PLAIN && ns_skip(res, it)) {
+    // skipped iteration: T = I, or a copy of the operand that is not T
+    const float *src = mode == NSG_SKIP_COPY_A ? A : B;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = row0 + tr * 4 + i, c = col0 + tc * 4;
+      float4 o;
+      if (mode == NSG_T)
+        o = make_float4(r == c ? 1.f : 0.f, r == c + 1 ? 1.f : 0.f, r == c + 2 ? 1.f : 0.f,
+                        r == c + 3 ? 1.f : 0.f);
+      else
+        o = *reinterpret_cast<const float4 *>(src + (size_t)r * n + c);
+      *reinterpret_cast<float4 *>(C + (size_t)r * n + c) = o;
+    }
+    return;
+  }
   // slice loads: A 32 x 32 (rows ar + 8q, columns ak .. ak+3), B 32 x 32
   // (rows ar + 8q, columns ak .. ak+3), four float4 each per thread
   const int ar = tid / 8, ak = (tid % 8) * 4;
@@ -168,6 +201,22 @@ __global__ void __launch_bounds__(NSS_THREADS)
   for (int i = 0; i < 4; ++i)
     *reinterpret_cast<float4 *>(C + (size_t)(row0 + tr * 4 + i) * n + col0 + tc * 4) =
         make_float4(o[i][0], o[i][1], o[i][2], o[i][3]);
+  if (mode == NSG_T) {                     // max |Z Y - I| of the tile, Z Y = acc
+    float mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = row0 + tr * 4 + i, c = col0 + tc * 4 + j;
+        mx = fmaxf(mx, fabsf(acc[i][j] - (r == c ? 1.f : 0.f)));
+        if (!(acc[i][j] == acc[i][j])) mx = __int_as_float(0x7fc00000);   // NaN stays
+      }
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+      const float v = __shfl_xor_sync(FULL, mx, o2);
+      mx = (v != v || mx != mx) ? __int_as_float(0x7fc00000) : fmaxf(mx, v);
+    }
+    if ((tid & 31) == 0) atomicMax(res + it, __float_as_uint(mx));
+  }
 }
 
 // A (FP64) = (m-1)/rho I + the Gram partials, and the row sums of squares;
@@ -185,7 +234,10 @@ __global__ void __launch_bounds__(256)
     const int a = i <= j ? i : j, b = i <= j ? j : i;
     double s = 0.0;
     for (int k = 0; k < kchunks; ++k) s += gpart[((size_t)k * mpt + a) * mpt + b];
-    if (i == j) s += i < I.m ? I.alpha : 1.0;
+    // (m-1)/rho on the diagonal, the padding included: the padding's
+    // eigenvalues then sit with the smallest real ones instead of at 1, far
+    // below |A|_F, where the iteration would need the most steps to reach them
+    if (i == j) s += I.alpha;
     A64[(size_t)i * mpt + j] = s;
     sq = fma(s, s, sq);
   }
@@ -203,14 +255,17 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// s_A = |A|_F from the row sums of squares, one warp in a fixed order.
+// s_A = |A|_F from the row sums of squares, one warp in a fixed order; clears
+// the iterations' residual words.
 __global__ void __launch_bounds__(32)
-    ns_scale_kernel(int mpt, const double *__restrict__ rowsq, double *__restrict__ scale) {
+    ns_scale_kernel(int mpt, const double *__restrict__ rowsq, double *__restrict__ scale,
+                    unsigned *__restrict__ res, int iters) {
   lk_pdl_wait();
   double t = 0.0;
   for (int i = threadIdx.x; i < mpt; i += 32) t += rowsq[i];
   t = lk_warp_sum(t);
   if (threadIdx.x == 0) *scale = sqrt(t);
+  for (int i = threadIdx.x; i < iters; i += 32) res[i] = 0u;
 }
 
 // Y = A / s_A, Z = I; wbar = 0.
@@ -346,10 +401,10 @@ cudaError_t gemm(cudaStream_t st, int M, int N, int K, const float *A, int lda, 
 }
 
 cudaError_t sq_gemm(cudaStream_t st, int n, const float *A, const float *B, float *C, float alpha,
-                    float beta) {
+                    float beta, int mode = NSG_PLAIN, unsigned *res = nullptr, int it = 0) {
   const unsigned nt = (unsigned)(n / NSS_TILE);
   return lk_launch_pdl(ns_sq_gemm_kernel, dim3(nt, nt), NSS_THREADS, 0, st, n, A, B, C, alpha,
-                       beta);
+                       beta, mode, res, it);
 }
 
 }  // namespace
@@ -367,7 +422,7 @@ static size_t ns_fp64_bytes(int mpt) {
 size_t lk_ns_workspace_bytes(int mpt, long long n_pad) {
   const size_t f = 4 * (size_t)mpt * mpt * 4 + 2 * (size_t)mpt * 4 +
                    2 * (size_t)n_pad * mpt * 4 + (size_t)n_pad * 4;
-  return ns_fp64_bytes(mpt) + f + 1024;
+  return ns_fp64_bytes(mpt) + f + 64 * sizeof(unsigned) + 1024;
 }
 
 cudaError_t lk_launch_ns_global(letkf_ctx *h, const double *gpart, const double *cpart,
@@ -383,6 +438,7 @@ cudaError_t lk_launch_ns_global(letkf_ctx *h, const double *gpart, const double 
   float *Z = Y + (size_t)mpt * mpt, *T = Z + (size_t)mpt * mpt, *U = T + (size_t)mpt * mpt;
   float *rv = U + (size_t)mpt * mpt, *vv = rv + mpt;
   float *Xp = vv + mpt, *Pr = Xp + (size_t)n_pad * mpt, *xm = Pr + (size_t)n_pad * mpt;
+  unsigned *res = reinterpret_cast<unsigned *>(xm + n_pad);   // [iters] residuals (early exit)
   cudaStream_t st = h->stream;
   cudaError_t e = lk_launch_pdl(ns_assemble_kernel, (unsigned)mpt, 256, 0, st,
                                 (const LkInst *)h->d_inst, gpart, cpart, kchunks, mpt, A64, c64,
@@ -391,16 +447,17 @@ cudaError_t lk_launch_ns_global(letkf_ctx *h, const double *gpart, const double 
                                      ? ((long long)mpt * mpt + 255) / 256
                                      : 2048);
   if (e == cudaSuccess)
-    e = lk_launch_pdl(ns_scale_kernel, 1u, 32, 0, st, mpt, (const double *)rowsq, scale);
+    e = lk_launch_pdl(ns_scale_kernel, 1u, 32, 0, st, mpt, (const double *)rowsq, scale, res,
+                      iters);
   if (e == cudaSuccess)
     e = lk_launch_pdl(ns_start_kernel, eb, 256, 0, st, mpt, (const double *)A64,
                       (const double *)scale, Y, Z, w64);
   // Newton-Schulz, buffers rotating: T = 1.5 I - 0.5 Z Y; U = Y T; Y' = U;
   // Z' = T Z written into the old Y
   for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-    e = sq_gemm(st, mpt, Z, Y, T, -0.5f, 1.5f);
-    if (e == cudaSuccess) e = sq_gemm(st, mpt, Y, T, U, 1.f, 0.f);
-    if (e == cudaSuccess) e = sq_gemm(st, mpt, T, Z, Y, 1.f, 0.f);
+    e = sq_gemm(st, mpt, Z, Y, T, -0.5f, 1.5f, NSG_T, res, it);
+    if (e == cudaSuccess) e = sq_gemm(st, mpt, Y, T, U, 1.f, 0.f, NSG_SKIP_COPY_A, res, it);
+    if (e == cudaSuccess) e = sq_gemm(st, mpt, T, Z, Y, 1.f, 0.f, NSG_SKIP_COPY_B, res, it);
     float *nY = U, *nZ = Y;
     U = Z;
     Y = nY;
