@@ -436,14 +436,15 @@ def domains_arm(torch, L, K: int = 200, Wm: int = 20):
                           "resvar_last": float(resv[-1].item())})
             entry["launch"] = ("update: one CTA per domain + piston solve + piston apply; "
                                "frames: letkf_run_graph (one launch, in-graph stamps)")
-        elif w.m <= 128:
+        elif w.m <= 64:
             entry["launch"] = ("update: FP64 Gram (split over slope chunks), one-CTA FP32 "
                                "Jacobi with FP64-refined mean solve, row-blocked apply; "
                                "timed on the prior draw")
         else:
-            entry["launch"] = ("update: FP64 Gram (split over slope chunks), 40 coupled "
-                               "Newton-Schulz iterations on FP32 matrix products, FP64-refined "
-                               "mean solve, matrix-product apply; timed on the prior draw")
+            entry["launch"] = ("update: FP64 Gram (split over slope chunks), coupled "
+                               "Newton-Schulz iterations on FP32 matrix products (at most 40, "
+                               "converged ones skipped), FP64-refined mean solve, "
+                               "matrix-product apply; timed on the prior draw")
         entry["paper_context"] = ("Section 5.3, Table 2 (2 x Xeon E5-2680 v2): update of one "
                                   "domain 0.94 ms on one core; full 16 m cycle 1.18 ms with "
                                   ">= 69 cores; 40 m: 2.64 ms plus ~2 ms of cluster communication")

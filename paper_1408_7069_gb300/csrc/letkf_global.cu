@@ -1,14 +1,16 @@
 // The global ETKF (Section 3.1.1: one domain observing every slope, partition
-// 1) for ensembles too wide for the one-CTA Jacobi (m > 128; the paper's
-// global curves reach m ~ 626, Section 5.1). The transform needs only
+// 1) for ensembles of more than 64 members (the paper's global curves reach
+// m ~ 626, Section 5.1; from m = 101 on this path is faster than the one-CTA
+// Jacobi, which also stops at 128 columns). The transform needs only
 // A^-1/2 and A^-1 c, so the eigendecomposition is replaced by matrix products:
 //   Gram     A = (m-1)/rho I + S^T S, c = S^T s in FP64 (the split-K Gram of
 //            letkf_domains.cu), s_A = |A|_F >= lambda_max
 //   root     coupled Newton-Schulz on Y0 = A / s_A, Z0 = I:
 //            T = (3 I - Z Y) / 2, Y <- Y T, Z <- T Z, converging to
 //            Y -> (A/s_A)^1/2 and Z -> (A/s_A)^-1/2 (the spectrum of A / s_A
-//            lies in (0, 1]); a fixed number of iterations, FP32 matrix
-//            products on a 64 x 64 tiled kernel, and a check of |I - Z Y|
+//            lies in (0, 1]); at most a fixed number of iterations (converged
+//            ones skipped on the device), FP32 matrix products in 32 x 32
+//            tiles, and a check of |I - Z Y|
 //   mean     wbar = A^-1 c by iterative refinement: residual c - A wbar in
 //            FP64, correction Z (Z r) / s_A in FP32
 //   apply    T = wbar 1^T + sqrt((m-1) / s_A) Z, Xa = xbar + X' T (the same

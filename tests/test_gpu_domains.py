@@ -201,7 +201,7 @@ def test_global_etkf_at_paper_size(frames):
 @pytest.mark.parametrize("m,frames", [(200, 0), (200, 2), (626, 0)],
                          ids=["m200-prior", "m200-f2", "m626-prior"])
 def test_global_etkf_wide_ensembles(m, frames):
-    """The global ETKF beyond the one-CTA eigensolver (m > 128, up to the
+    """The global ETKF beyond the one-CTA eigensolver's 128 columns (up to the
     paper's 626 members): Newton-Schulz root and FP64-refined mean solve
     against the oracle's eigendecomposition, 16 m pupil, all 1624 slopes."""
     w = replace(W.DOM_16M, name=f"global-16m-m{m}", m=m, partition=1, piston=0, taper=0)
