@@ -252,7 +252,9 @@ __device__ __forceinline__ void stage_pair_tile(const LkInst &I, int i0, int j0,
 template <int MP, int TI, int TJ>
 struct PairLaunch {
   static constexpr int threads = TI * TJ * 32 / PairCfg<MP>::NPW;
-  static constexpr int min_ctas = MP <= 32 ? 65536 / (threads * 128) : 1;
+  static constexpr int regs = MP <= 32 ? 128 : (MP == 48 ? 168 : 0);   // budget per thread
+  static constexpr int min_ctas =
+      regs == 0 || 65536 / (threads * (regs ? regs : 1)) == 0 ? 1 : 65536 / (threads * regs);
 };
 
 // BASIS (FP64 handles, S = double): the FP32 eigensolve alone, storing every
