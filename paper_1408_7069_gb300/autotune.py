@@ -23,7 +23,7 @@ def cache_path() -> str:
 
 
 # Bumped whenever the analysis kernels change, so that cached choices are retimed.
-KERNEL_REVISION = 4
+KERNEL_REVISION = 5
 
 
 def signature(gpu_name: str, shapes) -> str:
