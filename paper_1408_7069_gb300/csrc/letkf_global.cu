@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(NS_THREADS)
 // Y' = Z (what they give for T = I), so the buffers' rotation on the host stays
 // right. The iteration that reached NS_DONE still runs, and takes the residual
 // from about 1e-4 to FP32 rounding (it converges quadratically there).
-constexpr int NSS_TILE = 32, NSS_KT = 32, NSS_THREADS = 64;
+constexpr int NSS_TILE = 32, NSS_KT = 32, NSS_SPLIT = 4, NSS_GROUP = 64;
+constexpr int NSS_THREADS = NSS_SPLIT * NSS_GROUP, NSS_LD = NSS_TILE + 4;
 constexpr float NS_DONE = 1e-4f;
 enum { NSG_PLAIN = 0, NSG_T = 1, NSG_SKIP_COPY_A = 2, NSG_SKIP_COPY_B = 3 };
 
@@ -122,51 +123,56 @@ __device__ __forceinline__ bool ns_skip(const unsigned *res, int it) {
   return false;
 }
 
+// One 32 x 32 output tile per CTA, the K dimension split over four groups of
+// 64 threads (group q takes the 32-deep slices q, q + 4, ...; 4 x 4 outputs
+// per thread), whose partial tiles are added in group order through shared
+// memory: 400 CTAs of 8 warps at m = 626.
 __global__ void __launch_bounds__(NSS_THREADS)
     ns_sq_gemm_kernel(int n, const float *__restrict__ A, const float *__restrict__ B,
                       float *__restrict__ C, float alpha, float beta, int mode,
                       unsigned *__restrict__ res, int it) {
-  __shared__ __align__(16) float As[NSS_KT][NSS_TILE + 4];
-  __shared__ __align__(16) float Bs[NSS_KT][NSS_TILE + 4];
+  __shared__ __align__(16) float As[NSS_SPLIT][NSS_KT][NSS_LD];
+  __shared__ __align__(16) float Bs[NSS_SPLIT][NSS_KT][NSS_LD];
   lk_pdl_wait();
   const int row0 = blockIdx.y * NSS_TILE, col0 = blockIdx.x * NSS_TILE;
-  const int tid = threadIdx.x, tr = tid / 8, tc = tid % 8;
+  const int tid = threadIdx.x;
+  const int orow = tid / 8, ocol = (tid % 8) * 4;   // this thread's output float4
   if (mode != NSG_PLAIN && ns_skip(res, it)) {
     // skipped iteration: T = I, or a copy of the operand that is not T
-    const float *src = mode == NSG_SKIP_COPY_A ? A : B;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = row0 + tr * 4 + i, c = col0 + tc * 4;
-      float4 o;
-      if (mode == NSG_T)
-        o = make_float4(r == c ? 1.f : 0.f, r == c + 1 ? 1.f : 0.f, r == c + 2 ? 1.f : 0.f,
-                        r == c + 3 ? 1.f : 0.f);
-      else
-        o = *reinterpret_cast<const float4 *>(src + (size_t)r * n + c);
-      *reinterpret_cast<float4 *>(C + (size_t)r * n + c) = o;
-    }
+    const int r = row0 + orow, c = col0 + ocol;
+    float4 o;
+    if (mode == NSG_T)
+      o = make_float4(r == c ? 1.f : 0.f, r == c + 1 ? 1.f : 0.f, r == c + 2 ? 1.f : 0.f,
+                      r == c + 3 ? 1.f : 0.f);
+    else
+      o = *reinterpret_cast<const float4 *>((mode == NSG_SKIP_COPY_A ? A : B) + (size_t)r * n + c);
+    *reinterpret_cast<float4 *>(C + (size_t)r * n + c) = o;
     return;
   }
-  // slice loads: A 32 x 32 (rows ar + 8q, columns ak .. ak+3), B 32 x 32
-  // (rows ar + 8q, columns ak .. ak+3), four float4 each per thread
-  const int ar = tid / 8, ak = (tid % 8) * 4;
+  const int q = tid / NSS_GROUP, lt = tid % NSS_GROUP, tr = lt / 8, tc = lt % 8;
+  float(*as)[NSS_LD] = As[q];
+  float(*bs)[NSS_LD] = Bs[q];
+  // slice loads: A 32 x 32 (rows ar + 8j, columns ak .. ak+3), B 32 x 32
+  // (rows ar + 8j, columns ak .. ak+3), four float4 each per thread of the group
+  const int ar = lt / 8, ak = (lt % 8) * 4;
+  const int nk = n / NSS_KT, steps = (nk + NSS_SPLIT - 1) / NSS_SPLIT;
   float4 ra[4], rb[4];
   auto load = [&](int k0) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      ra[q] = *reinterpret_cast<const float4 *>(A + (size_t)(row0 + ar + 8 * q) * n + k0 + ak);
-      rb[q] = *reinterpret_cast<const float4 *>(B + (size_t)(k0 + ar + 8 * q) * n + col0 + ak);
+    for (int j = 0; j < 4; ++j) {
+      ra[j] = *reinterpret_cast<const float4 *>(A + (size_t)(row0 + ar + 8 * j) * n + k0 + ak);
+      rb[j] = *reinterpret_cast<const float4 *>(B + (size_t)(k0 + ar + 8 * j) * n + col0 + ak);
     }
   };
   auto store = [&]() {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = ar + 8 * q;
-      As[ak + 0][r] = ra[q].x;
-      As[ak + 1][r] = ra[q].y;
-      As[ak + 2][r] = ra[q].z;
-      As[ak + 3][r] = ra[q].w;
-      *reinterpret_cast<float4 *>(&Bs[r][ak]) = rb[q];
+    for (int j = 0; j < 4; ++j) {
+      const int r = ar + 8 * j;
+      as[ak + 0][r] = ra[j].x;
+      as[ak + 1][r] = ra[j].y;
+      as[ak + 2][r] = ra[j].z;
+      as[ak + 3][r] = ra[j].w;
+      *reinterpret_cast<float4 *>(&bs[r][ak]) = rb[j];
     }
   };
   float acc[4][4];
@@ -174,45 +180,54 @@ __global__ void __launch_bounds__(NSS_THREADS)
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  load(0);
-  for (int k0 = 0; k0 < n; k0 += NSS_KT) {
-    store();
+  // every group runs `steps` rounds (the barriers are the CTA's); a group
+  // whose slice index runs past nk idles in that round
+  if (q < nk) load(q * NSS_KT);
+  for (int s = 0; s < steps; ++s) {
+    const int kt = q + NSS_SPLIT * s;
+    const bool valid = kt < nk;
+    if (valid) store();
     __syncthreads();
-    if (k0 + NSS_KT < n) load(k0 + NSS_KT);
+    if (kt + NSS_SPLIT < nk) load((kt + NSS_SPLIT) * NSS_KT);
+    if (valid) {
 #pragma unroll
-    for (int k = 0; k < NSS_KT; ++k) {
-      const float4 a = *reinterpret_cast<const float4 *>(&As[k][tr * 4]);
-      const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tc * 4]);
-      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+      for (int k = 0; k < NSS_KT; ++k) {
+        const float4 a = *reinterpret_cast<const float4 *>(&as[k][tr * 4]);
+        const float4 b = *reinterpret_cast<const float4 *>(&bs[k][tc * 4]);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      }
     }
     __syncthreads();
   }
-  float o[4][4];
+  // the groups' partial tiles, added in group order (As is free now)
 #pragma unroll
   for (int i = 0; i < 4; ++i)
+    *reinterpret_cast<float4 *>(&As[q][tr * 4 + i][tc * 4]) =
+        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  __syncthreads();
+  float4 t = *reinterpret_cast<const float4 *>(&As[0][orow][ocol]);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int r = row0 + tr * 4 + i, c = col0 + tc * 4 + j;
-      o[i][j] = alpha * acc[i][j] + (r == c ? beta : 0.f);
-    }
+  for (int g = 1; g < NSS_SPLIT; ++g) {
+    const float4 u = *reinterpret_cast<const float4 *>(&As[g][orow][ocol]);
+    t = make_float4(t.x + u.x, t.y + u.y, t.z + u.z, t.w + u.w);
+  }
+  const int r = row0 + orow, c = col0 + ocol;
+  const float tv[4] = {t.x, t.y, t.z, t.w};
+  float ov[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-    *reinterpret_cast<float4 *>(C + (size_t)(row0 + tr * 4 + i) * n + col0 + tc * 4) =
-        make_float4(o[i][0], o[i][1], o[i][2], o[i][3]);
-  if (mode == NSG_T) {                     // max |Z Y - I| of the tile, Z Y = acc
+  for (int j = 0; j < 4; ++j) ov[j] = alpha * tv[j] + (r == c + j ? beta : 0.f);
+  *reinterpret_cast<float4 *>(C + (size_t)r * n + c) = make_float4(ov[0], ov[1], ov[2], ov[3]);
+  if (mode == NSG_T) {                     // max |Z Y - I| of the tile, Z Y = the sum
     float mx = 0.f;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int r = row0 + tr * 4 + i, c = col0 + tc * 4 + j;
-        mx = fmaxf(mx, fabsf(acc[i][j] - (r == c ? 1.f : 0.f)));
-        if (!(acc[i][j] == acc[i][j])) mx = __int_as_float(0x7fc00000);   // NaN stays
-      }
+    for (int j = 0; j < 4; ++j) {
+      mx = fmaxf(mx, fabsf(tv[j] - (r == c + j ? 1.f : 0.f)));
+      if (!(tv[j] == tv[j])) mx = __int_as_float(0x7fc00000);   // NaN stays
+    }
     for (int o2 = 16; o2 > 0; o2 >>= 1) {
       const float v = __shfl_xor_sync(FULL, mx, o2);
       mx = (v != v || mx != mx) ? __int_as_float(0x7fc00000) : fmaxf(mx, v);
