@@ -437,11 +437,11 @@ def domains_arm(torch, L, K: int = 200, Wm: int = 20):
             entry["launch"] = ("update: one CTA per domain + piston solve + piston apply; "
                                "frames: letkf_run_graph (one launch, in-graph stamps)")
         elif w.m <= 64:
-            entry["launch"] = ("update: FP64 Gram (split over slope chunks), one-CTA FP32 "
+            entry["launch"] = ("update: compensated-FP32 Gram (split over slope chunks), one-CTA FP32 "
                                "Jacobi with FP64-refined mean solve, row-blocked apply; "
                                "timed on the prior draw")
         else:
-            entry["launch"] = ("update: FP64 Gram (split over slope chunks), coupled "
+            entry["launch"] = ("update: compensated-FP32 Gram (split over slope chunks), coupled "
                                "Newton-Schulz iterations on FP32 matrix products (at most 40, "
                                "converged ones skipped), FP64-refined mean solve, "
                                "matrix-product apply; timed on the prior draw")
