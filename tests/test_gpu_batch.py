@@ -305,3 +305,42 @@ def test_config5_reduced_mix_closed_loop():
             w.a_ar1, w.noise_std, w.seeds[2], 10,
             X0=inp.X0.astype(np.float32).astype(np.float64), batched=True)
         assert np.max(np.abs(rv[:, k] - rv_ref) / rv_ref) <= 1e-3, (w.name, rv[:, k], rv_ref)
+
+
+FP64_BATCH = [replace(W.TOY_8X8, name="f64-a", seeds=(151, 152, 153)),
+              replace(W.TOY_8X8, name="f64-b", nsub=6, m=16, window=5, seeds=(154, 155, 156)),
+              replace(W.TOY_8X8, name="f64-c", nsub=10, m=24, window=3, seeds=(157, 158, 159))]
+
+
+def test_fp64_batch_matches_oracle_and_separate_handles():
+    """FP64 instances of both FP64 width classes (m = 10, 16: 16 columns; m = 24:
+    32 columns) in one handle: the FP32 basis pass runs over every instance's
+    tiles before the warm FP64 sweeps. Per instance the closed loop matches the
+    oracle at FP64 rounding and the batch equals the instances' own handles
+    bitwise."""
+    frames = 6
+    ins = [synth.make_loop_inputs(w, frames=frames) for w in FP64_BATCH]
+    f = L.Letkf.batch(FP64_BATCH, [i.bank for i in ins])
+    X0 = np.concatenate([i.X0.ravel() for i in ins])
+    y = torch.from_numpy(np.concatenate([i.slopes for i in ins], 1)).cuda()
+    t = torch.from_numpy(np.concatenate([i.truth for i in ins], 1)).cuda()
+    f.set_state(torch.from_numpy(X0).cuda())
+    rv = f.run(frames, y, t, use_graph=True).cpu().numpy()
+    f.sync()
+    Xb = f.get_state().cpu().numpy()
+    f.close()
+    parts = []
+    for k, (inp, w) in enumerate(zip(ins, FP64_BATCH)):
+        geom = oracle.build_geometry(inp.subap_mask, w.window, w.taper, w.loc_len)
+        rv_ref, _, _ = oracle.closed_loop(geom, inp.truth, inp.slopes, inp.bank, w.m, w.sigma2,
+                                          w.rho, w.a_ar1, w.noise_std, w.seeds[2], frames,
+                                          X0=inp.X0, batched=True)
+        assert np.max(np.abs(rv[:, k] - rv_ref) / rv_ref) <= 1e-8, w.name
+        g = L.Letkf.from_workload(w, bank=inp.bank)
+        g.set_state(torch.from_numpy(inp.X0).cuda())
+        g.run(frames, torch.from_numpy(inp.slopes).cuda(), torch.from_numpy(inp.truth).cuda(),
+              use_graph=True)
+        g.sync()
+        parts.append(g.get_state().cpu().numpy().ravel())
+        g.close()
+    assert np.array_equal(Xb, np.concatenate(parts))
