@@ -141,8 +141,9 @@ letkf_status letkf_query_domains(letkf_t h, int32_t *n_dom, int32_t *node_dom_ho
 letkf_status letkf_query_points(letkf_t h, int32_t *ij_host, int32_t *window_slopes_host);
 
 /* Copy the ensemble [n_pts][2][m] (real) from / into device memory.
- * letkf_set_state also resets every node's stored eigenbasis (the starting
- * point of the next FP32 eigensolve) to the identity, so the analyses that
+ * letkf_set_state also resets every node's stored eigenbasis (the FP32 basis
+ * that an analysis hands to its FP64 sweeps and to the reverse mode) to the
+ * identity; every analysis writes the bases it reads, so the results that
  * follow depend on the new ensemble only. */
 letkf_status letkf_get_state(letkf_t h, void *X_dev);
 letkf_status letkf_set_state(letkf_t h, const void *X_dev);
