@@ -29,3 +29,16 @@ def frame_analysis_ops(m: int, window_slopes) -> int:
     """Per-frame analysis ops of the per-node LETKF: every node is one local
     domain with n_d = 2 state rows and p_l = its window's slope count."""
     return sum(update_ops(m, 2, int(p)) for p in window_slopes)
+
+
+def frame_executed_flops(mp: int, window_slopes, mean_sweeps: float) -> float:
+    """Flops the FP32 analysis kernel executes per frame (an FMA counts as two),
+    from its loop structure, beside the paper's count: per node the Gram over
+    the window, 2 mp^2 flops per slope (both triangles of the mp x mp matrix),
+    and per Jacobi sweep mp rounds of mp/2 column pairs, each a dot product
+    (2 mp) and a rotation of both columns (6 mp), 4 mp^3 in all; the
+    eigenvector normalisation, transform and apply (about 10 mp^2) are added.
+    mean_sweeps: the measured mean sweep count per node."""
+    per_sweep = 4.0 * mp ** 3
+    return float(sum(2.0 * mp * mp * int(p) + mean_sweeps * per_sweep + 10.0 * mp * mp
+                     for p in window_slopes))
