@@ -58,7 +58,12 @@ def parse_args(argv=None):
     ap.add_argument("--phase-split", action="store_true",
                     help="print where the FP32 analysis kernel spends its cycles (builds and "
                          "loads the phase-clock variant of the library) instead of the bench line")
+    ap.add_argument("--phase-split-adjoint", action="store_true",
+                    help="print where the reverse mode's node kernel spends its cycles on the "
+                         "16 m system (FP32 and FP64 handles; phase-clock build) instead of the "
+                         "bench line")
     ap.add_argument("--phase-worker", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--adjoint-phase-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-worker-all", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -586,11 +591,57 @@ def phase_worker(args):
     return 0
 
 
+def adjoint_phase_worker(args):
+    """Runs with LETKF_LIBRARY pointing at the phase-clock build: for the FP32
+    and the FP64 16 m handle, `warmup` closed-loop frames from the prior draw,
+    then letkf_grad over the next `steps` frames (checkpoint every 20), and the
+    reverse-mode node kernel's cycles per phase and node."""
+    import numpy as np
+    import torch
+    from dataclasses import replace
+    from paper_1408_7069_gb300 import synth, workloads as W
+    from paper_1408_7069_gb300 import letkf as L
+    torch.cuda.set_device(0)
+    K, Wm = args.steps, args.warmup
+    names = ["window_staging", "gram_and_start", "jacobi", "transform_adjoint", "window_slopes"]
+    out = {}
+    for prec in (0, 1):
+        w = replace(W.ADJ_16M, precision=prec)
+        inp = synth.make_loop_inputs(w, frames=Wm + K)
+        rt = np.float64 if prec else np.float32
+        c = lambda a: torch.from_numpy(np.ascontiguousarray(np.asarray(a).astype(np.float32).astype(rt))).cuda()  # noqa: E731,E501
+        y, t = c(inp.slopes), c(inp.truth)
+        f = L.Letkf.from_workload(w, bank=inp.bank)
+        if not prec:
+            f.set_jacobi(4e-6, 0.0)
+        f.set_state(c(inp.X0))
+        f.run(Wm, y[:Wm].contiguous(), t[:Wm].contiguous(), use_graph=False)
+        f.sync()
+        if L.letkf_adjoint_phase_clocks() is None:
+            raise RuntimeError("the loaded library has no phase clocks")
+        f.grad(K, y[Wm:].contiguous(), t[Wm:].contiguous(), 20)
+        f.sync()
+        f.close()
+        pc = L.letkf_adjoint_phase_clocks()
+        for form, o in (("fp32", 0), ("fp64", 6)):
+            q = pc[o:o + 6]
+            if q[5] == 0:
+                continue
+            tot = sum(q[:5])
+            out[f"{'fp64' if prec else 'fp32'}_handle_{form}_form"] = {
+                "nodes": q[5], "cycles_per_node": {n: q[i] / q[5] for i, n in enumerate(names)},
+                "share": {n: q[i] / tot for i, n in enumerate(names)}}
+    print(json.dumps({"workload": W.ADJ_16M.name, "warmup_frames": Wm, "grad_frames": K,
+                      "adjoint_node_kernel": out}))
+    return 0
+
+
 def phase_split(args):
     from paper_1408_7069_gb300.build import build_library
     lib = build_library(phase_clocks=True)
     env = dict(os.environ, LETKF_LIBRARY=lib)
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--phase-worker", "--steps",
+    worker = "--adjoint-phase-worker" if args.phase_split_adjoint else "--phase-worker"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), worker, "--steps",
                         str(args.steps), "--warmup", str(args.warmup)], env=env, timeout=900)
     return r.returncode
 
@@ -974,6 +1025,8 @@ def main(argv=None):
         return 0
     if args.phase_worker:
         return phase_worker(args)
+    if args.adjoint_phase_worker:
+        return adjoint_phase_worker(args)
     if args.only_domains:
         import torch
         from paper_1408_7069_gb300 import letkf as L
@@ -986,7 +1039,7 @@ def main(argv=None):
         torch.cuda.set_device(0)
         print(json.dumps(small_configs_arm(torch, L, K=args.steps, Wm=args.warmup)))
         return 0
-    if args.phase_split:
+    if args.phase_split or args.phase_split_adjoint:
         return phase_split(args)
     if args.impl == "reference":
         return reference_arm(args)

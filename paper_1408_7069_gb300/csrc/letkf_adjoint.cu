@@ -169,14 +169,27 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
   const S *Ybp = static_cast<const S *>(I.Ybp);
   const S *dp = static_cast<const S *>(I.dp);
   const S *taper = static_cast<const S *>(I.taper);
-  for (int e = lane; e < wc * 2 * MP; e += 32) {
-    const int cell = e / (2 * MP);
-    const int r = e - cell * 2 * MP;
-    const int c = r / MP;
-    const int mm = r - c * MP;
-    const int ds = cell / w, dt = cell - (cell / w) * w;
-    const size_t src = (size_t)(ij.x + ds) * I.gs_cols + (ij.y + dt);
-    win[e] = mm < m ? Ybp[(src * 2 + c) * m + mm] : S(0);
+  // eight loads in flight per lane before their stores (the window's cells are
+  // independent; one at a time, each waited out its L2 latency)
+  for (int e0 = lane; e0 < wc * 2 * MP; e0 += 8 * 32) {
+    S v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + 32 * u;
+      v[u] = S(0);
+      if (e < wc * 2 * MP) {
+        const int cell = e / (2 * MP);
+        const int r = e - cell * 2 * MP;
+        const int c = r / MP;
+        const int mm = r - c * MP;
+        const int ds = cell / w, dt = cell - (cell / w) * w;
+        const size_t src = (size_t)(ij.x + ds) * I.gs_cols + (ij.y + dt);
+        if (mm < m) v[u] = Ybp[(src * 2 + c) * m + mm];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (e0 + 32 * u < wc * 2 * MP) win[e0 + 32 * u] = v[u];
   }
   for (int e = lane; e < wc * 2; e += 32) {
     const int cell = e >> 1;
@@ -423,9 +436,11 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
     for (int c = 0; c < 2; ++c) {
       const S *yv = win + (size_t)cell * 2 * MP + c * MP;
       const T yl = col ? T(yv[lane]) : T(0);
-      T ay = 0;
+      // (A_bar y_j)_lane as four interleaved chains: a quarter of the latency
+      T a4[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-      for (int i = 0; i < MP; ++i) ay = fma(as[i], T(yv[i]), ay);
+      for (int i = 0; i < MP; ++i) a4[i & 3] = fma(as[i], T(yv[i]), a4[i & 3]);
+      const T ay = (a4[0] + a4[1]) + (a4[2] + a4[3]);
       const T dj = T(dwin[cell * 2 + c]);
       const T yb = lk_warp_sum(yl * bbl);
       const T yay = lk_warp_sum(yl * ay);
