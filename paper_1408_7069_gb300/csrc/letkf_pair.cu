@@ -20,10 +20,13 @@
 // odd round. One shuffle moves MP values per pair visit, half of what a
 // lane-per-column layout needs. The end slot of an odd round (positions MP-1
 // and 0, held by the node's last lane) does not rotate; it swaps its columns
-// (an exact 90-degree rotation, the sign being irrelevant), which keeps the
-// register roles of every lane the same. A rotation is applied as
-// P' = c P - s Q, Q' = s P + c Q, exact for c = 1, s = 0 (no rotation) and for
-// the swap. A node is converged after a sweep whose rotations all had cosines
+// (a 90-degree rotation, the sign being irrelevant), which keeps the register
+// roles of every lane the same. Even rounds have no end slot, so they apply
+// their rotations without the cosine, P' = P - t Q, Q' = Q + t P (half the
+// packed FMAs), and leave the cosine as the scale of both columns; the odd
+// round folds the two scales into its rotation P' = c P - s Q, Q' = s P + c Q
+// and writes both columns back at scale 1. No rotation of a frozen node
+// changes a bit. A node is converged after a sweep whose rotations all had cosines
 // at most the stop cosine (letkf_set_jacobi; with stop <= the rotation
 // threshold, a sweep without rotations) and then freezes (its lanes shuffle
 // from themselves), so its result does not depend on the nodes that share its
@@ -124,47 +127,89 @@ __device__ __forceinline__ float combine(float v) {
   return v;
 }
 
-// One round on this lane's pair (P, Q) with tracked squared norms. `idle`:
-// the end slot of an odd round, which swaps instead of rotating. XO > 0: the
-// lane holds half of the pair's rows, the other half is on lane ^ XO, which
-// computes the same rotation. Returns whether the pair was rotated.
-template <int K2, int XO = 0>
-__device__ __forceinline__ int pair_round(float2 (&P)[K2], float2 (&Q)[K2], float &nP, float &nQ,
-                                          float tol2, float stop2, bool idle, bool frozen) {
-  const float dot = combine<XO>(dotk<K2>(P, Q));
-  // The rotation that makes the pair orthogonal, |theta| <= pi/4, from
-  // x = |q|^2 - |p|^2, y = 2 p.q and h = sqrt(x^2 + y^2): cos 2theta = |x|/h,
-  // sin 2theta = sign(x) y / h, c = sqrt((1 + cos 2theta)/2) >= 1/sqrt(2),
-  // s = sin 2theta / (2c), t = s / c. Two reciprocal square roots, no divide.
+// The rotation that makes a pair orthogonal, |theta| <= pi/4, from the true
+// squared norms and dot product: x = |q|^2 - |p|^2, y = 2 p.q, h = sqrt(x^2 + y^2),
+// cos 2theta = |x|/h, sin 2theta = sign(x) y / h, c = sqrt((1 + cos 2theta)/2)
+// >= 1/sqrt(2), s = sin 2theta / (2c), t = s / c. Two reciprocal square roots,
+// no divide. `rot`: the pair is rotated (not frozen, not the end slot, and
+// cos(p, q) above the rotation threshold); `big`: above the stopping cosine.
+struct Rot {
+  float c, s, t;
+  bool rot, big;
+};
+__device__ __forceinline__ Rot rotation(float nP, float nQ, float dot, float tol2, float stop2,
+                                        bool skip) {
   const float x = nQ - nP, y = 2.f * dot;
   const float rh = rsqrtf(fmaxf(fmaf(x, x, y * y), 1e-37f));
   const float c2 = fmaf(0.5f * fabsf(x), rh, 0.5f);
   const float rc = rsqrtf(c2);
-  const float cr = c2 * rc;
-  const float sr = (x >= 0.f ? y : -y) * (0.5f * rh) * rc;
-  const float t = sr * rc;
+  Rot R;
+  R.c = c2 * rc;
+  R.s = (x >= 0.f ? y : -y) * (0.5f * rh) * rc;
+  R.t = R.s * rc;
   const float dd = dot * dot, nn = nP * nQ;
-  const bool rot = !frozen && !idle && dd > tol2 * nn;
-  const bool swp = idle && !frozen;
-  // P' = c P - s Q, Q' = s P + c Q: exact for the swap (c = 0, s = 1) and for no
-  // rotation (c = 1, s = 0). A three-shear form would save one packed FMA per
-  // element pair but its swap leaks rounding of the larger column into the
-  // smaller one, which stalls convergence when their norms differ by kappa.
-  const float c = rot ? cr : (swp ? 0.f : 1.f);
-  const float s = rot ? sr : (swp ? 1.f : 0.f);
-  const float nP2 = rot ? fmaf(-t, dot, nP) : (swp ? nQ : nP);
-  const float nQ2 = rot ? fmaf(t, dot, nQ) : (swp ? nP : nQ);
-  const float2 cc = f2(c), ms = f2(-s), ps = f2(s);
+  R.rot = !skip && dd > tol2 * nn;
+  R.big = R.rot && dd > stop2 * nn;
+  return R;
+}
+
+// Even round of the odd-even network on this lane's pair (P, Q), both stored
+// at scale 1 (the odd round before normalised them), with tracked true
+// squared norms. The rotation is applied without its cosine,
+// P' = P - t Q, Q' = Q + t P (one packed FMA per element pair, exact for
+// t = 0), and the cosine is returned in `cs` as the scale of both stored
+// columns: the true columns are cs P' and cs Q'. XO > 0: the lane holds half
+// of the pair's rows, the other half is on lane ^ XO, which computes the same
+// rotation. Returns bit 0: rotated; bit 1: rotated with cos(p, q) above the
+// stopping cosine.
+template <int K2, int XO = 0>
+__device__ __forceinline__ int pair_round_even(float2 (&P)[K2], float2 (&Q)[K2], float &nP,
+                                               float &nQ, float &cs, float tol2, float stop2,
+                                               bool frozen) {
+  const float dot = combine<XO>(dotk<K2>(P, Q));
+  const Rot R = rotation(nP, nQ, dot, tol2, stop2, frozen);
+  const float t = R.rot ? R.t : 0.f;
+  cs = R.rot ? R.c : 1.f;
+  nP = fmaf(-t, dot, nP);
+  nQ = fmaf(t, dot, nQ);
+  const float2 mt = f2(-t), pt = f2(t);
 #pragma unroll
   for (int k = 0; k < K2; ++k) {
     const float2 p = P[k], q = Q[k];
-    P[k] = fma2(cc, p, mul2(ms, q));
-    Q[k] = fma2(cc, q, mul2(ps, p));
+    P[k] = fma2(mt, q, p);
+    Q[k] = fma2(pt, p, q);
+  }
+  return (R.rot ? 1 : 0) | (R.big ? 2 : 0);
+}
+
+// Odd round on (P, Q) stored at scales a and b (the cosines of the even rounds
+// that produced them; 1 for a frozen node). The true rotation
+// p' = c p - s q, q' = s p + c q of the true columns p = a P, q = b Q is
+// written back at scale 1: P' = (c a) P - (s b) Q, Q' = (s a) P + (c b) Q.
+// `idle`: the end slot, which swaps instead of rotating (c = 0, s = 1, so
+// P' = -b Q and Q' = a P: each column only rescaled, nothing of the other
+// mixed in). No rotation at a = b = 1 is exact.
+template <int K2, int XO = 0>
+__device__ __forceinline__ int pair_round_odd(float2 (&P)[K2], float2 (&Q)[K2], float &nP,
+                                              float &nQ, float a, float b, float tol2,
+                                              float stop2, bool idle, bool frozen) {
+  const float dot = combine<XO>(dotk<K2>(P, Q)) * (a * b);
+  const Rot R = rotation(nP, nQ, dot, tol2, stop2, frozen || idle);
+  const bool swp = idle && !frozen;
+  const float c = R.rot ? R.c : (swp ? 0.f : 1.f);
+  const float s = R.rot ? R.s : (swp ? 1.f : 0.f);
+  const float nP2 = R.rot ? fmaf(-R.t, dot, nP) : (swp ? nQ : nP);
+  const float nQ2 = R.rot ? fmaf(R.t, dot, nQ) : (swp ? nP : nQ);
+  const float2 ca = f2(c * a), msb = f2(-(s * b)), sa = f2(s * a), cb = f2(c * b);
+#pragma unroll
+  for (int k = 0; k < K2; ++k) {
+    const float2 p = P[k], q = Q[k];
+    P[k] = fma2(ca, p, mul2(msb, q));
+    Q[k] = fma2(cb, q, mul2(sa, p));
   }
   nP = nP2;
   nQ = nQ2;
-  // bit 0: rotated; bit 1: rotated with cos(p, q) above the stopping cosine
-  return (rot ? 1 : 0) | ((rot && dd > stop2 * nn) ? 2 : 0);
+  return (R.rot ? 1 : 0) | (R.big ? 2 : 0);
 }
 
 template <int K2>
@@ -383,10 +428,12 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
     const int su = frz ? lane : up, sd = frz ? lane : dn;
 #pragma unroll 2
     for (int r = 0; r < MP / 2; ++r) {
-      rotated |= pair_round<K2>(P, Q, nP, nQ, tol2, stop2, false, frz);
+      float cs;
+      rotated |= pair_round_even<K2>(P, Q, nP, nQ, cs, tol2, stop2, frz);
       shfl_cols<K2>(Q, su);
       nQ = __shfl_sync(FULL, nQ, su);
-      rotated |= pair_round<K2>(P, Q, nP, nQ, tol2, stop2, li == LPN - 1, frz);
+      const float cq = __shfl_sync(FULL, cs, su);
+      rotated |= pair_round_odd<K2>(P, Q, nP, nQ, cs, cq, tol2, stop2, li == LPN - 1, frz);
       shfl_cols<K2>(P, sd);
       nP = __shfl_sync(FULL, nP, sd);
     }
@@ -679,10 +726,12 @@ __global__ void __launch_bounds__(SplitLaunch<MP, TI, TJ>::threads, SplitLaunch<
     const int su = conv ? lane : up, sd = conv ? lane : dn;
 #pragma unroll 2
     for (int r = 0; r < MP / 2; ++r) {
-      rotated |= pair_round<KH, LPN>(P, Q, nP, nQ, tol2, stop2, false, conv);
+      float cs;
+      rotated |= pair_round_even<KH, LPN>(P, Q, nP, nQ, cs, tol2, stop2, conv);
       shfl_cols<KH>(Q, su);
       nQ = __shfl_sync(FULL, nQ, su);
-      rotated |= pair_round<KH, LPN>(P, Q, nP, nQ, tol2, stop2, li == LPN - 1, conv);
+      const float cq = __shfl_sync(FULL, cs, su);
+      rotated |= pair_round_odd<KH, LPN>(P, Q, nP, nQ, cs, cq, tol2, stop2, li == LPN - 1, conv);
       shfl_cols<KH>(P, sd);
       nP = __shfl_sync(FULL, nP, sd);
     }
