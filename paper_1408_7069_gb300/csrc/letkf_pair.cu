@@ -102,10 +102,10 @@ __device__ __forceinline__ float group_sum(float v) {
   return v;
 }
 
-// Dot product of two MP-element columns with eight independent packed chains.
+// Dot product of two MP-element columns with four independent packed chains.
 template <int K2>
 __device__ __forceinline__ float dotk(const float2 (&a)[K2], const float2 (&b)[K2]) {
-  constexpr int NC = K2 >= 8 ? 8 : K2;
+  constexpr int NC = K2 >= 4 ? 4 : K2;
   float2 s[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) s[c] = mul2(a[c], b[c]);
@@ -114,7 +114,7 @@ __device__ __forceinline__ float dotk(const float2 (&a)[K2], const float2 (&b)[K
 #pragma unroll
   for (int w = NC / 2; w > 0; w >>= 1)
 #pragma unroll
-    for (int c = 0; c < w; ++c) s[c] = make_float2(s[c].x + s[c + w].x, s[c].y + s[c + w].y);
+    for (int c = 0; c < w; ++c) s[c] = __fadd2_rn(s[c], s[c + w]);
   return s[0].x + s[0].y;
 }
 
@@ -160,10 +160,10 @@ __device__ __forceinline__ Rot rotation(float nP, float nQ, float dot, float tol
 // t = 0), and the cosine is returned in `cs` as the scale of both stored
 // columns: the true columns are cs P' and cs Q'. XO > 0: the lane holds half
 // of the pair's rows, the other half is on lane ^ XO, which computes the same
-// rotation. Returns bit 0: rotated; bit 1: rotated with cos(p, q) above the
+// rotation. Returns whether the pair was rotated with cos(p, q) above the
 // stopping cosine.
 template <int K2, int XO = 0>
-__device__ __forceinline__ int pair_round_even(float2 (&P)[K2], float2 (&Q)[K2], float &nP,
+__device__ __forceinline__ bool pair_round_even(float2 (&P)[K2], float2 (&Q)[K2], float &nP,
                                                float &nQ, float &cs, float tol2, float stop2,
                                                bool frozen) {
   const float dot = combine<XO>(dotk<K2>(P, Q));
@@ -179,7 +179,7 @@ __device__ __forceinline__ int pair_round_even(float2 (&P)[K2], float2 (&Q)[K2],
     P[k] = fma2(mt, q, p);
     Q[k] = fma2(pt, p, q);
   }
-  return (R.rot ? 1 : 0) | (R.big ? 2 : 0);
+  return R.big;
 }
 
 // Odd round on (P, Q) stored at scales a and b (the cosines of the even rounds
@@ -190,7 +190,7 @@ __device__ __forceinline__ int pair_round_even(float2 (&P)[K2], float2 (&Q)[K2],
 // P' = -b Q and Q' = a P: each column only rescaled, nothing of the other
 // mixed in). No rotation at a = b = 1 is exact.
 template <int K2, int XO = 0>
-__device__ __forceinline__ int pair_round_odd(float2 (&P)[K2], float2 (&Q)[K2], float &nP,
+__device__ __forceinline__ bool pair_round_odd(float2 (&P)[K2], float2 (&Q)[K2], float &nP,
                                               float &nQ, float a, float b, float tol2,
                                               float stop2, bool idle, bool frozen) {
   const float dot = combine<XO>(dotk<K2>(P, Q)) * (a * b);
@@ -209,7 +209,7 @@ __device__ __forceinline__ int pair_round_odd(float2 (&P)[K2], float2 (&Q)[K2], 
   }
   nP = nP2;
   nQ = nQ2;
-  return (R.rot ? 1 : 0) | (R.big ? 2 : 0);
+  return R.big;
 }
 
 template <int K2>
@@ -236,7 +236,7 @@ __device__ __forceinline__ float2 reduce_scatter(float2 (&v)[GL], int li) {
       float2 send = b ? lo : hi;
       send.x = __shfl_xor_sync(FULL, send.x, o);
       send.y = __shfl_xor_sync(FULL, send.y, o);
-      v[e] = make_float2(keep.x + send.x, keep.y + send.y);
+      v[e] = __fadd2_rn(keep, send);
     }
   }
   return v[0];
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (__all_sync(FULL, conv)) break;
     float nP = dotk<K2>(P, P), nQ = dotk<K2>(Q, Q);
-    int rotated = 0;
+    bool rotated = false;
     const bool frz = conv || !live;
     const int su = frz ? lane : up, sd = frz ? lane : dn;
 #pragma unroll 2
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
     // tol); a larger stop ends one or two sweeps earlier, leaving pairs within
     // about stop^2 except inside near-degenerate clusters, whose mixing does
     // not change W.
-    const unsigned big = __ballot_sync(FULL, rotated & 2);
+    const unsigned big = __ballot_sync(FULL, rotated);
     const unsigned gmask = (GL == 32) ? 0xffffffffu : (((1u << GL) - 1u) << base);
     if (!conv) {
       sweeps = sweep + 1;
@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(SplitLaunch<MP, TI, TJ>::threads, SplitLaunch<
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (__all_sync(FULL, conv)) break;
     float nP = combine<LPN>(dotk<KH>(P, P)), nQ = combine<LPN>(dotk<KH>(Q, Q));
-    int rotated = 0;
+    bool rotated = false;
     const int su = conv ? lane : up, sd = conv ? lane : dn;
 #pragma unroll 2
     for (int r = 0; r < MP / 2; ++r) {
@@ -735,7 +735,7 @@ __global__ void __launch_bounds__(SplitLaunch<MP, TI, TJ>::threads, SplitLaunch<
       shfl_cols<KH>(P, sd);
       nP = __shfl_sync(FULL, nP, sd);
     }
-    const unsigned big = __ballot_sync(FULL, rotated & 2);
+    const unsigned big = __ballot_sync(FULL, rotated);
     const unsigned gmask = (GL == 32) ? 0xffffffffu : (((1u << GL) - 1u) << (grp * GL));
     if (!conv) {
       sweeps = sweep + 1;
