@@ -432,6 +432,14 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32)
   double *db_out = a.dbw + (size_t)pid * wc * 2;
   for (int cell = 0; cell < wc; ++cell) {
     const T cj = tap[cell];
+    if (cj == T(0) && dtap[cell] == 0.0) {
+      // outside the taper's support for every nearby L: no slope of the cell
+      // reaches A, C d or J
+      if (mem)
+        for (int c = 0; c < 2; ++c) yb_out[((size_t)cell * 2 + c) * m + lane] = 0.0;
+      if (lane == 0) db_out[cell * 2] = db_out[cell * 2 + 1] = 0.0;
+      continue;
+    }
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const S *yv = win + (size_t)cell * 2 * MP + c * MP;

@@ -61,6 +61,7 @@ __device__ __forceinline__ void gram(const S *__restrict__ win, const S *__restr
       const int cell = ds * stride + dt;
       const S *cy2 = win + (size_t)cell * 2 * MP;
       const T tw = tap[ds * w + dt];
+      if (tw == T(0)) continue;                      // outside the taper's support
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const S *yv = cy2 + c * MP;

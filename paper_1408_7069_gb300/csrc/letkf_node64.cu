@@ -120,6 +120,7 @@ __device__ void node64(const LkInst &I, int pid, S *__restrict__ mean_out,
     for (int dt = 0; dt < w; ++dt) {
       const size_t src = (size_t)(ij.x + ds) * I.gs_cols + (ij.y + dt);
       const double tw = (double)taper[ds * w + dt];
+      if (tw == 0.0) continue;                       // outside the taper's support
 #pragma unroll
       for (int cc = 0; cc < 2; ++cc) {
         const S *yv = Ybp + (src * 2 + cc) * m;
@@ -495,6 +496,7 @@ __device__ void node64w(const LkInst &I, int pid, float *__restrict__ mean_out,
     for (int dt = 0; dt < w; ++dt) {
       const size_t src = (size_t)(ij.x + ds) * I.gs_cols + (ij.y + dt);
       const double tw = (double)taper[ds * w + dt];
+      if (tw == 0.0) continue;                       // outside the taper's support
 #pragma unroll
       for (int cc = 0; cc < 2; ++cc) {
         const float *yv = Ybp + (src * 2 + cc) * m;

@@ -353,6 +353,7 @@ __global__ void __launch_bounds__(PairLaunch<MP, TI, TJ>::threads, PairLaunch<MP
     for (int dt = 0; dt < w; ++dt) {
       const int cell = ds * HJ + dt;
       const float tw = tap[ds * w + dt];
+      if (tw == 0.f) continue;                       // outside the taper's support
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const float *yv = hwin + (size_t)cell * C::CELLF + c * MP;
@@ -662,6 +663,7 @@ __global__ void __launch_bounds__(SplitLaunch<MP, TI, TJ>::threads, SplitLaunch<
     for (int dt = 0; dt < w; ++dt) {
       const int cell = ds * HJ + dt;
       const float tw = tap[ds * w + dt];
+      if (tw == 0.f) continue;                       // outside the taper's support
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const float *yv = hwin + (size_t)cell * C::CELLF + c * MP;
