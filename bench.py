@@ -951,11 +951,14 @@ def gpu_arm(args):
     # the Jacobi executes several times the paper's m^3 for the EVD: the kernel's
     # own flops, from its loop counts and the measured mean sweeps
     mp = next(c for c in (16, 24, 32, 48, 64) if w.m <= c)
-    ex_flops = opcount.frame_executed_flops(mp, ws, total_sweeps / max(1, f.n_pts - nfp64))
+    n_sup = opcount.taper_support_cells(w.window, w.taper, w.loc_len)
+    ex_flops = opcount.frame_executed_flops(mp, f.n_pts, n_sup,
+                                            total_sweeps / max(1, f.n_pts - nfp64))
     executed = {"flops_per_launch": ex_flops, "achieved": ex_flops / ana_mean_s / 1e12,
                 "frac": ex_flops / ana_mean_s / 1e12 / fp32_peak,
-                "count": "per node: Gram 2 mp^2 p_l, Jacobi 4 mp^3 per sweep x the measured "
-                         "mean sweeps, transform and apply 10 mp^2 (an FMA counts as two)"}
+                "count": f"per node: Gram 2 mp^2 over the 2 x {n_sup} slopes of the window "
+                         "cells inside the taper's support, Jacobi 3.5 mp^3 per sweep x the "
+                         "measured mean sweeps, transform and apply 10 mp^2 (an FMA counts as two)"}
     line = {
         "metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": Wm, "ms_per_step": agg["ms_per_step"], "higher_is_better": True,

@@ -31,14 +31,29 @@ def frame_analysis_ops(m: int, window_slopes) -> int:
     return sum(update_ops(m, 2, int(p)) for p in window_slopes)
 
 
-def frame_executed_flops(mp: int, window_slopes, mean_sweeps: float) -> float:
+def taper_support_cells(window: int, taper: int, loc_len: float = 0.0) -> int:
+    """Window cells the analysis kernels visit: those whose subaperture centre,
+    at (ds - w//2 + 0.5, dt - w//2 + 0.5) pitches from the node, lies inside
+    the Gaspari-Cohn support (distance < 2 c, c = loc_len or w / 4); every
+    cell for the box taper."""
+    if taper != 1:
+        return window * window
+    hw = window // 2
+    c = loc_len if loc_len > 0 else window / 4.0
+    return sum(1 for ds in range(window) for dt in range(window)
+               if ((ds - hw + 0.5) ** 2 + (dt - hw + 0.5) ** 2) ** 0.5 / c < 2.0)
+
+
+def frame_executed_flops(mp: int, n_nodes: int, support_cells: int, mean_sweeps: float) -> float:
     """Flops the FP32 analysis kernel executes per frame (an FMA counts as two),
-    from its loop structure, beside the paper's count: per node the Gram over
-    the window, 2 mp^2 flops per slope (both triangles of the mp x mp matrix),
-    and per Jacobi sweep mp rounds of mp/2 column pairs, each a dot product
-    (2 mp) and a rotation of both columns (6 mp), 4 mp^3 in all; the
-    eigenvector normalisation, transform and apply (about 10 mp^2) are added.
+    from its loop structure, beside the paper's count. Per node: the Gram over
+    the window cells inside the taper's support (two slopes each, 2 mp^2 flops
+    per slope, both triangles of the mp x mp matrix, pupil or not); per Jacobi
+    sweep mp rounds of mp/2 column pairs, each a dot product (2 mp) and a
+    rotation of both columns, 4 mp in the even rounds (one FMA per element)
+    and 6 mp in the odd ones (a multiply and an FMA), 3.5 mp^3 in all; the
+    eigenvector normalisation, transform and apply (about 10 mp^2).
     mean_sweeps: the measured mean sweep count per node."""
-    per_sweep = 4.0 * mp ** 3
-    return float(sum(2.0 * mp * mp * int(p) + mean_sweeps * per_sweep + 10.0 * mp * mp
-                     for p in window_slopes))
+    per_sweep = 3.5 * mp ** 3
+    per_node = 2.0 * mp * mp * 2 * support_cells + mean_sweeps * per_sweep + 10.0 * mp * mp
+    return float(n_nodes * per_node)

@@ -269,6 +269,20 @@ def test_table1_operation_counts():
         assert abs(got - val) / val < 0.005, (kind, got, val)
 
 
+def test_taper_support_matches_the_oracle_windows():
+    """The kernels skip window cells outside the Gaspari-Cohn support; the
+    executed-flops count takes their number from opcount. For an interior
+    node of a full square pupil the oracle's window has exactly two slopes
+    with a nonzero taper per such cell."""
+    mask = np.ones((12, 12), bool)
+    for window, loc_len in ((3, 0.0), (5, 0.0), (7, 0.0), (7, 1.2), (5, 3.0)):
+        g = oracle.build_geometry(mask, window, taper=1, loc_len=loc_len)
+        q = 6 * 13 + 6                                  # node (6, 6), row-major over 13 x 13
+        nz = int(np.count_nonzero(np.asarray(g.win_tau[q]) > 0))
+        assert nz == 2 * opcount.taper_support_cells(window, 1, loc_len), (window, loc_len, nz)
+        assert opcount.taper_support_cells(window, 0) == window * window
+
+
 # ------------------------------------------------------------------ synthetic turbulence
 def test_T6_structure_function_kolmogorov():
     r0, dx = 0.15, 0.04
