@@ -25,7 +25,16 @@ __device__ __forceinline__ void ld4(const double *p, double &a, double &b, doubl
   a = u.x; b = u.y; c = v.x; d = v.y;
 }
 
-__device__ __forceinline__ float lk_rsqrt(float x) { return rsqrtf(x); }
+// Reciprocal square root of a positive normal float: the approximate PTX
+// instruction with subnormals flushed, which needs no range fix-up. The Jacobi
+// rotations of the node kernels call it on max(x^2 + y^2, 1e-37), on c^2 in
+// [1/2, 1] and on 1 + t^2.
+__device__ __forceinline__ float lk_rsqrt_normal(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lk_rsqrt(float x) { return lk_rsqrt_normal(x); }
 __device__ __forceinline__ double lk_rsqrt(double x) { return rsqrt(x); }
 
 // Dot product of two register columns with four independent FMA chains (the
@@ -112,7 +121,7 @@ __device__ __forceinline__ int jacobi_step(T (&b)[MP], T (&v)[MP], T &nrm, int t
       // then c = (1 + t^2)^-1/2 and s = c t in FP64: an orthogonal rotation whose
       // FP32-accurate angle leaves the pair's cosine at ~1e-7 of its value
       const float x = (float)(aqq - app), y = (float)(T(2) * dot);
-      const float rh = rsqrtf(fmaxf(fmaf(x, x, y * y), 1e-37f));
+      const float rh = lk_rsqrt_normal(fmaxf(fmaf(x, x, y * y), 1e-37f));
       const float c2 = fmaf(0.5f * fabsf(x), rh, 0.5f);
       tr = (T)((x >= 0.f ? y : -y) * (0.5f * rh) / c2);
     } else {

@@ -243,7 +243,7 @@ __device__ void node64(const LkInst &I, int pid, S *__restrict__ mean_out,
           // orthogonal to FP64 rounding; an FP32-accurate angle leaves the pair's
           // cosine at ~1e-7 of its value, which the next sweep removes.
           const float x = (float)(aqq - app), y = (float)(2.0 * dot);
-          const float rh = rsqrtf(fmaxf(fmaf(x, x, y * y), 1e-37f));
+          const float rh = lk_rsqrt_normal(fmaxf(fmaf(x, x, y * y), 1e-37f));
           const float c2 = fmaf(0.5f * fabsf(x), rh, 0.5f);
           const float t = (x >= 0.f ? y : -y) * (0.5f * rh) / c2;
           tr = (double)t;
@@ -598,7 +598,7 @@ __device__ void node64w(const LkInst &I, int pid, float *__restrict__ mean_out,
           // the tangent in FP32 from x = aqq - app and y = 2 dot formed in FP64,
           // then c = (1 + t^2)^-1/2 and s = c t in FP64 (orthogonal to FP64 rounding)
           const float x = (float)(aqq - app), y = (float)(2.0 * dot);
-          const float rh = rsqrtf(fmaxf(fmaf(x, x, y * y), 1e-37f));
+          const float rh = lk_rsqrt_normal(fmaxf(fmaf(x, x, y * y), 1e-37f));
           const float c2 = fmaf(0.5f * fabsf(x), rh, 0.5f);
           const float tt = (x >= 0.f ? y : -y) * (0.5f * rh) / c2;
           tr = (double)tt;

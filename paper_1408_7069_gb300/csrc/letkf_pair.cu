@@ -137,20 +137,13 @@ struct Rot {
   float c, s, t;
   bool rot, big;
 };
-// Reciprocal square root of a positive normal float: the approximate PTX
-// instruction with subnormals flushed, which needs no range fix-up (both
-// arguments below are at least 1e-37).
-__device__ __forceinline__ float rsqrt_normal(float x) {
-  float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
+
 __device__ __forceinline__ Rot rotation(float nP, float nQ, float dot, float tol2, float stop2,
                                         bool skip) {
   const float x = nQ - nP, y = 2.f * dot;
-  const float rh = rsqrt_normal(fmaxf(fmaf(x, x, y * y), 1e-37f));
+  const float rh = lk_rsqrt_normal(fmaxf(fmaf(x, x, y * y), 1e-37f));
   const float c2 = fmaf(0.5f * fabsf(x), rh, 0.5f);
-  const float rc = rsqrt_normal(c2);
+  const float rc = lk_rsqrt_normal(c2);
   Rot R;
   R.c = c2 * rc;
   R.s = (x >= 0.f ? y : -y) * (0.5f * rh) * rc;
