@@ -267,8 +267,9 @@ def batched_arm(torch, L, K, Wm):
 # --------------------------------------------------------------------------- smaller configs
 def small_configs_arm(torch, L, K: int = 500, Wm: int = 20):
     """The 8x8 FP64 system and the 16 m FP32 system: per-frame CUDA events
-    (launches as in the main measurement, L2 not flushed: both fit in L2) and
-    one CUDA-graph replay per frame. Returns the 'configs' object of the JSON line."""
+    around one letkf_run call per frame, as in the main measurement (L2 not
+    flushed: both fit in L2), and one CUDA-graph replay per frame. Returns the
+    'configs' object of the JSON line."""
     import numpy as np
     from paper_1408_7069_gb300 import synth, workloads as W
     from dataclasses import replace
@@ -293,9 +294,7 @@ def small_configs_arm(torch, L, K: int = 500, Wm: int = 20):
             for i in range(K):
                 k = Wm + i
                 ev[i][0].record(s)
-                L.letkf_residual(h, t[k], rv[k:k + 1])
-                L.letkf_analyze(h, y[k], None, None)
-                L.letkf_forecast(h)
+                L.letkf_run(h, 1, y[k:k + 1], t[k:k + 1], rv[k:k + 1], False)
                 ev[i][1].record(s)
         torch.cuda.synchronize()
         ms = [a.elapsed_time(b) for a, b in ev]
