@@ -960,7 +960,7 @@ def gpu_arm(args):
     ana_mean_s = statistics.mean(ana_ms) / 1e3
     achieved = flops / ana_mean_s / 1e12
     fallback = 1 if f.precision == 0 else 0
-    launches_per_frame = 1 + (2 + fallback) + 1   # residual, observe + pair (+ FP64 list), forecast
+    launches_per_frame = 1 + (1 + fallback) + 1   # observation with the residual, pair (+ FP64 list), forecast
     # the Jacobi executes several times the paper's m^3 for the EVD: the kernel's
     # own flops, from its loop counts and the measured mean sweeps
     mp = next(c for c in (16, 24, 32, 48, 64) if w.m <= c)

@@ -437,11 +437,17 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
 }
 
 // Residual and observation of a frame. Both read the prediction ensemble
-// only, so with a side stream the residual runs beside the observation kernel
-// and rejoins before the analysis overwrites the ensemble.
+// only, so they share one launch (the residual's CTAs first); with a
+// deformable mirror, whose residual needs N u first, the residual runs on a
+// side stream beside the observation kernel and rejoins before the analysis
+// overwrites the ensemble.
 letkf_status enqueue_head(letkf_ctx *h, const void *y, const void *truth, double *resvar,
                           const long long *ridx) {
   const bool res = truth && resvar;
+  if (res && !h->inst[0].dm) {
+    LK_CUDA(h, lk_launch_obs_residual(h, y, truth, resvar, ridx));
+    return LETKF_OK;
+  }
   const bool fork = res && h->side && h->stream;
   if (fork) {
     LK_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));

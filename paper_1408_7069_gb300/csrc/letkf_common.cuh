@@ -171,6 +171,10 @@ struct letkf_ctx {
 // NULL means element 0. y, truth, mean, spread and noise are concatenated over
 // the instances in instance order.
 cudaError_t lk_launch_obs(letkf_ctx *h, const void *y, const long long *run_idx);
+// Residual and observation of one frame in one launch (separate launches with a
+// deformable mirror, whose residual needs N u first).
+cudaError_t lk_launch_obs_residual(letkf_ctx *h, const void *y, const void *truth,
+                                   double *resvar, const long long *run_idx);
 cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread);
 cudaError_t lk_launch_analysis_class(letkf_ctx *h, int cls, void *mean, void *spread);
 // The forecast also advances the forecast counter and the run index (frame[0..1]).

@@ -12,17 +12,18 @@ namespace {
 // (Section 3.1, Eq. Cov_emp), Fried slopes of the anomalies Yb = D1 X'
 // (Appendix B) into the padded grid cell (s+h, t+h), and the innovation
 // d = y - D1 xbar (Section 3.1.1, with the correction known exactly).
+// The observation's part of CTA `bx`.
 template <typename S>
-__global__ void __launch_bounds__(LK_WARP_CTA) obs_kernel(const LkInst *__restrict__ insts,
-                                                  const int2 *__restrict__ items, long long n_items,
-                                                  long long p_total, const S *__restrict__ y,
-                                                  const long long *__restrict__ run_idx,
-                                                  int *__restrict__ counters) {
+__device__ __forceinline__ void obs_block(const LkInst *__restrict__ insts,
+                                          const int2 *__restrict__ items, long long n_items,
+                                          long long p_total, const S *__restrict__ y,
+                                          const long long *__restrict__ run_idx,
+                                          int *__restrict__ counters, int bx) {
   lk_pdl_wait();   // no early trigger: an analysis launched early would have its CTAs
                    // packed onto the SMs this kernel still occupies
   // the analysis that follows counts into counters[1..7] (queue lengths, sweeps)
-  if (blockIdx.x == 0 && threadIdx.x < 7) counters[1 + threadIdx.x] = 0;
-  const long long wi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (bx == 0 && threadIdx.x < 7) counters[1 + threadIdx.x] = 0;
+  const long long wi = ((long long)bx * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wi >= n_items) return;
   const int2 it = items[wi];
@@ -81,6 +82,15 @@ __global__ void __launch_bounds__(LK_WARP_CTA) obs_kernel(const LkInst *__restri
     dp[cell * 2 + 1] = dy;
     if (!isfinite(dx) || !isfinite(dy)) atomicOr(&counters[0], LK_BIT_NONFINITE);
   }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(LK_WARP_CTA) obs_kernel(const LkInst *__restrict__ insts,
+                                                  const int2 *__restrict__ items, long long n_items,
+                                                  long long p_total, const S *__restrict__ y,
+                                                  const long long *__restrict__ run_idx,
+                                                  int *__restrict__ counters) {
+  obs_block<S>(insts, items, n_items, p_total, y, run_idx, counters, blockIdx.x);
 }
 
 template <typename S>
@@ -145,22 +155,19 @@ __global__ void __launch_bounds__(LK_WARP_CTA) forecast_kernel(const LkInst *__r
 }
 
 // Spatial variance of truth - mean(row 0) over one instance's nodes, piston
-// removed (Section 2.1, Eq. Crit_Opt; Section 5). Grid (LK_RES_BLOCKS, n_inst):
-// thread per node, FP64 partial sums per CTA; the last CTA of an instance to
-// finish (ticket counter, reset by it) adds the partials in a fixed order and
-// writes the variance and, when piston is given, the piston (the mean).
+// removed (Section 2.1, Eq. Crit_Opt; Section 5): the part of CTA rb of nrb of
+// instance `inst`. Thread per node, FP64 partial sums per CTA; the last CTA of
+// an instance to finish (ticket counter, reset by it) adds the partials in a
+// fixed order and writes the variance and, when piston is given, the piston
+// (the mean).
 template <typename S>
-__global__ void __launch_bounds__(64) residual_kernel(const LkInst *__restrict__ insts,
-                                                       long long n_pts_total,
-                                                       const S *__restrict__ truth,
-                                                       const long long *__restrict__ run_idx,
-                                                       double2 *__restrict__ partial,
-                                                       int *__restrict__ tickets, int n_inst,
-                                                       double *__restrict__ resvar,
-                                                       double *__restrict__ piston) {
-  lk_pdl_wait();
-  lk_pdl_trigger();
-  const LkInst &I = insts[blockIdx.y];
+__device__ __forceinline__ void residual_block(const LkInst &I, int inst, int rb, int nrb,
+                                               long long n_pts_total, const S *__restrict__ truth,
+                                               const long long *__restrict__ run_idx,
+                                               double2 *__restrict__ partial,
+                                               int *__restrict__ tickets, int n_inst,
+                                               double *__restrict__ resvar,
+                                               double *__restrict__ piston) {
   const long long k = run_idx ? *run_idx : 0;
   const S *tr = truth + k * n_pts_total + I.node_off;
   const S *X = static_cast<const S *>(I.X);
@@ -169,7 +176,7 @@ __global__ void __launch_bounds__(64) residual_kernel(const LkInst *__restrict__
   const bool vec = sizeof(S) == 4 && (m & 3) == 0 &&
                    (reinterpret_cast<uintptr_t>(X) & 15) == 0;
   double s1 = 0.0, s2 = 0.0;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < I.n_pts; g += gridDim.x * blockDim.x) {
+  for (int g = rb * blockDim.x + threadIdx.x; g < I.n_pts; g += nrb * blockDim.x) {
     const S *row = X + (size_t)g * 2 * m;
     double x = 0.0;
     if (vec) {
@@ -204,22 +211,22 @@ __global__ void __launch_bounds__(64) residual_kernel(const LkInst *__restrict__
     sh2[wid] = s2;
   }
   __syncthreads();
-  double2 *pp = partial + (size_t)blockIdx.y * gridDim.x;
+  double2 *pp = partial + (size_t)inst * nrb;
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
       a += sh1[i];
       b += sh2[i];
     }
-    pp[blockIdx.x] = make_double2(a, b);
+    pp[rb] = make_double2(a, b);
     __threadfence();
-    last = atomicAdd(&tickets[blockIdx.y], 1) == (int)gridDim.x - 1;
+    last = atomicAdd(&tickets[inst], 1) == nrb - 1;
   }
   __syncthreads();
   if (last && threadIdx.x < 32) {
     __threadfence();
     double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) {
+    for (int i = threadIdx.x; i < nrb; i += 32) {
       const double2 v = __ldcg(pp + i);
       a += v.x;
       b += v.y;
@@ -229,11 +236,48 @@ __global__ void __launch_bounds__(64) residual_kernel(const LkInst *__restrict__
     if (threadIdx.x == 0) {
       const double n = I.n_pts;
       const double mu = a / n;
-      resvar[k * n_inst + blockIdx.y] = b / n - mu * mu;
-      if (piston) piston[k * n_inst + blockIdx.y] = mu;
-      tickets[blockIdx.y] = 0;
+      resvar[k * n_inst + inst] = b / n - mu * mu;
+      if (piston) piston[k * n_inst + inst] = mu;
+      tickets[inst] = 0;
     }
   }
+}
+
+// The residual alone. Grid (LK_RES_BLOCKS, n_inst), 64 threads.
+template <typename S>
+__global__ void __launch_bounds__(64) residual_kernel(const LkInst *__restrict__ insts,
+                                                       long long n_pts_total,
+                                                       const S *__restrict__ truth,
+                                                       const long long *__restrict__ run_idx,
+                                                       double2 *__restrict__ partial,
+                                                       int *__restrict__ tickets, int n_inst,
+                                                       double *__restrict__ resvar,
+                                                       double *__restrict__ piston) {
+  lk_pdl_wait();
+  lk_pdl_trigger();
+  residual_block<S>(insts[blockIdx.y], blockIdx.y, blockIdx.x, gridDim.x, n_pts_total, truth,
+                    run_idx, partial, tickets, n_inst, resvar, piston);
+}
+
+// Residual and observation of a frame in one launch (both read only the
+// prediction ensemble): the first res_blocks CTAs (LK_RES_BLOCKS per instance)
+// take the residual, the others the observation, 64 threads each.
+template <typename S>
+__global__ void __launch_bounds__(LK_WARP_CTA)
+    obs_residual_kernel(const LkInst *__restrict__ insts, const int2 *__restrict__ items,
+                        long long n_items, long long p_total, const S *__restrict__ y,
+                        const long long *__restrict__ run_idx, int *__restrict__ counters,
+                        int res_blocks, long long n_pts_total, const S *__restrict__ truth,
+                        double2 *__restrict__ partial, int *__restrict__ tickets, int n_inst,
+                        double *__restrict__ resvar) {
+  if ((int)blockIdx.x < res_blocks) {
+    lk_pdl_wait();
+    const int inst = blockIdx.x / LK_RES_BLOCKS, rb = blockIdx.x - inst * LK_RES_BLOCKS;
+    residual_block<S>(insts[inst], inst, rb, LK_RES_BLOCKS, n_pts_total, truth, run_idx, partial,
+                      tickets, n_inst, resvar, nullptr);
+    return;
+  }
+  obs_block<S>(insts, items, n_items, p_total, y, run_idx, counters, blockIdx.x - res_blocks);
 }
 
 // Every node's warm-start eigenbasis back to the identity (grid.y = instance).
@@ -265,6 +309,25 @@ cudaError_t lk_launch_obs(letkf_ctx *h, const void *y, const long long *run_idx)
   return lk_launch_pdl(obs_kernel<float>, blocks, LK_WARP_CTA, 0, h->stream, h->d_inst,
                        h->obs_items, h->sap_total, h->p_total, (const float *)y, run_idx,
                        h->counters);
+}
+
+cudaError_t lk_launch_obs_residual(letkf_ctx *h, const void *y, const void *truth,
+                                   double *resvar, const long long *run_idx) {
+  if (h->sap_total == 0 || h->inst[0].dm) {       // separately (with a mirror, N u first)
+    cudaError_t e = lk_launch_residual(h, truth, resvar, run_idx);
+    return e == cudaSuccess ? lk_launch_obs(h, y, run_idx) : e;
+  }
+  const int rblocks = LK_RES_BLOCKS * h->n_inst;
+  const int blocks = rblocks + warp_blocks(h->sap_total);
+  if (h->precision == 1)
+    return lk_launch_pdl(obs_residual_kernel<double>, blocks, LK_WARP_CTA, 0, h->stream,
+                         h->d_inst, h->obs_items, h->sap_total, h->p_total, (const double *)y,
+                         run_idx, h->counters, rblocks, h->n_pts_total, (const double *)truth,
+                         h->partial, h->tickets, h->n_inst, resvar);
+  return lk_launch_pdl(obs_residual_kernel<float>, blocks, LK_WARP_CTA, 0, h->stream, h->d_inst,
+                       h->obs_items, h->sap_total, h->p_total, (const float *)y, run_idx,
+                       h->counters, rblocks, h->n_pts_total, (const float *)truth, h->partial,
+                       h->tickets, h->n_inst, resvar);
 }
 
 cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise) {
