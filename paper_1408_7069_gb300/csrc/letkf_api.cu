@@ -74,7 +74,7 @@ void release(letkf_ctx *h) {
   void *bufs[] = {h->X,          h->Ybp,      h->dp,       h->taper,    h->pid_map,
                   h->pts,        h->saps,     h->bank,     h->basis,    h->basis64,  h->counters,
                   h->worklist,   h->frame,    h->partial,  h->tickets,  h->d_inst,   h->obs_items,
-                  h->node_items, h->tiles[0], h->tiles[1], h->tiles[2]};
+                  h->node_items, h->tiles[0], h->tiles[1], h->tiles[2], h->noise_pre};
   for (void *p : bufs)
     if (p) cudaFree(p);
 }
@@ -343,6 +343,7 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   LK_TRY(dalloc(h, &h->worklist, 3 * h->n_pts_total * sizeof(int2)));
   LK_TRY(dalloc(h, &h->frame, 2 * sizeof(long long)));
   LK_TRY(dalloc(h, &h->partial, (size_t)n * LK_RES_BLOCKS * sizeof(double2)));
+  LK_TRY(dalloc(h, &h->noise_pre, (size_t)h->noise_total * h->rsz));
   LK_TRY(dalloc(h, &h->tickets, (size_t)(n + 1) * sizeof(int)));
   LK_TRY(dalloc(h, &h->d_inst, (size_t)n * sizeof(LkInst)));
   LK_TRY(dalloc(h, &h->obs_items, h->sap_total * sizeof(int2)));
@@ -436,16 +437,22 @@ letkf_status build_handle(const letkf_config *cfgs, int n, void *stream, letkf_t
   return LETKF_OK;
 }
 
+bool all_have_banks(const letkf_ctx *h);
+
 // Residual and observation of a frame. Both read the prediction ensemble
-// only, so they share one launch (the residual's CTAs first); with a
-// deformable mirror, whose residual needs N u first, the residual runs on a
-// side stream beside the observation kernel and rejoins before the analysis
-// overwrites the ensemble.
+// only, so they share one launch (the residual's CTAs first), which also
+// draws the frame's forecast noise when every instance has a bank (*drawn is
+// set: the forecast then reads h->noise_pre). With a deformable mirror, whose
+// residual needs N u first, the residual runs on a side stream beside the
+// observation kernel and rejoins before the analysis overwrites the ensemble.
 letkf_status enqueue_head(letkf_ctx *h, const void *y, const void *truth, double *resvar,
-                          const long long *ridx) {
+                          const long long *ridx, bool *drawn) {
   const bool res = truth && resvar;
-  if (res && !h->inst[0].dm) {
-    LK_CUDA(h, lk_launch_obs_residual(h, y, truth, resvar, ridx));
+  *drawn = false;
+  if (!h->inst[0].dm && h->sap_total > 0) {
+    *drawn = all_have_banks(h);
+    LK_CUDA(h, lk_launch_obs_residual(h, y, res ? truth : nullptr, res ? resvar : nullptr, ridx,
+                                      *drawn ? h->noise_pre : nullptr));
     return LETKF_OK;
   }
   const bool fork = res && h->side && h->stream;
@@ -465,10 +472,11 @@ letkf_status enqueue_head(letkf_ctx *h, const void *y, const void *truth, double
 letkf_status enqueue_frame(letkf_ctx *h, const void *y_seq, const void *truth_seq,
                            double *resvar) {
   const long long *ridx = h->frame + 1;
-  letkf_status st = enqueue_head(h, y_seq, truth_seq, resvar, ridx);
+  bool drawn;
+  letkf_status st = enqueue_head(h, y_seq, truth_seq, resvar, ridx, &drawn);
   if (st != LETKF_OK) return st;
   LK_CUDA(h, lk_launch_analysis(h, nullptr, nullptr));
-  LK_CUDA(h, lk_launch_forecast(h, nullptr));
+  LK_CUDA(h, lk_launch_forecast(h, drawn ? h->noise_pre : nullptr));
   return LETKF_OK;
 }
 
@@ -483,8 +491,10 @@ letkf_status enqueue_step(letkf_ctx *h, bool with_truth) {
   // y and truth are adjacent in the staging buffers: one upload covers both
   const size_t up = with_truth ? h->step_off[1] + h->n_pts_total * h->rsz : h->p_total * h->rsz;
   LK_CUDA(h, cudaMemcpyAsync(yd, yp, up, cudaMemcpyHostToDevice, h->stream));
+  bool drawn;
   letkf_status st = enqueue_head(h, yd, with_truth ? td : nullptr,
-                                 with_truth ? reinterpret_cast<double *>(rd) : nullptr, nullptr);
+                                 with_truth ? reinterpret_cast<double *>(rd) : nullptr, nullptr,
+                                 &drawn);
   if (st != LETKF_OK) return st;
   LK_CUDA(h, lk_launch_analysis(h, md, nullptr));
   // mean and resvar are adjacent too: one download
@@ -493,7 +503,7 @@ letkf_status enqueue_step(letkf_ctx *h, bool with_truth) {
   LK_CUDA(h, cudaMemcpyAsync(mp, md, down, cudaMemcpyDeviceToHost, h->stream));
   if (h->ev_out)
     LK_CUDA(h, cudaEventRecordWithFlags(h->ev_out, h->stream, cudaEventRecordExternal));
-  LK_CUDA(h, lk_launch_forecast(h, nullptr));
+  LK_CUDA(h, lk_launch_forecast(h, drawn ? h->noise_pre : nullptr));
   return LETKF_OK;
 }
 

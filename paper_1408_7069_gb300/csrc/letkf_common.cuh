@@ -123,6 +123,7 @@ struct letkf_ctx {
   int2 *worklist = nullptr;         // [n_pts_total] (inst, point) queued for FP64
   long long *frame = nullptr;       // [0] forecast counter, [1] frame index within letkf_run
   double2 *partial = nullptr;       // [n_inst][LK_RES_BLOCKS] residual partial sums
+  void *noise_pre = nullptr;        // [noise_total] the frame's forecast noise, drawn ahead
   int *tickets = nullptr;           // [n_inst + 1] last-CTA counters: residual per instance, forecast
 
   // host copies
@@ -171,10 +172,12 @@ struct letkf_ctx {
 // NULL means element 0. y, truth, mean, spread and noise are concatenated over
 // the instances in instance order.
 cudaError_t lk_launch_obs(letkf_ctx *h, const void *y, const long long *run_idx);
-// Residual and observation of one frame in one launch (separate launches with a
-// deformable mirror, whose residual needs N u first).
+// Observation of one frame with, in the same launch, its residual (truth and
+// resvar given) and the model noise of the frame's forecast (noise_out given,
+// [n_pts][m] at each instance's noise_off). Not with a deformable mirror, whose
+// residual needs N u first, nor without subapertures.
 cudaError_t lk_launch_obs_residual(letkf_ctx *h, const void *y, const void *truth,
-                                   double *resvar, const long long *run_idx);
+                                   double *resvar, const long long *run_idx, void *noise_out);
 cudaError_t lk_launch_analysis(letkf_ctx *h, void *mean, void *spread);
 cudaError_t lk_launch_analysis_class(letkf_ctx *h, int cls, void *mean, void *spread);
 // The forecast also advances the forecast counter and the run index (frame[0..1]).

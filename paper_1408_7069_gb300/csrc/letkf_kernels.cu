@@ -93,6 +93,20 @@ __global__ void __launch_bounds__(LK_WARP_CTA) obs_kernel(const LkInst *__restri
   obs_block<S>(insts, items, n_items, p_total, y, run_idx, counters, blockIdx.x);
 }
 
+// Member i's model noise at node point ij for forecast number f (Section 3.1.2,
+// Eq. Mem_pre): a bank screen and a wrapped offset chosen by SplitMix64,
+// scaled by q.
+template <typename S>
+__device__ __forceinline__ S bank_draw(const LkInst &I, int2 ij, int i, long long f) {
+  const unsigned long long hsh =
+      lk_splitmix64(I.seed, ((unsigned long long)f << 16) | (unsigned long long)i);
+  const int B = I.bank_B, G = I.bank_G;
+  const int b = (int)(hsh % (unsigned long long)B);
+  const int ox = (int)((hsh >> 16) % (unsigned long long)G);
+  const int oy = (int)((hsh >> 40) % (unsigned long long)G);
+  return S(I.noise_std) * S(I.bank[((size_t)b * G + (ij.x + ox) % G) * G + (ij.y + oy) % G]);
+}
+
 template <typename S>
 __device__ __forceinline__ void forecast_node(const LkInst *__restrict__ insts, int2 it, int lane,
                                               const S *__restrict__ noise,
@@ -100,23 +114,12 @@ __device__ __forceinline__ void forecast_node(const LkInst *__restrict__ insts, 
   const LkInst &I = insts[it.x];
   const int gpt = it.y, m = I.m;
   S *row0 = static_cast<S *>(I.X) + (size_t)gpt * 2 * m;
-  const S a = S(I.a_ar1), q = S(I.noise_std);
+  const S a = S(I.a_ar1);
   const int2 ij = I.pts[gpt];
   S psum = S(0);
   for (int i = lane; i < m; i += 32) {
     const S x0 = row0[i];
-    S v;
-    if (noise) {
-      v = noise[I.noise_off + (long long)gpt * m + i];
-    } else {
-      const unsigned long long hsh =
-          lk_splitmix64(I.seed, ((unsigned long long)frame[0] << 16) | (unsigned long long)i);
-      const int B = I.bank_B, G = I.bank_G;
-      const int b = (int)(hsh % (unsigned long long)B);
-      const int ox = (int)((hsh >> 16) % (unsigned long long)G);
-      const int oy = (int)((hsh >> 40) % (unsigned long long)G);
-      v = q * S(I.bank[((size_t)b * G + (ij.x + ox) % G) * G + (ij.y + oy) % G]);
-    }
+    const S v = noise ? noise[I.noise_off + (long long)gpt * m + i] : bank_draw<S>(I, ij, i, frame[0]);
     row0[m + i] = x0;
     row0[i] = a * x0 + v;
     psum += row0[i];
@@ -259,9 +262,11 @@ __global__ void __launch_bounds__(64) residual_kernel(const LkInst *__restrict__
                     run_idx, partial, tickets, n_inst, resvar, piston);
 }
 
-// Residual and observation of a frame in one launch (both read only the
-// prediction ensemble): the first res_blocks CTAs (LK_RES_BLOCKS per instance)
-// take the residual, the others the observation, 64 threads each.
+// Residual, observation and the coming forecast's model noise of a frame in one
+// launch (all read only the prediction ensemble, the noise not even that): the
+// first res_blocks CTAs (LK_RES_BLOCKS per instance) take the residual, the
+// next noise_blocks draw the noise (warp per node, the draws the forecast would
+// make, into noise_out), the others the observation, 64 threads each.
 template <typename S>
 __global__ void __launch_bounds__(LK_WARP_CTA)
     obs_residual_kernel(const LkInst *__restrict__ insts, const int2 *__restrict__ items,
@@ -269,7 +274,9 @@ __global__ void __launch_bounds__(LK_WARP_CTA)
                         const long long *__restrict__ run_idx, int *__restrict__ counters,
                         int res_blocks, long long n_pts_total, const S *__restrict__ truth,
                         double2 *__restrict__ partial, int *__restrict__ tickets, int n_inst,
-                        double *__restrict__ resvar) {
+                        double *__restrict__ resvar, int noise_blocks,
+                        const int2 *__restrict__ node_items, const long long *__restrict__ frame,
+                        S *__restrict__ noise_out) {
   if ((int)blockIdx.x < res_blocks) {
     lk_pdl_wait();
     const int inst = blockIdx.x / LK_RES_BLOCKS, rb = blockIdx.x - inst * LK_RES_BLOCKS;
@@ -277,7 +284,22 @@ __global__ void __launch_bounds__(LK_WARP_CTA)
                       tickets, n_inst, resvar, nullptr);
     return;
   }
-  obs_block<S>(insts, items, n_items, p_total, y, run_idx, counters, blockIdx.x - res_blocks);
+  if ((int)blockIdx.x < res_blocks + noise_blocks) {
+    lk_pdl_wait();                  // the previous forecast advanced frame[0]
+    const long long wi =
+        ((long long)(blockIdx.x - res_blocks) * blockDim.x + threadIdx.x) >> 5;
+    if (wi >= n_pts_total) return;
+    const int lane = threadIdx.x & 31;
+    const int2 it = node_items[wi];
+    const LkInst &I = insts[it.x];
+    const int2 ij = I.pts[it.y];
+    const long long f = frame[0];
+    S *out = noise_out + I.noise_off + (long long)it.y * I.m;
+    for (int i = lane; i < I.m; i += 32) out[i] = bank_draw<S>(I, ij, i, f);
+    return;
+  }
+  obs_block<S>(insts, items, n_items, p_total, y, run_idx, counters,
+               blockIdx.x - res_blocks - noise_blocks);
 }
 
 // Every node's warm-start eigenbasis back to the identity (grid.y = instance).
@@ -312,22 +334,22 @@ cudaError_t lk_launch_obs(letkf_ctx *h, const void *y, const long long *run_idx)
 }
 
 cudaError_t lk_launch_obs_residual(letkf_ctx *h, const void *y, const void *truth,
-                                   double *resvar, const long long *run_idx) {
-  if (h->sap_total == 0 || h->inst[0].dm) {       // separately (with a mirror, N u first)
-    cudaError_t e = lk_launch_residual(h, truth, resvar, run_idx);
-    return e == cudaSuccess ? lk_launch_obs(h, y, run_idx) : e;
-  }
-  const int rblocks = LK_RES_BLOCKS * h->n_inst;
-  const int blocks = rblocks + warp_blocks(h->sap_total);
+                                   double *resvar, const long long *run_idx, void *noise_out) {
+  if (h->sap_total == 0 || h->inst[0].dm) return cudaErrorInvalidValue;
+  const int rblocks = (truth && resvar) ? LK_RES_BLOCKS * h->n_inst : 0;
+  const int nblocks = noise_out ? warp_blocks(h->n_pts_total) : 0;
+  const int blocks = rblocks + nblocks + warp_blocks(h->sap_total);
   if (h->precision == 1)
     return lk_launch_pdl(obs_residual_kernel<double>, blocks, LK_WARP_CTA, 0, h->stream,
                          h->d_inst, h->obs_items, h->sap_total, h->p_total, (const double *)y,
                          run_idx, h->counters, rblocks, h->n_pts_total, (const double *)truth,
-                         h->partial, h->tickets, h->n_inst, resvar);
+                         h->partial, h->tickets, h->n_inst, resvar, nblocks, h->node_items,
+                         h->frame, (double *)noise_out);
   return lk_launch_pdl(obs_residual_kernel<float>, blocks, LK_WARP_CTA, 0, h->stream, h->d_inst,
                        h->obs_items, h->sap_total, h->p_total, (const float *)y, run_idx,
                        h->counters, rblocks, h->n_pts_total, (const float *)truth, h->partial,
-                       h->tickets, h->n_inst, resvar);
+                       h->tickets, h->n_inst, resvar, nblocks, h->node_items, h->frame,
+                       (float *)noise_out);
 }
 
 cudaError_t lk_launch_forecast(letkf_ctx *h, const void *noise) {
