@@ -836,8 +836,8 @@ def gpu_arm(args):
     torch.cuda.synchronize()
 
     def frame(k):
-        # one frame through the library's frame path: residual beside the
-        # observation (side stream), analysis, FP64 list, forecast
+        # one frame through the library's frame path: residual, observation and
+        # the forecast's noise draw in one launch, analysis, FP64 list, forecast
         L.letkf_run(h, 1, y[k:k + 1], truth[k:k + 1], resvar[k:k + 1], False)
 
     with torch.cuda.stream(s):
@@ -981,8 +981,8 @@ def gpu_arm(args):
                    "fp64_fallback_kappa": 300.0, "parallelism": f"replicas x{world}",
                    "tile_shape": tune.get("tiles"),
                    "l2": "flushed between timed frames (256 MiB write, outside the frame events)",
-                   "step": "residual (beside the observation) + observation + local analysis + "
-                           "forecast: one letkf_run call per frame, no graph"},
+                   "step": "residual, observation and the forecast's noise draw (one launch) + "
+                           "local analysis + forecast: one letkf_run call per frame, no graph"},
         "p50_us": 1e3 * percentile(frame_ms, 50), "p99_us": 1e3 * percentile(frame_ms, 99),
         "max_us": 1e3 * max(frame_ms),
         "graph_frames_per_s": graph_fps,
